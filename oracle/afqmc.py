@@ -1,0 +1,303 @@
+"""Correlated-sampling phaseless AFQMC, one step at a time (oracle side, FP64).
+
+Notation follows Sec. II.A-B of the paper.  A walker is a Slater determinant
+Phi [M, N] (complex; columns 0..N_up-1 spin up, N_up..N-1 spin down) with a
+weight w and the log of its overlap with the trial, log O = log <psi_T|phi>.
+The trial psi_T is the real M x N matrix [Psi_up | Psi_dn].
+
+Definitions used throughout
+  O_s     = Psi_s^T Phi_s,   Theta_s = Phi_s O_s^{-1}
+  G_s[i,j] = <psi_T| c+_i c_j |phi> / <psi_T|phi> = (Theta_s Psi_s^T)[j, i]
+  rho_g   = sum_ik L^g_ik sum_s c+_is c_ks          (so v_g = i rho_g, Sec. II.A)
+  <rho_g>_T = sum_s tr(L_g Psi_s Psi_s^T)           (trial expectation, Eq. 2)
+  rhobar_g  = sum_s tr(L_g G_s)                      (so vbar_g = i rhobar_g, Eq. 9)
+
+Normal-ordering Eq. 1 with V_ijkl = sum_g L^g_ik L^g_jl and expanding Eq. 2
+gives H = H_1 + H_2 with the one-body part
+  H_1 = sum_ij K_ij sum_s c+_is c_js + C,
+  K = h1 - 1/2 sum_g L_g L_g + sum_g <rho_g>_T L_g,   C = -1/2 sum_g <rho_g>_T^2.
+
+One step (Eqs. 3-5, 8-9 and the hybrid weight of Sec. II.D), per live walker:
+  1. xbar_g = -sqrt(dt) (vbar_g - <v_g>) = -i sqrt(dt) (rhobar_g - <rho_g>_T)   (Eq. 9)
+     optionally capped: |xbar_g| > cap  ->  xbar_g * cap / |xbar_g|
+  2. c_g = x_g - xbar_g;  A = i sqrt(dt) sum_g c_g L_g  (one-body matrix of Eq. 10's
+     middle factor); its scalar part s = exp(-i sqrt(dt) sum_g c_g <rho_g>_T)
+  3. Phi' = e^{-dt K/2} T_n(A) e^{-dt K/2} Phi,  T_n(A) = sum_{m<=n} A^m / m!
+     (Eq. 3 split, Eq. 5 read with a half step on each side, Thouless theorem)
+  4. R = s * O(Phi') / O(Phi)  (overlap ratio of the propagated walker)
+     I = R * exp(x.xbar - xbar.xbar/2) * exp(-dt (C - E_T))   (hybrid weight, Sec. II.D;
+     squares unconjugated)
+  5. phaseless: dtheta = arg R,  w <- w |I| max(0, cos dtheta)  (Sec. II.A); w <= 0 kills
+     the walker for good, it is no longer propagated (Sec. II.B).
+     free projection: xbar = 0 and w <- w I (complex).
+Every ``mgs_every`` steps each spin block is replaced by its modified
+Gram-Schmidt Q factor (Sec. II.D) and log O recomputed.
+Energy (Eqs. 6-7, 11): E_L = sum_s tr(h1 G_s)
+      + 1/2 sum_g [ rhobar_g^2 - sum_s tr(L_g G_s L_g G_s) ],
+  E = sum_k w_k Re E_L,k / sum_k w_k  (phaseless);  Re(sum w E_L / sum w) (free).
+"""
+import numpy as np
+
+from .philox import gaussian_fields
+
+PHASELESS = "phaseless"
+FREE = "free"
+
+
+class System:
+    """Static data of one system: h1, L, trial, and the derived K, e^{-dt K/2}, C, E_T."""
+
+    def __init__(self, h1, L, trial, n_up, n_dn, dt, fb_cap=1.0, mode=PHASELESS,
+                 taylor_order=6):
+        self.h1 = np.asarray(h1, dtype=np.float64)
+        self.L = np.asarray(L, dtype=np.float64)
+        self.trial = np.asarray(trial, dtype=np.float64)
+        self.M = self.h1.shape[0]
+        self.X = self.L.shape[0]
+        self.n_up, self.n_dn = int(n_up), int(n_dn)
+        self.N = self.n_up + self.n_dn
+        self.dt = float(dt)
+        self.sqrt_dt = np.sqrt(self.dt)
+        self.fb_cap = float(fb_cap)
+        self.mode = mode
+        self.taylor_order = int(taylor_order)
+        self.spins = [(0, self.n_up), (self.n_up, self.N)]
+        # <rho_g>_T = sum_s tr(L_g P_s)  with P_s = Psi_s Psi_s^T
+        self.rho_mf = np.zeros(self.X)
+        for a, b in self.spins:
+            P = self.trial[:, a:b] @ self.trial[:, a:b].T
+            self.rho_mf += np.einsum("gij,ji->g", self.L, P)
+        # one-body part of H = H_1 + H_2 (normal ordering of Eq. 1, expansion of Eq. 2)
+        self.K = (self.h1 - 0.5 * np.einsum("gik,gkj->ij", self.L, self.L)
+                  + np.einsum("g,gij->ij", self.rho_mf, self.L))
+        self.C = -0.5 * float(self.rho_mf @ self.rho_mf)
+        lam, U = np.linalg.eigh(self.K)
+        self.expK = (U * np.exp(-0.5 * self.dt * lam)) @ U.T
+        # trial energy E_T = E_L(psi_T): the energy shift of exp(dt (E_T - H))
+        self.E_T = float(local_energy(self, self.trial[None].astype(np.complex128))[0].real)
+
+
+class Walkers:
+    """Walker population: Phi [Nw, M, N] complex, w complex, log O complex, alive bool."""
+
+    def __init__(self, sys: System, n_walkers: int, phi=None, w=None):
+        if phi is None:
+            phi = np.broadcast_to(sys.trial, (n_walkers, sys.M, sys.N))
+        self.phi = np.array(phi, dtype=np.complex128)
+        self.w = np.ones(n_walkers, dtype=np.complex128) if w is None else np.array(w, np.complex128)
+        self.logO = overlap(sys, self.phi)
+        self.alive = np.ones(n_walkers, dtype=bool) if w is None else (np.abs(self.w) > 0)
+
+    def copy(self):
+        c = object.__new__(Walkers)
+        c.phi, c.w, c.logO, c.alive = self.phi.copy(), self.w.copy(), self.logO.copy(), self.alive.copy()
+        return c
+
+
+def overlap(sys: System, phi):
+    """log <psi_T|phi> = sum_s log det(Psi_s^T Phi_s)  (Cauchy-Binet)."""
+    logO = np.zeros(phi.shape[0], dtype=np.complex128)
+    for a, b in sys.spins:
+        if b == a:
+            continue
+        O = np.einsum("ia,wib->wab", sys.trial[:, a:b], phi[:, :, a:b])
+        sign, lad = np.linalg.slogdet(O)
+        logO += lad + np.log(sign)
+    return logO
+
+
+def green(sys: System, phi):
+    """Mixed Green's functions G_s [Nw, M, M], G_s[i,j] = <c+_i c_j>_mixed, for s = up, down."""
+    out = []
+    for a, b in sys.spins:
+        if b == a:
+            out.append(np.zeros((phi.shape[0], sys.M, sys.M), dtype=np.complex128))
+            continue
+        Psi = sys.trial[:, a:b]
+        O = np.einsum("ia,wib->wab", Psi, phi[:, :, a:b])
+        Theta = phi[:, :, a:b] @ np.linalg.inv(O)
+        out.append(np.swapaxes(Theta @ Psi.T, 1, 2))
+    return out
+
+
+def rhobar(sys: System, G):
+    """rhobar_g = sum_s tr(L_g G_s)  [Nw, X]  (vbar_g = i rhobar_g, Eq. 9)."""
+    return sum(np.einsum("gij,wji->wg", sys.L, Gs) for Gs in G)
+
+
+def force_bias(sys: System, G):
+    """Optimal force bias of Eq. 9, xbar_g = -i sqrt(dt) (rhobar_g - <rho_g>_T), with the cap."""
+    xbar = -1j * sys.sqrt_dt * (rhobar(sys, G) - sys.rho_mf[None, :])
+    if sys.fb_cap > 0:
+        mag = np.abs(xbar)
+        big = mag > sys.fb_cap
+        xbar = np.where(big, xbar * (sys.fb_cap / np.where(big, mag, 1.0)), xbar)
+    return xbar
+
+
+def taylor_apply(A, phi, order):
+    """T_order(A) phi = sum_{m=0}^{order} A^m phi / m!, by repeated products."""
+    term = phi
+    acc = phi.copy()
+    for m in range(1, order + 1):
+        term = (A @ term) / m
+        acc = acc + term
+    return acc
+
+
+def step_determinant(sys: System, phi, logO, x, xbar):
+    """One application of Eq. 10 with fields x and shift xbar to determinants phi.
+
+    Returns (Phi', log O', log R, log I): R is the overlap ratio including the scalar
+    part s of the shifted HS exponential, I the hybrid weight factor of Sec. II.D.
+    """
+    c = x - xbar
+    A = 1j * sys.sqrt_dt * np.einsum("wg,gij->wij", c, sys.L)
+    log_s = -1j * sys.sqrt_dt * (c @ sys.rho_mf)
+    phi1 = sys.expK @ phi
+    phi2 = taylor_apply(A, phi1, sys.taylor_order)
+    phi3 = sys.expK @ phi2
+    logO_new = overlap(sys, phi3)
+    logR = log_s + logO_new - logO
+    logI = logR + np.sum(x * xbar, axis=1) - 0.5 * np.sum(xbar * xbar, axis=1) \
+        - sys.dt * (sys.C - sys.E_T)
+    return phi3, logO_new, logR, logI
+
+
+def propagate(sys: System, wk: Walkers, x):
+    """Advance every live walker by one step with fields x [Nw, X] (float64)."""
+    live = wk.alive
+    if not np.any(live):
+        return
+    phi = wk.phi[live]
+    xs = np.asarray(x, dtype=np.float64)[live]
+    if sys.mode == PHASELESS:
+        xbar = force_bias(sys, green(sys, phi))
+    else:
+        xbar = np.zeros_like(xs, dtype=np.complex128)
+    phi3, logO_new, logR, logI = step_determinant(sys, phi, wk.logO[live], xs, xbar)
+    if sys.mode == PHASELESS:
+        dtheta = logR.imag
+        w_new = wk.w[live].real * np.exp(logI.real) * np.maximum(0.0, np.cos(dtheta))
+        w_new = w_new.astype(np.complex128)
+        still = w_new.real > 0
+    else:
+        w_new = wk.w[live] * np.exp(logI)
+        still = np.ones(w_new.shape, dtype=bool)
+    idx = np.nonzero(live)[0]
+    wk.phi[idx] = phi3
+    wk.logO[idx] = logO_new
+    wk.w[idx] = np.where(still, w_new, 0.0)
+    wk.alive[idx] = still
+
+
+def modified_gram_schmidt(phi_s):
+    """Column-by-column MGS of phi_s [Nw, M, n]: returns Q with orthonormal columns."""
+    Q = np.array(phi_s, dtype=np.complex128)
+    for j in range(Q.shape[2]):
+        v = Q[:, :, j]
+        for i in range(j):
+            r = np.sum(np.conj(Q[:, :, i]) * v, axis=1)
+            v = v - r[:, None] * Q[:, :, i]
+        nrm = np.sqrt(np.sum(np.abs(v) ** 2, axis=1))
+        Q[:, :, j] = v / nrm[:, None]
+    return Q
+
+
+def orthonormalise(sys: System, wk: Walkers):
+    """Replace each spin block of every live walker by its MGS Q factor; recompute log O."""
+    live = wk.alive
+    if not np.any(live):
+        return
+    idx = np.nonzero(live)[0]
+    phi = wk.phi[idx]
+    for a, b in sys.spins:
+        if b > a:
+            phi[:, :, a:b] = modified_gram_schmidt(phi[:, :, a:b])
+    wk.phi[idx] = phi
+    wk.logO[idx] = overlap(sys, phi)
+
+
+def local_energy(sys: System, phi, chunk: int = 0):
+    """E_L [Nw] complex, from the mixed Green's functions (Eq. 7 with Wick's theorem)."""
+    nw = phi.shape[0]
+    if chunk <= 0:
+        chunk = max(1, int(2e7 // max(1, sys.X * sys.M * sys.M)))
+    out = np.empty(nw, dtype=np.complex128)
+    for s0 in range(0, nw, chunk):
+        G = green(sys, phi[s0:s0 + chunk])
+        e1 = sum(np.einsum("ij,wji->w", sys.h1, Gs) for Gs in G)
+        rb = rhobar(sys, G)
+        exch = 0.0
+        for Gs in G:
+            LG = np.einsum("gij,wjk->wgik", sys.L, Gs)
+            exch = exch + np.einsum("wgik,wgki->wg", LG, LG)
+        out[s0:s0 + chunk] = e1 + 0.5 * np.sum(rb * rb - exch, axis=1)
+    return out
+
+
+def repeat_groups(n_walkers: int, n_repeats: int):
+    """Repeat index of each global walker index k: floor(k R / Nw)."""
+    return (np.arange(n_walkers) * n_repeats) // n_walkers
+
+
+def mixed_energy(sys: System, w, eloc, groups, n_repeats):
+    """Per-repeat mixed estimate sum w E_L / sum w (Eq. 6; Re E_L for phaseless, Eq. 11)."""
+    E = np.empty(n_repeats)
+    W = np.empty(n_repeats)
+    for r in range(n_repeats):
+        m = groups == r
+        if sys.mode == PHASELESS:
+            num = np.sum(w[m].real * eloc[m].real)
+            den = np.sum(w[m].real)
+            E[r] = num / den if den != 0 else np.nan
+            W[r] = den
+        else:
+            den = np.sum(w[m])
+            E[r] = (np.sum(w[m] * eloc[m]) / den).real
+            W[r] = den.real
+    return E, W
+
+
+def run_pair(sysA: System, sysB: System, n_walkers: int, n_steps: int, seed: int,
+             energy_every: int = 5, mgs_every: int = 5, n_repeats: int = 1,
+             walker_index=None, fields=None, record_walkers=False):
+    """Correlated pair run (Sec. II.B): walker k of A and walker k of B share x_{t,k,g}.
+
+    ``walker_index`` (default 0..Nw-1) gives the global pair index k of every walker
+    propagated here, so a subset of a large population can be followed exactly.
+    ``fields`` (optional) is an explicit [n_steps, Nw, max(X_A, X_B)] array used in
+    place of the counter-based stream.  Returns dict with per-measurement per-repeat
+    mixed energies for both systems and (optionally) per-walker records.
+    Order within a step boundary: propagate, then MGS, then measure.
+    """
+    systems = [s for s in (sysA, sysB) if s is not None]
+    k = np.arange(n_walkers) if walker_index is None else np.asarray(walker_index)
+    groups = repeat_groups(n_walkers, n_repeats)[k] if walker_index is None else \
+        (k * n_repeats) // n_walkers
+    wks = [Walkers(s, k.size) for s in systems]
+    out = dict(steps=[], E=[[] for _ in systems], W=[[] for _ in systems],
+               records=[[] for _ in systems])
+    for t in range(n_steps):
+        for s, wk in zip(systems, wks):
+            if fields is None:
+                x = gaussian_fields(seed, t, k, s.X)
+            else:
+                x = fields[t][:, :s.X]
+            propagate(s, wk, x)
+        if mgs_every > 0 and (t + 1) % mgs_every == 0:
+            for s, wk in zip(systems, wks):
+                orthonormalise(s, wk)
+        if energy_every > 0 and (t + 1) % energy_every == 0:
+            out["steps"].append(t + 1)
+            for i, (s, wk) in enumerate(zip(systems, wks)):
+                el = local_energy(s, wk.phi)
+                E, W = mixed_energy(s, wk.w, el, groups, n_repeats)
+                out["E"][i].append(E)
+                out["W"][i].append(W)
+                if record_walkers:
+                    out["records"][i].append(dict(eloc=el, w=wk.w.copy(), logO=wk.logO.copy()))
+    out["E"] = [np.array(e) for e in out["E"]]
+    out["W"] = [np.array(e) for e in out["W"]]
+    out["walkers"] = wks
+    return out

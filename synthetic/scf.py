@@ -1,0 +1,93 @@
+"""Real single-determinant trial from a plain SCF (input preparation).
+
+The paper takes RHF/ROHF/UHF trials from NWChem (Sec. II.D).  Here the trial
+for the synthetic Hamiltonian comes from a Roothaan iteration with Pulay DIIS,
+started from the eigenvectors of h1:
+
+  F^s = h1 + J - K^s,  J = sum_g L_g tr(L_g P),  K^s = sum_g (L_g C_s)(L_g C_s)^T
+  P = P^up + P^dn,  P^s = C_s C_s^T  (C_s: the N_s lowest orbitals of F^s)
+
+RHF (one shared orbital set) when N_up == N_dn, UHF otherwise.  The synthetic
+interaction grows with the number of Cholesky vectors, and for the larger
+shapes the iteration need not settle; it then stops after ``max_iter`` steps
+and returns the lowest-energy determinant it visited (deterministic for a
+given Hamiltonian).  The trial is the M x (N_up + N_dn) matrix
+[Psi_up | Psi_dn] with orthonormal columns.
+"""
+import numpy as np
+
+
+def _fock(h1, L, C_up, C_dn):
+    P = C_up @ C_up.T + C_dn @ C_dn.T
+    J = np.einsum("g,gij->ij", np.einsum("gij,ji->g", L, P), L)
+    out = []
+    for C in (C_up, C_dn):
+        LC = L @ C  # [X, M, Ns]
+        K = np.einsum("gia,gja->ij", LC, LC)
+        out.append(h1 + J - K)
+    return out
+
+
+def hf_energy(h1, L, C_up, C_dn):
+    F_up, F_dn = _fock(h1, L, C_up, C_dn)
+    e = 0.0
+    for C, F in ((C_up, F_up), (C_dn, F_dn)):
+        P = C @ C.T
+        e += 0.5 * np.trace((h1 + F) @ P)
+    return float(e)
+
+
+def scf_trial(h1, L, n_up: int, n_dn: int, max_iter: int = 60, tol: float = 1e-10,
+              n_diis: int = 8):
+    """Return (trial [M, n_up+n_dn], converged: bool, n_iter: int)."""
+    M = h1.shape[0]
+    if not (0 <= n_dn <= M and 0 <= n_up <= M):
+        raise ValueError("occupations out of range")
+    restricted = n_up == n_dn
+
+    def occ(F, n):
+        _, V = np.linalg.eigh(F)
+        return V[:, :n].copy()
+
+    _, V = np.linalg.eigh(h1)
+    C = [V[:, :n_up].copy(), V[:, :n_dn].copy()]
+    best = (np.inf, C)
+    hist_F, hist_e = [], []
+    converged = False
+    it = 0
+    for it in range(1, max_iter + 1):
+        F = _fock(h1, L, C[0], C[1])
+        if restricted:
+            Fa = 0.5 * (F[0] + F[1])
+            F = [Fa, Fa]
+        e = hf_energy(h1, L, C[0], C[1])
+        if e < best[0]:
+            best = (e, [C[0].copy(), C[1].copy()])
+        P = [C[0] @ C[0].T, C[1] @ C[1].T]
+        err = np.concatenate([(F[s] @ P[s] - P[s] @ F[s]).ravel() for s in range(2)])
+        if np.max(np.abs(err)) < tol:
+            converged = True
+            best = (e, C)
+            break
+        hist_F.append([F[0].copy(), F[1].copy()])
+        hist_e.append(err)
+        hist_F, hist_e = hist_F[-n_diis:], hist_e[-n_diis:]
+        n = len(hist_F)
+        if n >= 2:
+            B = -np.ones((n + 1, n + 1))
+            B[n, n] = 0.0
+            E = np.array(hist_e)
+            B[:n, :n] = E @ E.T
+            rhs = np.zeros(n + 1)
+            rhs[n] = -1.0
+            try:
+                coef = np.linalg.solve(B, rhs)[:n]
+                F = [sum(c * f[s] for c, f in zip(coef, hist_F)) for s in range(2)]
+            except np.linalg.LinAlgError:
+                pass
+        C = [occ(F[0], n_up), occ(F[1], n_dn)]
+    C = best[1]
+    if restricted:
+        C = [C[0], C[0].copy()]
+    trial = np.concatenate(C, axis=1)
+    return np.ascontiguousarray(trial), converged, it
