@@ -121,8 +121,13 @@ def green(sys: System, phi):
 
 
 def rhobar(sys: System, G):
-    """rhobar_g = sum_s tr(L_g G_s)  [Nw, X]  (vbar_g = i rhobar_g, Eq. 9)."""
-    return sum(np.einsum("gij,wji->wg", sys.L, Gs) for Gs in G)
+    """rhobar_g = sum_s tr(L_g G_s) = sum_s sum_ij L^g_ij G_s[j, i]  [Nw, X]  (vbar_g = i rhobar_g, Eq. 9)."""
+    Lf = sys.L.reshape(sys.X, sys.M * sys.M)
+    out = 0
+    for Gs in G:
+        GT = np.swapaxes(Gs, 1, 2).reshape(Gs.shape[0], sys.M * sys.M)
+        out = out + GT @ Lf.T
+    return out
 
 
 def force_bias(sys: System, G):
@@ -152,7 +157,7 @@ def step_determinant(sys: System, phi, logO, x, xbar):
     part s of the shifted HS exponential, I the hybrid weight factor of Sec. II.D.
     """
     c = x - xbar
-    A = 1j * sys.sqrt_dt * np.einsum("wg,gij->wij", c, sys.L)
+    A = 1j * sys.sqrt_dt * (c @ sys.L.reshape(sys.X, sys.M * sys.M)).reshape(-1, sys.M, sys.M)
     log_s = -1j * sys.sqrt_dt * (c @ sys.rho_mf)
     phi1 = sys.expK @ phi
     phi2 = taylor_apply(A, phi1, sys.taylor_order)
@@ -222,7 +227,7 @@ def local_energy(sys: System, phi, chunk: int = 0):
     """E_L [Nw] complex, from the mixed Green's functions (Eq. 7 with Wick's theorem)."""
     nw = phi.shape[0]
     if chunk <= 0:
-        chunk = max(1, int(2e7 // max(1, sys.X * sys.M * sys.M)))
+        chunk = max(1, int(4e6 // max(1, sys.X * sys.M * sys.M)))
     out = np.empty(nw, dtype=np.complex128)
     for s0 in range(0, nw, chunk):
         G = green(sys, phi[s0:s0 + chunk])
@@ -230,7 +235,7 @@ def local_energy(sys: System, phi, chunk: int = 0):
         rb = rhobar(sys, G)
         exch = 0.0
         for Gs in G:
-            LG = np.einsum("gij,wjk->wgik", sys.L, Gs)
+            LG = sys.L[None, :, :, :] @ Gs[:, None, :, :]          # [w, g, M, M] = L_g G_s
             exch = exch + np.einsum("wgik,wgki->wg", LG, LG)
         out[s0:s0 + chunk] = e1 + 0.5 * np.sum(rb * rb - exch, axis=1)
     return out

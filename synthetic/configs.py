@@ -8,7 +8,7 @@ C4  A: M=200, X=1000, 9/9; B: M=190, X=950, 8/8 (B drawn with seed+1000), 2048 w
 C5  M=96,  X=480,  12/12, 1024 walkers x 200 steps (adjoint)
 Energy measurement and modified Gram-Schmidt every 5 steps in all of them.
 """
-from .hamiltonian import make_hamiltonian
+from .hamiltonian import make_hamiltonian, moderate_coupling
 from .scf import scf_trial
 
 CONFIGS = {
@@ -31,12 +31,18 @@ CONFIGS = {
 _cache = {}
 
 
-def build_system(M, X, n_up, n_dn, seed=1703):
-    """Return dict(h1, L, trial, n_up, n_dn, M, X) for one system (cached)."""
-    key = (M, X, n_up, n_dn, seed)
+def build_system(M, X, n_up, n_dn, seed=1703, coupling=1.0):
+    """Return dict(h1, L, trial, n_up, n_dn, M, X) for one system (cached).
+
+    ``coupling``: 1.0 is the recipe as stated; the string "moderate" selects
+    ``moderate_coupling(X)`` (long-lived walkers for long-run statistics).
+    """
+    if coupling == "moderate":
+        coupling = moderate_coupling(X)
+    key = (M, X, n_up, n_dn, seed, float(coupling))
     if key not in _cache:
-        h1, L = make_hamiltonian(M, X, seed)
+        h1, L = make_hamiltonian(M, X, seed, coupling=coupling)
         trial, ok, _ = scf_trial(h1, L, n_up, n_dn)
         _cache[key] = dict(h1=h1, L=L, trial=trial, n_up=n_up, n_dn=n_dn, M=M, X=X,
-                           scf_converged=ok)
+                           scf_converged=ok, coupling=float(coupling))
     return _cache[key]
