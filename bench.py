@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the correlated-pair walker propagation (one JSON line on rank 0).
+
+Workload (default): the M=64 synthetic pair -- Nchol=320, neutral 8/8 vs ion 8/7,
+2048 walkers per system, dt=0.005, 11 repeats, shared Philox field stream.  One
+benchmark step = one measurement block of the method for BOTH systems: 5
+propagation steps (force bias, fields, V_HS, split propagator with Taylor
+exponential, overlap/ratio/phaseless weight), one modified Gram-Schmidt pass and
+one mixed-energy evaluation (Coulomb + exchange), i.e. every stage of the path.
+Metric: correlated-pair walker-steps per second = walkers x propagation steps / s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (a bounded walker
+sample per step; the reference arm).  Under torchrun each rank runs an independent
+replica on its own walker range (weak scaling; no collective on the data path).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+STEPS_PER_BLOCK = 5
+WORKLOADS = {
+    "C2": dict(cfg="C2", n_walkers=2048, dt=0.005, repeats=11,
+               desc="synthetic pair M=64, Nchol=320, neutral 8/8 vs ion 8/7, 2048 walkers per "
+                    "system, dt=0.005, energy+MGS every 5 steps, 11 repeats"),
+}
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (no tcgen05 FP64 kind; DFMA/DMMA pipe)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
+    ap.add_argument("--coupling", default="moderate", choices=["literal", "moderate"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=["vhs", "force_bias", "taylor", "energy"],
+                    help="profiling aid: set up the workload, take one step, then launch only "
+                         "this kernel --reps times (no JSON line)")
+    ap.add_argument("--walkers", type=int, default=None, help="override walkers per system")
+    ap.add_argument("--reps", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def systems(wl, coupling):
+    from synthetic import CONFIGS, build_system
+    cfg = CONFIGS[wl["cfg"]]
+    c = 1.0 if coupling == "literal" else "moderate"
+    return [build_system(**dict(cfg[w], coupling=c)) for w in ("A", "B")]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def time_oracle_sample(wl, coupling, n_walkers, blocks=1):
+    """Oracle (CPU, FP64) on n_walkers pair indices for `blocks` measurement blocks of both systems."""
+    from oracle import afqmc as orc
+    from oracle.philox import gaussian_fields
+    dA, dB = systems(wl, coupling)
+    osys = [orc.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], wl["dt"]) for d in (dA, dB)]
+    k = np.arange(n_walkers)
+    wks = [orc.Walkers(s, n_walkers) for s in osys]
+    t0 = time.perf_counter()
+    t = 0
+    for _ in range(blocks):
+        for _ in range(STEPS_PER_BLOCK):
+            for s, wk in zip(osys, wks):
+                orc.propagate(s, wk, gaussian_fields(1, t, k, s.X))
+            t += 1
+        for s, wk in zip(osys, wks):
+            orc.orthonormalise(s, wk)
+            orc.local_energy(s, wk.phi)
+    return time.perf_counter() - t0
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(v):
+            return int(os.environ[v])
+    return os.cpu_count()
+
+
+def traffic_for(kernel_file, name):
+    """dram bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        data = json.load(open(path))
+        ent = data[name]
+        src = open(os.path.join(ROOT, "paper_1703_01545_gb300", "csrc", kernel_file), "rb").read()
+        if ent.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return ent
+    except Exception:
+        return None
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    n_sample = 16
+    for _ in range(args.warmup):
+        time_oracle_sample(wl, args.coupling, n_sample)
+    tot = 0.0
+    for _ in range(args.steps):
+        tot += time_oracle_sample(wl, args.coupling, n_sample)
+    value = n_sample * STEPS_PER_BLOCK * args.steps / tot
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": "correlated-pair walker-steps/s", "value": value,
+        "unit": "walker-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "coupling": args.coupling,
+                   "sample": f"{n_sample} of {wl['n_walkers']} pair indices per step"},
+        "cpu_baseline": {"value": value, "unit": "walker-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n_sample} pair indices x {STEPS_PER_BLOCK} steps + MGS + "
+                                   "energy, both systems, per step"},
+        "e2e": {"value": value, "unit": "walker-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_kernel(args, wl):
+    """Launch one step kernel in isolation (for a small, bounded ncu capture)."""
+    import torch
+    import paper_1703_01545_gb300 as afq
+    afq.build()
+    d = systems(wl, args.coupling)[0]
+    nw = args.walkers or wl["n_walkers"]
+    A = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=wl["dt"], n_walkers=nw)
+    A.propagate(1)
+    which = {"vhs": afq.K_VHS, "force_bias": afq.K_FORCE_BIAS, "taylor": afq.K_TAYLOR,
+             "energy": afq.K_EXCHANGE}[args.kernel]
+    ms = afq.afqmc_time_kernel(A.h, which, args.reps)
+    torch.cuda.synchronize()
+    print(f"{args.kernel}: {ms:.3f} ms per launch ({nw} walkers)")
+    A.close()
+
+
+def run_ours(args, wl, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import paper_1703_01545_gb300 as afq
+
+    torch.cuda.set_device(local_rank)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    afq.build()
+    dA, dB = systems(wl, args.coupling)
+    nw, dt, R = wl["n_walkers"], wl["dt"], wl["repeats"]
+
+    def make(d):
+        return afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt, n_walkers=nw,
+                          seed=1, n_repeats=R, walker_offset=rank * nw)
+
+    A, B = make(dA), make(dB)
+    K, W = args.steps, args.warmup
+    afq.pair_delta_E(A, B, W * STEPS_PER_BLOCK, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
+                     raise_on_dead=False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    res = afq.pair_delta_E(A, B, K * STEPS_PER_BLOCK, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
+                           raise_on_dead=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        if world > 1:
+            dist.barrier()
+    walker_steps = world * nw * STEPS_PER_BLOCK * K
+    value = walker_steps / (ms / 1e3)
+    alive = [A.info().n_alive, B.info().n_alive]
+
+    # dominant kernel: the V_HS contraction, timed alone on this stream with CUDA events
+    M, X = dA["M"], dA["X"]
+    P = M * (M + 1) // 2
+    vhs_ms = afq.afqmc_time_kernel(A.h, afq.K_VHS, 5, stream.cuda_stream)
+    vhs_flops = 2.0 * P * X * (2 * nw)
+    achieved = vhs_flops / (vhs_ms / 1e3) / 1e12
+    tr = traffic_for("gemm_f64.cu", "vhs_gemm_C2")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "kernel": "k_gemm_tn_f64 (V_HS, packed symmetric L)",
+                "algorithmic_flops_per_launch": vhs_flops, "ms_per_launch": vhs_ms,
+                "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe); cuBLAS DGEMM measured 1.10"}
+    A.close()
+    B.close()
+
+    # end to end through the public API: host inputs -> setup -> pair run -> results on host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    A2, B2 = make(dA), make(dB)
+    res2 = afq.pair_delta_E(A2, B2, K * STEPS_PER_BLOCK, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
+                            raise_on_dead=False)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    A2.close()
+    B2.close()
+    h2d = sum(8 * (d["h1"].size + d["L"].size + d["trial"].size) for d in (dA, dB))
+    d2h = 8 * res2["E"].size
+    e2e = {"value": world * nw * STEPS_PER_BLOCK * K / e2e_s, "unit": "walker-steps/s",
+           "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+           "note": "setup of both systems from host arrays + pair run + energy series to host"}
+
+    other = None
+    if world == 1:
+        oc = "literal" if args.coupling == "moderate" else "moderate"
+        dA3, dB3 = systems(wl, oc)
+        A3, B3 = make(dA3), make(dB3)
+        afq.pair_delta_E(A3, B3, W * STEPS_PER_BLOCK, 5, 5, raise_on_dead=False)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        afq.pair_delta_E(A3, B3, K * STEPS_PER_BLOCK, 5, 5, raise_on_dead=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        other = {"coupling": oc, "value": nw * STEPS_PER_BLOCK * K / (e0.elapsed_time(e1) / 1e3),
+                 "alive_walkers": [A3.info().n_alive, B3.info().n_alive]}
+        A3.close()
+        B3.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_s = 96
+        ts = time_oracle_sample(wl, args.coupling, n_s)
+        cpu = {"value": n_s * STEPS_PER_BLOCK / ts, "unit": "walker-steps/s", "cores": blas_threads(),
+               "kind": "oracle",
+               "sample": f"{n_s} pair indices x {STEPS_PER_BLOCK} steps + MGS + energy, both systems"}
+    per_block = 2 * (STEPS_PER_BLOCK * 8 + 2 + 2) + 1
+    if rank == 0:
+        line = {
+            "metric": "correlated-pair walker-steps/s", "value": value, "unit": "walker-steps/s",
+            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "coupling": args.coupling,
+                       "step": "one measurement block (5 propagation steps + MGS + energy) of both systems",
+                       "l2": "inputs larger than L2 (per-step working set ~0.5 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
+            "gpu_launches": per_block * K, "alive_walkers": alive, "other_coupling": other,
+            "dE": {"mean": res["dE_mean"], "sigma": res["dE_sigma"]},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    wl = WORKLOADS[args.workload]
+    if args.kernel:
+        run_kernel(args, wl)
+    elif args.impl == "reference":
+        run_reference(args, wl, rank, world)
+    else:
+        run_ours(args, wl, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * afqmc.h -- C ABI of the GB300 (sm_103a) correlated-sampling phaseless AFQMC
+ * walker-propagation library.
+ *
+ * Method: Shee, Zhang, Reichman, Friesner, "Chemical transformations approaching
+ * chemical accuracy via correlated sampling in auxiliary-field quantum Monte
+ * Carlo" (arXiv:1703.01545).  Section and equation numbers below refer to it.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an afqmc_status; nothing aborts, exits or prints.
+ *    After a failure on a handle, afqmc_last_error(h) gives a one-line message.
+ *  - Real matrices are row-major float64.  Complex arrays are planar: the real
+ *    parts of all elements first, then the imaginary parts ("[2][...]").
+ *  - Any pointer argument may be a host pointer or a device pointer of the
+ *    current device (unified addressing decides; host memory may be pageable).
+ *  - Work is issued on the caller's stream and is asynchronous unless stated.
+ *    Outputs written to host memory are complete when the call returns.
+ *  - Orbital index i, j < M; Cholesky index g < X (X = number of vectors);
+ *    electron column n < N = N_up + N_dn, spin-up columns first.
+ *  - Ownership: afqmc_setup copies every input into library-owned device
+ *    memory; the caller may free its copies on return.  The library owns its
+ *    device workspaces until afqmc_destroy.  Output buffers are caller-owned.
+ */
+#ifndef AFQMC_H
+#define AFQMC_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AFQMC_OK = 0,
+  AFQMC_ERR_ARG = 1,      /* invalid argument (sizes, null pointers, mismatched pair)       */
+  AFQMC_ERR_CUDA = 2,     /* a CUDA runtime call or kernel launch failed                     */
+  AFQMC_ERR_NUMERIC = 3,  /* singular trial overlap at setup, or every walker is dead       */
+  AFQMC_ERR_STATE = 4,    /* call not valid in the handle's current state                    */
+  AFQMC_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up                              */
+  AFQMC_ERR_NOMEM = 6     /* device allocation failed                                        */
+} afqmc_status;
+
+/* Projection mode (Sec. II.A): phaseless (force bias + cos cut, real weights) or
+ * free projection (no force bias, complex weights). */
+enum { AFQMC_PHASELESS = 0, AFQMC_FREE = 1 };
+
+/* Arithmetic of the Cholesky contractions (force bias, V_HS, exchange).
+ * Determinants, ratios, phases, weights and MGS are always float64. */
+enum { AFQMC_FP64 = 0 };
+
+typedef struct afqmc_ctx* afqmc_handle;
+
+typedef struct {
+  double dt;          /* imaginary-time step in Ha^-1 (> 0)                                 */
+  int n_walkers;      /* walkers of this system, Nw >= 1                                    */
+  int taylor_order;   /* order n of the Taylor exponential T_n(A) = sum_{m<=n} A^m/m!, >= 1 */
+  int precision;      /* AFQMC_FP64                                                         */
+  int mode;           /* AFQMC_PHASELESS or AFQMC_FREE                                      */
+  int n_repeats;      /* R >= 1 independent repeats; walker k belongs to repeat k*R/Nw      */
+  uint64_t seed;      /* key of the counter-based field stream                              */
+  double fb_cap;      /* |xbar_g| above fb_cap is scaled back to fb_cap; <= 0 disables      */
+  int64_t walker_offset; /* global pair index of walker 0 (replicas on several GPUs take
+                            disjoint ranges of k); 0 <= walker_offset, + Nw <= 2^32          */
+} afqmc_options;
+
+typedef struct {
+  int M, X, n_up, n_dn, n_walkers, n_repeats;
+  uint64_t step;      /* propagation steps taken since setup / afqmc_set_walkers            */
+  double e_trial;     /* E_T = E_L(psi_T), the trial (HF) energy used as the energy shift   */
+  double c_mf;        /* C = -1/2 sum_g <rho_g>_T^2, scalar of the one-body part H_1        */
+  int n_alive;        /* live walkers (synchronises the stream)                             */
+} afqmc_info;
+
+/* Fill *o with dt = 0.01, n_walkers = 128, taylor_order = 6, FP64, phaseless,
+ * n_repeats = 1, seed = 1, fb_cap = 1.0, walker_offset = 0. */
+void afqmc_default_options(afqmc_options* o);
+
+const char* afqmc_status_string(afqmc_status s);
+
+/* Message of the last failure on h (empty string if none).  Never NULL. */
+const char* afqmc_last_error(afqmc_handle h);
+
+/*
+ * afqmc_setup -- Sec. II.A, Eqs. 1-2.  Creates a system from the Hamiltonian
+ *   H = sum_ij h1_ij sum_s c+_is c_js + 1/2 sum_ijkl V_ijkl sum_st c+_is c+_jt c_lt c_ks,
+ *   V_ijkl = sum_g L^g_ik L^g_jl,
+ * and a single-determinant trial.  On the device it forms <rho_g>_T, the one-body
+ * matrix K = h1 - 1/2 sum_g L_g L_g + sum_g <rho_g>_T L_g of H_1, exp(-dt K/2),
+ * C, the half-rotated tensors Psi_s^T L_g and Psi_s^T h1, the packed transposed
+ * Cholesky tensor, E_T, and initialises every walker to the trial with weight 1.
+ *   h1    [M][M] symmetric.
+ *   L     [X][M][M], each L_g symmetric.
+ *   trial [M][N] = [Psi_up | Psi_dn], real, orthonormal columns within each spin.
+ *   M >= 1, X >= 1, 1 <= N, 0 <= n_up, n_dn <= min(M, 32).
+ * Synchronises the stream.  Errors: ARG (sizes, nulls, options), NUMERIC (trial has
+ * zero overlap with itself), NOMEM, CUDA.  *out is NULL on failure.
+ */
+afqmc_status afqmc_setup(afqmc_handle* out, const double* h1, const double* L,
+                         const double* trial, int M, int X, int n_up, int n_dn,
+                         const afqmc_options* opt, cudaStream_t stream);
+
+/* Release every device buffer of h.  h may be NULL. */
+afqmc_status afqmc_destroy(afqmc_handle h);
+
+/*
+ * afqmc_set_walkers -- replace the population (e.g. to seed a secondary system
+ * from another one's determinants).  phi [2][Nw][M][N] planar complex; w [2][Nw]
+ * planar complex (imaginary part ignored in phaseless mode), or NULL for w = 1.
+ * Walkers with w == 0 are dead.  Resets the step counter to 0 and recomputes
+ * log <psi_T|phi>.  Errors: ARG, CUDA.
+ */
+afqmc_status afqmc_set_walkers(afqmc_handle h, const double* phi, const double* w,
+                               cudaStream_t stream);
+
+/*
+ * afqmc_get_state -- copy the population out.  Any output may be NULL.
+ *   phi  [2][Nw][M][N]  walker determinants
+ *   logO [2][Nw]        log <psi_T|phi_k> (branch of the imaginary part unspecified)
+ *   w    [2][Nw]        weights
+ *   alive [Nw]          1 live, 0 dead
+ * Synchronises the stream.
+ */
+afqmc_status afqmc_get_state(afqmc_handle h, double* phi, double* logO, double* w,
+                             int* alive, cudaStream_t stream);
+
+afqmc_status afqmc_get_info(afqmc_handle h, afqmc_info* info, cudaStream_t stream);
+
+/*
+ * afqmc_propagate -- Eqs. 3-5, 8-9, 11 and the hybrid weight of Sec. II.D; n_steps
+ * steps of every walker.  Per step and walker k:
+ *   xbar_g = -i sqrt(dt) (rhobar_g - <rho_g>_T)            (Eq. 9, capped by fb_cap)
+ *   c_g = x_g - xbar_g,  A = i sqrt(dt) sum_g c_g L_g,  s = exp(-i sqrt(dt) sum_g c_g <rho_g>_T)
+ *   phi' = e^{-dt K/2} T_n(A) e^{-dt K/2} phi
+ *   R = s <psi_T|phi'>/<psi_T|phi>,  I = R exp(x.xbar - xbar.xbar/2) exp(-dt (C - E_T))
+ *   phaseless: w <- w |I| max(0, cos arg R), w <= 0 kills the walker for good;
+ *   free:      w <- w I (xbar = 0).
+ * fields: NULL draws x_{t,k,g} ~ N(0,1) from Philox-4x32-10 with key (seed low, seed
+ *   high 32 bits), counter (g/2, k, t, 0), k = walker_offset + walker, and Box-Muller
+ *   (u1 = (top 53 bits of words 1:0, + 1) 2^-53, u2 = (top 53 bits of words 3:2) 2^-53,
+ *   x_{2j} = sqrt(-2 ln u1) cos(2 pi u2), x_{2j+1} = sqrt(-2 ln u1) sin(2 pi u2));
+ *   otherwise [n_steps][Nw][X] explicit fields.  Dead walkers are carried through the
+ *   batched arithmetic but their determinants and weights no longer change.
+ * Errors: ARG, CUDA.
+ */
+afqmc_status afqmc_propagate(afqmc_handle h, int n_steps, const double* fields,
+                             cudaStream_t stream);
+
+/* afqmc_orthonormalise -- Sec. II.D: modified Gram-Schmidt of each spin block of
+ * every live walker (columns in order), then log <psi_T|phi> is recomputed.  The
+ * weights are unchanged.  Errors: CUDA. */
+afqmc_status afqmc_orthonormalise(afqmc_handle h, cudaStream_t stream);
+
+/*
+ * afqmc_energy -- Eqs. 6-7 and 10.  Local energies
+ *   E_L = sum_s tr(h1 G_s) + 1/2 sum_g [ (sum_s tr(L_g G_s))^2 - sum_s tr(L_g G_s L_g G_s) ]
+ * with the mixed Green's function G_s; and per repeat r the mixed estimate
+ *   E_r = sum_k w_k Re E_L,k / sum_k w_k       (phaseless)
+ *   E_r = Re( sum_k w_k E_L,k / sum_k w_k )    (free projection).
+ *   e_local [2][Nw] or NULL;  e_mixed [R] or NULL;  w_sum [R] (Re sum_k w_k) or NULL.
+ * Synchronises the stream when any output is host memory.  Errors: ARG, CUDA.
+ */
+afqmc_status afqmc_energy(afqmc_handle h, double* e_local, double* e_mixed, double* w_sum,
+                          cudaStream_t stream);
+
+/*
+ * afqmc_pair_delta_E -- Sec. II.B.  Correlated sampling of two systems: walker k
+ * of A and walker k of B draw the same x_{t,k,g} for every g both have (systems
+ * with different X share the first min(X_A, X_B) fields).  No population control;
+ * each system keeps its own force bias and mean field.  Runs n_steps steps of both
+ * systems; every mgs_every steps orthonormalises, every energy_every steps measures
+ * (order: propagate, orthonormalise, measure).  One measurement block is captured
+ * once as a CUDA graph and replayed.  Requirements: same seed, Nw, R, dt, mode and
+ * step counter on both handles; the step counter a multiple of energy_every;
+ * energy_every a multiple of mgs_every; n_steps a multiple of energy_every.
+ * Outputs (host or device, any may be NULL):
+ *   e_series [n_meas][2][R]   E_A,r and E_B,r at each measurement
+ *   dE_mean, dE_sigma, tau_at_min: mean and standard error (over the R repeats) of
+ *     the cumulative averages of dE = E_B - E_A over measurements with tau >= tau_eq,
+ *     at the tau (relative to the start of this call) where the error is smallest,
+ *     earliest on ties (Sec. II.B).  sigma is NaN when R == 1.
+ * Synchronises the stream.  Errors: ARG, STATE, NUMERIC (all walkers of a system
+ * dead), CUDA.
+ */
+afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n_steps,
+                                int energy_every, int mgs_every, double tau_eq,
+                                double* e_series, double* dE_mean, double* dE_sigma,
+                                double* tau_at_min, cudaStream_t stream);
+
+/*
+ * afqmc_delta_E_stats -- host-only statistics of Sec. II.B (no GPU needed).
+ *   dE [n_meas][R] energy differences per measurement and repeat, taus [n_meas].
+ *   mean_tau, se_tau [n_meas] (may be NULL): mean and standard error sd/sqrt(R) per tau.
+ *   est [3]: mean, SE and tau of the cumulative averages (tau >= tau_eq) at the
+ *   earliest minimum SE.  Errors: ARG.
+ */
+afqmc_status afqmc_delta_E_stats(const double* dE, const double* taus, int n_meas, int R,
+                                 double tau_eq, double* mean_tau, double* se_tau,
+                                 double* est);
+
+/*
+ * afqmc_time_kernel -- benchmarking aid (no counterpart in the paper).  Launches one
+ * kernel of the propagation step `reps` times on `stream` with the handle's current
+ * data, timed with CUDA events recorded on that stream, and stores the mean duration
+ * of one launch in *ms.  which: AFQMC_K_VHS (V_HS contraction), AFQMC_K_FORCE_BIAS
+ * (force-bias contraction), AFQMC_K_TAYLOR (Taylor exponential, on scratch memory),
+ * AFQMC_K_EXCHANGE (local-energy kernel).  None of them changes the walkers.
+ * Synchronises the stream.  Errors: ARG, CUDA.
+ */
+enum { AFQMC_K_VHS = 0, AFQMC_K_FORCE_BIAS = 1, AFQMC_K_TAYLOR = 2, AFQMC_K_EXCHANGE = 3 };
+afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms,
+                               cudaStream_t stream);
+
+/* Flyvbjerg-Petersen reblocking error of the mean of series[n] (host only): the
+ * largest block-level estimate among levels with >= 16 blocks. */
+double afqmc_reblock_error(const double* series, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFQMC_H */

@@ -20,7 +20,7 @@ gives H = H_1 + H_2 with the one-body part
 One step (Eqs. 3-5, 8-9 and the hybrid weight of Sec. II.D), per live walker:
   1. xbar_g = -sqrt(dt) (vbar_g - <v_g>) = -i sqrt(dt) (rhobar_g - <rho_g>_T)   (Eq. 9)
      optionally capped: |xbar_g| > cap  ->  xbar_g * cap / |xbar_g|
-  2. c_g = x_g - xbar_g;  A = i sqrt(dt) sum_g c_g L_g  (one-body matrix of Eq. 10's
+  2. c_g = x_g - xbar_g;  A = i sqrt(dt) sum_g c_g L_g  (one-body matrix of Eq. 11's
      middle factor); its scalar part s = exp(-i sqrt(dt) sum_g c_g <rho_g>_T)
   3. Phi' = e^{-dt K/2} T_n(A) e^{-dt K/2} Phi,  T_n(A) = sum_{m<=n} A^m / m!
      (Eq. 3 split, Eq. 5 read with a half step on each side, Thouless theorem)
@@ -32,7 +32,7 @@ One step (Eqs. 3-5, 8-9 and the hybrid weight of Sec. II.D), per live walker:
      free projection: xbar = 0 and w <- w I (complex).
 Every ``mgs_every`` steps each spin block is replaced by its modified
 Gram-Schmidt Q factor (Sec. II.D) and log O recomputed.
-Energy (Eqs. 6-7, 11): E_L = sum_s tr(h1 G_s)
+Energy (Eqs. 6-7, 10): E_L = sum_s tr(h1 G_s)
       + 1/2 sum_g [ rhobar_g^2 - sum_s tr(L_g G_s L_g G_s) ],
   E = sum_k w_k Re E_L,k / sum_k w_k  (phaseless);  Re(sum w E_L / sum w) (free).
 """
@@ -151,7 +151,7 @@ def taylor_apply(A, phi, order):
 
 
 def step_determinant(sys: System, phi, logO, x, xbar):
-    """One application of Eq. 10 with fields x and shift xbar to determinants phi.
+    """One application of Eq. 11 with fields x and shift xbar to determinants phi.
 
     Returns (Phi', log O', log R, log I): R is the overlap ratio including the scalar
     part s of the shifted HS exponential, I the hybrid weight factor of Sec. II.D.
@@ -247,7 +247,7 @@ def repeat_groups(n_walkers: int, n_repeats: int):
 
 
 def mixed_energy(sys: System, w, eloc, groups, n_repeats):
-    """Per-repeat mixed estimate sum w E_L / sum w (Eq. 6; Re E_L for phaseless, Eq. 11)."""
+    """Per-repeat mixed estimate sum w E_L / sum w (Eq. 7; Re E_L for phaseless, Eq. 10)."""
     E = np.empty(n_repeats)
     W = np.empty(n_repeats)
     for r in range(n_repeats):

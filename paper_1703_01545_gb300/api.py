@@ -1,0 +1,233 @@
+"""Python binding of the C ABI in include/afqmc.h (argument marshalling only).
+
+The functions keep the C names.  Arrays may be numpy arrays (host) or torch
+tensors (host or CUDA); every step of the method runs in the CUDA library.
+``System`` and ``pair_delta_E`` are thin conveniences over the same calls.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+PHASELESS, FREE = 0, 1
+FP64 = 0
+
+
+class AfqmcError(RuntimeError):
+    pass
+
+
+def _torch():
+    try:
+        import torch
+        return torch
+    except ImportError:  # pragma: no cover
+        return None
+
+
+def _ptr(a):
+    """Raw pointer of a C-contiguous float64/int32 numpy array or torch tensor (or None)."""
+    if a is None:
+        return None
+    t = _torch()
+    if t is not None and isinstance(a, t.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    t = _torch()
+    if t is not None and t.cuda.is_available():
+        return ctypes.c_void_p(t.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _check(code, handle=None, what=""):
+    if code != 0:
+        lib = _lib.load()
+        msg = lib.afqmc_last_error(handle).decode() if handle else ""
+        raise AfqmcError(f"{what}: {_lib.STATUS.get(code, code)} {msg}".strip())
+
+
+def afqmc_default_options():
+    o = _lib.AfqmcOptions()
+    _lib.load().afqmc_default_options(ctypes.byref(o))
+    return o
+
+
+def afqmc_setup(h1, L, trial, M, X, n_up, n_dn, opt, stream=None):
+    h = ctypes.c_void_p()
+    code = _lib.load().afqmc_setup(ctypes.byref(h), _ptr(h1), _ptr(L), _ptr(trial), M, X, n_up,
+                                   n_dn, ctypes.byref(opt), _stream(stream))
+    _check(code, None, "afqmc_setup")
+    return h
+
+
+def afqmc_destroy(h):
+    _check(_lib.load().afqmc_destroy(h), None, "afqmc_destroy")
+
+
+def afqmc_set_walkers(h, phi, w=None, stream=None):
+    _check(_lib.load().afqmc_set_walkers(h, _ptr(phi), _ptr(w), _stream(stream)), h,
+           "afqmc_set_walkers")
+
+
+def afqmc_get_state(h, phi=None, logO=None, w=None, alive=None, stream=None):
+    _check(_lib.load().afqmc_get_state(h, _ptr(phi), _ptr(logO), _ptr(w), _ptr(alive),
+                                       _stream(stream)), h, "afqmc_get_state")
+
+
+def afqmc_get_info(h, stream=None):
+    info = _lib.AfqmcInfo()
+    _check(_lib.load().afqmc_get_info(h, ctypes.byref(info), _stream(stream)), h, "afqmc_get_info")
+    return info
+
+
+def afqmc_propagate(h, n_steps, fields=None, stream=None):
+    _check(_lib.load().afqmc_propagate(h, int(n_steps), _ptr(fields), _stream(stream)), h,
+           "afqmc_propagate")
+
+
+def afqmc_orthonormalise(h, stream=None):
+    _check(_lib.load().afqmc_orthonormalise(h, _stream(stream)), h, "afqmc_orthonormalise")
+
+
+def afqmc_energy(h, e_local=None, e_mixed=None, w_sum=None, stream=None):
+    _check(_lib.load().afqmc_energy(h, _ptr(e_local), _ptr(e_mixed), _ptr(w_sum), _stream(stream)),
+           h, "afqmc_energy")
+
+
+def afqmc_pair_delta_E(A, B, n_steps, energy_every, mgs_every, tau_eq, e_series=None,
+                       dE_mean=None, dE_sigma=None, tau_at_min=None, stream=None,
+                       raise_on_dead=True):
+    """Returns the status code (0, or 3 = every walker of a system dead when
+    raise_on_dead is False; the outputs are written in both cases)."""
+    code = _lib.load().afqmc_pair_delta_E(A, B, int(n_steps), int(energy_every), int(mgs_every),
+                                          float(tau_eq), _ptr(e_series), _ptr(dE_mean),
+                                          _ptr(dE_sigma), _ptr(tau_at_min), _stream(stream))
+    if code == 3 and not raise_on_dead:
+        return code
+    _check(code, A, "afqmc_pair_delta_E")
+    return code
+
+
+def afqmc_delta_E_stats(dE, taus, tau_eq):
+    """Host statistics; returns (mean_tau, se_tau, (mean, se, tau_at_min))."""
+    dE = np.ascontiguousarray(dE, dtype=np.float64)
+    taus = np.ascontiguousarray(taus, dtype=np.float64)
+    n, R = dE.shape
+    mt, st, est = np.empty(n), np.empty(n), np.empty(3)
+    code = _lib.load().afqmc_delta_E_stats(_ptr(dE), _ptr(taus), n, R, float(tau_eq), _ptr(mt),
+                                           _ptr(st), _ptr(est))
+    _check(code, None, "afqmc_delta_E_stats")
+    return mt, st, tuple(est)
+
+
+K_VHS, K_FORCE_BIAS, K_TAYLOR, K_EXCHANGE = 0, 1, 2, 3
+
+
+def afqmc_time_kernel(h, which, reps, stream=None):
+    ms = ctypes.c_double()
+    _check(_lib.load().afqmc_time_kernel(h, int(which), int(reps), ctypes.byref(ms),
+                                         _stream(stream)), h, "afqmc_time_kernel")
+    return ms.value
+
+
+def afqmc_reblock_error(series):
+    s = np.ascontiguousarray(series, dtype=np.float64)
+    return float(_lib.load().afqmc_reblock_error(_ptr(s), s.size))
+
+
+class System:
+    """One system (h1, L, trial) and its walker population on the current CUDA device."""
+
+    def __init__(self, h1, L, trial, n_up, n_dn, dt=0.01, n_walkers=128, taylor_order=6,
+                 mode=PHASELESS, n_repeats=1, seed=1, fb_cap=1.0, walker_offset=0,
+                 stream=None):
+        h1 = np.ascontiguousarray(h1, dtype=np.float64)
+        L = np.ascontiguousarray(L, dtype=np.float64)
+        trial = np.ascontiguousarray(trial, dtype=np.float64)
+        self.M, self.X = h1.shape[0], L.shape[0]
+        self.n_up, self.n_dn, self.N = int(n_up), int(n_dn), int(n_up) + int(n_dn)
+        self.n_walkers, self.n_repeats, self.dt = int(n_walkers), int(n_repeats), float(dt)
+        o = afqmc_default_options()
+        o.dt, o.n_walkers, o.taylor_order = float(dt), int(n_walkers), int(taylor_order)
+        o.precision, o.mode, o.n_repeats = FP64, int(mode), int(n_repeats)
+        o.seed, o.fb_cap, o.walker_offset = int(seed), float(fb_cap), int(walker_offset)
+        self.opt = o
+        self.h = afqmc_setup(h1, L, trial, self.M, self.X, self.n_up, self.n_dn, o, stream)
+
+    def close(self):
+        if self.h is not None:
+            afqmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return afqmc_get_info(self.h)
+
+    def propagate(self, n_steps, fields=None):
+        if isinstance(fields, np.ndarray):
+            fields = np.ascontiguousarray(fields, dtype=np.float64)
+        afqmc_propagate(self.h, n_steps, fields)
+
+    def orthonormalise(self):
+        afqmc_orthonormalise(self.h)
+
+    def energy(self):
+        """(E_L complex [Nw], E_mixed [R], sum w [R]) as numpy arrays."""
+        el = np.empty(2 * self.n_walkers)
+        em = np.empty(self.n_repeats)
+        ws = np.empty(self.n_repeats)
+        afqmc_energy(self.h, el, em, ws)
+        return el[:self.n_walkers] + 1j * el[self.n_walkers:], em, ws
+
+    def state(self):
+        nw, M, N = self.n_walkers, self.M, self.N
+        phi = np.empty(2 * nw * M * N)
+        lo = np.empty(2 * nw)
+        w = np.empty(2 * nw)
+        al = np.empty(nw, dtype=np.int32)
+        afqmc_get_state(self.h, phi, lo, w, al)
+        phi = phi.reshape(2, nw, M, N)
+        return dict(phi=phi[0] + 1j * phi[1], logO=lo[:nw] + 1j * lo[nw:],
+                    w=w[:nw] + 1j * w[nw:], alive=al.astype(bool))
+
+    def set_walkers(self, phi, w=None):
+        phi = np.asarray(phi)
+        p = np.ascontiguousarray(np.stack([phi.real, phi.imag]), dtype=np.float64)
+        wp = None
+        if w is not None:
+            w = np.asarray(w)
+            wp = np.ascontiguousarray(np.stack([w.real, w.imag]), dtype=np.float64)
+        afqmc_set_walkers(self.h, p, wp)
+
+
+def pair_delta_E(A: System, B: System, n_steps, energy_every=5, mgs_every=5, tau_eq=0.0,
+                 raise_on_dead=True):
+    """Correlated pair run; returns dict(E [n_meas, 2, R], dE_mean, dE_sigma, tau_at_min,
+    all_dead).  With raise_on_dead=False a run in which every walker of a system died
+    returns its (NaN-bearing) results with all_dead=True instead of raising."""
+    R = A.n_repeats
+    n_meas = n_steps // energy_every
+    es = np.empty(max(1, n_meas * 2 * R))
+    m, s, t = np.empty(1), np.empty(1), np.empty(1)
+    code = afqmc_pair_delta_E(A.h, B.h, n_steps, energy_every, mgs_every, tau_eq, es, m, s, t,
+                              raise_on_dead=raise_on_dead)
+    return dict(E=es[:n_meas * 2 * R].reshape(n_meas, 2, R), dE_mean=float(m[0]),
+                dE_sigma=float(s[0]), tau_at_min=float(t[0]), all_dead=code == 3,
+                taus=np.arange(1, n_meas + 1) * energy_every * A.dt)

@@ -1,0 +1,452 @@
+// C-ABI entry points: argument checking, device memory, the setup sequence, the
+// per-step kernel schedule, and the CUDA-graph driven correlated pair run.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+struct afqmc_ctx : afq::Ctx {};
+
+namespace {
+
+using afq::Ctx;
+
+afqmc_status set_err(Ctx* h, afqmc_status code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+afqmc_status cuda_fail(Ctx* h, const char* what, cudaError_t e) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  return set_err(h, AFQMC_ERR_CUDA, buf);
+}
+
+#define AFQ_CK(call)                                  \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, #call, e_); \
+  } while (0)
+
+template <class T>
+afqmc_status dalloc(Ctx* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(h, AFQMC_ERR_NOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  return AFQMC_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_ctx(Ctx* h) {
+  afq::destroy_pair_cache(h);
+  double* bufs[] = {h->h1, h->L, h->Lt, h->Ltil, h->htil, h->psi, h->expK, h->rho_mf, h->phi,
+                    h->phi2, h->theta, h->logO, h->w, h->rhobar, h->U, h->Avhs, h->aux,
+                    h->eloc, h->esum};
+  for (double* b : bufs)
+    if (b) cudaFree(b);
+  if (h->alive) cudaFree(h->alive);
+  if (h->d_step) cudaFree(h->d_step);
+  if (h->d_flags) cudaFree(h->d_flags);
+}
+
+// One propagation step of every walker of system h (Eqs. 3-5, 8-9, 11, hybrid weight).
+afqmc_status step_launch(Ctx* h, const double* fields_t, cudaStream_t s) {
+  const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
+  const int64_t NM = (int64_t)N * M;
+  if (h->opt.mode == AFQMC_PHASELESS) {
+    // rhobar[(p,w)][g] = sum_(n,i) Ltil[g][(n,i)] Theta[(p,w)][(n,i)]       (Eq. 9)
+    AFQ_CK(afq::gemm_tn_f64(X, 2 * Nw, (int)NM, 1.0, h->Ltil, NM, 0, h->theta, NM, 0, 0.0,
+                            h->rhobar, X, 0, 1, s, afq::GEMM_FORCE_BIAS));
+  }
+  AFQ_CK(afq::launch_fields(*h, fields_t, s));
+  // packed A[(p,w)][ij] = sum_g Lt[ij][g] U[(p,w)][g]                         (Eq. 11)
+  AFQ_CK(afq::gemm_tn_f64((int)h->P, 2 * Nw, X, 1.0, h->Lt, X, 0, h->U, X, 0, 0.0, h->Avhs,
+                          h->P, 0, 1, s, afq::GEMM_VHS));
+  // e^{-dt K/2} on every column of every walker
+  AFQ_CK(afq::gemm_tn_f64(M, 2 * Nw * N, M, 1.0, h->expK, M, 0, h->phi, M, 0, 0.0, h->phi2, M,
+                          0, 1, s, afq::GEMM_ONEBODY));
+  AFQ_CK(afq::launch_taylor(*h, h->phi2, s));
+  AFQ_CK(afq::gemm_tn_f64(M, 2 * Nw * N, M, 1.0, h->expK, M, 0, h->phi2, M, 0, 0.0, h->theta,
+                          M, 0, 1, s, afq::GEMM_ONEBODY));
+  // new overlaps, Theta, ratio, phase, weight; live walkers take the new determinant
+  AFQ_CK(afq::launch_overlap(*h, h->theta, afq::OV_UPDATE, s));
+  AFQ_CK(afq::launch_step_advance(*h, s));
+  return AFQMC_OK;
+}
+
+afqmc_status ortho_launch(Ctx* h, cudaStream_t s) {
+  AFQ_CK(afq::launch_mgs(*h, s));
+  AFQ_CK(afq::launch_overlap(*h, nullptr, afq::OV_REFRESH, s));
+  return AFQMC_OK;
+}
+
+afqmc_status check_opts(const afqmc_options* o, std::string& why) {
+  if (!o) { why = "options is NULL"; return AFQMC_ERR_ARG; }
+  if (!(o->dt > 0.0) || !std::isfinite(o->dt)) { why = "dt must be > 0"; return AFQMC_ERR_ARG; }
+  if (o->n_walkers < 1) { why = "n_walkers must be >= 1"; return AFQMC_ERR_ARG; }
+  if (o->taylor_order < 1 || o->taylor_order > 64) { why = "taylor_order must be in [1, 64]"; return AFQMC_ERR_ARG; }
+  if (o->precision != AFQMC_FP64) { why = "unsupported precision"; return AFQMC_ERR_ARG; }
+  if (o->mode != AFQMC_PHASELESS && o->mode != AFQMC_FREE) { why = "unknown mode"; return AFQMC_ERR_ARG; }
+  if (o->n_repeats < 1 || o->n_repeats > o->n_walkers) { why = "n_repeats must be in [1, n_walkers]"; return AFQMC_ERR_ARG; }
+  if (!std::isfinite(o->fb_cap)) { why = "fb_cap must be finite"; return AFQMC_ERR_ARG; }
+  if (o->walker_offset < 0 || o->walker_offset + (int64_t)o->n_walkers > ((int64_t)1 << 32)) {
+    why = "walker_offset out of range";
+    return AFQMC_ERR_ARG;
+  }
+  return AFQMC_OK;
+}
+
+}  // namespace
+
+namespace afq {
+afqmc_status pair_step(Ctx* h, cudaStream_t s) { return step_launch(h, nullptr, s); }
+afqmc_status pair_ortho(Ctx* h, cudaStream_t s) { return ortho_launch(h, s); }
+}  // namespace afq
+
+extern "C" {
+
+void afqmc_default_options(afqmc_options* o) {
+  if (!o) return;
+  o->dt = 0.01;
+  o->n_walkers = 128;
+  o->taylor_order = 6;
+  o->precision = AFQMC_FP64;
+  o->mode = AFQMC_PHASELESS;
+  o->n_repeats = 1;
+  o->seed = 1;
+  o->fb_cap = 1.0;
+  o->walker_offset = 0;
+}
+
+const char* afqmc_status_string(afqmc_status s) {
+  switch (s) {
+    case AFQMC_OK: return "ok";
+    case AFQMC_ERR_ARG: return "invalid argument";
+    case AFQMC_ERR_CUDA: return "CUDA error";
+    case AFQMC_ERR_NUMERIC: return "numerical failure";
+    case AFQMC_ERR_STATE: return "invalid state";
+    case AFQMC_ERR_TIMEOUT: return "device wait timed out";
+    case AFQMC_ERR_NOMEM: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+const char* afqmc_last_error(afqmc_handle h) { return h ? h->err.c_str() : ""; }
+
+afqmc_status afqmc_setup(afqmc_handle* out, const double* h1_in, const double* L_in,
+                         const double* trial_in, int M, int X, int n_up, int n_dn,
+                         const afqmc_options* opt, cudaStream_t s) {
+  if (!out) return AFQMC_ERR_ARG;
+  *out = nullptr;
+  std::string why;
+  if (check_opts(opt, why) != AFQMC_OK) return AFQMC_ERR_ARG;
+  if (!h1_in || !L_in || !trial_in) return AFQMC_ERR_ARG;
+  const int N = n_up + n_dn;
+  if (M < 1 || X < 1 || n_up < 0 || n_dn < 0 || N < 1 || n_up > M || n_dn > M || n_up > 32 ||
+      n_dn > 32 || (int64_t)N * M > 4096)
+    return AFQMC_ERR_ARG;
+  if ((int64_t)opt->n_walkers * N * M * 2 > (int64_t)1 << 40) return AFQMC_ERR_ARG;
+
+  afqmc_ctx* h = new afqmc_ctx();
+  h->M = M; h->X = X; h->n_up = n_up; h->n_dn = n_dn; h->N = N;
+  h->Nw = opt->n_walkers; h->R = opt->n_repeats; h->opt = *opt;
+  h->P = afq::packed_size(M);
+  h->sqrt_dt = std::sqrt(opt->dt);
+  cudaGetDevice(&h->device);
+  {
+    static uint64_t next_uid = 0;
+    h->uid = ++next_uid;
+  }
+  const int64_t NM = (int64_t)N * M, Nw = h->Nw;
+  afqmc_status st = AFQMC_OK;
+#define AFQ_ALLOC(p, n) \
+  if ((st = dalloc(h, &(p), (size_t)(n))) != AFQMC_OK) { free_ctx(h); delete h; return st; }
+  AFQ_ALLOC(h->h1, (int64_t)M * M);
+  AFQ_ALLOC(h->L, (int64_t)X * M * M);
+  AFQ_ALLOC(h->Lt, h->P * X);
+  AFQ_ALLOC(h->Ltil, (int64_t)X * NM);
+  AFQ_ALLOC(h->htil, NM);
+  AFQ_ALLOC(h->psi, NM);
+  AFQ_ALLOC(h->expK, (int64_t)M * M);
+  AFQ_ALLOC(h->rho_mf, X);
+  AFQ_ALLOC(h->phi, 2 * Nw * NM);
+  AFQ_ALLOC(h->phi2, 2 * Nw * NM);
+  AFQ_ALLOC(h->theta, 2 * Nw * NM);
+  AFQ_ALLOC(h->logO, 2 * Nw);
+  AFQ_ALLOC(h->w, 2 * Nw);
+  AFQ_ALLOC(h->alive, Nw);
+  AFQ_ALLOC(h->rhobar, 2 * Nw * X);
+  AFQ_ALLOC(h->U, 2 * Nw * X);
+  AFQ_ALLOC(h->Avhs, 2 * Nw * h->P);
+  AFQ_ALLOC(h->aux, 4 * Nw);
+  AFQ_ALLOC(h->eloc, 2 * Nw);
+  AFQ_ALLOC(h->esum, 4 * (int64_t)h->R);
+  AFQ_ALLOC(h->d_step, 1);
+  AFQ_ALLOC(h->d_flags, 4);
+#undef AFQ_ALLOC
+  // scratch for the setup only
+  double *tmp = nullptr, *Q = nullptr, *Kb = nullptr, *E0 = nullptr, *E1 = nullptr, *dnorm = nullptr;
+  auto cleanup_tmp = [&]() {
+    for (double* p : {tmp, Q, Kb, E0, E1, dnorm})
+      if (p) cudaFree(p);
+  };
+  auto bail = [&](afqmc_status code) {
+    cleanup_tmp();
+    std::string msg = h->err;
+    free_ctx(h);
+    delete h;
+    return code;
+  };
+  if (dalloc(h, &tmp, std::max<int64_t>((int64_t)X * M * M, NM)) != AFQMC_OK ||
+      dalloc(h, &Q, (int64_t)M * M) != AFQMC_OK || dalloc(h, &Kb, (int64_t)M * M) != AFQMC_OK ||
+      dalloc(h, &E0, (int64_t)M * M) != AFQMC_OK || dalloc(h, &E1, (int64_t)M * M) != AFQMC_OK ||
+      dalloc(h, &dnorm, 1) != AFQMC_OK)
+    return bail(AFQMC_ERR_NOMEM);
+
+#define AFQ_SCK(call)                              \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) {                       \
+      cuda_fail(h, #call, e_);                     \
+      return bail(AFQMC_ERR_CUDA);                 \
+    }                                              \
+  } while (0)
+
+  AFQ_SCK(afq::prepare_kernels(*h));
+  AFQ_SCK(cudaMemcpyAsync(h->h1, h1_in, sizeof(double) * M * M, cudaMemcpyDefault, s));
+  AFQ_SCK(cudaMemcpyAsync(h->L, L_in, sizeof(double) * X * M * M, cudaMemcpyDefault, s));
+  AFQ_SCK(cudaMemcpyAsync(tmp, trial_in, sizeof(double) * NM, cudaMemcpyDefault, s));
+  AFQ_SCK(afq::launch_transpose(tmp, h->psi, M, N, s));   // [M][N] -> [N][M]
+  // Ltil[g][n][i] = sum_j L_g[i][j] psi[n][j]  (rows of Psi_s^T L_g)
+  AFQ_SCK(afq::gemm_tn_f64(M, N, M, 1.0, h->L, M, (int64_t)M * M, h->psi, M, 0, 0.0, h->Ltil, M,
+                           NM, X, s));
+  AFQ_SCK(afq::gemm_tn_f64(M, N, M, 1.0, h->h1, M, 0, h->psi, M, 0, 0.0, h->htil, M, 0, 1, s));
+  AFQ_SCK(afq::launch_rho_mf(h->Ltil, h->psi, h->rho_mf, X, (int)NM, s));
+  // Q = sum_g L_g L_g through the permuted tensor Lp[i][(g,k)] = L_g[i][k]
+  AFQ_SCK(afq::launch_permute_L(h->L, tmp, M, X, s));
+  AFQ_SCK(afq::gemm_tn_f64(M, M, X * M, 1.0, tmp, (int64_t)X * M, 0, tmp, (int64_t)X * M, 0, 0.0,
+                           Q, M, 0, 1, s));
+  // B = -(dt/2) K,  K = h1 - Q/2 + sum_g <rho_g>_T L_g
+  AFQ_SCK(afq::launch_build_K(h->h1, Q, h->L, h->rho_mf, Kb, M, X, -0.5 * opt->dt, s));
+  AFQ_SCK(afq::launch_pack_Lt(h->L, h->Lt, M, X, s));
+  AFQ_SCK(afq::launch_norm1(Kb, M, dnorm, s));
+  double nrm = 0;
+  std::vector<double> rho(X);
+  AFQ_SCK(cudaMemcpyAsync(&nrm, dnorm, sizeof(double), cudaMemcpyDeviceToHost, s));
+  AFQ_SCK(cudaMemcpyAsync(rho.data(), h->rho_mf, sizeof(double) * X, cudaMemcpyDeviceToHost, s));
+  AFQ_SCK(cudaStreamSynchronize(s));
+  if (!std::isfinite(nrm)) {
+    set_err(h, AFQMC_ERR_ARG, "non-finite one-body matrix");
+    return bail(AFQMC_ERR_ARG);
+  }
+  double cmf = 0;
+  for (double r : rho) cmf += r * r;
+  h->c_mf = -0.5 * cmf;
+  // exp(B) by scaling and squaring around a degree-20 Taylor polynomial (Horner form):
+  // ||B / 2^sq||_1 <= 1/2 makes the truncation error below 2^-75.
+  int sq = 0;
+  while (nrm / std::ldexp(1.0, sq) > 0.5) ++sq;
+  const double sc = std::ldexp(1.0, -sq);
+  const int deg = 20;
+  AFQ_SCK(cudaMemsetAsync(E0, 0, sizeof(double) * M * M, s));
+  AFQ_SCK(afq::launch_add_identity(E0, M, 1.0, s));
+  for (int k = deg; k >= 1; --k) {
+    // E1 = (sc/k) * B E0 + I   (B and E0 symmetric and commuting)
+    AFQ_SCK(afq::gemm_tn_f64(M, M, M, sc / k, E0, M, 0, Kb, M, 0, 0.0, E1, M, 0, 1, s));
+    AFQ_SCK(afq::launch_add_identity(E1, M, 1.0, s));
+    std::swap(E0, E1);
+  }
+  for (int q = 0; q < sq; ++q) {
+    AFQ_SCK(afq::gemm_tn_f64(M, M, M, 1.0, E0, M, 0, E0, M, 0, 0.0, E1, M, 0, 1, s));
+    std::swap(E0, E1);
+  }
+  AFQ_SCK(cudaMemcpyAsync(h->expK, E0, sizeof(double) * M * M, cudaMemcpyDeviceToDevice, s));
+  // walkers = trial, w = 1; trial energy E_T = E_L(psi_T)
+  AFQ_SCK(afq::launch_broadcast_walkers(h->psi, h->phi, (int)Nw, (int)NM, s));
+  AFQ_SCK(afq::launch_init_weights(h->w, h->alive, nullptr, (int)Nw, s));
+  AFQ_SCK(cudaMemsetAsync(h->d_step, 0, sizeof(unsigned long long), s));
+  AFQ_SCK(cudaMemsetAsync(h->d_flags, 0, sizeof(int) * 4, s));
+  AFQ_SCK(afq::launch_overlap(*h, nullptr, afq::OV_REFRESH, s));
+  AFQ_SCK(afq::launch_energy(*h, s, 1));   // every walker is the trial: one is enough
+  double et = 0;
+  int flags = 0;
+  AFQ_SCK(cudaMemcpyAsync(&et, h->eloc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  AFQ_SCK(cudaMemcpyAsync(&flags, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AFQ_SCK(cudaStreamSynchronize(s));
+  if (flags != 0 || !std::isfinite(et)) {
+    set_err(h, AFQMC_ERR_NUMERIC, "trial determinant has a singular overlap with itself");
+    return bail(AFQMC_ERR_NUMERIC);
+  }
+  h->e_trial = et;
+  cleanup_tmp();
+#undef AFQ_SCK
+  *out = h;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_destroy(afqmc_handle h) {
+  if (!h) return AFQMC_OK;
+  free_ctx(h);
+  delete h;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_set_walkers(afqmc_handle h, const double* phi, const double* w, cudaStream_t s) {
+  if (!h) return AFQMC_ERR_ARG;
+  if (!phi) return set_err(h, AFQMC_ERR_ARG, "phi is NULL");
+  const int64_t n = 2 * (int64_t)h->Nw * h->N * h->M;
+  // stage the external layout in theta, convert into phi
+  AFQ_CK(cudaMemcpyAsync(h->theta, phi, sizeof(double) * n, cudaMemcpyDefault, s));
+  AFQ_CK(afq::launch_phi_layout(h->theta, h->phi, h->Nw, h->M, h->N, 1, s));
+  const double* wd = nullptr;
+  if (w) {
+    AFQ_CK(cudaMemcpyAsync(h->eloc, w, sizeof(double) * 2 * h->Nw, cudaMemcpyDefault, s));
+    wd = h->eloc;
+  }
+  AFQ_CK(afq::launch_init_weights(h->w, h->alive, wd, h->Nw, s));
+  AFQ_CK(cudaMemsetAsync(h->d_step, 0, sizeof(unsigned long long), s));
+  AFQ_CK(afq::launch_overlap(*h, nullptr, afq::OV_REFRESH, s));
+  h->step = 0;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_get_state(afqmc_handle h, double* phi, double* logO, double* w, int* alive,
+                             cudaStream_t s) {
+  if (!h) return AFQMC_ERR_ARG;
+  if (phi) {
+    const int64_t n = 2 * (int64_t)h->Nw * h->N * h->M;
+    AFQ_CK(afq::launch_phi_layout(h->phi, h->phi2, h->Nw, h->M, h->N, 0, s));
+    AFQ_CK(cudaMemcpyAsync(phi, h->phi2, sizeof(double) * n, cudaMemcpyDefault, s));
+  }
+  if (logO) AFQ_CK(cudaMemcpyAsync(logO, h->logO, sizeof(double) * 2 * h->Nw, cudaMemcpyDefault, s));
+  if (w) AFQ_CK(cudaMemcpyAsync(w, h->w, sizeof(double) * 2 * h->Nw, cudaMemcpyDefault, s));
+  if (alive) AFQ_CK(cudaMemcpyAsync(alive, h->alive, sizeof(int) * h->Nw, cudaMemcpyDefault, s));
+  AFQ_CK(cudaStreamSynchronize(s));
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_get_info(afqmc_handle h, afqmc_info* info, cudaStream_t s) {
+  if (!h || !info) return AFQMC_ERR_ARG;
+  info->M = h->M; info->X = h->X; info->n_up = h->n_up; info->n_dn = h->n_dn;
+  info->n_walkers = h->Nw; info->n_repeats = h->R; info->step = h->step;
+  info->e_trial = h->e_trial; info->c_mf = h->c_mf;
+  std::vector<int> al(h->Nw);
+  AFQ_CK(cudaMemcpyAsync(al.data(), h->alive, sizeof(int) * h->Nw, cudaMemcpyDeviceToHost, s));
+  AFQ_CK(cudaStreamSynchronize(s));
+  int n = 0;
+  for (int a : al) n += a != 0;
+  info->n_alive = n;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_propagate(afqmc_handle h, int n_steps, const double* fields, cudaStream_t s) {
+  if (!h) return AFQMC_ERR_ARG;
+  if (n_steps < 0) return set_err(h, AFQMC_ERR_ARG, "n_steps < 0");
+  if (n_steps == 0) return AFQMC_OK;
+  const int64_t per = (int64_t)h->Nw * h->X;
+  const double* fd = nullptr;
+  double* staged = nullptr;
+  if (fields) {
+    if (is_device_ptr(fields)) {
+      fd = fields;
+    } else {
+      if (dalloc(h, &staged, (size_t)(per * n_steps)) != AFQMC_OK) return AFQMC_ERR_NOMEM;
+      cudaError_t e = cudaMemcpyAsync(staged, fields, sizeof(double) * per * n_steps,
+                                      cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) { cudaFree(staged); return cuda_fail(h, "staging fields", e); }
+      fd = staged;
+    }
+  }
+  afqmc_status st = AFQMC_OK;
+  for (int t = 0; t < n_steps && st == AFQMC_OK; ++t) st = step_launch(h, fd ? fd + per * t : nullptr, s);
+  if (staged) {
+    cudaStreamSynchronize(s);
+    cudaFree(staged);
+  }
+  if (st == AFQMC_OK) h->step += (uint64_t)n_steps;
+  return st;
+}
+
+afqmc_status afqmc_orthonormalise(afqmc_handle h, cudaStream_t s) {
+  if (!h) return AFQMC_ERR_ARG;
+  return ortho_launch(h, s);
+}
+
+afqmc_status afqmc_energy(afqmc_handle h, double* e_local, double* e_mixed, double* w_sum,
+                          cudaStream_t s) {
+  if (!h) return AFQMC_ERR_ARG;
+  AFQ_CK(afq::launch_energy(*h, s));
+  if (e_local) AFQ_CK(cudaMemcpyAsync(e_local, h->eloc, sizeof(double) * 2 * h->Nw, cudaMemcpyDefault, s));
+  if (e_mixed || w_sum) {
+    AFQ_CK(afq::launch_mixed_sum(*h, h->esum, nullptr, 0, s));
+    std::vector<double> es(4 * (size_t)h->R);
+    AFQ_CK(cudaMemcpyAsync(es.data(), h->esum, sizeof(double) * es.size(), cudaMemcpyDeviceToHost, s));
+    AFQ_CK(cudaStreamSynchronize(s));
+    std::vector<double> em(h->R), ws(h->R);
+    for (int r = 0; r < h->R; ++r) {
+      const double nr = es[4 * r], ni = es[4 * r + 1], dr = es[4 * r + 2], di = es[4 * r + 3];
+      const double d2 = dr * dr + di * di;
+      em[r] = d2 > 0 ? (nr * dr + ni * di) / d2 : NAN;
+      ws[r] = dr;
+    }
+    if (e_mixed) AFQ_CK(cudaMemcpyAsync(e_mixed, em.data(), sizeof(double) * h->R, cudaMemcpyDefault, s));
+    if (w_sum) AFQ_CK(cudaMemcpyAsync(w_sum, ws.data(), sizeof(double) * h->R, cudaMemcpyDefault, s));
+    AFQ_CK(cudaStreamSynchronize(s));
+  } else if (e_local && !is_device_ptr(e_local)) {
+    AFQ_CK(cudaStreamSynchronize(s));
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, cudaStream_t s) {
+  if (!h || !ms || reps < 1 || which < 0 || which > 3) return AFQMC_ERR_ARG;
+  const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
+  const int64_t NM = (int64_t)N * M;
+  cudaEvent_t e0, e1;
+  AFQ_CK(cudaEventCreate(&e0));
+  AFQ_CK(cudaEventCreate(&e1));
+  auto one = [&]() -> cudaError_t {
+    switch (which) {
+      case AFQMC_K_VHS:
+        return afq::gemm_tn_f64((int)h->P, 2 * Nw, X, 1.0, h->Lt, X, 0, h->U, X, 0, 0.0, h->Avhs,
+                                h->P, 0, 1, s, afq::GEMM_VHS);
+      case AFQMC_K_FORCE_BIAS:
+        return afq::gemm_tn_f64(X, 2 * Nw, (int)NM, 1.0, h->Ltil, NM, 0, h->theta, NM, 0, 0.0,
+                                h->rhobar, X, 0, 1, s, afq::GEMM_FORCE_BIAS);
+      case AFQMC_K_TAYLOR:
+        return afq::launch_taylor(*h, h->phi2, s);
+      default:
+        return afq::launch_energy(*h, s);
+    }
+  };
+  cudaError_t e = one();  // warm
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = one();
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(h, "afqmc_time_kernel", e);
+  *ms = (double)t / reps;
+  return AFQMC_OK;
+}
+
+}  // extern "C"

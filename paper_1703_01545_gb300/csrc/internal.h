@@ -1,0 +1,92 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <cuda_runtime.h>
+#include "../../include/afqmc.h"
+
+namespace afq {
+
+// Packed upper triangle (i <= j) of a symmetric M x M matrix, row-major:
+// idx(i, j) = i*M - i*(i-1)/2 + (j - i).
+inline int64_t packed_size(int M) { return (int64_t)M * (M + 1) / 2; }
+
+struct Workspace;
+
+struct Ctx {
+  int M = 0, X = 0, n_up = 0, n_dn = 0, N = 0, Nw = 0, R = 1;
+  int64_t P = 0;              // packed size of a symmetric M x M matrix
+  afqmc_options opt{};
+  double sqrt_dt = 0, c_mf = 0, e_trial = 0;
+  uint64_t step = 0;          // host mirror of the device step counter
+  int device = 0;
+  // constants (device)
+  double* h1 = nullptr;       // [M][M]
+  double* L = nullptr;        // [X][M][M]
+  double* Lt = nullptr;       // [P][X]  packed upper triangle of every L_g, g fastest
+  double* Ltil = nullptr;     // [X][N][M]  rows of Psi_s^T L_g
+  double* htil = nullptr;     // [N][M]     rows of Psi_s^T h1
+  double* psi = nullptr;      // [N][M]     trial columns
+  double* expK = nullptr;     // [M][M]     exp(-dt K / 2)
+  double* rho_mf = nullptr;   // [X]        <rho_g>_T
+  // walker state (device), planar complex
+  double* phi = nullptr;      // [2][Nw][N][M]
+  double* phi2 = nullptr;     // [2][Nw][N][M]  propagation scratch
+  double* theta = nullptr;    // [2][Nw][N][M]  Theta = Phi O^{-1}, then scratch within a step
+  double* logO = nullptr;     // [2][Nw]
+  double* w = nullptr;        // [2][Nw]
+  int* alive = nullptr;       // [Nw]
+  // per-step scratch
+  double* rhobar = nullptr;   // [2][Nw][X]
+  double* U = nullptr;        // [2][Nw][X]   sqrt(dt)-scaled coefficients of A = sum_g (U_re + i U_im)_g L_g
+  double* Avhs = nullptr;     // [2][Nw][P]   packed A of every walker
+  double* aux = nullptr;      // [Nw][4]      log s (re, im), x.xbar - xbar.xbar/2 (re, im)
+  double* eloc = nullptr;     // [2][Nw]
+  double* esum = nullptr;     // [R][4]       sum w E_L (re, im), sum w (re, im)
+  unsigned long long* d_step = nullptr;  // device step counter t of the field stream
+  int* d_flags = nullptr;     // [4] error counters: [0] singular overlaps
+  // pair-run graph cache (owned; see pair.cu)
+  void* pair_cache = nullptr;
+  uint64_t uid = 0;           // unique per handle, so a cached graph never outlives its partner
+  std::string err;
+};
+void destroy_pair_cache(Ctx* h);
+
+// ---- kernel launchers (implemented in the .cu files) ----
+// C[z][n*ldc + m] = alpha * sum_k A[z][m*lda + k] * B[z][n*ldb + k] + beta * C[...]
+enum GemmUse { GEMM_GENERIC = 0, GEMM_FORCE_BIAS = 1, GEMM_VHS = 2, GEMM_ONEBODY = 3 };
+cudaError_t gemm_tn_f64(int Md, int Nd, int Kd, double alpha, const double* A, int64_t lda,
+                        int64_t sA, const double* B, int64_t ldb, int64_t sB, double beta,
+                        double* C, int64_t ldc, int64_t sC, int batch, cudaStream_t s,
+                        GemmUse use = GEMM_GENERIC);
+
+enum OverlapMode { OV_REFRESH = 0, OV_UPDATE = 1 };
+cudaError_t prepare_kernels(const Ctx& c);
+cudaError_t launch_overlap(const Ctx& c, const double* src, int mode, cudaStream_t s,
+                           int n_walkers = -1);
+cudaError_t launch_fields(const Ctx& c, const double* fields, cudaStream_t s);
+cudaError_t launch_taylor(const Ctx& c, double* phi_io, cudaStream_t s);
+cudaError_t launch_mgs(const Ctx& c, cudaStream_t s);
+cudaError_t launch_energy(const Ctx& c, cudaStream_t s, int n_walkers = -1);
+cudaError_t launch_mixed_sum(const Ctx& c, double* out, const int* slot, int slot_stride,
+                             cudaStream_t s);
+cudaError_t launch_step_advance(const Ctx& c, cudaStream_t s);
+
+// setup helpers
+cudaError_t launch_transpose(const double* in, double* out, int rows, int cols, cudaStream_t s);
+cudaError_t launch_pack_Lt(const double* L, double* Lt, int M, int X, cudaStream_t s);
+cudaError_t launch_rho_mf(const double* Ltil, const double* psi, double* rho, int X, int NM,
+                          cudaStream_t s);
+cudaError_t launch_build_K(const double* h1, const double* Q, const double* L, const double* rho,
+                           double* K, int M, int X, double scale, cudaStream_t s);
+cudaError_t launch_add_identity(double* A, int M, double a, cudaStream_t s);
+cudaError_t launch_norm1(const double* A, int M, double* out, cudaStream_t s);
+cudaError_t launch_permute_L(const double* L, double* Lp, int M, int X, cudaStream_t s);
+cudaError_t launch_broadcast_walkers(const double* psi, double* phi, int Nw, int NM,
+                                     cudaStream_t s);
+cudaError_t launch_init_weights(double* w, int* alive, const double* w_in, int Nw,
+                                cudaStream_t s);
+cudaError_t launch_phi_layout(const double* in, double* out, int Nw, int M, int N, int to_internal,
+                              cudaStream_t s);
+
+}  // namespace afq

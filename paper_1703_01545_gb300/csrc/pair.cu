@@ -1,0 +1,179 @@
+// Correlated-sampling pair run (Sec. II.B): both systems advance in lockstep on the
+// shared field stream.  One measurement block (energy_every steps of A and B on two
+// forked capture streams, the Gram-Schmidt passes, both energies and their per-repeat
+// sums) is captured once as a CUDA graph and replayed n_meas times; the only host
+// crossing is one copy of the energy series at the end.
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+struct afqmc_ctx : afq::Ctx {};
+
+namespace afq {
+afqmc_status pair_step(Ctx* h, cudaStream_t s);
+afqmc_status pair_ortho(Ctx* h, cudaStream_t s);
+cudaError_t launch_meas_advance(int* meas, cudaStream_t s);
+}  // namespace afq
+
+namespace {
+
+// Captured measurement block of one (A, B, energy_every, mgs_every) pair, kept in A.
+struct Res {
+  uint64_t partner_uid = 0;
+  int ee = 0, me = 0, capacity = 0;
+  cudaStream_t cs = nullptr, cs2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, ready = nullptr, done = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double* series = nullptr;
+  int* meas = nullptr;
+  ~Res() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (series) cudaFree(series);
+    if (meas) cudaFree(meas);
+    for (cudaEvent_t e : {fork, join, ready, done})
+      if (e) cudaEventDestroy(e);
+    if (cs) cudaStreamDestroy(cs);
+    if (cs2) cudaStreamDestroy(cs2);
+  }
+};
+
+afqmc_status fail(afqmc_ctx* A, afqmc_ctx* B, afqmc_status code, const std::string& msg) {
+  if (A) A->err = msg;
+  if (B) B->err = msg;
+  return code;
+}
+
+}  // namespace
+
+namespace afq {
+void destroy_pair_cache(Ctx* h) {
+  if (h->pair_cache) {
+    delete static_cast<Res*>(h->pair_cache);
+    h->pair_cache = nullptr;
+  }
+}
+}  // namespace afq
+
+extern "C" afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n_steps,
+                                           int energy_every, int mgs_every, double tau_eq,
+                                           double* e_series, double* dE_mean, double* dE_sigma,
+                                           double* tau_at_min, cudaStream_t s) {
+  if (!A || !B || A == B) return fail(A, B, AFQMC_ERR_ARG, "need two distinct handles");
+  if (A->opt.seed != B->opt.seed || A->Nw != B->Nw || A->R != B->R || A->opt.dt != B->opt.dt ||
+      A->opt.mode != B->opt.mode || A->opt.walker_offset != B->opt.walker_offset)
+    return fail(A, B, AFQMC_ERR_ARG, "pair handles differ in seed, walkers, repeats, dt, mode or walker offset");
+  if (A->step != B->step) return fail(A, B, AFQMC_ERR_STATE, "pair handles are at different steps");
+  if (energy_every < 1 || mgs_every < 1 || energy_every % mgs_every != 0 || n_steps < 0 ||
+      n_steps % energy_every != 0)
+    return fail(A, B, AFQMC_ERR_ARG, "need energy_every % mgs_every == 0 and n_steps % energy_every == 0");
+  if (A->step % (uint64_t)energy_every != 0)
+    return fail(A, B, AFQMC_ERR_STATE, "step counter is not a multiple of energy_every");
+  const int n_meas = n_steps / energy_every, R = A->R;
+  const int stride = 8 * R;  // per measurement: [A: R x 4][B: R x 4]
+#define AFQ_PCK(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(A, B, AFQMC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+  Res* r = static_cast<Res*>(A->pair_cache);
+  if (n_meas > 0 && (!r || r->partner_uid != B->uid || r->ee != energy_every ||
+                     r->me != mgs_every || r->capacity < n_meas)) {
+    afq::destroy_pair_cache(A);
+    r = new Res();
+    A->pair_cache = r;
+    r->partner_uid = B->uid;
+    r->ee = energy_every;
+    r->me = mgs_every;
+    r->capacity = n_meas;
+    AFQ_PCK(cudaMalloc(&r->series, sizeof(double) * (size_t)n_meas * stride));
+    AFQ_PCK(cudaMalloc(&r->meas, sizeof(int)));
+    AFQ_PCK(cudaStreamCreateWithFlags(&r->cs, cudaStreamNonBlocking));
+    AFQ_PCK(cudaStreamCreateWithFlags(&r->cs2, cudaStreamNonBlocking));
+    AFQ_PCK(cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming));
+    AFQ_PCK(cudaEventCreateWithFlags(&r->join, cudaEventDisableTiming));
+    AFQ_PCK(cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming));
+    AFQ_PCK(cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming));
+
+    AFQ_PCK(cudaStreamBeginCapture(r->cs, cudaStreamCaptureModeRelaxed));
+    afqmc_status st = AFQMC_OK;
+    cudaError_t ce = cudaEventRecord(r->fork, r->cs);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(r->cs2, r->fork, 0);
+    for (int j = 0; j < energy_every && st == AFQMC_OK && ce == cudaSuccess; ++j) {
+      st = afq::pair_step(A, r->cs);
+      if (st == AFQMC_OK) st = afq::pair_step(B, r->cs2);
+      if (st == AFQMC_OK && (j + 1) % mgs_every == 0) {
+        st = afq::pair_ortho(A, r->cs);
+        if (st == AFQMC_OK) st = afq::pair_ortho(B, r->cs2);
+      }
+    }
+    if (st == AFQMC_OK && ce == cudaSuccess) {
+      ce = afq::launch_energy(*A, r->cs);
+      if (ce == cudaSuccess) ce = afq::launch_mixed_sum(*A, r->series, r->meas, stride, r->cs);
+      if (ce == cudaSuccess) ce = afq::launch_energy(*B, r->cs2);
+      if (ce == cudaSuccess) ce = afq::launch_mixed_sum(*B, r->series + 4 * R, r->meas, stride, r->cs2);
+      if (ce == cudaSuccess) ce = cudaEventRecord(r->join, r->cs2);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(r->cs, r->join, 0);
+      if (ce == cudaSuccess) ce = afq::launch_meas_advance(r->meas, r->cs);
+    }
+    cudaError_t ce2 = cudaStreamEndCapture(r->cs, &r->graph);
+    if (st != AFQMC_OK || ce != cudaSuccess || ce2 != cudaSuccess) {
+      afq::destroy_pair_cache(A);
+      if (st != AFQMC_OK) return st;
+      return fail(A, B, AFQMC_ERR_CUDA, std::string("graph capture: ") +
+                                            cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+    }
+    AFQ_PCK(cudaGraphInstantiate(&r->exec, r->graph, 0));
+  }
+  cudaStream_t cs = s;
+  if (n_meas > 0) {
+    cs = r->cs;
+    AFQ_PCK(cudaEventRecord(r->ready, s));
+    AFQ_PCK(cudaStreamWaitEvent(r->cs, r->ready, 0));
+    AFQ_PCK(cudaMemsetAsync(r->meas, 0, sizeof(int), r->cs));
+    for (int m = 0; m < n_meas; ++m) AFQ_PCK(cudaGraphLaunch(r->exec, r->cs));
+    A->step += (uint64_t)n_steps;
+    B->step += (uint64_t)n_steps;
+  }
+  std::vector<double> ser((size_t)n_meas * stride);
+  std::vector<int> alA(A->Nw), alB(B->Nw);
+  if (n_meas > 0)
+    AFQ_PCK(cudaMemcpyAsync(ser.data(), r->series, sizeof(double) * ser.size(), cudaMemcpyDeviceToHost, cs));
+  AFQ_PCK(cudaMemcpyAsync(alA.data(), A->alive, sizeof(int) * A->Nw, cudaMemcpyDeviceToHost, cs));
+  AFQ_PCK(cudaMemcpyAsync(alB.data(), B->alive, sizeof(int) * B->Nw, cudaMemcpyDeviceToHost, cs));
+  if (n_meas > 0) {
+    AFQ_PCK(cudaEventRecord(r->done, cs));
+    AFQ_PCK(cudaStreamWaitEvent(s, r->done, 0));   // the caller's stream sees the whole run
+  }
+  AFQ_PCK(cudaStreamSynchronize(cs));
+  // E_r = Re(sum w E_L / sum w) per system, measurement and repeat
+  std::vector<double> E((size_t)n_meas * 2 * R), dE((size_t)n_meas * R), taus(n_meas);
+  for (int m = 0; m < n_meas; ++m) {
+    taus[m] = (double)(m + 1) * energy_every * A->opt.dt;
+    for (int sy = 0; sy < 2; ++sy)
+      for (int q = 0; q < R; ++q) {
+        const double* v = ser.data() + (size_t)m * stride + sy * 4 * R + 4 * q;
+        const double d2 = v[2] * v[2] + v[3] * v[3];
+        E[((size_t)m * 2 + sy) * R + q] = d2 > 0 ? (v[0] * v[2] + v[1] * v[3]) / d2 : NAN;
+      }
+    for (int q = 0; q < R; ++q)
+      dE[(size_t)m * R + q] = E[((size_t)m * 2 + 1) * R + q] - E[((size_t)m * 2) * R + q];
+  }
+  double est[3] = {NAN, NAN, NAN};
+  if (n_meas > 0) afqmc_delta_E_stats(dE.data(), taus.data(), n_meas, R, tau_eq, nullptr, nullptr, est);
+  if (e_series && n_meas > 0)
+    AFQ_PCK(cudaMemcpy(e_series, E.data(), sizeof(double) * E.size(), cudaMemcpyDefault));
+  if (dE_mean) AFQ_PCK(cudaMemcpy(dE_mean, &est[0], sizeof(double), cudaMemcpyDefault));
+  if (dE_sigma) AFQ_PCK(cudaMemcpy(dE_sigma, &est[1], sizeof(double), cudaMemcpyDefault));
+  if (tau_at_min) AFQ_PCK(cudaMemcpy(tau_at_min, &est[2], sizeof(double), cudaMemcpyDefault));
+#undef AFQ_PCK
+  int na = 0, nb = 0;
+  for (int a : alA) na += a != 0;
+  for (int b : alB) nb += b != 0;
+  if (na == 0 || nb == 0) return fail(A, B, AFQMC_ERR_NUMERIC, "every walker of a system is dead");
+  return AFQMC_OK;
+}
