@@ -211,6 +211,30 @@ enum { AFQMC_K_VHS = 0, AFQMC_K_FORCE_BIAS = 1, AFQMC_K_TAYLOR = 2, AFQMC_K_EXCH
 afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms,
                                cudaStream_t stream);
 
+/*
+ * afqmc_local_energy_static -- local energies E_L of the walkers phi, like
+ * afqmc_energy's e_local, for callers that cannot allocate device memory (code
+ * inside another framework's memory pool or under a fixed memory budget, or an
+ * embedding that only hands over existing device buffers).  The paper has no
+ * counterpart: this is a deployment variant of the energy evaluation.
+ * It needs no handle and allocates nothing: its intermediates live in one 32 MiB
+ * static device array that every GPU loading this library holds until the process
+ * exits; walkers are processed in chunks that fit it.  All pointers must be device
+ * memory of the current device (ERR_ARG otherwise):
+ *   h1 [M][M], L [X][M][M], trial [M][N] as in afqmc_setup; phi [2][Nw][M][N];
+ *   e_local [2][Nw] (real parts, then imaginary parts).
+ * Problems whose fixed part (X*N*M + 2*N*M doubles plus one walker) exceeds the
+ * array are rejected with ERR_ARG before anything is launched.
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.
+ * Asynchronous on `stream`.  Every call shares the one array, so calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race; serialise
+ * them.  Errors: ARG, CUDA.
+ */
+afqmc_status afqmc_local_energy_static(const double* h1, const double* L, const double* trial,
+                                       const double* phi, int M, int X, int n_up, int n_dn,
+                                       int n_walkers, double* e_local, cudaStream_t stream);
+
 /* Flyvbjerg-Petersen reblocking error of the mean of series[n] (host only): the
  * largest block-level estimate among levels with >= 16 blocks. */
 double afqmc_reblock_error(const double* series, int n);

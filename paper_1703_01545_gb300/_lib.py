@@ -48,6 +48,9 @@ SIGNATURES = {
     "afqmc_delta_E_stats": (ctypes.c_int, [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            VP, VP, VP]),
     "afqmc_reblock_error": (ctypes.c_double, [VP, ctypes.c_int]),
+    "afqmc_local_energy_static": (ctypes.c_int, [VP, VP, VP, VP, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, VP,
+                                                 VP]),
     "afqmc_time_kernel": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_double), VP]),
 }
