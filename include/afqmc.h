@@ -235,6 +235,17 @@ afqmc_status afqmc_local_energy_static(const double* h1, const double* L, const 
                                        const double* phi, int M, int X, int n_up, int n_dn,
                                        int n_walkers, double* e_local, cudaStream_t stream);
 
+/*
+ * afqmc_test_gemm -- testing aid (no counterpart in the paper): one of the library's
+ * contraction kernels on given operands, C[n][m] = alpha sum_k A[m][k] B[n][k] with
+ * A [Md][K], B [Nd][K] (row-major float64, host or device) and C [Nd][Md].
+ * impl 0: FP64 kernel; impl 1: split-BF16 tensor-core kernel (hi/lo operands, three MMAs
+ * per product, FP32 accumulation).  Allocates temporary device memory; synchronises.
+ * Errors: ARG, CUDA, TIMEOUT (a bounded wait inside the tensor-core kernel expired).
+ */
+afqmc_status afqmc_test_gemm(int impl, int Md, int Nd, int K, const double* A, const double* B,
+                             double alpha, double* C, cudaStream_t stream);
+
 /* Flyvbjerg-Petersen reblocking error of the mean of series[n] (host only): the
  * largest block-level estimate among levels with >= 16 blocks. */
 double afqmc_reblock_error(const double* series, int n);

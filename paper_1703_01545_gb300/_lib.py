@@ -51,6 +51,8 @@ SIGNATURES = {
     "afqmc_local_energy_static": (ctypes.c_int, [VP, VP, VP, VP, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, VP,
                                                  VP]),
+    "afqmc_test_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, VP,
+                                       VP, ctypes.c_double, VP, VP]),
     "afqmc_time_kernel": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_double), VP]),
 }

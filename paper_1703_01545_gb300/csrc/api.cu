@@ -449,4 +449,67 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
   return AFQMC_OK;
 }
 
+afqmc_status afqmc_test_gemm(int impl, int Md, int Nd, int K, const double* A, const double* B,
+                             double alpha, double* C, cudaStream_t s) {
+  if (Md < 1 || Nd < 1 || K < 1 || !A || !B || !C || impl < 0 || impl > 1) return AFQMC_ERR_ARG;
+  Ctx tmp;
+  Ctx* h = &tmp;
+  double *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  float* fC = nullptr;
+  __nv_bfloat16 *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+  int* err = nullptr;
+  const int Kp = afq::pad64(K);
+  auto cleanup = [&]() {
+    for (void* p : {(void*)dA, (void*)dB, (void*)dC, (void*)fC, (void*)ah, (void*)al, (void*)bh,
+                    (void*)bl, (void*)err})
+      if (p) cudaFree(p);
+  };
+  afqmc_status st = AFQMC_OK;
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((e = cudaMalloc(&dA, sizeof(double) * Md * (size_t)K)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&dB, sizeof(double) * Nd * (size_t)K)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&dC, sizeof(double) * Md * (size_t)Nd)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&err, sizeof(int))) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(err, 0, sizeof(int), s)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(dA, A, sizeof(double) * Md * (size_t)K, cudaMemcpyDefault, s)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(dB, B, sizeof(double) * Nd * (size_t)K, cudaMemcpyDefault, s)) != cudaSuccess) break;
+    if (impl == 0) {
+      if ((e = afq::gemm_tn_f64(Md, Nd, K, alpha, dA, K, 0, dB, K, 0, 0.0, dC, Md, 0, 1, s)) != cudaSuccess) break;
+    } else {
+      const int Mp = afq::tc_pad_rows(Md), Np = afq::tc_pad_rows(Nd);
+      if ((e = cudaMalloc(&fC, sizeof(float) * Md * (size_t)Nd)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&ah, 2 * (size_t)Mp * Kp)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&al, 2 * (size_t)Mp * Kp)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&bh, 2 * (size_t)Np * Kp)) != cudaSuccess) break;
+      if ((e = cudaMalloc(&bl, 2 * (size_t)Np * Kp)) != cudaSuccess) break;
+      for (void* p : {(void*)ah, (void*)al})
+        if ((e = cudaMemsetAsync(p, 0, 2 * (size_t)Mp * Kp, s)) != cudaSuccess) break;
+      for (void* p : {(void*)bh, (void*)bl})
+        if ((e = cudaMemsetAsync(p, 0, 2 * (size_t)Np * Kp, s)) != cudaSuccess) break;
+      if (e != cudaSuccess) break;
+      if ((e = afq::split_bf16(dA, K, Md, K, Kp, ah, al, s)) != cudaSuccess) break;
+      if ((e = afq::split_bf16(dB, K, Nd, K, Kp, bh, bl, s)) != cudaSuccess) break;
+      afq::TcOperand oa, ob;
+      if ((e = afq::tc_make_operand(oa, ah, al, Mp, Kp, 128)) != cudaSuccess) break;
+      if ((e = afq::tc_make_operand(ob, bh, bl, Np, Kp, afq::tc_bn())) != cudaSuccess) break;
+      if ((e = afq::gemm_bf16x3(oa, ob, Md, Nd, (float)alpha, fC, Md, err, s)) != cudaSuccess) break;
+      std::vector<float> hf((size_t)Md * Nd);
+      if ((e = cudaMemcpyAsync(hf.data(), fC, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+      int herr = 0;
+      if ((e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+      if (herr) { st = AFQMC_ERR_TIMEOUT; break; }
+      std::vector<double> hd(hf.begin(), hf.end());
+      if ((e = cudaMemcpy(C, hd.data(), sizeof(double) * hd.size(), cudaMemcpyDefault)) != cudaSuccess) break;
+      break;
+    }
+    if ((e = cudaMemcpyAsync(C, dC, sizeof(double) * Md * (size_t)Nd, cudaMemcpyDefault, s)) != cudaSuccess) break;
+    e = cudaStreamSynchronize(s);
+  } while (0);
+  cleanup();
+  if (st != AFQMC_OK) return st;
+  return e == cudaSuccess ? AFQMC_OK : AFQMC_ERR_CUDA;
+}
+
 }  // extern "C"

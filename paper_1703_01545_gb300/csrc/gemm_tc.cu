@@ -1,0 +1,340 @@
+// Split-BF16 ("BF16x3") tensor-core GEMM for the Cholesky contractions on sm_103a.
+//
+//   C[n*ldc + m] = alpha * sum_k (Ahi + Alo)[m][k] (Bhi + Blo)[n][k]     (lo*lo dropped)
+//
+// A float64 operand x is carried as x ~ hi + lo with hi = bf16(x), lo = bf16(x - hi), so
+// each product needs three BF16 MMAs (hi*hi, hi*lo, lo*hi) accumulated in FP32 in tensor
+// memory; the product error is about 2^-17 relative instead of BF16's 2^-9.
+//
+// Structure (one 128 x BN output tile per CTA, 4 warps):
+//   warp 0 / lane 0  TMA producer: 128B-swizzled boxes of Ahi, Alo, Bhi, Blo per 64-wide
+//                    k slice into a STAGES-deep ring, completion on a "full" mbarrier.
+//   warp 1 / lane 0  MMA issuer: per k slice 4 x 3 tcgen05.mma (K = 16 each) into one TMEM
+//                    accumulator, then tcgen05.commit frees the stage ("empty" mbarrier);
+//                    a final commit signals "done".
+//   all 4 warps      epilogue: tcgen05.ld of their 32 TMEM lanes (= 32 output rows m),
+//                    scaled by alpha, stored so that a warp writes 32 consecutive m.
+// Every mbarrier wait is bounded; on expiry the kernel sets *err, drains what it issued,
+// frees its TMEM and returns.  Operand rows are K-major with K padded to a multiple of 64
+// (zero-filled), so every TMA box starts on a 128-byte boundary.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "internal.h"
+
+namespace afq {
+namespace {
+
+constexpr int BM = 128, BK = 64, NTHREADS = 128;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait here
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the phase with the given parity; false (and *err set) on expiry.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 255u) == 255u && global_ns() - t0 > kWaitLimitNs) break;
+  }
+  atomicOr(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile written by TMA with 128-byte
+// swizzle (rows of 64 bf16, 8-row core groups 1024 bytes apart).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);      // start address
+  d |= (uint64_t)1u << 16;                       // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;             // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1u << 46;                       // descriptor version
+  d |= (uint64_t)2u << 61;                       // layout: 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B, FP32 D, both K-major, M = 128, N = BN.
+template <int BN>
+__device__ __forceinline__ uint32_t idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+        "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+        "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN, int STAGES>
+struct TcLayout {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int BAR_OFFSET = STAGES * STAGE_BYTES;
+  static constexpr int SMEM_BYTES = BAR_OFFSET + 256 + 1024;  // barriers + TMEM slot + alignment
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm_bf16x3_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                     int Md, int Nd, int nkb, float alpha, float* __restrict__ C, int64_t ldc,
+                     int* err) {
+  using Lay = TcLayout<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lay::BAR_OFFSET);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES),
+                 done = smem_u32(bars + 2 * STAGES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, use = kb / STAGES;
+      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (use - 1) & 1, err)) break;
+      const uint32_t st = smem_u32(smem + s * Lay::STAGE_BYTES);
+      const uint32_t fb = full0 + 8 * s;
+      mbar_expect_tx(fb, Lay::STAGE_BYTES);
+      tma_load_2d(st, &tmAh, fb, kb * BK, m0);
+      tma_load_2d(st + Lay::A_BYTES, &tmAl, fb, kb * BK, m0);
+      tma_load_2d(st + 2 * Lay::A_BYTES, &tmBh, fb, kb * BK, n0);
+      tma_load_2d(st + 2 * Lay::A_BYTES + Lay::B_BYTES, &tmBl, fb, kb * BK, n0);
+      issued = kb + 1;
+    }
+    // drain: every issued stage must have landed before the CTA may exit
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+      mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, err);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    const uint32_t idesc = idesc_bf16<BN>();
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, use = kb / STAGES;
+      if (!mbar_wait(full0 + 8 * s, use & 1, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = smem_u32(smem + s * Lay::STAGE_BYTES);
+      const uint64_t ah = sw128_desc(st), al = sw128_desc(st + Lay::A_BYTES);
+      const uint64_t bh = sw128_desc(st + 2 * Lay::A_BYTES);
+      const uint64_t bl = sw128_desc(st + 2 * Lay::A_BYTES + Lay::B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t dk = (uint64_t)((kk * 32) >> 4);  // advance 16 bf16 inside the swizzle atom
+        mma_bf16(tmem, ah + dk, bh + dk, idesc, (kb | kk) != 0);
+        mma_bf16(tmem, ah + dk, bl + dk, idesc, 1u);
+        mma_bf16(tmem, al + dk, bh + dk, idesc, 1u);
+      }
+      mma_commit(empty0 + 8 * s);
+    }
+    mma_commit(done);  // also on an early exit: arrives once the issued MMAs are complete
+  }
+  __syncwarp();
+
+  // ---- epilogue: TMEM lanes 32*warp .. 32*warp+31 hold output rows m ----
+  const bool ok = mbar_wait(done, 0, err);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncwarp();
+  const int m = m0 + warp * 32 + lane;
+  if (__all_sync(0xffffffffu, ok && *(volatile int*)err == 0)) {
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (m < Md) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < Nd) C[(int64_t)n * ldc + m] = alpha * __uint_as_float(v[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+                 : "memory");
+}
+
+// ---- operand preparation ----
+
+// split rows of a float64 matrix into bf16 hi/lo, K padded with zeros:
+// out_{hi,lo}[r][k] for k < Kp; in[r*ld_in + k] for k < K.
+__global__ void k_split_bf16(const double* __restrict__ in, int64_t ld_in, int rows, int K, int Kp,
+                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t total = (int64_t)rows * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / Kp;
+    const int k = (int)(e % Kp);
+    const double x = k < K ? in[r * ld_in + k] : 0.0;
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+template <int BN, int STAGES>
+cudaError_t launch_tc(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha, float* C,
+                      int64_t ldc, int* err, cudaStream_t s) {
+  using Lay = TcLayout<BN, STAGES>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x3_tc<BN, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((Md + BM - 1) / BM, (Nd + BN - 1) / BN);
+  k_gemm_bf16x3_tc<BN, STAGES><<<grid, NTHREADS, Lay::SMEM_BYTES, s>>>(
+      A.map_hi, A.map_lo, B.map_hi, B.map_lo, Md, Nd, A.Kp / BK, alpha, C, ldc, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_make_operand(TcOperand& op, __nv_bfloat16* hi, __nv_bfloat16* lo, int rows, int Kp,
+                            int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  // rows must be whole boxes (buffers are padded), so no box ever reaches outside the tensor
+  if (Kp % BK != 0 || rows < 1 || rows % box_rows != 0) return cudaErrorInvalidValue;
+  op.hi = hi;
+  op.lo = lo;
+  op.rows = rows;
+  op.Kp = Kp;
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  for (int q = 0; q < 2; ++q) {
+    CUresult r = fn(q == 0 ? &op.map_hi : &op.map_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    q == 0 ? (void*)hi : (void*)lo, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t split_bf16(const double* in, int64_t ld_in, int rows, int K, int Kp, __nv_bfloat16* hi,
+                       __nv_bfloat16* lo, cudaStream_t s) {
+  const int64_t total = (int64_t)rows * Kp;
+  int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 64);
+  if (grid < 1) grid = 1;
+  k_split_bf16<<<grid, 256, 0, s>>>(in, ld_in, rows, K, Kp, hi, lo);
+  return cudaGetLastError();
+}
+
+// A operand boxes are BM = 128 rows; B operand boxes are tc_bn() rows.  Operand buffers
+// hold pad_rows(rows) rows (zero-filled beyond `rows`).
+int tc_bn() { return 128; }
+int tc_pad_rows(int rows) { return (rows + 127) / 128 * 128; }
+
+cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,
+                        float* C, int64_t ldc, int* err, cudaStream_t s) {
+  if (A.Kp != B.Kp) return cudaErrorInvalidValue;
+  if (Md <= 0 || Nd <= 0) return cudaSuccess;
+  return launch_tc<128, 3>(A, B, Md, Nd, alpha, C, ldc, err, s);
+}
+
+}  // namespace afq

@@ -2,6 +2,8 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include "../../include/afqmc.h"
 
@@ -59,6 +61,26 @@ cudaError_t gemm_tn_f64(int Md, int Nd, int Kd, double alpha, const double* A, i
                         int64_t sA, const double* B, int64_t ldb, int64_t sB, double beta,
                         double* C, int64_t ldc, int64_t sC, int batch, cudaStream_t s,
                         GemmUse use = GEMM_GENERIC);
+
+// ---- split-BF16 tensor-core GEMM (gemm_tc.cu) ----
+// A K-major operand split into bf16 hi/lo rows of Kp (multiple of 64) elements, with
+// its two TMA descriptors (128-row boxes, 128-byte swizzle).
+struct TcOperand {
+  CUtensorMap map_hi, map_lo;
+  __nv_bfloat16* hi = nullptr;
+  __nv_bfloat16* lo = nullptr;
+  int rows = 0, Kp = 0;
+};
+cudaError_t tc_make_operand(TcOperand& op, __nv_bfloat16* hi, __nv_bfloat16* lo, int rows, int Kp,
+                            int box_rows);
+cudaError_t split_bf16(const double* in, int64_t ld_in, int rows, int K, int Kp, __nv_bfloat16* hi,
+                       __nv_bfloat16* lo, cudaStream_t s);
+int tc_bn();
+int tc_pad_rows(int rows);
+// C[n*ldc + m] = alpha * sum_k A[m][k] B[n][k] with both operands split (3 MMAs per product)
+cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,
+                        float* C, int64_t ldc, int* err, cudaStream_t s);
+inline int pad64(int k) { return (k + 63) / 64 * 64; }
 
 enum OverlapMode { OV_REFRESH = 0, OV_UPDATE = 1 };
 cudaError_t prepare_kernels(const Ctx& c);
