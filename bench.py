@@ -39,14 +39,25 @@ WORKLOADS = {
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (no tcgen05 FP64 kind; DFMA/DMMA pipe)
 
 
+def _measured_bf16_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        return 1900.0   # recipe fallback (burst)
+
+
+BF16_PEAK_TFLOPS = _measured_bf16_peak()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
     ap.add_argument("--coupling", default="moderate", choices=["literal", "moderate"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", choices=["vhs", "force_bias", "taylor", "energy"],
                     help="profiling aid: set up the workload, take one step, then launch only "
@@ -200,7 +211,8 @@ def run_kernel(args, wl):
     afq.build()
     d = systems(wl, args.coupling)[0]
     nw = args.walkers or wl["n_walkers"]
-    A = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=wl["dt"], n_walkers=nw)
+    A = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=wl["dt"], n_walkers=nw,
+                   precision={"fp64": afq.FP64, "bf16x3": afq.BF16X3}[args.precision])
     A.propagate(1)
     which = {"vhs": afq.K_VHS, "force_bias": afq.K_FORCE_BIAS, "taylor": afq.K_TAYLOR,
              "energy": afq.K_EXCHANGE}[args.kernel]
@@ -219,90 +231,121 @@ def run_ours(args, wl, rank, world, local_rank):
     if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     afq.build()
-    dA, dB = systems(wl, args.coupling)
     nw, dt, R = wl["n_walkers"], wl["dt"], wl["repeats"]
-
-    def make(d):
-        return afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt, n_walkers=nw,
-                          seed=1, n_repeats=R, walker_offset=rank * nw)
-
-    A, B = make(dA), make(dB)
     K, W = args.steps, args.warmup
-    afq.pair_delta_E(A, B, W * STEPS_PER_BLOCK, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
-                     raise_on_dead=False)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    time.sleep(0.3)
+    n_steps = K * STEPS_PER_BLOCK
+    tau_eq = 0.25 * n_steps * dt
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    res = afq.pair_delta_E(A, B, K * STEPS_PER_BLOCK, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
-                           raise_on_dead=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    prec_id = {"fp64": afq.FP64, "bf16x3": afq.BF16X3}
+
+    def make(d, prec):
+        return afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt, n_walkers=nw,
+                          seed=1, n_repeats=R, walker_offset=rank * nw, precision=prec_id[prec])
+
+    def timed(prec, coupling, clocks=None):
+        dA, dB = systems(wl, coupling)
+        A, B = make(dA, prec), make(dB, prec)
+        afq.pair_delta_E(A, B, W * STEPS_PER_BLOCK, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
+                         raise_on_dead=False)
+        torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-    walker_steps = world * nw * STEPS_PER_BLOCK * K
-    value = walker_steps / (ms / 1e3)
-    alive = [A.info().n_alive, B.info().n_alive]
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        res = afq.pair_delta_E(A, B, n_steps, STEPS_PER_BLOCK, STEPS_PER_BLOCK, tau_eq=tau_eq,
+                               raise_on_dead=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        alive = [A.info().n_alive, B.info().n_alive]
+        return dict(ms=ms, res=res, alive=alive, clocks=ck, A=A, B=B, dA=dA)
 
-    # dominant kernel: the V_HS contraction, timed alone on this stream with CUDA events
+    main = timed(args.precision, args.coupling, ClockSampler(torch.cuda.current_device()))
+    ms = main["ms"]
+    value = world * nw * n_steps / (ms / 1e3)
+
+    # dominant contraction (V_HS), timed alone on this stream with CUDA events
+    A, dA = main["A"], main["dA"]
     M, X = dA["M"], dA["X"]
-    P = M * (M + 1) // 2
     vhs_ms = afq.afqmc_time_kernel(A.h, afq.K_VHS, 5, stream.cuda_stream)
-    vhs_flops = 2.0 * P * X * (2 * nw)
-    achieved = vhs_flops / (vhs_ms / 1e3) / 1e12
-    tr = traffic_for("gemm_f64.cu", "vhs_gemm_C2")
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                "kernel": "k_gemm_tn_f64 (V_HS, packed symmetric L)",
-                "algorithmic_flops_per_launch": vhs_flops, "ms_per_launch": vhs_ms,
-                "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe); cuBLAS DGEMM measured 1.10"}
-    A.close()
-    B.close()
+    if args.precision == "fp64":
+        P = M * (M + 1) // 2
+        flops = 2.0 * P * X * (2 * nw)
+        achieved = flops / (vhs_ms / 1e3) / 1e12
+        tr = traffic_for("gemm_f64.cu", "vhs_gemm_C2")
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                    "kernel": "k_gemm_f64_vhs (V_HS, packed symmetric L, FP64)",
+                    "algorithmic_flops_per_launch": flops, "ms_per_launch": vhs_ms,
+                    "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe); cuBLAS DGEMM measured 1.10"}
+    else:
+        useful = 2.0 * M * M * X * (2 * nw)
+        flops = 3.0 * useful     # hi*hi + hi*lo + lo*hi BF16 products
+        achieved = flops / (vhs_ms / 1e3) / 1e12
+        peak = BF16_PEAK_TFLOPS
+        tr = traffic_for("gemm_tc.cu", "vhs_tc_C2")
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                    "kernel": "k_gemm_bf16x3_tc (V_HS, split-BF16 tcgen05, full M^2 rows)",
+                    "algorithmic_flops_per_launch": flops, "useful_flops_per_launch": useful,
+                    "ms_per_launch": vhs_ms,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, kernel timed alone)"}
+    main["A"].close()
+    main["B"].close()
+
+    # the FP64 path on the same fields: throughput and sigma_dE * sqrt(GPU seconds)
+    other_prec = "fp64" if args.precision != "fp64" else None
+    comp = {}
+    runs = {args.precision: main}
+    if other_prec and world == 1:
+        o = timed(other_prec, args.coupling)
+        o["A"].close()
+        o["B"].close()
+        runs[other_prec] = o
+    for p_, r_ in runs.items():
+        sig = r_["res"]["dE_sigma"]
+        comp[p_] = {"walker_steps_per_s": world * nw * n_steps / (r_["ms"] / 1e3),
+                    "gpu_s": r_["ms"] / 1e3, "dE_mean_Ha": r_["res"]["dE_mean"],
+                    "dE_sigma_Ha": sig, "sigma_sqrt_gpu_s": sig * (r_["ms"] / 1e3) ** 0.5}
+    if "fp64" in comp and "bf16x3" in comp:
+        comp["gpu_time_ratio_at_equal_sigma"] = (comp["fp64"]["sigma_sqrt_gpu_s"] /
+                                                 comp["bf16x3"]["sigma_sqrt_gpu_s"]) ** 2
+        comp["dE_difference_mHa"] = 1e3 * (comp["bf16x3"]["dE_mean_Ha"] - comp["fp64"]["dE_mean_Ha"])
 
     # end to end through the public API: host inputs -> setup -> pair run -> results on host
+    dA, dB = systems(wl, args.coupling)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    A2, B2 = make(dA), make(dB)
-    res2 = afq.pair_delta_E(A2, B2, K * STEPS_PER_BLOCK, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
-                            raise_on_dead=False)
+    A2, B2 = make(dA, args.precision), make(dB, args.precision)
+    res2 = afq.pair_delta_E(A2, B2, n_steps, STEPS_PER_BLOCK, STEPS_PER_BLOCK, raise_on_dead=False)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     A2.close()
     B2.close()
     h2d = sum(8 * (d["h1"].size + d["L"].size + d["trial"].size) for d in (dA, dB))
     d2h = 8 * res2["E"].size
-    e2e = {"value": world * nw * STEPS_PER_BLOCK * K / e2e_s, "unit": "walker-steps/s",
+    e2e = {"value": world * nw * n_steps / e2e_s, "unit": "walker-steps/s",
            "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
            "note": "setup of both systems from host arrays + pair run + energy series to host"}
 
     other = None
     if world == 1:
         oc = "literal" if args.coupling == "moderate" else "moderate"
-        dA3, dB3 = systems(wl, oc)
-        A3, B3 = make(dA3), make(dB3)
-        afq.pair_delta_E(A3, B3, W * STEPS_PER_BLOCK, 5, 5, raise_on_dead=False)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        afq.pair_delta_E(A3, B3, K * STEPS_PER_BLOCK, 5, 5, raise_on_dead=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        other = {"coupling": oc, "value": nw * STEPS_PER_BLOCK * K / (e0.elapsed_time(e1) / 1e3),
-                 "alive_walkers": [A3.info().n_alive, B3.info().n_alive]}
-        A3.close()
-        B3.close()
+        r3 = timed(args.precision, oc)
+        other = {"coupling": oc, "value": nw * n_steps / (r3["ms"] / 1e3), "alive_walkers": r3["alive"]}
+        r3["A"].close()
+        r3["B"].close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -311,20 +354,25 @@ def run_ours(args, wl, rank, world, local_rank):
         cpu = {"value": n_s * STEPS_PER_BLOCK / ts, "unit": "walker-steps/s", "cores": blas_threads(),
                "kind": "oracle",
                "sample": f"{n_s} pair indices x {STEPS_PER_BLOCK} steps + MGS + energy, both systems"}
-    per_block = 2 * (STEPS_PER_BLOCK * 8 + 2 + 2) + 1
+    # per system and block: 5 steps x (force bias, fields, V_HS, 2 one-body, Taylor, overlap,
+    # step counter) + MGS + overlap refresh + energy + per-repeat sum; the split-precision step
+    # adds the two operand splits; one measurement counter per block
+    per_step = 8 if args.precision == "fp64" else 10
+    per_block = 2 * (STEPS_PER_BLOCK * per_step + 2 + 2) + 1
     if rank == 0:
         line = {
             "metric": "correlated-pair walker-steps/s", "value": value, "unit": "walker-steps/s",
             "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "bf16x3+f32 (f64 determinants/weights/MGS)",
             "data": "synthetic",
-            "config": {"workload": wl["desc"], "coupling": args.coupling,
+            "config": {"workload": wl["desc"], "coupling": args.coupling, "precision": args.precision,
                        "step": "one measurement block (5 propagation steps + MGS + energy) of both systems",
                        "l2": "inputs larger than L2 (per-step working set ~0.5 GB)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
-            "gpu_launches": per_block * K, "alive_walkers": alive, "other_coupling": other,
-            "dE": {"mean": res["dE_mean"], "sigma": res["dE_sigma"]},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clocks"],
+            "gpu_launches": per_block * K, "alive_walkers": main["alive"],
+            "sigma_sqrt_t": comp, "other_coupling": other,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

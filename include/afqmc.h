@@ -45,9 +45,15 @@ typedef enum {
  * free projection (no force bias, complex weights). */
 enum { AFQMC_PHASELESS = 0, AFQMC_FREE = 1 };
 
-/* Arithmetic of the Cholesky contractions (force bias, V_HS, exchange).
- * Determinants, ratios, phases, weights and MGS are always float64. */
-enum { AFQMC_FP64 = 0 };
+/* Arithmetic of the step.  Determinants, overlaps, ratios, phases, weights and MGS are
+ * float64 in every mode.
+ *   AFQMC_FP64:   every contraction in float64.
+ *   AFQMC_BF16X3: the Cholesky contractions (force bias, Eq. 9; V_HS, Eq. 11) on the
+ *                 tensor cores with split operands x = hi + lo (two bf16), three MMAs per
+ *                 product (hi*hi + hi*lo + lo*hi) accumulated in FP32; the propagator
+ *                 products (one-body half steps, Taylor exponential) and the exchange
+ *                 energy in FP32. */
+enum { AFQMC_FP64 = 0, AFQMC_BF16X3 = 1 };
 
 typedef struct afqmc_ctx* afqmc_handle;
 
@@ -55,7 +61,7 @@ typedef struct {
   double dt;          /* imaginary-time step in Ha^-1 (> 0)                                 */
   int n_walkers;      /* walkers of this system, Nw >= 1                                    */
   int taylor_order;   /* order n of the Taylor exponential T_n(A) = sum_{m<=n} A^m/m!, >= 1 */
-  int precision;      /* AFQMC_FP64                                                         */
+  int precision;      /* AFQMC_FP64 or AFQMC_BF16X3                                        */
   int mode;           /* AFQMC_PHASELESS or AFQMC_FREE                                      */
   int n_repeats;      /* R >= 1 independent repeats; walker k belongs to repeat k*R/Nw      */
   uint64_t seed;      /* key of the counter-based field stream                              */
@@ -141,7 +147,9 @@ afqmc_status afqmc_get_info(afqmc_handle h, afqmc_info* info, cudaStream_t strea
  *   x_{2j} = sqrt(-2 ln u1) cos(2 pi u2), x_{2j+1} = sqrt(-2 ln u1) sin(2 pi u2));
  *   otherwise [n_steps][Nw][X] explicit fields.  Dead walkers are carried through the
  *   batched arithmetic but their determinants and weights no longer change.
- * Errors: ARG, CUDA.
+ * Errors: ARG, CUDA.  In AFQMC_BF16X3 mode an expired bounded wait inside a tensor-core
+ * kernel is reported as TIMEOUT by the next call that synchronises (energy with host
+ * outputs, get_state, get_info, pair_delta_E).
  */
 afqmc_status afqmc_propagate(afqmc_handle h, int n_steps, const double* fields,
                              cudaStream_t stream);

@@ -11,7 +11,7 @@ import numpy as np
 from . import _lib
 
 PHASELESS, FREE = 0, 1
-FP64 = 0
+FP64, BF16X3 = 0, 1
 
 
 class AfqmcError(RuntimeError):
@@ -152,7 +152,7 @@ class System:
 
     def __init__(self, h1, L, trial, n_up, n_dn, dt=0.01, n_walkers=128, taylor_order=6,
                  mode=PHASELESS, n_repeats=1, seed=1, fb_cap=1.0, walker_offset=0,
-                 stream=None):
+                 precision=FP64, stream=None):
         h1 = np.ascontiguousarray(h1, dtype=np.float64)
         L = np.ascontiguousarray(L, dtype=np.float64)
         trial = np.ascontiguousarray(trial, dtype=np.float64)
@@ -161,7 +161,7 @@ class System:
         self.n_walkers, self.n_repeats, self.dt = int(n_walkers), int(n_repeats), float(dt)
         o = afqmc_default_options()
         o.dt, o.n_walkers, o.taylor_order = float(dt), int(n_walkers), int(taylor_order)
-        o.precision, o.mode, o.n_repeats = FP64, int(mode), int(n_repeats)
+        o.precision, o.mode, o.n_repeats = int(precision), int(mode), int(n_repeats)
         o.seed, o.fb_cap, o.walker_offset = int(seed), float(fb_cap), int(walker_offset)
         self.opt = o
         self.h = afqmc_setup(h1, L, trial, self.M, self.X, self.n_up, self.n_dn, o, stream)

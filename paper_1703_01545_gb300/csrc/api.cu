@@ -63,10 +63,115 @@ void free_ctx(Ctx* h) {
   if (h->alive) cudaFree(h->alive);
   if (h->d_step) cudaFree(h->d_step);
   if (h->d_flags) cudaFree(h->d_flags);
+  for (afq::TcOperand* op : {h->tc_L, h->tc_Ltil, h->tc_U, h->tc_Theta})
+    if (op) {
+      if (op->hi) cudaFree(op->hi);
+      if (op->lo) cudaFree(op->lo);
+      delete op;
+    }
+  for (float* b : {h->Avhs32, h->phi32, h->expK32, h->Ltil32})
+    if (b) cudaFree(b);
+  if (h->d_tc_err) cudaFree(h->d_tc_err);
 }
+
+// Allocate a split operand of `rows` logical rows (padded to whole TMA boxes, zero-filled)
+// and K = Kp columns, and encode its tensor maps.
+afqmc_status make_operand(Ctx* h, afq::TcOperand** out, int rows, int K, cudaStream_t s) {
+  auto* op = new afq::TcOperand();
+  *out = op;
+  const int rp = afq::tc_pad_rows(rows), Kp = afq::pad64(K);
+  const size_t bytes = 2 * (size_t)rp * Kp;
+  if (dalloc(h, &op->hi, bytes / 2) != AFQMC_OK || dalloc(h, &op->lo, bytes / 2) != AFQMC_OK)
+    return AFQMC_ERR_NOMEM;
+  AFQ_CK(cudaMemsetAsync(op->hi, 0, bytes, s));
+  AFQ_CK(cudaMemsetAsync(op->lo, 0, bytes, s));
+  AFQ_CK(afq::tc_make_operand(*op, op->hi, op->lo, rp, Kp, 128));
+  return AFQMC_OK;
+}
+
+// Split-precision operands and FP32 copies, built from the FP64 setup results.
+afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
+  const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
+  const int64_t NM = (int64_t)N * M, MM = (int64_t)M * M;
+  afqmc_status st;
+  AFQ_CK(afq::prepare_tc_kernels());
+  AFQ_CK(afq::prepare_mixed_kernels(*h));
+  if ((st = make_operand(h, &h->tc_L, (int)MM, X, s)) != AFQMC_OK) return st;
+  if ((st = make_operand(h, &h->tc_Ltil, X, (int)NM, s)) != AFQMC_OK) return st;
+  if ((st = make_operand(h, &h->tc_U, 2 * Nw, X, s)) != AFQMC_OK) return st;
+  if ((st = make_operand(h, &h->tc_Theta, 2 * Nw, (int)NM, s)) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->Avhs32, 2 * (size_t)Nw * MM)) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->phi32, 2 * (size_t)Nw * NM)) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->expK32, (size_t)MM)) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->Ltil32, (size_t)X * NM)) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->d_tc_err, 1)) != AFQMC_OK) return st;
+  AFQ_CK(cudaMemsetAsync(h->d_tc_err, 0, sizeof(int), s));
+  // L as rows ij with g contiguous: transpose [X][M*M] -> [M*M][X] through phi2 (large enough
+  // only when 2*Nw*N*M >= X*M*M; otherwise a temporary)
+  double* tmp = nullptr;
+  const bool own = 2 * (int64_t)Nw * NM < (int64_t)X * MM;
+  if (own) {
+    if ((st = dalloc(h, &tmp, (size_t)X * MM)) != AFQMC_OK) return st;
+  } else {
+    tmp = h->phi2;
+  }
+  cudaError_t e = afq::launch_transpose(h->L, tmp, X, (int)MM, s);
+  if (e == cudaSuccess) e = afq::split_bf16(tmp, X, (int)MM, X, h->tc_L->Kp, h->tc_L->hi, h->tc_L->lo, s);
+  if (e == cudaSuccess) e = afq::split_bf16(h->Ltil, NM, X, (int)NM, h->tc_Ltil->Kp, h->tc_Ltil->hi, h->tc_Ltil->lo, s);
+  if (e == cudaSuccess) e = afq::to_float(h->expK, h->expK32, MM, s);
+  if (e == cudaSuccess) e = afq::to_float(h->Ltil, h->Ltil32, (int64_t)X * NM, s);
+  if (own) {
+    cudaStreamSynchronize(s);
+    cudaFree(tmp);
+  }
+  AFQ_CK(e);
+  return AFQMC_OK;
+}
+
+// One split-precision step: tensor-core contractions, FP32 propagator, FP64 overlaps.
+afqmc_status step_launch_mixed(Ctx* h, const double* fields_t, cudaStream_t s) {
+  const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
+  const int64_t NM = (int64_t)N * M, MM = (int64_t)M * M;
+  if (h->opt.mode == AFQMC_PHASELESS) {
+    AFQ_CK(afq::split_bf16(h->theta, NM, 2 * Nw, (int)NM, h->tc_Theta->Kp, h->tc_Theta->hi,
+                           h->tc_Theta->lo, s));
+    AFQ_CK(afq::gemm_bf16x3(*h->tc_Ltil, *h->tc_Theta, X, 2 * Nw, 1.0f, h->rhobar, X,
+                            h->d_tc_err, s));
+  }
+  AFQ_CK(afq::launch_fields(*h, fields_t, s));
+  AFQ_CK(afq::split_bf16(h->U, X, 2 * Nw, X, h->tc_U->Kp, h->tc_U->hi, h->tc_U->lo, s));
+  AFQ_CK(afq::gemm_bf16x3(*h->tc_L, *h->tc_U, (int)MM, 2 * Nw, 1.0f, h->Avhs32, MM, h->d_tc_err, s));
+  AFQ_CK(afq::gemm_f32_from_f64(M, 2 * Nw * N, M, 1.0f, h->expK32, M, h->phi, M, h->phi32, M, s));
+  AFQ_CK(afq::launch_taylor_f32(*h, h->phi32, h->Avhs32, s));
+  AFQ_CK(afq::gemm_f32_to_f64(M, 2 * Nw * N, M, 1.0f, h->expK32, M, h->phi32, M, h->theta, M, s));
+  AFQ_CK(afq::launch_overlap(*h, h->theta, afq::OV_UPDATE, s));
+  AFQ_CK(afq::launch_step_advance(*h, s));
+  return AFQMC_OK;
+}
+
+afqmc_status energy_launch(Ctx* h, cudaStream_t s) {
+  if (h->opt.precision == AFQMC_BF16X3) {
+    AFQ_CK(afq::launch_energy_f32(*h, h->Ltil32, s));
+  } else {
+    AFQ_CK(afq::launch_energy(*h, s));
+  }
+  return AFQMC_OK;
+}
+
+// After a synchronisation: report an expired tensor-core wait.
+afqmc_status check_tc(Ctx* h) {
+  if (!h->d_tc_err) return AFQMC_OK;
+  int v = 0;
+  AFQ_CK(cudaMemcpy(&v, h->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) return set_err(h, AFQMC_ERR_TIMEOUT, "a tensor-core kernel's bounded wait expired");
+  return AFQMC_OK;
+}
+
+afqmc_status step_launch_mixed(Ctx* h, const double* fields_t, cudaStream_t s);
 
 // One propagation step of every walker of system h (Eqs. 3-5, 8-9, 11, hybrid weight).
 afqmc_status step_launch(Ctx* h, const double* fields_t, cudaStream_t s) {
+  if (h->opt.precision == AFQMC_BF16X3) return step_launch_mixed(h, fields_t, s);
   const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
   const int64_t NM = (int64_t)N * M;
   if (h->opt.mode == AFQMC_PHASELESS) {
@@ -101,7 +206,7 @@ afqmc_status check_opts(const afqmc_options* o, std::string& why) {
   if (!(o->dt > 0.0) || !std::isfinite(o->dt)) { why = "dt must be > 0"; return AFQMC_ERR_ARG; }
   if (o->n_walkers < 1) { why = "n_walkers must be >= 1"; return AFQMC_ERR_ARG; }
   if (o->taylor_order < 1 || o->taylor_order > 64) { why = "taylor_order must be in [1, 64]"; return AFQMC_ERR_ARG; }
-  if (o->precision != AFQMC_FP64) { why = "unsupported precision"; return AFQMC_ERR_ARG; }
+  if (o->precision != AFQMC_FP64 && o->precision != AFQMC_BF16X3) { why = "unsupported precision"; return AFQMC_ERR_ARG; }
   if (o->mode != AFQMC_PHASELESS && o->mode != AFQMC_FREE) { why = "unknown mode"; return AFQMC_ERR_ARG; }
   if (o->n_repeats < 1 || o->n_repeats > o->n_walkers) { why = "n_repeats must be in [1, n_walkers]"; return AFQMC_ERR_ARG; }
   if (!std::isfinite(o->fb_cap)) { why = "fb_cap must be finite"; return AFQMC_ERR_ARG; }
@@ -117,6 +222,8 @@ afqmc_status check_opts(const afqmc_options* o, std::string& why) {
 namespace afq {
 afqmc_status pair_step(Ctx* h, cudaStream_t s) { return step_launch(h, nullptr, s); }
 afqmc_status pair_ortho(Ctx* h, cudaStream_t s) { return ortho_launch(h, s); }
+afqmc_status pair_energy(Ctx* h, cudaStream_t s) { return energy_launch(h, s); }
+afqmc_status pair_check(Ctx* h) { return check_tc(h); }
 }  // namespace afq
 
 extern "C" {
@@ -294,6 +401,11 @@ afqmc_status afqmc_setup(afqmc_handle* out, const double* h1_in, const double* L
     return bail(AFQMC_ERR_NUMERIC);
   }
   h->e_trial = et;
+  if (opt->precision == AFQMC_BF16X3) {
+    afqmc_status ms = setup_mixed(h, s);
+    if (ms != AFQMC_OK) return bail(ms);
+    AFQ_SCK(cudaStreamSynchronize(s));
+  }
   cleanup_tmp();
 #undef AFQ_SCK
   *out = h;
@@ -338,7 +450,7 @@ afqmc_status afqmc_get_state(afqmc_handle h, double* phi, double* logO, double* 
   if (w) AFQ_CK(cudaMemcpyAsync(w, h->w, sizeof(double) * 2 * h->Nw, cudaMemcpyDefault, s));
   if (alive) AFQ_CK(cudaMemcpyAsync(alive, h->alive, sizeof(int) * h->Nw, cudaMemcpyDefault, s));
   AFQ_CK(cudaStreamSynchronize(s));
-  return AFQMC_OK;
+  return check_tc(h);
 }
 
 afqmc_status afqmc_get_info(afqmc_handle h, afqmc_info* info, cudaStream_t s) {
@@ -352,7 +464,7 @@ afqmc_status afqmc_get_info(afqmc_handle h, afqmc_info* info, cudaStream_t s) {
   int n = 0;
   for (int a : al) n += a != 0;
   info->n_alive = n;
-  return AFQMC_OK;
+  return check_tc(h);
 }
 
 afqmc_status afqmc_propagate(afqmc_handle h, int n_steps, const double* fields, cudaStream_t s) {
@@ -391,7 +503,8 @@ afqmc_status afqmc_orthonormalise(afqmc_handle h, cudaStream_t s) {
 afqmc_status afqmc_energy(afqmc_handle h, double* e_local, double* e_mixed, double* w_sum,
                           cudaStream_t s) {
   if (!h) return AFQMC_ERR_ARG;
-  AFQ_CK(afq::launch_energy(*h, s));
+  afqmc_status est = energy_launch(h, s);
+  if (est != AFQMC_OK) return est;
   if (e_local) AFQ_CK(cudaMemcpyAsync(e_local, h->eloc, sizeof(double) * 2 * h->Nw, cudaMemcpyDefault, s));
   if (e_mixed || w_sum) {
     AFQ_CK(afq::launch_mixed_sum(*h, h->esum, nullptr, 0, s));
@@ -408,6 +521,7 @@ afqmc_status afqmc_energy(afqmc_handle h, double* e_local, double* e_mixed, doub
     if (e_mixed) AFQ_CK(cudaMemcpyAsync(e_mixed, em.data(), sizeof(double) * h->R, cudaMemcpyDefault, s));
     if (w_sum) AFQ_CK(cudaMemcpyAsync(w_sum, ws.data(), sizeof(double) * h->R, cudaMemcpyDefault, s));
     AFQ_CK(cudaStreamSynchronize(s));
+    return check_tc(h);
   } else if (e_local && !is_device_ptr(e_local)) {
     AFQ_CK(cudaStreamSynchronize(s));
   }
@@ -424,14 +538,22 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
   auto one = [&]() -> cudaError_t {
     switch (which) {
       case AFQMC_K_VHS:
+        if (h->tc_L)
+          return afq::gemm_bf16x3(*h->tc_L, *h->tc_U, M * M, 2 * Nw, 1.0f, h->Avhs32,
+                                  (int64_t)M * M, h->d_tc_err, s);
         return afq::gemm_tn_f64((int)h->P, 2 * Nw, X, 1.0, h->Lt, X, 0, h->U, X, 0, 0.0, h->Avhs,
                                 h->P, 0, 1, s, afq::GEMM_VHS);
       case AFQMC_K_FORCE_BIAS:
+        if (h->tc_Ltil)
+          return afq::gemm_bf16x3(*h->tc_Ltil, *h->tc_Theta, X, 2 * Nw, 1.0f, h->rhobar, X,
+                                  h->d_tc_err, s);
         return afq::gemm_tn_f64(X, 2 * Nw, (int)NM, 1.0, h->Ltil, NM, 0, h->theta, NM, 0, 0.0,
                                 h->rhobar, X, 0, 1, s, afq::GEMM_FORCE_BIAS);
       case AFQMC_K_TAYLOR:
+        if (h->phi32) return afq::launch_taylor_f32(*h, h->phi32, h->Avhs32, s);
         return afq::launch_taylor(*h, h->phi2, s);
       default:
+        if (h->Ltil32) return afq::launch_energy_f32(*h, h->Ltil32, s);
         return afq::launch_energy(*h, s);
     }
   };
@@ -452,8 +574,6 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
 afqmc_status afqmc_test_gemm(int impl, int Md, int Nd, int K, const double* A, const double* B,
                              double alpha, double* C, cudaStream_t s) {
   if (Md < 1 || Nd < 1 || K < 1 || !A || !B || !C || impl < 0 || impl > 1) return AFQMC_ERR_ARG;
-  Ctx tmp;
-  Ctx* h = &tmp;
   double *dA = nullptr, *dB = nullptr, *dC = nullptr;
   float* fC = nullptr;
   __nv_bfloat16 *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;

@@ -137,11 +137,11 @@ struct TcLayout {
   static constexpr int SMEM_BYTES = BAR_OFFSET + 256 + 1024;  // barriers + TMEM slot + alignment
 };
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, class TC>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_bf16x3_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                     int Md, int Nd, int nkb, float alpha, float* __restrict__ C, int64_t ldc,
+                     int Md, int Nd, int nkb, float alpha, TC* __restrict__ C, int64_t ldc,
                      int* err) {
   using Lay = TcLayout<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = n0 + c0 + j;
-          if (n < Nd) C[(int64_t)n * ldc + m] = alpha * __uint_as_float(v[j]);
+          if (n < Nd) C[(int64_t)n * ldc + m] = (TC)(alpha * __uint_as_float(v[j]));
         }
       }
     }
@@ -273,19 +273,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-template <int BN, int STAGES>
-cudaError_t launch_tc(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha, float* C,
+template <int BN, int STAGES, class TC>
+cudaError_t launch_tc(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha, TC* C,
                       int64_t ldc, int* err, cudaStream_t s) {
   using Lay = TcLayout<BN, STAGES>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x3_tc<BN, STAGES>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   dim3 grid((Md + BM - 1) / BM, (Nd + BN - 1) / BN);
-  k_gemm_bf16x3_tc<BN, STAGES><<<grid, NTHREADS, Lay::SMEM_BYTES, s>>>(
+  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  k_gemm_bf16x3_tc<BN, STAGES, TC><<<grid, NTHREADS, Lay::SMEM_BYTES, s>>>(
       A.map_hi, A.map_lo, B.map_hi, B.map_lo, Md, Nd, A.Kp / BK, alpha, C, ldc, err);
   return cudaGetLastError();
 }
@@ -332,9 +326,31 @@ int tc_pad_rows(int rows) { return (rows + 127) / 128 * 128; }
 
 cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,
                         float* C, int64_t ldc, int* err, cudaStream_t s) {
-  if (A.Kp != B.Kp) return cudaErrorInvalidValue;
+  if (A.Kp != B.Kp || Md > A.rows || Nd > B.rows) return cudaErrorInvalidValue;
   if (Md <= 0 || Nd <= 0) return cudaSuccess;
-  return launch_tc<128, 3>(A, B, Md, Nd, alpha, C, ldc, err, s);
+  return launch_tc<128, 3, float>(A, B, Md, Nd, alpha, C, ldc, err, s);
+}
+
+cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,
+                        double* C, int64_t ldc, int* err, cudaStream_t s) {
+  if (A.Kp != B.Kp || Md > A.rows || Nd > B.rows) return cudaErrorInvalidValue;
+  if (Md <= 0 || Nd <= 0) return cudaSuccess;
+  return launch_tc<128, 3, double>(A, B, Md, Nd, alpha, C, ldc, err, s);
+}
+
+// Once per process, before any launch or capture: the ring needs ~194 KB of shared memory.
+cudaError_t prepare_tc_kernels() {
+  static cudaError_t st = cudaErrorNotReady;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    using Lay = TcLayout<128, 3>;
+    st = cudaFuncSetAttribute(k_gemm_bf16x3_tc<128, 3, float>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM_BYTES);
+    if (st == cudaSuccess)
+      st = cudaFuncSetAttribute(k_gemm_bf16x3_tc<128, 3, double>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM_BYTES);
+  });
+  return st;
 }
 
 }  // namespace afq

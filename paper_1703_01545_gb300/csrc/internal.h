@@ -47,6 +47,16 @@ struct Ctx {
   double* esum = nullptr;     // [R][4]       sum w E_L (re, im), sum w (re, im)
   unsigned long long* d_step = nullptr;  // device step counter t of the field stream
   int* d_flags = nullptr;     // [4] error counters: [0] singular overlaps
+  // split-precision (AFQMC_BF16X3) operands and FP32 work arrays; null in FP64 mode
+  struct TcOperand* tc_L = nullptr;      // A of V_HS: rows ij (M^2), K = g
+  struct TcOperand* tc_Ltil = nullptr;   // A of the force bias: rows g, K = (n, i)
+  struct TcOperand* tc_U = nullptr;      // B of V_HS: rows (p, w), K = g
+  struct TcOperand* tc_Theta = nullptr;  // B of the force bias: rows (p, w), K = (n, i)
+  float* Avhs32 = nullptr;    // [2][Nw][M*M]
+  float* phi32 = nullptr;     // [2][Nw][N][M]
+  float* expK32 = nullptr;    // [M][M]
+  float* Ltil32 = nullptr;    // [X][N][M]
+  int* d_tc_err = nullptr;    // set by a tensor-core kernel whose bounded wait expired
   // pair-run graph cache (owned; see pair.cu)
   void* pair_cache = nullptr;
   uint64_t uid = 0;           // unique per handle, so a cached graph never outlives its partner
@@ -80,6 +90,18 @@ int tc_pad_rows(int rows);
 // C[n*ldc + m] = alpha * sum_k A[m][k] B[n][k] with both operands split (3 MMAs per product)
 cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,
                         float* C, int64_t ldc, int* err, cudaStream_t s);
+cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,
+                        double* C, int64_t ldc, int* err, cudaStream_t s);
+cudaError_t prepare_tc_kernels();
+// FP32 kernels of the split-precision step (mixed_kernels.cu)
+cudaError_t prepare_mixed_kernels(const Ctx& c);
+cudaError_t gemm_f32_from_f64(int Md, int Nd, int Kd, float alpha, const float* A, int64_t lda,
+                              const double* B, int64_t ldb, float* C, int64_t ldc, cudaStream_t s);
+cudaError_t gemm_f32_to_f64(int Md, int Nd, int Kd, float alpha, const float* A, int64_t lda,
+                            const float* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
+cudaError_t launch_taylor_f32(const Ctx& c, float* phi32, const float* A32, cudaStream_t s);
+cudaError_t launch_energy_f32(const Ctx& c, const float* Ltil32, cudaStream_t s, int n_walkers = -1);
+cudaError_t to_float(const double* in, float* out, int64_t n, cudaStream_t s);
 inline int pad64(int k) { return (k + 63) / 64 * 64; }
 
 enum OverlapMode { OV_REFRESH = 0, OV_UPDATE = 1 };

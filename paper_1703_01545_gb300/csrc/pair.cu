@@ -14,6 +14,8 @@ struct afqmc_ctx : afq::Ctx {};
 namespace afq {
 afqmc_status pair_step(Ctx* h, cudaStream_t s);
 afqmc_status pair_ortho(Ctx* h, cudaStream_t s);
+afqmc_status pair_energy(Ctx* h, cudaStream_t s);
+afqmc_status pair_check(Ctx* h);
 cudaError_t launch_meas_advance(int* meas, cudaStream_t s);
 }  // namespace afq
 
@@ -64,7 +66,8 @@ extern "C" afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n
                                            double* tau_at_min, cudaStream_t s) {
   if (!A || !B || A == B) return fail(A, B, AFQMC_ERR_ARG, "need two distinct handles");
   if (A->opt.seed != B->opt.seed || A->Nw != B->Nw || A->R != B->R || A->opt.dt != B->opt.dt ||
-      A->opt.mode != B->opt.mode || A->opt.walker_offset != B->opt.walker_offset)
+      A->opt.mode != B->opt.mode || A->opt.walker_offset != B->opt.walker_offset ||
+      A->opt.precision != B->opt.precision)
     return fail(A, B, AFQMC_ERR_ARG, "pair handles differ in seed, walkers, repeats, dt, mode or walker offset");
   if (A->step != B->step) return fail(A, B, AFQMC_ERR_STATE, "pair handles are at different steps");
   if (energy_every < 1 || mgs_every < 1 || energy_every % mgs_every != 0 || n_steps < 0 ||
@@ -111,10 +114,10 @@ extern "C" afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n
         if (st == AFQMC_OK) st = afq::pair_ortho(B, r->cs2);
       }
     }
+    if (st == AFQMC_OK && ce == cudaSuccess) st = afq::pair_energy(A, r->cs);
+    if (st == AFQMC_OK && ce == cudaSuccess) st = afq::pair_energy(B, r->cs2);
     if (st == AFQMC_OK && ce == cudaSuccess) {
-      ce = afq::launch_energy(*A, r->cs);
-      if (ce == cudaSuccess) ce = afq::launch_mixed_sum(*A, r->series, r->meas, stride, r->cs);
-      if (ce == cudaSuccess) ce = afq::launch_energy(*B, r->cs2);
+      ce = afq::launch_mixed_sum(*A, r->series, r->meas, stride, r->cs);
       if (ce == cudaSuccess) ce = afq::launch_mixed_sum(*B, r->series + 4 * R, r->meas, stride, r->cs2);
       if (ce == cudaSuccess) ce = cudaEventRecord(r->join, r->cs2);
       if (ce == cudaSuccess) ce = cudaStreamWaitEvent(r->cs, r->join, 0);
@@ -171,6 +174,9 @@ extern "C" afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n
   if (dE_sigma) AFQ_PCK(cudaMemcpy(dE_sigma, &est[1], sizeof(double), cudaMemcpyDefault));
   if (tau_at_min) AFQ_PCK(cudaMemcpy(tau_at_min, &est[2], sizeof(double), cudaMemcpyDefault));
 #undef AFQ_PCK
+  afqmc_status tcs = afq::pair_check(A);
+  if (tcs == AFQMC_OK) tcs = afq::pair_check(B);
+  if (tcs != AFQMC_OK) return tcs;
   int na = 0, nb = 0;
   for (int a : alA) na += a != 0;
   for (int b : alB) nb += b != 0;

@@ -1,0 +1,95 @@
+"""Split-precision path (AFQMC_BF16X3) against the FP64 oracle and the FP64 GPU path.
+
+Both paths take the same fields, so their difference is deterministic.  Criteria:
+per-walker weights and local energies within the accumulated error of the split
+arithmetic (the tensor-core products carry ~2^-16 relative error, propagated through
+50 steps), and, the method's target, the correlated-pair energy difference within
+0.1 mHa of the FP64 path.  The measured errors are written to gpurun_out/ when it exists.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu, system_data
+from oracle import afqmc as orc
+from synthetic import CONFIGS, explicit_fields
+
+pytestmark = pytest.mark.gpu
+OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+REPORT = {}
+
+
+def dump():
+    if os.path.isdir(OUT):
+        with open(os.path.join(OUT, "mixed_errors.json"), "w") as f:
+            json.dump(REPORT, f, indent=1)
+
+
+def gpu_sys(afq, d, nw, dt, precision, seed=1, R=1):
+    return afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt, n_walkers=nw,
+                      seed=seed, n_repeats=R, precision=precision)
+
+
+@pytest.mark.parametrize("cfg,which,coupling,nw", [("C1", "A", 1.0, 128), ("C1", "B", 1.0, 128),
+                                                   ("C2", "B", "moderate", 96)])
+def test_mixed_walkers_track_fp64_oracle(cfg, which, coupling, nw):
+    afq = need_gpu()
+    d = system_data(cfg, which, coupling)
+    dt = CONFIGS[cfg]["dt"]
+    fields = explicit_fields(50, nw, d["X"], seed=8)
+    g = gpu_sys(afq, d, nw, dt, afq.BF16X3)
+    o = orc.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt)
+    wk = orc.Walkers(o, nw)
+    errs = []
+    for blk in range(10):
+        g.propagate(5, fields[5 * blk:5 * blk + 5])
+        for t in range(5 * blk, 5 * blk + 5):
+            orc.propagate(o, wk, fields[t])
+        g.orthonormalise()
+        orc.orthonormalise(o, wk)
+    el, em, _ = g.energy()
+    el_o = orc.local_energy(o, wk.phi)
+    st = g.state()
+    live = wk.alive & st["alive"]
+    assert live.sum() >= 0.9 * wk.alive.sum()
+    e_rel = np.max(np.abs(el[live] - el_o[live]) / np.abs(el_o[live]))
+    w_rel = np.max(np.abs(st["w"].real[live] - wk.w.real[live]) / np.abs(wk.w.real[live]))
+    em_o, _ = orc.mixed_energy(o, wk.w, el_o, np.zeros(nw, int), 1)
+    REPORT[f"{cfg}{which}_walkers"] = dict(max_rel_E_L=float(e_rel), max_rel_w=float(w_rel),
+                                           mixed_E_err_Ha=float(em[0] - em_o[0]))
+    dump()
+    assert e_rel < 1e-3 and w_rel < 1e-2
+    assert abs(em[0] - em_o[0]) < 1e-3
+
+
+def test_mixed_pair_delta_E_within_0p1_mHa_of_fp64():
+    """C2 at full size, moderate coupling: the correlated pair in both precisions, same fields."""
+    afq = need_gpu()
+    cfg = CONFIGS["C2"]
+    nw, R, steps = cfg["n_walkers"], 11, 200
+    dA, dB = system_data("C2", "A", "moderate"), system_data("C2", "B", "moderate")
+    res = {}
+    for prec in (afq.FP64, afq.BF16X3):
+        A = gpu_sys(afq, dA, nw, cfg["dt"], prec, R=R)
+        B = gpu_sys(afq, dB, nw, cfg["dt"], prec, R=R)
+        res[prec] = afq.pair_delta_E(A, B, steps, 5, 5, tau_eq=0.25)
+        A.close()
+        B.close()
+    f, m = res[afq.FP64], res[afq.BF16X3]
+    dE_f = f["E"][:, 1, :] - f["E"][:, 0, :]
+    dE_m = m["E"][:, 1, :] - m["E"][:, 0, :]
+    err_series = np.abs(dE_m - dE_f).max()
+    err_E = np.abs(m["E"] - f["E"]).max()
+    REPORT["C2_pair"] = dict(max_abs_dE_err_mHa=1e3 * float(err_series),
+                             max_abs_E_err_mHa=1e3 * float(err_E),
+                             estimate_fp64=[f["dE_mean"], f["dE_sigma"]],
+                             estimate_bf16x3=[m["dE_mean"], m["dE_sigma"]],
+                             estimate_diff_mHa=1e3 * abs(m["dE_mean"] - f["dE_mean"]))
+    dump()
+    # the estimate (cumulative averages after tau_eq, 11 repeats) within 0.1 mHa, same error bar
+    assert abs(m["dE_mean"] - f["dE_mean"]) < 1e-4
+    assert abs(m["dE_sigma"] / f["dE_sigma"] - 1) < 0.05
+    # per-tau means over the repeats stay close (single-repeat values drift further apart)
+    assert np.abs(dE_m.mean(axis=1) - dE_f.mean(axis=1)).max() < 5e-4
