@@ -69,10 +69,12 @@ void free_ctx(Ctx* h) {
       if (op->lo) cudaFree(op->lo);
       delete op;
     }
-  for (float* b : {h->Avhs32, h->phi32, h->expK32, h->Ltil32})
+  for (float* b : {h->Avhs32, h->phi32, h->expK32, h->Ltil32, h->theta32, h->LtT})
     if (b) cudaFree(b);
   if (h->d_tc_err) cudaFree(h->d_tc_err);
 }
+
+afqmc_status overlap_launch(Ctx* h, const double* src, int mode, cudaStream_t s);
 
 // Allocate a split operand of `rows` logical rows (padded to whole TMA boxes, zero-filled)
 // and K = Kp columns, and encode its tensor maps.
@@ -96,6 +98,8 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   afqmc_status st;
   AFQ_CK(afq::prepare_tc_kernels());
   AFQ_CK(afq::prepare_mixed_kernels(*h));
+  AFQ_CK(afq::prepare_mixed_kernels2(*h));
+  AFQ_CK(afq::prepare_fast_walker_kernels(*h));
   if ((st = make_operand(h, &h->tc_L, (int)MM, X, s)) != AFQMC_OK) return st;
   if ((st = make_operand(h, &h->tc_Ltil, X, (int)NM, s)) != AFQMC_OK) return st;
   if ((st = make_operand(h, &h->tc_U, 2 * Nw, X, s)) != AFQMC_OK) return st;
@@ -105,6 +109,8 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   if ((st = dalloc(h, &h->expK32, (size_t)MM)) != AFQMC_OK) return st;
   if ((st = dalloc(h, &h->Ltil32, (size_t)X * NM)) != AFQMC_OK) return st;
   if ((st = dalloc(h, &h->d_tc_err, 1)) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->theta32, 2 * (size_t)Nw * NM)) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->LtT, (size_t)afq::LtT_size(*h))) != AFQMC_OK) return st;
   AFQ_CK(cudaMemsetAsync(h->d_tc_err, 0, sizeof(int), s));
   // L as rows ij with g contiguous: transpose [X][M*M] -> [M*M][X] through phi2 (large enough
   // only when 2*Nw*N*M >= X*M*M; otherwise a temporary)
@@ -120,6 +126,10 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   if (e == cudaSuccess) e = afq::split_bf16(h->Ltil, NM, X, (int)NM, h->tc_Ltil->Kp, h->tc_Ltil->hi, h->tc_Ltil->lo, s);
   if (e == cudaSuccess) e = afq::to_float(h->expK, h->expK32, MM, s);
   if (e == cudaSuccess) e = afq::to_float(h->Ltil, h->Ltil32, (int64_t)X * NM, s);
+  if (e == cudaSuccess) e = afq::build_LtT(*h, h->LtT, s);
+  // Theta of the current walkers in FP32 and as the split force-bias operand
+  if (e == cudaSuccess && overlap_launch(h, nullptr, afq::OV_REFRESH, s) != AFQMC_OK)
+    e = cudaErrorUnknown;
   if (own) {
     cudaStreamSynchronize(s);
     cudaFree(tmp);
@@ -131,27 +141,26 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
 // One split-precision step: tensor-core contractions, FP32 propagator, FP64 overlaps.
 afqmc_status step_launch_mixed(Ctx* h, const double* fields_t, cudaStream_t s) {
   const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
-  const int64_t NM = (int64_t)N * M, MM = (int64_t)M * M;
+  const int64_t MM = (int64_t)M * M;
   if (h->opt.mode == AFQMC_PHASELESS) {
-    AFQ_CK(afq::split_bf16(h->theta, NM, 2 * Nw, (int)NM, h->tc_Theta->Kp, h->tc_Theta->hi,
-                           h->tc_Theta->lo, s));
+    // the Theta operand was written by the last overlap kernel
     AFQ_CK(afq::gemm_bf16x3(*h->tc_Ltil, *h->tc_Theta, X, 2 * Nw, 1.0f, h->rhobar, X,
                             h->d_tc_err, s));
   }
-  AFQ_CK(afq::launch_fields(*h, fields_t, s));
-  AFQ_CK(afq::split_bf16(h->U, X, 2 * Nw, X, h->tc_U->Kp, h->tc_U->hi, h->tc_U->lo, s));
+  AFQ_CK(afq::launch_fields_mixed(*h, fields_t, s));
   AFQ_CK(afq::gemm_bf16x3(*h->tc_L, *h->tc_U, (int)MM, 2 * Nw, 1.0f, h->Avhs32, MM, h->d_tc_err, s));
   AFQ_CK(afq::gemm_f32_from_f64(M, 2 * Nw * N, M, 1.0f, h->expK32, M, h->phi, M, h->phi32, M, s));
-  AFQ_CK(afq::launch_taylor_f32(*h, h->phi32, h->Avhs32, s));
+  AFQ_CK(afq::launch_taylor_f32_best(*h, h->phi32, h->Avhs32, s));
   AFQ_CK(afq::gemm_f32_to_f64(M, 2 * Nw * N, M, 1.0f, h->expK32, M, h->phi32, M, h->theta, M, s));
-  AFQ_CK(afq::launch_overlap(*h, h->theta, afq::OV_UPDATE, s));
+  afqmc_status os = overlap_launch(h, h->theta, afq::OV_UPDATE, s);
+  if (os != AFQMC_OK) return os;
   AFQ_CK(afq::launch_step_advance(*h, s));
   return AFQMC_OK;
 }
 
 afqmc_status energy_launch(Ctx* h, cudaStream_t s) {
   if (h->opt.precision == AFQMC_BF16X3) {
-    AFQ_CK(afq::launch_energy_f32(*h, h->Ltil32, s));
+    AFQ_CK(afq::launch_energy_tiled(*h, h->theta32, h->LtT, s));
   } else {
     AFQ_CK(afq::launch_energy(*h, s));
   }
@@ -195,10 +204,23 @@ afqmc_status step_launch(Ctx* h, const double* fields_t, cudaStream_t s) {
   return AFQMC_OK;
 }
 
-afqmc_status ortho_launch(Ctx* h, cudaStream_t s) {
-  AFQ_CK(afq::launch_mgs(*h, s));
-  AFQ_CK(afq::launch_overlap(*h, nullptr, afq::OV_REFRESH, s));
+// Overlap / Theta / weight kernel: the warp-synchronous variant in split-precision mode.
+afqmc_status overlap_launch(Ctx* h, const double* src, int mode, cudaStream_t s) {
+  if (h->theta32 && h->tc_Theta && afq::fast_walker_kernels_ok(*h)) {
+    AFQ_CK(afq::launch_overlap_fast(*h, src, mode, s));
+  } else {
+    AFQ_CK(afq::launch_overlap(*h, src, mode, s));
+  }
   return AFQMC_OK;
+}
+
+afqmc_status ortho_launch(Ctx* h, cudaStream_t s) {
+  if (h->theta32 && afq::fast_walker_kernels_ok(*h)) {
+    AFQ_CK(afq::launch_mgs_warp(*h, s));
+  } else {
+    AFQ_CK(afq::launch_mgs(*h, s));
+  }
+  return overlap_launch(h, nullptr, afq::OV_REFRESH, s);
 }
 
 afqmc_status check_opts(const afqmc_options* o, std::string& why) {
@@ -433,7 +455,8 @@ afqmc_status afqmc_set_walkers(afqmc_handle h, const double* phi, const double* 
   }
   AFQ_CK(afq::launch_init_weights(h->w, h->alive, wd, h->Nw, s));
   AFQ_CK(cudaMemsetAsync(h->d_step, 0, sizeof(unsigned long long), s));
-  AFQ_CK(afq::launch_overlap(*h, nullptr, afq::OV_REFRESH, s));
+  afqmc_status rs = overlap_launch(h, nullptr, afq::OV_REFRESH, s);
+  if (rs != AFQMC_OK) return rs;
   h->step = 0;
   return AFQMC_OK;
 }
@@ -550,10 +573,10 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
         return afq::gemm_tn_f64(X, 2 * Nw, (int)NM, 1.0, h->Ltil, NM, 0, h->theta, NM, 0, 0.0,
                                 h->rhobar, X, 0, 1, s, afq::GEMM_FORCE_BIAS);
       case AFQMC_K_TAYLOR:
-        if (h->phi32) return afq::launch_taylor_f32(*h, h->phi32, h->Avhs32, s);
+        if (h->phi32) return afq::launch_taylor_f32_best(*h, h->phi32, h->Avhs32, s);
         return afq::launch_taylor(*h, h->phi2, s);
       default:
-        if (h->Ltil32) return afq::launch_energy_f32(*h, h->Ltil32, s);
+        if (h->LtT) return afq::launch_energy_tiled(*h, h->theta32, h->LtT, s);
         return afq::launch_energy(*h, s);
     }
   };
@@ -597,6 +620,7 @@ afqmc_status afqmc_test_gemm(int impl, int Md, int Nd, int K, const double* A, c
     if (impl == 0) {
       if ((e = afq::gemm_tn_f64(Md, Nd, K, alpha, dA, K, 0, dB, K, 0, 0.0, dC, Md, 0, 1, s)) != cudaSuccess) break;
     } else {
+      if ((e = afq::prepare_tc_kernels()) != cudaSuccess) break;
       const int Mp = afq::tc_pad_rows(Md), Np = afq::tc_pad_rows(Nd);
       if ((e = cudaMalloc(&fC, sizeof(float) * Md * (size_t)Nd)) != cudaSuccess) break;
       if ((e = cudaMalloc(&ah, 2 * (size_t)Mp * Kp)) != cudaSuccess) break;

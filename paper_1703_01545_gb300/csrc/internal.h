@@ -56,6 +56,8 @@ struct Ctx {
   float* phi32 = nullptr;     // [2][Nw][N][M]
   float* expK32 = nullptr;    // [M][M]
   float* Ltil32 = nullptr;    // [X][N][M]
+  float* theta32 = nullptr;   // [2][Nw][N][M]  Theta in FP32 (split-precision mode)
+  float* LtT = nullptr;       // [X][M][NPT]    Psi_s^T L_g transposed, spin-padded (FP32)
   int* d_tc_err = nullptr;    // set by a tensor-core kernel whose bounded wait expired
   // pair-run graph cache (owned; see pair.cu)
   void* pair_cache = nullptr;
@@ -102,6 +104,18 @@ cudaError_t gemm_f32_to_f64(int Md, int Nd, int Kd, float alpha, const float* A,
 cudaError_t launch_taylor_f32(const Ctx& c, float* phi32, const float* A32, cudaStream_t s);
 cudaError_t launch_energy_f32(const Ctx& c, const float* Ltil32, cudaStream_t s, int n_walkers = -1);
 cudaError_t to_float(const double* in, float* out, int64_t n, cudaStream_t s);
+cudaError_t prepare_mixed_kernels2(const Ctx& c);
+cudaError_t build_LtT(const Ctx& c, float* LtT, cudaStream_t s);
+int64_t LtT_size(const Ctx& c);
+cudaError_t launch_energy_tiled(const Ctx& c, const float* theta32, const float* LtT,
+                                cudaStream_t s, int n_walkers = -1);
+cudaError_t launch_taylor_f32_best(const Ctx& c, float* phi32, const float* A32, cudaStream_t s);
+// latency-oriented FP64 walker kernels of the split-precision step (walker_fast.cu)
+bool fast_walker_kernels_ok(const Ctx& c);
+cudaError_t prepare_fast_walker_kernels(const Ctx& c);
+cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaStream_t s);
+cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s);
+cudaError_t launch_fields_mixed(const Ctx& c, const double* fields, cudaStream_t s);
 inline int pad64(int k) { return (k + 63) / 64 * 64; }
 
 enum OverlapMode { OV_REFRESH = 0, OV_UPDATE = 1 };

@@ -315,3 +315,374 @@ cudaError_t to_float(const double* in, float* out, int64_t n, cudaStream_t s) {
 }
 
 }  // namespace afq
+
+// ===========================================================================
+// Second-generation FP32 kernels of the split-precision step.
+// ===========================================================================
+namespace afq {
+namespace {
+
+// Exchange + Coulomb local energy with several walkers per CTA.
+//   LtT  [X][M][NPT]  float: (Psi_s^T L_g) transposed, spin blocks padded to multiples of 4
+//   th   [2][Nw][N][M] float: Theta (planar)
+// For each chunk of GC Cholesky vectors the CTA stages LtT for the chunk, every thread forms
+// 4x4 tiles of T^s_g = Psi_s^T L_g Theta_s for one (walker, g) from float4 shared reads,
+// tiles land in shared memory, and each walker's own thread group accumulates
+// sum_ab T_ab T_ba and (sum_s tr T^s_g)^2.
+template <int WB>
+__global__ void __launch_bounds__(256) k_energy_f32_tiled(const float* __restrict__ th,
+                                                          const float* __restrict__ LtT,
+                                                          const double* __restrict__ htil,
+                                                          double* __restrict__ eloc, int M, int N,
+                                                          int n_up, int X, int Nw, int GC) {
+  extern __shared__ __align__(16) float s4[];
+  const int nu = n_up, nd = N - n_up;
+  const int PU = (nu + 3) & ~3, PD = (nd + 3) & ~3, NPT = PU + PD;
+  const int tu = PU / 4, td = PD / 4, ntiles = tu * tu + td * td;
+  const int tid = threadIdx.x;
+  const int w0 = blockIdx.x * WB;
+  float* thr = s4;                         // [WB][M][NPT]
+  float* thi = thr + WB * M * NPT;
+  float* Ls = thi + WB * M * NPT;          // [GC][M][NPT]
+  const int nnp = PU * PU + PD * PD;
+  const int nst = nnp + 1;                 // odd stride between (walker, g) blocks: no bank conflicts
+  float* Tr = Ls + GC * M * NPT;           // [WB][GC][nst]
+  float* Ti = Tr + WB * GC * nst;
+  double* red = reinterpret_cast<double*>(Ti + WB * GC * nst + ((2 * WB * GC * nst) & 1));
+  const int64_t plane = (int64_t)Nw * N * M;
+  // stage Theta of the CTA's walkers, spin-padded columns, zero elsewhere
+  for (int e = tid; e < WB * M * NPT; e += blockDim.x) {
+    const int wl = e / (M * NPT), r = e % (M * NPT), i = r / NPT, c = r % NPT;
+    int n = -1;
+    if (c < PU) { if (c < nu) n = c; }
+    else if (c - PU < nd) n = nu + (c - PU);
+    float vr = 0.f, vi = 0.f;
+    const int wk = w0 + wl;
+    if (n >= 0 && wk < Nw) {
+      const int64_t gi = ((int64_t)wk * N + n) * M + i;
+      vr = th[gi];
+      vi = th[plane + gi];
+    }
+    thr[e] = vr;
+    thi[e] = vi;
+  }
+  // one-body part: threads of walker group wl
+  const int per_w = blockDim.x / WB;       // threads per walker in the reduction
+  const int wl_me = tid / per_w, lt = tid % per_w;
+  double acc[4] = {0, 0, 0, 0};            // sum for walker wl_me: E1+coul (re, im), -exch/2 (re, im)
+  if (wl_me < WB && w0 + wl_me < Nw) {
+    const int wk = w0 + wl_me;
+    for (int e = lt; e < N * M; e += per_w) {
+      const double h = __ldg(htil + e);
+      const int64_t gi = (int64_t)wk * N * M + e;
+      acc[0] = fma(h, (double)th[gi], acc[0]);
+      acc[1] = fma(h, (double)th[plane + gi], acc[1]);
+    }
+  }
+  __syncthreads();
+  const int items = WB * GC * ntiles;
+  for (int g0 = 0; g0 < X; g0 += GC) {
+    const int gc = min(GC, X - g0);
+    for (int e = tid; e < gc * M * NPT; e += blockDim.x) Ls[e] = LtT[(int64_t)g0 * M * NPT + e];
+    __syncthreads();
+    for (int it = tid; it < items; it += blockDim.x) {
+      const int wl = it / (GC * ntiles), r = it % (GC * ntiles), gl = r / ntiles, t = r % ntiles;
+      if (gl >= gc) continue;
+      int c0a, c0b, toff, P;
+      if (t < tu * tu) { c0a = 4 * (t / tu); c0b = 4 * (t % tu); toff = 0; P = PU; }
+      else { const int t2 = t - tu * tu; c0a = PU + 4 * (t2 / td); c0b = PU + 4 * (t2 % td); toff = PU * PU; P = PD; }
+      float ar[4][4], ai[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) ar[x][y] = ai[x][y] = 0.f;
+      const float* Lp = Ls + gl * M * NPT + c0a;
+      const float* Rp = thr + wl * M * NPT + c0b;
+      const float* Ip = thi + wl * M * NPT + c0b;
+      for (int i = 0; i < M; ++i) {
+        const float4 l = *reinterpret_cast<const float4*>(Lp + i * NPT);
+        const float4 tr = *reinterpret_cast<const float4*>(Rp + i * NPT);
+        const float4 ti = *reinterpret_cast<const float4*>(Ip + i * NPT);
+        const float lv[4] = {l.x, l.y, l.z, l.w}, rv[4] = {tr.x, tr.y, tr.z, tr.w},
+                    iv[4] = {ti.x, ti.y, ti.z, ti.w};
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            ar[x][y] = fmaf(lv[x], rv[y], ar[x][y]);
+            ai[x][y] = fmaf(lv[x], iv[y], ai[x][y]);
+          }
+      }
+      // store tile: block-local indices (a, b) inside the spin block
+      const int la = c0a - (toff ? PU : 0), lb = c0b - (toff ? PU : 0);
+      float* Trp = Tr + (wl * GC + gl) * nst + toff;
+      float* Tip = Ti + (wl * GC + gl) * nst + toff;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          Trp[(la + x) * P + lb + y] = ar[x][y];
+          Tip[(la + x) * P + lb + y] = ai[x][y];
+        }
+    }
+    __syncthreads();
+    if (wl_me < WB) {
+      float ex_r = 0.f, ex_i = 0.f;
+      for (int e = lt; e < gc * nnp; e += per_w) {
+        const int gl = e / nnp, r = e % nnp;
+        int et;
+        if (r < PU * PU) { const int a = r / PU, b = r % PU; et = b * PU + a; }
+        else { const int r2 = r - PU * PU, a = r2 / PD, b = r2 % PD; et = PU * PU + b * PD + a; }
+        const float* trp = Tr + (wl_me * GC + gl) * nst;
+        const float* tip = Ti + (wl_me * GC + gl) * nst;
+        ex_r += trp[r] * trp[et] - tip[r] * tip[et];
+        ex_i += trp[r] * tip[et] + tip[r] * trp[et];
+      }
+      acc[2] -= 0.5 * (double)ex_r;
+      acc[3] -= 0.5 * (double)ex_i;
+      for (int gl = lt; gl < gc; gl += per_w) {
+        const float* trp = Tr + (wl_me * GC + gl) * nst;
+        const float* tip = Ti + (wl_me * GC + gl) * nst;
+        float cr = 0.f, ci = 0.f;
+        for (int a = 0; a < nu; ++a) { cr += trp[a * PU + a]; ci += tip[a * PU + a]; }
+        for (int a = 0; a < nd; ++a) { cr += trp[PU * PU + a * PD + a]; ci += tip[PU * PU + a * PD + a]; }
+        acc[0] += 0.5 * ((double)cr * cr - (double)ci * ci);
+        acc[1] += (double)cr * ci;
+      }
+    }
+    __syncthreads();
+  }
+  // per-walker reduction over its per_w threads (whole warps: per_w is a multiple of 32)
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+  const int lane = tid & 31, wid = tid >> 5;
+  if (lane == 0)
+    for (int q = 0; q < 4; ++q) red[q * 8 + wid] = acc[q];
+  __syncthreads();
+  if (tid < WB && w0 + tid < Nw) {
+    const int wpw = per_w / 32;
+    double v[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q)
+      for (int k = 0; k < wpw; ++k) v[q] += red[q * 8 + tid * wpw + k];
+    eloc[w0 + tid] = v[0] + v[2];
+    eloc[Nw + w0 + tid] = v[1] + v[3];
+  }
+}
+
+// LtT[g][i][c] from Ltil[g][n][i] (float64), spin-padded columns
+__global__ void k_build_LtT(const double* __restrict__ Ltil, float* __restrict__ LtT, int X, int M,
+                            int N, int n_up) {
+  const int nu = n_up, nd = N - n_up, PU = (nu + 3) & ~3, PD = (nd + 3) & ~3, NPT = PU + PD;
+  const int64_t total = (int64_t)X * M * NPT;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % NPT);
+    const int64_t r = e / NPT;
+    const int i = (int)(r % M);
+    const int g = (int)(r / M);
+    int n = -1;
+    if (c < PU) { if (c < nu) n = c; }
+    else if (c - PU < nd) n = nu + (c - PU);
+    LtT[e] = n >= 0 ? (float)Ltil[((int64_t)g * N + n) * M + i] : 0.f;
+  }
+}
+
+// Taylor exponential, A_w staged in shared memory.  A is complex symmetric, so row j of A
+// is column j: the loop reads A[j][i..i+1] contiguously.  Each thread owns rows
+// (2ip, 2ip+1) and columns (4bg .. 4bg+3): per j two float2 and two float4 shared loads
+// feed 32 FMAs.
+__global__ void __launch_bounds__(256) k_taylor_f32_smem(float* __restrict__ phi,
+                                                         const float* __restrict__ Av, int M,
+                                                         int N, int Nw, int order) {
+  extern __shared__ __align__(16) float sm2[];
+  const int wk = blockIdx.x, tid = threadIdx.x;
+  const int NP = (N + 3) & ~3, NG = NP / 4, MP = (M + 1) & ~1, RH = MP / 2;
+  const int64_t MM = (int64_t)M * M;
+  float* Ar = sm2;                   // [M][MP]
+  float* Ai = Ar + M * MP;
+  float* tr = Ai + M * MP;           // [MP][NP]
+  float* ti = tr + MP * NP;
+  float* nr = ti + MP * NP;
+  float* ni = nr + MP * NP;
+  const float* ar_g = Av + (int64_t)wk * MM;
+  const float* ai_g = Av + (int64_t)Nw * MM + (int64_t)wk * MM;
+  for (int e = tid; e < M * MP; e += blockDim.x) {
+    const int j = e / MP, i = e % MP;
+    Ar[e] = i < M ? ar_g[(int64_t)j * M + i] : 0.f;
+    Ai[e] = i < M ? ai_g[(int64_t)j * M + i] : 0.f;
+  }
+  const int64_t plane = (int64_t)Nw * N * M, base = (int64_t)wk * N * M;
+  for (int e = tid; e < MP * NP; e += blockDim.x) {
+    const int i = e / NP, b = e % NP;
+    float vr = 0.f, vi = 0.f;
+    if (b < N && i < M) {
+      vr = phi[base + (int64_t)b * M + i];
+      vi = phi[plane + base + (int64_t)b * M + i];
+    }
+    tr[e] = vr;
+    ti[e] = vi;
+    nr[e] = 0.f;
+    ni[e] = 0.f;
+  }
+  __syncthreads();
+  const int items = RH * NG;
+  // each thread: at most 2 items (RH*NG <= 512)
+  float sr[2][2][4], si[2][2][4];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int o = tid + q * 256;
+    const int ip = o / NG, b0 = (o % NG) * 4;
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        sr[q][rr][c] = (o < items) ? tr[(2 * ip + rr) * NP + b0 + c] : 0.f;
+        si[q][rr][c] = (o < items) ? ti[(2 * ip + rr) * NP + b0 + c] : 0.f;
+      }
+  }
+  for (int m = 1; m <= order; ++m) {
+    const float inv = 1.f / (float)m;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int o = tid + q * 256;
+      if (o < items) {
+        const int ip = o / NG, b0 = (o % NG) * 4;
+        float xr[2][4], xi[2][4];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) xr[rr][c] = xi[rr][c] = 0.f;
+        for (int j = 0; j < M; ++j) {
+          const float2 a_r = *reinterpret_cast<const float2*>(Ar + j * MP + 2 * ip);
+          const float2 a_i = *reinterpret_cast<const float2*>(Ai + j * MP + 2 * ip);
+          const float4 yr = *reinterpret_cast<const float4*>(tr + j * NP + b0);
+          const float4 yi = *reinterpret_cast<const float4*>(ti + j * NP + b0);
+          const float Rr[2] = {a_r.x, a_r.y}, Ri[2] = {a_i.x, a_i.y};
+          const float vr[4] = {yr.x, yr.y, yr.z, yr.w}, vi[4] = {yi.x, yi.y, yi.z, yi.w};
+#pragma unroll
+          for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              xr[rr][c] = fmaf(Rr[rr], vr[c], fmaf(-Ri[rr], vi[c], xr[rr][c]));
+              xi[rr][c] = fmaf(Rr[rr], vi[c], fmaf(Ri[rr], vr[c], xi[rr][c]));
+            }
+        }
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float a = xr[rr][c] * inv, b = xi[rr][c] * inv;
+            nr[(2 * ip + rr) * NP + b0 + c] = a;
+            ni[(2 * ip + rr) * NP + b0 + c] = b;
+            sr[q][rr][c] += a;
+            si[q][rr][c] += b;
+          }
+      }
+    }
+    __syncthreads();
+    float* t0 = tr; tr = nr; nr = t0;
+    float* t1 = ti; ti = ni; ni = t1;
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int o = tid + q * 256;
+    if (o < items) {
+      const int ip = o / NG, b0 = (o % NG) * 4;
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int i = 2 * ip + rr, b = b0 + c;
+          if (i < M && b < N) {
+            phi[base + (int64_t)b * M + i] = sr[q][rr][c];
+            phi[plane + base + (int64_t)b * M + i] = si[q][rr][c];
+          }
+        }
+    }
+  }
+}
+
+}  // namespace
+
+int energy_wb() { return 4; }
+
+size_t smem_energy_tiled(const Ctx& c, int GC) {
+  const int nu = c.n_up, nd = c.N - c.n_up, PU = (nu + 3) & ~3, PD = (nd + 3) & ~3, NPT = PU + PD;
+  const int WB = energy_wb();
+  const size_t nst = (size_t)PU * PU + (size_t)PD * PD + 1;
+  return sizeof(float) * (2 * (size_t)WB * c.M * NPT + (size_t)GC * c.M * NPT + 2 * WB * GC * nst + 2) +
+         sizeof(double) * 40;
+}
+
+int energy_gc(const Ctx& c) {
+  const int nu = c.n_up, nd = c.N - c.n_up, PU = (nu + 3) & ~3, PD = (nd + 3) & ~3;
+  const int ntiles = (PU / 4) * (PU / 4) + (PD / 4) * (PD / 4);
+  int gc = 256 / (energy_wb() * ntiles);
+  if (gc < 1) gc = 1;
+  while (gc > 1 && smem_energy_tiled(c, gc) > 200 * 1024) --gc;
+  return gc;
+}
+
+size_t smem_taylor_smem(const Ctx& c) {
+  const size_t NP = (c.N + 3) & ~3, MP = (c.M + 1) & ~1;
+  return sizeof(float) * (2 * (size_t)c.M * MP + 4 * MP * NP);
+}
+
+bool taylor_smem_ok(const Ctx& c) {
+  const int NP = (c.N + 3) & ~3, MP = (c.M + 1) & ~1;
+  return smem_taylor_smem(c) <= 200 * 1024 && (MP / 2) * (NP / 4) <= 512;
+}
+
+cudaError_t prepare_mixed_kernels2(const Ctx& c) {
+  static size_t have_e = 0, have_t = 0;
+  cudaError_t e;
+  const size_t se = smem_energy_tiled(c, energy_gc(c));
+  if (se > have_e) {
+    if ((e = cudaFuncSetAttribute(k_energy_f32_tiled<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)se)) != cudaSuccess)
+      return e;
+    have_e = se;
+  }
+  if (taylor_smem_ok(c)) {
+    const size_t st = smem_taylor_smem(c);
+    if (st > have_t) {
+      if ((e = cudaFuncSetAttribute(k_taylor_f32_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)st)) != cudaSuccess)
+        return e;
+      have_t = st;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t build_LtT(const Ctx& c, float* LtT, cudaStream_t s) {
+  const int nu = c.n_up, nd = c.N - c.n_up, NPT = ((nu + 3) & ~3) + ((nd + 3) & ~3);
+  const int64_t total = (int64_t)c.X * c.M * NPT;
+  int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 64);
+  k_build_LtT<<<grid < 1 ? 1 : grid, 256, 0, s>>>(c.Ltil, LtT, c.X, c.M, c.N, c.n_up);
+  return cudaGetLastError();
+}
+
+int64_t LtT_size(const Ctx& c) {
+  const int nu = c.n_up, nd = c.N - c.n_up, NPT = ((nu + 3) & ~3) + ((nd + 3) & ~3);
+  return (int64_t)c.X * c.M * NPT;
+}
+
+cudaError_t launch_energy_tiled(const Ctx& c, const float* theta32, const float* LtT,
+                                cudaStream_t s, int n_walkers) {
+  const int nw = n_walkers > 0 ? n_walkers : c.Nw;
+  const int GC = energy_gc(c), WB = energy_wb();
+  k_energy_f32_tiled<4><<<(nw + WB - 1) / WB, 256, smem_energy_tiled(c, GC), s>>>(
+      theta32, LtT, c.htil, c.eloc, c.M, c.N, c.n_up, c.X, nw, GC);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_taylor_f32_best(const Ctx& c, float* phi32, const float* A32, cudaStream_t s) {
+  if (!taylor_smem_ok(c)) return launch_taylor_f32(c, phi32, A32, s);
+  k_taylor_f32_smem<<<c.Nw, 256, smem_taylor_smem(c), s>>>(phi32, A32, c.M, c.N, c.Nw,
+                                                           c.opt.taylor_order);
+  return cudaGetLastError();
+}
+
+}  // namespace afq

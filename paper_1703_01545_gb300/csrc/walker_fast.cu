@@ -1,0 +1,449 @@
+// Latency-oriented FP64 walker kernels for the split-precision step: overlap /
+// Gauss-Jordan / weight update and modified Gram-Schmidt with one warp per spin block, so
+// the small dense linear algebra (N_s <= 16) synchronises with __syncwarp only.  The
+// arithmetic (overlaps, determinants, ratios, weights, Gram-Schmidt) is FP64 as in the
+// reference kernels; only Theta = Phi O^{-1} is formed in FP32 here.
+#include <cmath>
+#include <cstdint>
+#include <cuda_bf16.h>
+
+#include "device_util.cuh"
+#include "internal.h"
+
+namespace afq {
+namespace {
+
+constexpr int kNsMax = 16;   // spin block size handled by the warp Gauss-Jordan
+
+struct FastOvArgs {
+  const double* src;  // [2][Nw][N][M]  (propagated walkers in update mode)
+  double* phi;
+  float* theta32;
+  __nv_bfloat16* op_hi;
+  __nv_bfloat16* op_lo;
+  int Kp;
+  const double* psi;  // [N][M]
+  double* logO;
+  double* w;
+  int* alive;
+  const double* aux;
+  int* flags;
+  int M, N, n_up, Nw, mode, free_proj;
+  double log_shift;
+};
+
+// One CTA (256 threads) per walker.  Shared: phi [2][N][M] (FP64), per spin the augmented
+// matrix [O | I] as [2][ns][2 ns] (FP64).
+__global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
+  extern __shared__ double smo[];
+  const int wk = blockIdx.x, tid = threadIdx.x, M = a.M, N = a.N, NM = N * M;
+  const int lane = tid & 31, warp = tid >> 5;
+  double* pr = smo;            // [N][M]
+  double* pi = pr + NM;        // [N][M]
+  double* aug = pi + NM;       // spin s at aug + s * 2 * 16 * 32: re [16][32], im [16][32]
+  __shared__ double s_ld[2][2];
+  __shared__ int s_bad[2];
+  const bool live = a.alive[wk] != 0;
+  const bool upd = (a.mode == OV_UPDATE) && live;
+  const double* src = upd ? a.src : a.phi;
+  const int64_t plane = (int64_t)a.Nw * NM, wbase = (int64_t)wk * NM;
+  for (int e = tid; e < NM; e += blockDim.x) {
+    pr[e] = src[wbase + e];
+    pi[e] = src[plane + wbase + e];
+  }
+  if (tid < 2) { s_ld[tid][0] = 0.0; s_ld[tid][1] = 0.0; s_bad[tid] = 0; }
+  __syncthreads();
+  // O_s[a][b] = sum_i psi[n0+a][i] phi[n0+b][i]; 4 threads per entry, shuffle-combined
+  const int nu = a.n_up, nd = N - nu, nn = nu * nu + nd * nd;
+  for (int base = 0; base < nn * 4; base += blockDim.x) {
+    const int q = base + tid, ent = q >> 2, part = q & 3;
+    double re = 0.0, im = 0.0;
+    int sp = 0, r = 0, c = 0, ns = nu;
+    if (ent < nn) {
+      if (ent < nu * nu) { r = ent / nu; c = ent % nu; }
+      else { sp = 1; ns = nd; const int e2 = ent - nu * nu; r = e2 / nd; c = e2 % nd; }
+      const int n0 = sp ? nu : 0;
+      const double* ps = a.psi + (int64_t)(n0 + r) * M;
+      const double* fr = pr + (n0 + c) * M;
+      const double* fi = pi + (n0 + c) * M;
+      for (int i = part; i < M; i += 4) {
+        const double p = __ldg(ps + i);
+        re = fma(p, fr[i], re);
+        im = fma(p, fi[i], im);
+      }
+    }
+    re += __shfl_xor_sync(0xffffffffu, re, 1);
+    im += __shfl_xor_sync(0xffffffffu, im, 1);
+    re += __shfl_xor_sync(0xffffffffu, re, 2);
+    im += __shfl_xor_sync(0xffffffffu, im, 2);
+    if (ent < nn && part == 0) {
+      double* ar = aug + sp * 2 * kNsMax * 32;
+      double* ai = ar + kNsMax * 32;
+      ar[r * 32 + c] = re;
+      ai[r * 32 + c] = im;
+      ar[r * 32 + ns + c] = (r == c) ? 1.0 : 0.0;
+      ai[r * 32 + ns + c] = 0.0;
+    }
+  }
+  __syncthreads();
+  // warp-synchronous Gauss-Jordan with partial pivoting on [O | I] (ns x 2ns): warp sp
+  // handles spin sp; lane l owns column l % 2ns and rows l / 2ns, l / 2ns + RS, ... so all
+  // lanes work.  The determinant is the product of the pivots (times the swap signs), kept
+  // as a complex number with a separate power-of-two exponent; one log at the end.
+  if (warp < 2) {
+    const int sp = warp, ns = sp ? nd : nu;
+    if (ns > 0) {
+      double* ar = aug + sp * 2 * kNsMax * 32;
+      double* ai = ar + kNsMax * 32;
+      const int w2 = 2 * ns, RS = 32 / w2 > 0 ? 32 / w2 : 1;  // row stride between a lane's rows
+      const int c = lane % w2, r0 = lane / w2;
+      const bool active = lane < RS * w2;
+      double dr = 1.0, di = 0.0;
+      int dexp = 0;
+      bool bad = false;
+      for (int k = 0; k < ns; ++k) {
+        int p = k;
+        double best = -1.0;
+        for (int r = k; r < ns; ++r) {
+          const double m2 = ar[r * 32 + k] * ar[r * 32 + k] + ai[r * 32 + k] * ai[r * 32 + k];
+          if (m2 > best) { best = m2; p = r; }
+        }
+        if (!(best > 0.0) || !isfinite(best)) { bad = true; break; }
+        __syncwarp();
+        if (p != k && active && r0 == 0) {
+          double t = ar[k * 32 + c]; ar[k * 32 + c] = ar[p * 32 + c]; ar[p * 32 + c] = t;
+          t = ai[k * 32 + c]; ai[k * 32 + c] = ai[p * 32 + c]; ai[p * 32 + c] = t;
+        }
+        __syncwarp();
+        cplx inv = {0.0, 0.0};
+        if (lane == 0) {
+          const double vr = ar[k * 32 + k], vi = ai[k * 32 + k];
+          const cplx d = cmul({dr, di}, {vr, vi});
+          int e2;
+          const double mag = frexp(fmax(fabs(d.re), fabs(d.im)), &e2);
+          (void)mag;
+          dr = ldexp(d.re, -e2);
+          di = ldexp(d.im, -e2);
+          dexp += e2;
+          if (p != k) { dr = -dr; di = -di; }
+          inv = cinv({vr, vi});
+        }
+        inv.re = __shfl_sync(0xffffffffu, inv.re, 0);
+        inv.im = __shfl_sync(0xffffffffu, inv.im, 0);
+        __syncwarp();
+        if (active && r0 == 0) {
+          const cplx v = cmul({ar[k * 32 + c], ai[k * 32 + c]}, inv);
+          ar[k * 32 + c] = v.re;
+          ai[k * 32 + c] = v.im;
+        }
+        __syncwarp();
+        if (active) {
+          const double kr = ar[k * 32 + c], ki = ai[k * 32 + c];
+          for (int r = r0; r < ns; r += RS) {
+            if (r == k) continue;
+            const double fr = ar[r * 32 + k], fi = ai[r * 32 + k];
+            // column k itself is read (fr, fi) by other lanes of this row: update it last
+            if (c == k) continue;
+            ar[r * 32 + c] -= fr * kr - fi * ki;
+            ai[r * 32 + c] -= fr * ki + fi * kr;
+          }
+        }
+        __syncwarp();
+        if (active && c == k)
+          for (int r = r0; r < ns; r += RS)
+            if (r != k) { ar[r * 32 + k] = 0.0; ai[r * 32 + k] = 0.0; }
+        __syncwarp();
+      }
+      if (lane == 0) {
+        // log det = log(d) + dexp ln 2
+        s_ld[sp][0] = 0.5 * log(dr * dr + di * di) + dexp * M_LN2;
+        s_ld[sp][1] = atan2(di, dr);
+        s_bad[sp] = bad ? 1 : 0;
+      }
+    }
+  }
+  __syncthreads();
+  const bool bad = s_bad[0] || s_bad[1];
+  // Theta_s = Phi_s O_s^{-1} in FP32; FP32 copy and split bf16 force-bias operand
+  for (int e = tid; e < NM; e += blockDim.x) {
+    const int n = e / M, i = e % M;
+    const int sp = n < nu ? 0 : 1, ns = sp ? nd : nu, n0 = sp ? nu : 0, b = n - n0;
+    const double* ar = aug + sp * 2 * kNsMax * 32;
+    const double* ai = ar + kNsMax * 32;
+    float re = 0.f, im = 0.f;
+    if (!bad)
+      for (int c = 0; c < ns; ++c) {
+        const float xr = (float)pr[(n0 + c) * M + i], xi = (float)pi[(n0 + c) * M + i];
+        const float orr = (float)ar[c * 32 + ns + b], oi = (float)ai[c * 32 + ns + b];
+        re = fmaf(xr, orr, fmaf(-xi, oi, re));
+        im = fmaf(xr, oi, fmaf(xi, orr, im));
+      }
+    const int64_t gi = wbase + e;
+    a.theta32[gi] = re;
+    a.theta32[plane + gi] = im;
+    const int64_t r0 = (int64_t)wk * a.Kp + e, r1 = (int64_t)(a.Nw + wk) * a.Kp + e;
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(re), h1 = __float2bfloat16_rn(im);
+    a.op_hi[r0] = h0;
+    a.op_lo[r0] = __float2bfloat16_rn(re - __bfloat162float(h0));
+    a.op_hi[r1] = h1;
+    a.op_lo[r1] = __float2bfloat16_rn(im - __bfloat162float(h1));
+    if (upd) {
+      a.phi[gi] = pr[e];
+      a.phi[plane + gi] = pi[e];
+    }
+  }
+  if (tid != 0) return;
+  const double ld_re = s_ld[0][0] + s_ld[1][0], ld_im = s_ld[0][1] + s_ld[1][1];
+  if (bad || !isfinite(ld_re) || !isfinite(ld_im)) {
+    atomicAdd(a.flags, 1);
+    if (upd || a.mode == OV_REFRESH) {
+      a.w[wk] = 0.0;
+      a.w[a.Nw + wk] = 0.0;
+      a.alive[wk] = 0;
+    }
+    return;
+  }
+  if (!upd) {
+    a.logO[wk] = ld_re;
+    a.logO[a.Nw + wk] = ld_im;
+    return;
+  }
+  const double* x = a.aux + 4 * (int64_t)wk;
+  const double lr_re = x[0] + ld_re - a.logO[wk];
+  const double lr_im = x[1] + ld_im - a.logO[a.Nw + wk];
+  const double li_re = lr_re + x[2] + a.log_shift;
+  const double li_im = lr_im + x[3];
+  a.logO[wk] = ld_re;
+  a.logO[a.Nw + wk] = ld_im;
+  if (a.free_proj) {
+    const double mag = exp(li_re);
+    double sn, cs;
+    sincos(li_im, &sn, &cs);
+    const cplx nw = cmul({a.w[wk], a.w[a.Nw + wk]}, {mag * cs, mag * sn});
+    a.w[wk] = nw.re;
+    a.w[a.Nw + wk] = nw.im;
+  } else {
+    const double nw = a.w[wk] * exp(li_re) * fmax(0.0, cos(lr_im));
+    if (nw > 0.0) {
+      a.w[wk] = nw;
+    } else {
+      a.w[wk] = 0.0;
+      a.alive[wk] = 0;
+    }
+    a.w[a.Nw + wk] = 0.0;
+  }
+}
+
+// Modified Gram-Schmidt, one warp per spin block: columns in order, each projection
+// removed one at a time (warp-shuffle inner products), then normalised.  FP64.
+__global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const int* __restrict__ alive,
+                                                 int M, int N, int n_up, int Nw) {
+  extern __shared__ double smg[];
+  const int wk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, sp = tid >> 5;
+  if (!alive[wk]) return;
+  const int NM = N * M;
+  double* vr = smg;
+  double* vi = smg + NM;
+  const int64_t plane = (int64_t)Nw * NM, base = (int64_t)wk * NM;
+  for (int e = tid; e < NM; e += blockDim.x) {
+    vr[e] = phi[base + e];
+    vi[e] = phi[plane + base + e];
+  }
+  __syncthreads();
+  const int n0 = sp == 0 ? 0 : n_up, n1 = sp == 0 ? n_up : N;
+  for (int j = n0; j < n1; ++j) {
+    double* xr = vr + j * M;
+    double* xi = vi + j * M;
+    for (int q = n0; q < j; ++q) {
+      const double* qr = vr + q * M;
+      const double* qi = vi + q * M;
+      double s0 = 0, s1 = 0;
+      for (int i = lane; i < M; i += 32) {
+        s0 += qr[i] * xr[i] + qi[i] * xi[i];
+        s1 += qr[i] * xi[i] - qi[i] * xr[i];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      for (int i = lane; i < M; i += 32) {
+        const double u = xr[i] - (s0 * qr[i] - s1 * qi[i]);
+        const double v = xi[i] - (s0 * qi[i] + s1 * qr[i]);
+        xr[i] = u;
+        xi[i] = v;
+      }
+      __syncwarp();
+    }
+    double s = 0;
+    for (int i = lane; i < M; i += 32) s += xr[i] * xr[i] + xi[i] * xi[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double inv = 1.0 / sqrt(s);
+    for (int i = lane; i < M; i += 32) {
+      xr[i] *= inv;
+      xi[i] *= inv;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = tid; e < NM; e += blockDim.x) {
+    phi[base + e] = vr[e];
+    phi[plane + base + e] = vi[e];
+  }
+}
+
+size_t smem_fast_overlap(const Ctx& c) {
+  return sizeof(double) * (2 * (size_t)c.N * c.M + 2 * 2 * kNsMax * 32);
+}
+size_t smem_mgs_warp(const Ctx& c) { return sizeof(double) * 2 * (size_t)c.N * c.M; }
+
+}  // namespace
+
+bool fast_walker_kernels_ok(const Ctx& c) {
+  return c.n_up <= kNsMax && c.N - c.n_up <= kNsMax && smem_fast_overlap(c) <= 200 * 1024;
+}
+
+cudaError_t prepare_fast_walker_kernels(const Ctx& c) {
+  static size_t have_o = 0, have_m = 0;
+  cudaError_t e;
+  if (smem_fast_overlap(c) > have_o) {
+    if ((e = cudaFuncSetAttribute(k_overlap_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_fast_overlap(c))) != cudaSuccess)
+      return e;
+    have_o = smem_fast_overlap(c);
+  }
+  if (smem_mgs_warp(c) > have_m) {
+    if ((e = cudaFuncSetAttribute(k_mgs_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_mgs_warp(c))) != cudaSuccess)
+      return e;
+    have_m = smem_mgs_warp(c);
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaStream_t s) {
+  FastOvArgs a;
+  a.src = src; a.phi = c.phi; a.theta32 = c.theta32;
+  a.op_hi = c.tc_Theta->hi; a.op_lo = c.tc_Theta->lo; a.Kp = c.tc_Theta->Kp;
+  a.psi = c.psi; a.logO = c.logO; a.w = c.w; a.alive = c.alive; a.aux = c.aux; a.flags = c.d_flags;
+  a.M = c.M; a.N = c.N; a.n_up = c.n_up; a.Nw = c.Nw; a.mode = mode;
+  a.free_proj = c.opt.mode == AFQMC_FREE;
+  a.log_shift = -c.opt.dt * (c.c_mf - c.e_trial);
+  k_overlap_fast<<<c.Nw, 256, smem_fast_overlap(c), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s) {
+  k_mgs_warp<<<c.Nw, 64, smem_mgs_warp(c), s>>>(c.phi, c.alive, c.M, c.N, c.n_up, c.Nw);
+  return cudaGetLastError();
+}
+
+}  // namespace afq
+
+namespace afq {
+namespace {
+
+// Fields for the split-precision step: the same Philox-4x32-10 bits and Box-Muller
+// transform as the FP64 kernel, evaluated in FP32; force bias, shifted fields and the
+// V_HS coefficients U = i sqrt(dt) c in FP32, written straight into the split bf16
+// operand of the tensor-core V_HS GEMM; the two scalar sums accumulate in FP64.
+struct FieldArgsM {
+  const double* rhobar;   // [2][Nw][X]
+  const double* rho_mf;   // [X]
+  const double* fields;   // [Nw][X] or null
+  __nv_bfloat16* u_hi;    // [(p, w)][Kp]
+  __nv_bfloat16* u_lo;
+  int Kp;
+  double* aux;            // [Nw][4]
+  const unsigned long long* step;
+  uint2 key;
+  uint32_t k0;
+  int X, Nw, free_proj;
+  float sqrt_dt, fb_cap;
+};
+
+__device__ __forceinline__ void put_split(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[i] = h;
+  lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__global__ void __launch_bounds__(128) k_fields_mixed(FieldArgsM a) {
+  __shared__ double red[4 * 4 + 4];
+  const int wk = blockIdx.x, X = a.X;
+  const uint32_t t = (uint32_t)(*a.step);
+  const int64_t row = (int64_t)wk * X, plane = (int64_t)a.Nw * X;
+  const int64_t o0 = (int64_t)wk * a.Kp, o1 = (int64_t)(a.Nw + wk) * a.Kp;
+  double acc[4] = {0, 0, 0, 0};
+  const int npair = (X + 1) / 2;
+  for (int j = threadIdx.x; j < npair; j += blockDim.x) {
+    float z[2];
+    if (a.fields == nullptr) {
+      const uint4 r = philox4x32_10(make_uint4((uint32_t)j, a.k0 + (uint32_t)wk, t, 0u), a.key);
+      const uint64_t hi64 = ((uint64_t)r.y << 32) | r.x;
+      const uint64_t lo64 = ((uint64_t)r.w << 32) | r.z;
+      const float u1 = (float)((double)((hi64 >> 11) + 1ull) * 0x1p-53);
+      const float u2 = (float)((double)(lo64 >> 11) * 0x1p-53);
+      const float rad = sqrtf(-2.0f * logf(u1));
+      float sn, cs;
+      sincospif(2.0f * u2, &sn, &cs);
+      z[0] = rad * cs;
+      z[1] = rad * sn;
+    }
+    float s0 = 0.f, s1 = 0.f, f0 = 0.f, f1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int g = 2 * j + q;
+      if (g >= X) break;
+      const float x = a.fields ? (float)a.fields[row + g] : z[q];
+      float xb_re = 0.f, xb_im = 0.f;
+      const float rm = (float)a.rho_mf[g];
+      if (!a.free_proj) {
+        xb_re = a.sqrt_dt * (float)a.rhobar[plane + row + g];
+        xb_im = -a.sqrt_dt * ((float)a.rhobar[row + g] - rm);
+        if (a.fb_cap > 0.f) {
+          const float m2 = xb_re * xb_re + xb_im * xb_im;
+          if (m2 > a.fb_cap * a.fb_cap) {
+            const float sc = a.fb_cap * rsqrtf(m2);
+            xb_re *= sc;
+            xb_im *= sc;
+          }
+        }
+      }
+      const float c_re = x - xb_re, c_im = -xb_im;
+      put_split(a.u_hi, a.u_lo, o0 + g, -a.sqrt_dt * c_im);
+      put_split(a.u_hi, a.u_lo, o1 + g, a.sqrt_dt * c_re);
+      s0 = fmaf(c_re, rm, s0);
+      s1 = fmaf(c_im, rm, s1);
+      f0 += x * xb_re - 0.5f * (xb_re * xb_re - xb_im * xb_im);
+      f1 += x * xb_im - xb_re * xb_im;
+    }
+    acc[0] += s0;
+    acc[1] += s1;
+    acc[2] += f0;
+    acc[3] += f1;
+  }
+  block_sum<4>(acc, red);
+  if (threadIdx.x == 0) {
+    double* o = a.aux + 4 * (int64_t)wk;
+    o[0] = (double)a.sqrt_dt * acc[1];
+    o[1] = -(double)a.sqrt_dt * acc[0];
+    o[2] = acc[2];
+    o[3] = acc[3];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fields_mixed(const Ctx& c, const double* fields, cudaStream_t s) {
+  FieldArgsM a;
+  a.rhobar = c.rhobar; a.rho_mf = c.rho_mf; a.fields = fields;
+  a.u_hi = c.tc_U->hi; a.u_lo = c.tc_U->lo; a.Kp = c.tc_U->Kp; a.aux = c.aux; a.step = c.d_step;
+  a.key = make_uint2((uint32_t)(c.opt.seed & 0xffffffffull), (uint32_t)(c.opt.seed >> 32));
+  a.k0 = (uint32_t)c.opt.walker_offset;
+  a.X = c.X; a.Nw = c.Nw; a.free_proj = c.opt.mode == AFQMC_FREE;
+  a.sqrt_dt = (float)c.sqrt_dt; a.fb_cap = (float)c.opt.fb_cap;
+  k_fields_mixed<<<c.Nw, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace afq

@@ -3,6 +3,7 @@
 // Taylor products, Gram-Schmidt, exchange trace) runs out of shared memory with
 // coalesced loads from the planar walker layout [2][Nw][N][M].
 #include <cmath>
+#include <cuda_bf16.h>
 #include "device_util.cuh"
 #include "internal.h"
 
@@ -24,6 +25,10 @@ constexpr int kThreads = 256;
 // A singular or non-finite overlap kills the walker (weight 0) and is counted.
 // ---------------------------------------------------------------------------
 struct OverlapArgs {
+  float* theta32;              // split-precision mode: Theta in FP32 [2][Nw][N][M]
+  __nv_bfloat16* op_hi;        // split-precision mode: force-bias operand rows [(p,w)][Kp]
+  __nv_bfloat16* op_lo;
+  int Kp;
   const double* src;   // [2][Nw][N][M]
   double* phi;         // [2][Nw][N][M]
   double* theta;       // [2][Nw][N][M]
@@ -37,6 +42,9 @@ struct OverlapArgs {
   double log_shift;    // -dt (C - E_T)
 };
 
+// MIXED: Theta = Phi O^{-1} is formed in FP32 (O, its inverse and log det stay FP64) and
+// written as FP32 plus the split bf16 operand of the force-bias tensor-core GEMM.
+template <bool MIXED>
 __global__ void __launch_bounds__(kThreads) k_overlap(OverlapArgs a) {
   extern __shared__ double sm[];
   const int wk = blockIdx.x, tid = threadIdx.x, M = a.M, N = a.N;
@@ -144,17 +152,37 @@ __global__ void __launch_bounds__(kThreads) k_overlap(OverlapArgs a) {
     // Theta_s[:, b] = sum_c Phi_s[:, c] Oinv[c][b]; copy Phi' into Phi for live updates
     for (int e = tid; e < ns * M; e += blockDim.x) {
       const int b = e / M, i = e % M;
-      double re = 0, im = 0;
-      if (!bad)
-        for (int c = 0; c < ns; ++c) {
-          const double xr = ph[c * M + i], xi = ph[nmax * M + c * M + i];
-          const double orr = ar[c * w2 + ns + b], oi = ai[c * w2 + ns + b];
-          re = fma(xr, orr, fma(-xi, oi, re));
-          im = fma(xr, oi, fma(xi, orr, im));
-        }
       const int64_t gi = wbase + (int64_t)(n0 + b) * M + i;
-      a.theta[gi] = re;
-      a.theta[plane + gi] = im;
+      if (MIXED) {
+        float re = 0.f, im = 0.f;
+        if (!bad)
+          for (int c = 0; c < ns; ++c) {
+            const float xr = (float)ph[c * M + i], xi = (float)ph[nmax * M + c * M + i];
+            const float orr = (float)ar[c * w2 + ns + b], oi = (float)ai[c * w2 + ns + b];
+            re = fmaf(xr, orr, fmaf(-xi, oi, re));
+            im = fmaf(xr, oi, fmaf(xi, orr, im));
+          }
+        a.theta32[gi] = re;
+        a.theta32[plane + gi] = im;
+        const int64_t col = (int64_t)(n0 + b) * M + i;
+        const int64_t r0 = (int64_t)wk * a.Kp + col, r1 = (int64_t)(a.Nw + wk) * a.Kp + col;
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(re), h1 = __float2bfloat16_rn(im);
+        a.op_hi[r0] = h0;
+        a.op_lo[r0] = __float2bfloat16_rn(re - __bfloat162float(h0));
+        a.op_hi[r1] = h1;
+        a.op_lo[r1] = __float2bfloat16_rn(im - __bfloat162float(h1));
+      } else {
+        double re = 0, im = 0;
+        if (!bad)
+          for (int c = 0; c < ns; ++c) {
+            const double xr = ph[c * M + i], xi = ph[nmax * M + c * M + i];
+            const double orr = ar[c * w2 + ns + b], oi = ai[c * w2 + ns + b];
+            re = fma(xr, orr, fma(-xi, oi, re));
+            im = fma(xr, oi, fma(xi, orr, im));
+          }
+        a.theta[gi] = re;
+        a.theta[plane + gi] = im;
+      }
       if (upd) {
         a.phi[gi] = ph[b * M + i];
         a.phi[plane + gi] = ph[nmax * M + b * M + i];
@@ -564,7 +592,8 @@ cudaError_t ensure_smem(F* f, int slot, size_t bytes) {
 // Called once per handle at setup, before any launch or graph capture.
 cudaError_t prepare_kernels(const Ctx& c) {
   cudaError_t e;
-  if ((e = ensure_smem(k_overlap, 0, smem_overlap(c))) != cudaSuccess) return e;
+  if ((e = ensure_smem(k_overlap<false>, 0, smem_overlap(c))) != cudaSuccess) return e;
+  if ((e = ensure_smem(k_overlap<true>, 7, smem_overlap(c))) != cudaSuccess) return e;
   if ((e = ensure_smem(k_mgs, 1, smem_mgs(c))) != cudaSuccess) return e;
   if ((e = ensure_smem(k_energy, 2, smem_energy(c))) != cudaSuccess) return e;
   const size_t st = smem_taylor(c);
@@ -578,6 +607,10 @@ cudaError_t prepare_kernels(const Ctx& c) {
 cudaError_t launch_overlap(const Ctx& c, const double* src, int mode, cudaStream_t s,
                            int n_walkers) {
   OverlapArgs a;
+  a.theta32 = c.theta32;
+  a.op_hi = c.tc_Theta ? c.tc_Theta->hi : nullptr;
+  a.op_lo = c.tc_Theta ? c.tc_Theta->lo : nullptr;
+  a.Kp = c.tc_Theta ? c.tc_Theta->Kp : 0;
   a.src = src; a.phi = c.phi; a.theta = c.theta; a.psi = c.psi; a.logO = c.logO; a.w = c.w;
   a.alive = c.alive; a.aux = c.aux; a.flags = c.d_flags;
   a.M = c.M; a.N = c.N; a.n_up = c.n_up; a.Nw = c.Nw; a.mode = mode;
@@ -586,7 +619,9 @@ cudaError_t launch_overlap(const Ctx& c, const double* src, int mode, cudaStream
   const int nmax = c.n_up > c.N - c.n_up ? c.n_up : c.N - c.n_up;
   const size_t smem = smem_overlap(c);
   (void)nmax;
-  k_overlap<<<n_walkers > 0 ? n_walkers : c.Nw, kThreads, smem, s>>>(a);
+  const int grid = n_walkers > 0 ? n_walkers : c.Nw;
+  if (c.theta32 && c.tc_Theta) k_overlap<true><<<grid, kThreads, smem, s>>>(a);
+  else k_overlap<false><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
