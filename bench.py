@@ -35,6 +35,12 @@ WORKLOADS = {
     "C2": dict(cfg="C2", n_walkers=2048, dt=0.005, repeats=11,
                desc="synthetic pair M=64, Nchol=320, neutral 8/8 vs ion 8/7, 2048 walkers per "
                     "system, dt=0.005, energy+MGS every 5 steps, 11 repeats"),
+    "C3": dict(cfg="C3", n_walkers=4096, dt=0.005, repeats=11,
+               desc="synthetic pair M=128, Nchol=768, neutral 16/16 vs ion 16/15, 4096 walkers "
+                    "per system, dt=0.005, energy+MGS every 5 steps, 11 repeats"),
+    "C4": dict(cfg="C4", n_walkers=2048, dt=0.005, repeats=11,
+               desc="uneven synthetic pair A: M=200, Nchol=1000, 9/9; B: M=190, Nchol=950, 8/8 "
+                    "(own Hamiltonian), 2048 walkers per system, dt=0.005, 11 repeats"),
 }
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (no tcgen05 FP64 kind; DFMA/DMMA pipe)
 
@@ -59,7 +65,7 @@ def parse():
     ap.add_argument("--coupling", default="moderate", choices=["literal", "moderate"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", choices=["vhs", "force_bias", "taylor", "energy"],
+    ap.add_argument("--kernel", choices=["vhs", "force_bias", "taylor", "energy", "overlap"],
                     help="profiling aid: set up the workload, take one step, then launch only "
                          "this kernel --reps times (no JSON line)")
     ap.add_argument("--walkers", type=int, default=None, help="override walkers per system")
@@ -215,7 +221,7 @@ def run_kernel(args, wl):
                    precision={"fp64": afq.FP64, "bf16x3": afq.BF16X3}[args.precision])
     A.propagate(1)
     which = {"vhs": afq.K_VHS, "force_bias": afq.K_FORCE_BIAS, "taylor": afq.K_TAYLOR,
-             "energy": afq.K_EXCHANGE}[args.kernel]
+             "energy": afq.K_EXCHANGE, "overlap": afq.K_OVERLAP}[args.kernel]
     ms = afq.afqmc_time_kernel(A.h, which, args.reps)
     torch.cuda.synchronize()
     print(f"{args.kernel}: {ms:.3f} ms per launch ({nw} walkers)")
@@ -273,34 +279,57 @@ def run_ours(args, wl, rank, world, local_rank):
     ms = main["ms"]
     value = world * nw * n_steps / (ms / 1e3)
 
-    # dominant contraction (V_HS), timed alone on this stream with CUDA events
+    # kernels timed alone on this stream with CUDA events: the path's time-dominant kernel
+    # (by its share of the step in the ncu launch list) and the dominant contraction, V_HS
     A, dA = main["A"], main["dA"]
-    M, X = dA["M"], dA["X"]
+    M, X, nu, nd = dA["M"], dA["X"], dA["n_up"], dA["n_dn"]
+    N, N2 = nu + nd, nu * nu + nd * nd
+    P = M * (M + 1) // 2
     vhs_ms = afq.afqmc_time_kernel(A.h, afq.K_VHS, 5, stream.cuda_stream)
     if args.precision == "fp64":
-        P = M * (M + 1) // 2
-        flops = 2.0 * P * X * (2 * nw)
-        achieved = flops / (vhs_ms / 1e3) / 1e12
+        vflops = 2.0 * P * X * (2 * nw)
         tr = traffic_for("gemm_f64.cu", "vhs_gemm_C2")
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                    "kernel": "k_gemm_f64_vhs (V_HS, packed symmetric L, FP64)",
-                    "algorithmic_flops_per_launch": flops, "ms_per_launch": vhs_ms,
-                    "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe); cuBLAS DGEMM measured 1.10"}
+        contraction = {"bound": "alu", "achieved": vflops / (vhs_ms / 1e3) / 1e12,
+                       "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "kernel": "k_gemm_f64_vhs (V_HS, packed symmetric L, FP64)",
+                       "algorithmic_flops_per_launch": vflops, "ms_per_launch": vhs_ms,
+                       "traffic": tr["dram_bytes_per_launch"] if tr else None}
+        # time-dominant kernel of the FP64 step: the Taylor exponential
+        t_ms = afq.afqmc_time_kernel(A.h, afq.K_TAYLOR, 5, stream.cuda_stream)
+        tflops = 6 * 8.0 * M * M * N * nw
+        ach = tflops / (t_ms / 1e3) / 1e12
+        trt = traffic_for("walker_kernels.cu", "taylor_f64_C2")
+        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS,
+                    "traffic": trt["dram_bytes_per_launch"] if trt else None,
+                    "kernel": "k_taylor (Taylor exponential, FP64; largest share of the FP64 step)",
+                    "algorithmic_flops_per_launch": tflops, "ms_per_launch": t_ms,
+                    "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe table); cuBLAS DGEMM measured 1.10"}
     else:
         useful = 2.0 * M * M * X * (2 * nw)
-        flops = 3.0 * useful     # hi*hi + hi*lo + lo*hi BF16 products
-        achieved = flops / (vhs_ms / 1e3) / 1e12
-        peak = BF16_PEAK_TFLOPS
+        vflops = 3.0 * useful     # hi*hi + hi*lo + lo*hi BF16 products
         tr = traffic_for("gemm_tc.cu", "vhs_tc_C2")
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak,
-                    "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                    "kernel": "k_gemm_bf16x3_tc (V_HS, split-BF16 tcgen05, full M^2 rows)",
-                    "algorithmic_flops_per_launch": flops, "useful_flops_per_launch": useful,
-                    "ms_per_launch": vhs_ms,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, kernel timed alone)"}
+        contraction = {"bound": "tensor", "achieved": vflops / (vhs_ms / 1e3) / 1e12,
+                       "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "kernel": "k_gemm_bf16x3_tc (V_HS, split-BF16 tcgen05, full M^2 rows)",
+                       "algorithmic_flops_per_launch": vflops, "useful_flops_per_launch": useful,
+                       "ms_per_launch": vhs_ms,
+                       "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                       "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, kernel timed alone)"}
+        # time-dominant kernel of the split-precision step: the FP64 overlap / inverse / det
+        o_ms = afq.afqmc_time_kernel(A.h, afq.K_OVERLAP, 5, stream.cuda_stream)
+        oflops = (4.0 * M * N2 + 8.0 * (nu ** 3 + nd ** 3)) * nw   # FP64: Psi^T Phi, Gauss-Jordan
+        ach = oflops / (o_ms / 1e3) / 1e12
+        tro = traffic_for("walker_fast.cu", "overlap_fast_C2")
+        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS,
+                    "traffic": tro["dram_bytes_per_launch"] if tro else None,
+                    "kernel": "k_overlap_fast (FP64 overlap, Gauss-Jordan inverse, log det; "
+                              "largest share of the split-precision step)",
+                    "algorithmic_flops_per_launch": oflops, "ms_per_launch": o_ms,
+                    "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe table)"}
+    contraction["frac"] = contraction["achieved"] / contraction["peak"]
+    roofline["contraction_vhs"] = contraction
     main["A"].close()
     main["B"].close()
 

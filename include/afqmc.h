@@ -212,10 +212,13 @@ afqmc_status afqmc_delta_E_stats(const double* dE, const double* taus, int n_mea
  * data, timed with CUDA events recorded on that stream, and stores the mean duration
  * of one launch in *ms.  which: AFQMC_K_VHS (V_HS contraction), AFQMC_K_FORCE_BIAS
  * (force-bias contraction), AFQMC_K_TAYLOR (Taylor exponential, on scratch memory),
- * AFQMC_K_EXCHANGE (local-energy kernel).  None of them changes the walkers.
+ * AFQMC_K_EXCHANGE (local-energy kernel), AFQMC_K_OVERLAP (overlap / inverse / log det /
+ * Theta kernel in its refresh form, which recomputes the same values from the current
+ * walkers).  None of them changes the walkers.
  * Synchronises the stream.  Errors: ARG, CUDA.
  */
-enum { AFQMC_K_VHS = 0, AFQMC_K_FORCE_BIAS = 1, AFQMC_K_TAYLOR = 2, AFQMC_K_EXCHANGE = 3 };
+enum { AFQMC_K_VHS = 0, AFQMC_K_FORCE_BIAS = 1, AFQMC_K_TAYLOR = 2, AFQMC_K_EXCHANGE = 3,
+       AFQMC_K_OVERLAP = 4 };
 afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms,
                                cudaStream_t stream);
 

@@ -552,7 +552,7 @@ afqmc_status afqmc_energy(afqmc_handle h, double* e_local, double* e_mixed, doub
 }
 
 afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, cudaStream_t s) {
-  if (!h || !ms || reps < 1 || which < 0 || which > 3) return AFQMC_ERR_ARG;
+  if (!h || !ms || reps < 1 || which < 0 || which > 4) return AFQMC_ERR_ARG;
   const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
   const int64_t NM = (int64_t)N * M;
   cudaEvent_t e0, e1;
@@ -572,6 +572,10 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
                                   h->d_tc_err, s);
         return afq::gemm_tn_f64(X, 2 * Nw, (int)NM, 1.0, h->Ltil, NM, 0, h->theta, NM, 0, 0.0,
                                 h->rhobar, X, 0, 1, s, afq::GEMM_FORCE_BIAS);
+      case AFQMC_K_OVERLAP:
+        if (h->theta32 && h->tc_Theta && afq::fast_walker_kernels_ok(*h))
+          return afq::launch_overlap_fast(*h, nullptr, afq::OV_REFRESH, s);
+        return afq::launch_overlap(*h, nullptr, afq::OV_REFRESH, s);
       case AFQMC_K_TAYLOR:
         if (h->phi32) return afq::launch_taylor_f32_best(*h, h->phi32, h->Avhs32, s);
         return afq::launch_taylor(*h, h->phi2, s);

@@ -102,13 +102,28 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
       int dexp = 0;
       bool bad = false;
       for (int k = 0; k < ns; ++k) {
-        int p = k;
-        double best = -1.0;
-        for (int r = k; r < ns; ++r) {
-          const double m2 = ar[r * 32 + k] * ar[r * 32 + k] + ai[r * 32 + k] * ai[r * 32 + k];
-          if (m2 > best) { best = m2; p = r; }
+        // pivot choice by magnitude only: FP32 compare, warp argmax (lowest row on ties)
+        float m2 = -1.f;
+        if (lane >= k && lane < ns) {
+          const float xr = (float)ar[lane * 32 + k], xi = (float)ai[lane * 32 + k];
+          m2 = xr * xr + xi * xi;
         }
-        if (!(best > 0.0) || !isfinite(best)) { bad = true; break; }
+        int p = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+          const float om = __shfl_xor_sync(0xffffffffu, m2, o);
+          const int op = __shfl_xor_sync(0xffffffffu, p, o);
+          if (om > m2 || (om == m2 && op < p)) { m2 = om; p = op; }
+        }
+        if (!(m2 > 0.f) || !isfinite(m2)) {
+          // tiny pivots that FP32 cannot resolve: fall back to the FP64 scan
+          double best = -1.0;
+          p = k;
+          for (int r = k; r < ns; ++r) {
+            const double d2 = ar[r * 32 + k] * ar[r * 32 + k] + ai[r * 32 + k] * ai[r * 32 + k];
+            if (d2 > best) { best = d2; p = r; }
+          }
+          if (!(best > 0.0) || !isfinite(best)) { bad = true; break; }
+        }
         __syncwarp();
         if (p != k && active && r0 == 0) {
           double t = ar[k * 32 + c]; ar[k * 32 + c] = ar[p * 32 + c]; ar[p * 32 + c] = t;

@@ -18,23 +18,31 @@ import numpy as np
 
 
 def _fock(h1, L, C_up, C_dn):
+    X, M, _ = L.shape
+    Lf = L.reshape(X, M * M)
     P = C_up @ C_up.T + C_dn @ C_dn.T
-    J = np.einsum("g,gij->ij", np.einsum("gij,ji->g", L, P), L)
+    J = (Lf.T @ (Lf @ P.T.reshape(M * M))).reshape(M, M)      # sum_g L_g tr(L_g P)
     out = []
     for C in (C_up, C_dn):
-        LC = L @ C  # [X, M, Ns]
-        K = np.einsum("gia,gja->ij", LC, LC)
-        out.append(h1 + J - K)
+        ns = C.shape[1]
+        if ns == 0:
+            out.append(h1 + J)
+            continue
+        LC = (L.reshape(X * M, M) @ C).reshape(X, M, ns)        # L_g C
+        W = LC.transpose(1, 0, 2).reshape(M, X * ns)
+        out.append(h1 + J - W @ W.T)                            # sum_g (L_g C)(L_g C)^T
     return out
 
 
-def hf_energy(h1, L, C_up, C_dn):
-    F_up, F_dn = _fock(h1, L, C_up, C_dn)
+def _energy(h1, F, C_up, C_dn):
     e = 0.0
-    for C, F in ((C_up, F_up), (C_dn, F_dn)):
-        P = C @ C.T
-        e += 0.5 * np.trace((h1 + F) @ P)
+    for C, Fs in zip((C_up, C_dn), F):
+        e += 0.5 * np.sum((h1 + Fs) * (C @ C.T))
     return float(e)
+
+
+def hf_energy(h1, L, C_up, C_dn):
+    return _energy(h1, _fock(h1, L, C_up, C_dn), C_up, C_dn)
 
 
 def scf_trial(h1, L, n_up: int, n_dn: int, max_iter: int = 60, tol: float = 1e-10,
@@ -57,10 +65,10 @@ def scf_trial(h1, L, n_up: int, n_dn: int, max_iter: int = 60, tol: float = 1e-1
     it = 0
     for it in range(1, max_iter + 1):
         F = _fock(h1, L, C[0], C[1])
+        e = _energy(h1, F, C[0], C[1])
         if restricted:
             Fa = 0.5 * (F[0] + F[1])
             F = [Fa, Fa]
-        e = hf_energy(h1, L, C[0], C[1])
         if e < best[0]:
             best = (e, [C[0].copy(), C[1].copy()])
         P = [C[0] @ C[0].T, C[1] @ C[1].T]
