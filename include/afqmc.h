@@ -68,6 +68,10 @@ typedef struct {
   double fb_cap;      /* |xbar_g| above fb_cap is scaled back to fb_cap; <= 0 disables      */
   int64_t walker_offset; /* global pair index of walker 0 (replicas on several GPUs take
                             disjoint ranges of k); 0 <= walker_offset, + Nw <= 2^32          */
+  int autotune;       /* AFQMC_BF16X3 only: 1 = time the kernel variants at setup on this
+                         handle's buffers and keep the fastest (default), 0 = defaults    */
+  const char* autotune_cache; /* NULL, or a JSON file of tuned choices keyed by kernel and
+                         shape; read at setup, rewritten when a new shape was timed        */
 } afqmc_options;
 
 typedef struct {
@@ -76,10 +80,13 @@ typedef struct {
   double e_trial;     /* E_T = E_L(psi_T), the trial (HF) energy used as the energy shift   */
   double c_mf;        /* C = -1/2 sum_g <rho_g>_T^2, scalar of the one-body part H_1        */
   int n_alive;        /* live walkers (synchronises the stream)                             */
+  int tuned_energy_walkers_per_cta; /* autotuned exchange-kernel variant, -1 if not tuned    */
+  int tuned_taylor_smem;            /* autotuned Taylor variant (1: A in shared memory), -1 */
 } afqmc_info;
 
 /* Fill *o with dt = 0.01, n_walkers = 128, taylor_order = 6, FP64, phaseless,
- * n_repeats = 1, seed = 1, fb_cap = 1.0, walker_offset = 0. */
+ * n_repeats = 1, seed = 1, fb_cap = 1.0, walker_offset = 0, autotune = 1,
+ * autotune_cache = NULL. */
 void afqmc_default_options(afqmc_options* o);
 
 const char* afqmc_status_string(afqmc_status s);
@@ -251,7 +258,10 @@ afqmc_status afqmc_local_energy_static(const double* h1, const double* L, const 
  * contraction kernels on given operands, C[n][m] = alpha sum_k A[m][k] B[n][k] with
  * A [Md][K], B [Nd][K] (row-major float64, host or device) and C [Nd][Md].
  * impl 0: FP64 kernel; impl 1: split-BF16 tensor-core kernel (hi/lo operands, three MMAs
- * per product, FP32 accumulation).  Allocates temporary device memory; synchronises.
+ * per product, FP32 accumulation); impl 2: self-test of the tensor-core kernel's bounded
+ * waits -- its TMA producer issues nothing, so the first wait expires after 20 ms and the
+ * call must return TIMEOUT with the CUDA context still usable.  Allocates temporary
+ * device memory; synchronises.
  * Errors: ARG, CUDA, TIMEOUT (a bounded wait inside the tensor-core kernel expired).
  */
 afqmc_status afqmc_test_gemm(int impl, int Md, int Nd, int K, const double* A, const double* B,

@@ -15,14 +15,16 @@ class AfqmcOptions(ctypes.Structure):
                 ("taylor_order", ctypes.c_int), ("precision", ctypes.c_int),
                 ("mode", ctypes.c_int), ("n_repeats", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("fb_cap", ctypes.c_double),
-                ("walker_offset", ctypes.c_int64)]
+                ("walker_offset", ctypes.c_int64), ("autotune", ctypes.c_int),
+                ("autotune_cache", ctypes.c_char_p)]
 
 
 class AfqmcInfo(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("X", ctypes.c_int), ("n_up", ctypes.c_int),
                 ("n_dn", ctypes.c_int), ("n_walkers", ctypes.c_int), ("n_repeats", ctypes.c_int),
                 ("step", ctypes.c_uint64), ("e_trial", ctypes.c_double),
-                ("c_mf", ctypes.c_double), ("n_alive", ctypes.c_int)]
+                ("c_mf", ctypes.c_double), ("n_alive", ctypes.c_int),
+                ("tuned_energy_walkers_per_cta", ctypes.c_int), ("tuned_taylor_smem", ctypes.c_int)]
 
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "numerical failure",

@@ -152,7 +152,7 @@ class System:
 
     def __init__(self, h1, L, trial, n_up, n_dn, dt=0.01, n_walkers=128, taylor_order=6,
                  mode=PHASELESS, n_repeats=1, seed=1, fb_cap=1.0, walker_offset=0,
-                 precision=FP64, stream=None):
+                 precision=FP64, autotune=True, autotune_cache=None, stream=None):
         h1 = np.ascontiguousarray(h1, dtype=np.float64)
         L = np.ascontiguousarray(L, dtype=np.float64)
         trial = np.ascontiguousarray(trial, dtype=np.float64)
@@ -163,6 +163,8 @@ class System:
         o.dt, o.n_walkers, o.taylor_order = float(dt), int(n_walkers), int(taylor_order)
         o.precision, o.mode, o.n_repeats = int(precision), int(mode), int(n_repeats)
         o.seed, o.fb_cap, o.walker_offset = int(seed), float(fb_cap), int(walker_offset)
+        o.autotune = 1 if autotune else 0
+        o.autotune_cache = autotune_cache.encode() if autotune_cache else None
         self.opt = o
         self.h = afqmc_setup(h1, L, trial, self.M, self.X, self.n_up, self.n_dn, o, stream)
 

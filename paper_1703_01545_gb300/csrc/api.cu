@@ -130,6 +130,9 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   // Theta of the current walkers in FP32 and as the split force-bias operand
   if (e == cudaSuccess && overlap_launch(h, nullptr, afq::OV_REFRESH, s) != AFQMC_OK)
     e = cudaErrorUnknown;
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Avhs32, 0, sizeof(float) * 2 * (size_t)Nw * MM, s);
+  if (e == cudaSuccess && h->opt.autotune)
+    e = afq::autotune_mixed(*h, h->opt.autotune_cache, s);
   if (own) {
     cudaStreamSynchronize(s);
     cudaFree(tmp);
@@ -261,6 +264,8 @@ void afqmc_default_options(afqmc_options* o) {
   o->seed = 1;
   o->fb_cap = 1.0;
   o->walker_offset = 0;
+  o->autotune = 1;
+  o->autotune_cache = nullptr;
 }
 
 const char* afqmc_status_string(afqmc_status s) {
@@ -295,6 +300,7 @@ afqmc_status afqmc_setup(afqmc_handle* out, const double* h1_in, const double* L
   afqmc_ctx* h = new afqmc_ctx();
   h->M = M; h->X = X; h->n_up = n_up; h->n_dn = n_dn; h->N = N;
   h->Nw = opt->n_walkers; h->R = opt->n_repeats; h->opt = *opt;
+  h->opt.autotune_cache = nullptr;   // used only inside setup (below), never kept
   h->P = afq::packed_size(M);
   h->sqrt_dt = std::sqrt(opt->dt);
   cudaGetDevice(&h->device);
@@ -424,7 +430,9 @@ afqmc_status afqmc_setup(afqmc_handle* out, const double* h1_in, const double* L
   }
   h->e_trial = et;
   if (opt->precision == AFQMC_BF16X3) {
+    h->opt.autotune_cache = opt->autotune_cache;
     afqmc_status ms = setup_mixed(h, s);
+    h->opt.autotune_cache = nullptr;
     if (ms != AFQMC_OK) return bail(ms);
     AFQ_SCK(cudaStreamSynchronize(s));
   }
@@ -481,6 +489,8 @@ afqmc_status afqmc_get_info(afqmc_handle h, afqmc_info* info, cudaStream_t s) {
   info->M = h->M; info->X = h->X; info->n_up = h->n_up; info->n_dn = h->n_dn;
   info->n_walkers = h->Nw; info->n_repeats = h->R; info->step = h->step;
   info->e_trial = h->e_trial; info->c_mf = h->c_mf;
+  info->tuned_energy_walkers_per_cta = h->tune_energy_wb;
+  info->tuned_taylor_smem = h->tune_taylor_smem;
   std::vector<int> al(h->Nw);
   AFQ_CK(cudaMemcpyAsync(al.data(), h->alive, sizeof(int) * h->Nw, cudaMemcpyDeviceToHost, s));
   AFQ_CK(cudaStreamSynchronize(s));
@@ -600,7 +610,7 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
 
 afqmc_status afqmc_test_gemm(int impl, int Md, int Nd, int K, const double* A, const double* B,
                              double alpha, double* C, cudaStream_t s) {
-  if (Md < 1 || Nd < 1 || K < 1 || !A || !B || !C || impl < 0 || impl > 1) return AFQMC_ERR_ARG;
+  if (Md < 1 || Nd < 1 || K < 1 || !A || !B || !C || impl < 0 || impl > 2) return AFQMC_ERR_ARG;
   double *dA = nullptr, *dB = nullptr, *dC = nullptr;
   float* fC = nullptr;
   __nv_bfloat16 *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
@@ -641,7 +651,13 @@ afqmc_status afqmc_test_gemm(int impl, int Md, int Nd, int K, const double* A, c
       afq::TcOperand oa, ob;
       if ((e = afq::tc_make_operand(oa, ah, al, Mp, Kp, 128)) != cudaSuccess) break;
       if ((e = afq::tc_make_operand(ob, bh, bl, Np, Kp, afq::tc_bn())) != cudaSuccess) break;
-      if ((e = afq::gemm_bf16x3(oa, ob, Md, Nd, (float)alpha, fC, Md, err, s)) != cudaSuccess) break;
+      if (impl == 2) {
+        if ((e = afq::gemm_bf16x3_wait_selftest(oa, ob, Md, Nd, fC, Md, err, 20000000ull, s)) !=
+            cudaSuccess)
+          break;
+      } else if ((e = afq::gemm_bf16x3(oa, ob, Md, Nd, (float)alpha, fC, Md, err, s)) != cudaSuccess) {
+        break;
+      }
       std::vector<float> hf((size_t)Md * Nd);
       if ((e = cudaMemcpyAsync(hf.data(), fC, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
       int herr = 0;

@@ -53,7 +53,8 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Bounded wait for the phase with the given parity; false (and *err set) on expiry.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err,
+                                          uint64_t limit_ns) {
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0;; ++it) {
     uint32_t ok;
@@ -65,7 +66,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
-    if ((it & 255u) == 255u && global_ns() - t0 > kWaitLimitNs) break;
+    if ((it & 255u) == 255u && global_ns() - t0 > limit_ns) break;
   }
   atomicOr(err, 1);
   return false;
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_bf16x3_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                      int Md, int Nd, int nkb, float alpha, TC* __restrict__ C, int64_t ldc,
-                     int* err) {
+                     int* err, uint64_t wait_ns, int skip_producer) {
   using Lay = TcLayout<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -175,11 +176,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer ----
+    // ---- TMA producer (skip_producer: self-test of the bounded waits, nothing is issued) ----
     int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
+    for (int kb = 0; kb < (skip_producer ? 0 : nkb); ++kb) {
       const int s = kb % STAGES, use = kb / STAGES;
-      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (use - 1) & 1, err)) break;
+      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (use - 1) & 1, err, wait_ns)) break;
       const uint32_t st = smem_u32(smem + s * Lay::STAGE_BYTES);
       const uint32_t fb = full0 + 8 * s;
       mbar_expect_tx(fb, Lay::STAGE_BYTES);
@@ -191,13 +192,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     // drain: every issued stage must have landed before the CTA may exit
     for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-      mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, err);
+      mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, err, wait_ns);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
     const uint32_t idesc = idesc_bf16<BN>();
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES, use = kb / STAGES;
-      if (!mbar_wait(full0 + 8 * s, use & 1, err)) break;
+      if (!mbar_wait(full0 + 8 * s, use & 1, err, wait_ns)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = smem_u32(smem + s * Lay::STAGE_BYTES);
       const uint64_t ah = sw128_desc(st), al = sw128_desc(st + Lay::A_BYTES);
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncwarp();
 
   // ---- epilogue: TMEM lanes 32*warp .. 32*warp+31 hold output rows m ----
-  const bool ok = mbar_wait(done, 0, err);
+  const bool ok = mbar_wait(done, 0, err, 2 * wait_ns);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncwarp();
   const int m = m0 + warp * 32 + lane;
@@ -275,12 +276,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 template <int BN, int STAGES, class TC>
 cudaError_t launch_tc(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha, TC* C,
-                      int64_t ldc, int* err, cudaStream_t s) {
+                      int64_t ldc, int* err, cudaStream_t s, uint64_t wait_ns = kWaitLimitNs,
+                      int skip_producer = 0) {
   using Lay = TcLayout<BN, STAGES>;
   dim3 grid((Md + BM - 1) / BM, (Nd + BN - 1) / BN);
   if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
   k_gemm_bf16x3_tc<BN, STAGES, TC><<<grid, NTHREADS, Lay::SMEM_BYTES, s>>>(
-      A.map_hi, A.map_lo, B.map_hi, B.map_lo, Md, Nd, A.Kp / BK, alpha, C, ldc, err);
+      A.map_hi, A.map_lo, B.map_hi, B.map_lo, Md, Nd, A.Kp / BK, alpha, C, ldc, err, wait_ns,
+      skip_producer);
   return cudaGetLastError();
 }
 
@@ -336,6 +339,15 @@ cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, 
   if (A.Kp != B.Kp || Md > A.rows || Nd > B.rows) return cudaErrorInvalidValue;
   if (Md <= 0 || Nd <= 0) return cudaSuccess;
   return launch_tc<128, 3, double>(A, B, Md, Nd, alpha, C, ldc, err, s);
+}
+
+// Self-test of the bounded waits: the producer issues nothing, so the MMA issuer's wait on
+// the first stage expires after `wait_ns`; the kernel must set *err and exit cleanly.
+cudaError_t gemm_bf16x3_wait_selftest(const TcOperand& A, const TcOperand& B, int Md, int Nd,
+                                      float* C, int64_t ldc, int* err, uint64_t wait_ns,
+                                      cudaStream_t s) {
+  if (A.Kp != B.Kp || Md > A.rows || Nd > B.rows || Md <= 0 || Nd <= 0) return cudaErrorInvalidValue;
+  return launch_tc<128, 3, float>(A, B, Md, Nd, 1.0f, C, ldc, err, s, wait_ns, 1);
 }
 
 // Once per process, before any launch or capture: the ring needs ~194 KB of shared memory.

@@ -59,6 +59,9 @@ struct Ctx {
   float* theta32 = nullptr;   // [2][Nw][N][M]  Theta in FP32 (split-precision mode)
   float* LtT = nullptr;       // [X][M][NPT]    Psi_s^T L_g transposed, spin-padded (FP32)
   int* d_tc_err = nullptr;    // set by a tensor-core kernel whose bounded wait expired
+  // autotuned variants (autotune.cpp); -1 = not tuned, use the default
+  int tune_energy_wb = -1;    // walkers per CTA of the FP32 exchange kernel: 2, 4 or 8
+  int tune_taylor_smem = -1;  // 1: A_w staged in shared memory, 0: read through L1
   // pair-run graph cache (owned; see pair.cu)
   void* pair_cache = nullptr;
   uint64_t uid = 0;           // unique per handle, so a cached graph never outlives its partner
@@ -95,6 +98,9 @@ cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, 
 cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,
                         double* C, int64_t ldc, int* err, cudaStream_t s);
 cudaError_t prepare_tc_kernels();
+cudaError_t gemm_bf16x3_wait_selftest(const TcOperand& A, const TcOperand& B, int Md, int Nd,
+                                      float* C, int64_t ldc, int* err, uint64_t wait_ns,
+                                      cudaStream_t s);
 // FP32 kernels of the split-precision step (mixed_kernels.cu)
 cudaError_t prepare_mixed_kernels(const Ctx& c);
 cudaError_t gemm_f32_from_f64(int Md, int Nd, int Kd, float alpha, const float* A, int64_t lda,
@@ -108,7 +114,13 @@ cudaError_t prepare_mixed_kernels2(const Ctx& c);
 cudaError_t build_LtT(const Ctx& c, float* LtT, cudaStream_t s);
 int64_t LtT_size(const Ctx& c);
 cudaError_t launch_energy_tiled(const Ctx& c, const float* theta32, const float* LtT,
-                                cudaStream_t s, int n_walkers = -1);
+                                cudaStream_t s, int n_walkers = -1, int wb = -1);
+bool energy_variant_ok(const Ctx& c, int wb);
+bool taylor_variant_ok(const Ctx& c, int use_smem);
+cudaError_t launch_taylor_f32_variant(const Ctx& c, float* phi32, const float* A32, cudaStream_t s,
+                                      int use_smem);
+// runtime autotuner (autotune.cpp): times the variants on the handle's buffers at setup
+cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s);
 cudaError_t launch_taylor_f32_best(const Ctx& c, float* phi32, const float* A32, cudaStream_t s);
 // latency-oriented FP64 walker kernels of the split-precision step (walker_fast.cu)
 bool fast_walker_kernels_ok(const Ctx& c);

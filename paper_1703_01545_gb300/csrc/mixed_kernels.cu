@@ -343,10 +343,11 @@ __global__ void __launch_bounds__(256) k_energy_f32_tiled(const float* __restric
   const int w0 = blockIdx.x * WB;
   float* thr = s4;                         // [WB][M][NPT]
   float* thi = thr + WB * M * NPT;
-  float* Ls = thi + WB * M * NPT;          // [GC][M][NPT]
+  const int LS = M * NPT + 4;              // per-g stride: +4 floats shifts banks, keeps float4
+  float* Ls = thi + WB * M * NPT;          // [GC][LS]
   const int nnp = PU * PU + PD * PD;
   const int nst = nnp + 1;                 // odd stride between (walker, g) blocks: no bank conflicts
-  float* Tr = Ls + GC * M * NPT;           // [WB][GC][nst]
+  float* Tr = Ls + GC * LS;                // [WB][GC][nst]
   float* Ti = Tr + WB * GC * nst;
   double* red = reinterpret_cast<double*>(Ti + WB * GC * nst + ((2 * WB * GC * nst) & 1));
   const int64_t plane = (int64_t)Nw * N * M;
@@ -383,7 +384,8 @@ __global__ void __launch_bounds__(256) k_energy_f32_tiled(const float* __restric
   const int items = WB * GC * ntiles;
   for (int g0 = 0; g0 < X; g0 += GC) {
     const int gc = min(GC, X - g0);
-    for (int e = tid; e < gc * M * NPT; e += blockDim.x) Ls[e] = LtT[(int64_t)g0 * M * NPT + e];
+    for (int e = tid; e < gc * M * NPT; e += blockDim.x)
+      Ls[(e / (M * NPT)) * LS + e % (M * NPT)] = LtT[(int64_t)g0 * M * NPT + e];
     __syncthreads();
     for (int it = tid; it < items; it += blockDim.x) {
       const int wl = it / (GC * ntiles), r = it % (GC * ntiles), gl = r / ntiles, t = r % ntiles;
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(256) k_energy_f32_tiled(const float* __restric
       for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) ar[x][y] = ai[x][y] = 0.f;
-      const float* Lp = Ls + gl * M * NPT + c0a;
+      const float* Lp = Ls + gl * LS + c0a;
       const float* Rp = thr + wl * M * NPT + c0b;
       const float* Ip = thi + wl * M * NPT + c0b;
       for (int i = 0; i < M; ++i) {
@@ -605,24 +607,24 @@ __global__ void __launch_bounds__(256) k_taylor_f32_smem(float* __restrict__ phi
 
 }  // namespace
 
-int energy_wb() { return 4; }
-
-size_t smem_energy_tiled(const Ctx& c, int GC) {
+size_t smem_energy_tiled(const Ctx& c, int GC, int WB) {
   const int nu = c.n_up, nd = c.N - c.n_up, PU = (nu + 3) & ~3, PD = (nd + 3) & ~3, NPT = PU + PD;
-  const int WB = energy_wb();
   const size_t nst = (size_t)PU * PU + (size_t)PD * PD + 1;
-  return sizeof(float) * (2 * (size_t)WB * c.M * NPT + (size_t)GC * c.M * NPT + 2 * WB * GC * nst + 2) +
+  return sizeof(float) * (2 * (size_t)WB * c.M * NPT + (size_t)GC * ((size_t)c.M * NPT + 4) +
+                          2 * WB * GC * nst + 2) +
          sizeof(double) * 40;
 }
 
-int energy_gc(const Ctx& c) {
+int energy_gc(const Ctx& c, int WB) {
   const int nu = c.n_up, nd = c.N - c.n_up, PU = (nu + 3) & ~3, PD = (nd + 3) & ~3;
   const int ntiles = (PU / 4) * (PU / 4) + (PD / 4) * (PD / 4);
-  int gc = 256 / (energy_wb() * ntiles);
+  int gc = 256 / (WB * ntiles);
   if (gc < 1) gc = 1;
-  while (gc > 1 && smem_energy_tiled(c, gc) > 200 * 1024) --gc;
+  while (gc > 1 && smem_energy_tiled(c, gc, WB) > 200 * 1024) --gc;
   return gc;
 }
+
+bool energy_wb_ok(const Ctx& c, int WB) { return smem_energy_tiled(c, energy_gc(c, WB), WB) <= 200 * 1024; }
 
 size_t smem_taylor_smem(const Ctx& c) {
   const size_t NP = (c.N + 3) & ~3, MP = (c.M + 1) & ~1;
@@ -635,14 +637,19 @@ bool taylor_smem_ok(const Ctx& c) {
 }
 
 cudaError_t prepare_mixed_kernels2(const Ctx& c) {
-  static size_t have_e = 0, have_t = 0;
+  static size_t have_e[3] = {0, 0, 0}, have_t = 0;
   cudaError_t e;
-  const size_t se = smem_energy_tiled(c, energy_gc(c));
-  if (se > have_e) {
-    if ((e = cudaFuncSetAttribute(k_energy_f32_tiled<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)se)) != cudaSuccess)
-      return e;
-    have_e = se;
+  const int wbs[3] = {2, 4, 8};
+  for (int q = 0; q < 3; ++q) {
+    if (!energy_wb_ok(c, wbs[q])) continue;
+    const size_t se = smem_energy_tiled(c, energy_gc(c, wbs[q]), wbs[q]);
+    if (se > have_e[q]) {
+      auto f = q == 0 ? k_energy_f32_tiled<2> : q == 1 ? k_energy_f32_tiled<4> : k_energy_f32_tiled<8>;
+      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se)) !=
+          cudaSuccess)
+        return e;
+      have_e[q] = se;
+    }
   }
   if (taylor_smem_ok(c)) {
     const size_t st = smem_taylor_smem(c);
@@ -670,16 +677,35 @@ int64_t LtT_size(const Ctx& c) {
 }
 
 cudaError_t launch_energy_tiled(const Ctx& c, const float* theta32, const float* LtT,
-                                cudaStream_t s, int n_walkers) {
+                                cudaStream_t s, int n_walkers, int wb) {
   const int nw = n_walkers > 0 ? n_walkers : c.Nw;
-  const int GC = energy_gc(c), WB = energy_wb();
-  k_energy_f32_tiled<4><<<(nw + WB - 1) / WB, 256, smem_energy_tiled(c, GC), s>>>(
-      theta32, LtT, c.htil, c.eloc, c.M, c.N, c.n_up, c.X, nw, GC);
+  int WB = wb > 0 ? wb : (c.tune_energy_wb > 0 ? c.tune_energy_wb : 4);
+  if (!energy_wb_ok(c, WB)) WB = 2;
+  const int GC = energy_gc(c, WB);
+  const size_t sm = smem_energy_tiled(c, GC, WB);
+  const int grid = (nw + WB - 1) / WB;
+  if (WB == 2)
+    k_energy_f32_tiled<2><<<grid, 256, sm, s>>>(theta32, LtT, c.htil, c.eloc, c.M, c.N, c.n_up, c.X, nw, GC);
+  else if (WB == 8)
+    k_energy_f32_tiled<8><<<grid, 256, sm, s>>>(theta32, LtT, c.htil, c.eloc, c.M, c.N, c.n_up, c.X, nw, GC);
+  else
+    k_energy_f32_tiled<4><<<grid, 256, sm, s>>>(theta32, LtT, c.htil, c.eloc, c.M, c.N, c.n_up, c.X, nw, GC);
+  return cudaGetLastError();
+}
+
+bool energy_variant_ok(const Ctx& c, int wb) { return energy_wb_ok(c, wb); }
+bool taylor_variant_ok(const Ctx& c, int use_smem) { return use_smem ? taylor_smem_ok(c) : true; }
+
+cudaError_t launch_taylor_f32_variant(const Ctx& c, float* phi32, const float* A32, cudaStream_t s,
+                                      int use_smem) {
+  if (!use_smem || !taylor_smem_ok(c)) return launch_taylor_f32(c, phi32, A32, s);
+  k_taylor_f32_smem<<<c.Nw, 256, smem_taylor_smem(c), s>>>(phi32, A32, c.M, c.N, c.Nw,
+                                                           c.opt.taylor_order);
   return cudaGetLastError();
 }
 
 cudaError_t launch_taylor_f32_best(const Ctx& c, float* phi32, const float* A32, cudaStream_t s) {
-  if (!taylor_smem_ok(c)) return launch_taylor_f32(c, phi32, A32, s);
+  if (c.tune_taylor_smem == 0 || !taylor_smem_ok(c)) return launch_taylor_f32(c, phi32, A32, s);
   k_taylor_f32_smem<<<c.Nw, 256, smem_taylor_smem(c), s>>>(phi32, A32, c.M, c.N, c.Nw,
                                                            c.opt.taylor_order);
   return cudaGetLastError();

@@ -41,6 +41,11 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   double* pr = smo;            // [N][M]
   double* pi = pr + NM;        // [N][M]
   double* aug = pi + NM;       // spin s at aug + s * 2 * 16 * 32: re [16][32], im [16][32]
+  // FP32 copies for Theta: converting once here keeps double->float conversions (which run
+  // on the FP64 pipe) off the Theta loop
+  float* pfr = reinterpret_cast<float*>(aug + 2 * 2 * kNsMax * 32);  // [N][M]
+  float* pfi = pfr + NM;
+  float* invf = pfi + NM;      // spin s at invf + s * 2 * 16 * 16: re [16][16], im [16][16]
   __shared__ double s_ld[2][2];
   __shared__ int s_bad[2];
   const bool live = a.alive[wk] != 0;
@@ -48,8 +53,11 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   const double* src = upd ? a.src : a.phi;
   const int64_t plane = (int64_t)a.Nw * NM, wbase = (int64_t)wk * NM;
   for (int e = tid; e < NM; e += blockDim.x) {
-    pr[e] = src[wbase + e];
-    pi[e] = src[plane + wbase + e];
+    const double xr = src[wbase + e], xi = src[plane + wbase + e];
+    pr[e] = xr;
+    pi[e] = xi;
+    pfr[e] = (float)xr;
+    pfi[e] = (float)xi;
   }
   if (tid < 2) { s_ld[tid][0] = 0.0; s_ld[tid][1] = 0.0; s_bad[tid] = 0; }
   __syncthreads();
@@ -179,17 +187,27 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   }
   __syncthreads();
   const bool bad = s_bad[0] || s_bad[1];
+  for (int e = tid; e < nn; e += blockDim.x) {   // O^{-1} blocks to FP32, once
+    int sp = 0, r, c, ns = nu;
+    if (e < nu * nu) { r = e / nu; c = e % nu; }
+    else { sp = 1; ns = nd; r = (e - nu * nu) / nd; c = (e - nu * nu) % nd; }
+    const double* ar = aug + sp * 2 * kNsMax * 32;
+    float* fr = invf + sp * 2 * kNsMax * kNsMax;
+    fr[r * kNsMax + c] = (float)ar[r * 32 + ns + c];
+    fr[kNsMax * kNsMax + r * kNsMax + c] = (float)ar[kNsMax * 32 + r * 32 + ns + c];
+  }
+  __syncthreads();
   // Theta_s = Phi_s O_s^{-1} in FP32; FP32 copy and split bf16 force-bias operand
   for (int e = tid; e < NM; e += blockDim.x) {
     const int n = e / M, i = e % M;
     const int sp = n < nu ? 0 : 1, ns = sp ? nd : nu, n0 = sp ? nu : 0, b = n - n0;
-    const double* ar = aug + sp * 2 * kNsMax * 32;
-    const double* ai = ar + kNsMax * 32;
+    const float* fr = invf + sp * 2 * kNsMax * kNsMax;
+    const float* fi = fr + kNsMax * kNsMax;
     float re = 0.f, im = 0.f;
     if (!bad)
       for (int c = 0; c < ns; ++c) {
-        const float xr = (float)pr[(n0 + c) * M + i], xi = (float)pi[(n0 + c) * M + i];
-        const float orr = (float)ar[c * 32 + ns + b], oi = (float)ai[c * 32 + ns + b];
+        const float xr = pfr[(n0 + c) * M + i], xi = pfi[(n0 + c) * M + i];
+        const float orr = fr[c * kNsMax + b], oi = fi[c * kNsMax + b];
         re = fmaf(xr, orr, fmaf(-xi, oi, re));
         im = fmaf(xr, oi, fmaf(xi, orr, im));
       }
@@ -307,7 +325,8 @@ __global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const
 }
 
 size_t smem_fast_overlap(const Ctx& c) {
-  return sizeof(double) * (2 * (size_t)c.N * c.M + 2 * 2 * kNsMax * 32);
+  return sizeof(double) * (2 * (size_t)c.N * c.M + 2 * 2 * kNsMax * 32) +
+         sizeof(float) * (2 * (size_t)c.N * c.M + 2 * 2 * kNsMax * kNsMax);
 }
 size_t smem_mgs_warp(const Ctx& c) { return sizeof(double) * 2 * (size_t)c.N * c.M; }
 

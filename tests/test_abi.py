@@ -46,10 +46,11 @@ def test_struct_layout_matches_header(tmp_path):
         pytest.skip("no C compiler")
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "afqmc.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(afqmc_options),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(afqmc_options),'
                    ' offsetof(afqmc_options, seed), offsetof(afqmc_options, walker_offset),'
+                   ' offsetof(afqmc_options, autotune_cache),'
                    ' sizeof(afqmc_info), offsetof(afqmc_info, step), offsetof(afqmc_info, c_mf),'
-                   ' offsetof(afqmc_info, n_alive)); return 0;}\n')
+                   ' offsetof(afqmc_info, n_alive), offsetof(afqmc_info, tuned_taylor_smem)); return 0;}\n')
     exe = tmp_path / "layout"
     cuda_inc = "/usr/local/cuda/include"
     r = subprocess.run([cc, "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, str(src), "-o",
@@ -57,8 +58,9 @@ def test_struct_layout_matches_header(tmp_path):
     assert r.returncode == 0, r.stderr
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     O, I = _lib.AfqmcOptions, _lib.AfqmcInfo
-    want = [ctypes.sizeof(O), O.seed.offset, O.walker_offset.offset, ctypes.sizeof(I), I.step.offset,
-            I.c_mf.offset, I.n_alive.offset]
+    want = [ctypes.sizeof(O), O.seed.offset, O.walker_offset.offset, O.autotune_cache.offset,
+            ctypes.sizeof(I), I.step.offset,
+            I.c_mf.offset, I.n_alive.offset, I.tuned_taylor_smem.offset]
     assert got == want
 
 

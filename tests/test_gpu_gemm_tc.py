@@ -47,3 +47,21 @@ def test_contraction_kernels_against_numpy(Md, Nd, K):
     assert np.all(err <= bound), (err / bound).max()
     # far better than one BF16 product: the split really carries the low bits
     assert np.median(err / np.maximum(np.abs(ref), 1e-300)) < 1e-4
+
+
+def test_bounded_wait_expires_cleanly_and_context_survives():
+    """Failure detection without a GPU fault: a wait on a barrier that nothing completes
+    expires (20 ms), the kernel reports it, frees its tensor memory and returns; the same
+    process then runs a normal tensor-core GEMM correctly."""
+    need_gpu()
+    from paper_1703_01545_gb300 import _lib
+    lib = _lib.load()
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((128, 64))
+    B = rng.standard_normal((128, 64))
+    code, _ = run(lib, 2, A, B)
+    assert code == 5          # AFQMC_ERR_TIMEOUT
+    code, C = run(lib, 1, A, B)
+    assert code == 0
+    ref = B @ A.T
+    assert np.all(np.abs(C - ref) <= (2.0 ** -15 + 64 * 2.0 ** -23) * (np.abs(B) @ np.abs(A).T))

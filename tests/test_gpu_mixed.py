@@ -93,3 +93,30 @@ def test_mixed_pair_delta_E_within_0p1_mHa_of_fp64():
     assert abs(m["dE_sigma"] / f["dE_sigma"] - 1) < 0.05
     # per-tau means over the repeats stay close (single-repeat values drift further apart)
     assert np.abs(dE_m.mean(axis=1) - dE_f.mean(axis=1)).max() < 5e-4
+
+
+def test_autotuner_picks_valid_variants_and_persists(tmp_path):
+    afq = need_gpu()
+    d = system_data("C2", "A", "moderate")
+    cache = tmp_path / "tune.json"
+    s1 = gpu_sys(afq, d, 512, 0.005, afq.BF16X3)
+    s1.close()
+    s2 = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=0.005, n_walkers=512,
+                    precision=afq.BF16X3, autotune_cache=str(cache))
+    info = s2.info()
+    assert info.tuned_energy_walkers_per_cta in (2, 4, 8)
+    assert info.tuned_taylor_smem in (0, 1)
+    text = cache.read_text()
+    assert "energy_wb:M64X320u8d8w512" in text and "taylor_smem" in text
+    s2.close()
+    # a second setup of the same shape reads the choices back
+    s3 = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=0.005, n_walkers=512,
+                    precision=afq.BF16X3, autotune_cache=str(cache))
+    i3 = s3.info()
+    assert (i3.tuned_energy_walkers_per_cta, i3.tuned_taylor_smem) == \
+        (info.tuned_energy_walkers_per_cta, info.tuned_taylor_smem)
+    s3.close()
+    s4 = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=0.005, n_walkers=512,
+                    precision=afq.FP64)
+    assert s4.info().tuned_energy_walkers_per_cta == -1
+    s4.close()
