@@ -203,6 +203,32 @@ afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n_steps,
                                 double* tau_at_min, cudaStream_t stream);
 
 /*
+ * afqmc_set_tangent -- tangent-mode (forward) derivative along a one-body perturbation
+ * h1 -> h1 + lambda P of Eq. 1, with the fields and the trial held fixed: the paper has no
+ * derivative; this gives d/dlambda of the mixed estimate of Eq. 7 (with Eq. 10) along one
+ * field realisation.  P [M][M] symmetric, host or device; NULL switches tangent mode off.
+ * FP64 phaseless handles only (ERR_ARG otherwise).  Resets dPhi = 0 and d log w = 0.
+ * While on, afqmc_propagate and afqmc_orthonormalise also advance the tangents:
+ *   e^{-dt K/2} -> its Frechet derivative along -dt P/2 (2M x 2M block exponential),
+ *   Taylor terms by the product rule, d log O = tr(O^{-1} Psi^T dPhi),
+ *   dTheta = (dPhi - Theta Psi^T dPhi) O^{-1}, the force bias through its cap,
+ *   d log w += Re d log I - tan(arg R) Im d log R while cos(arg R) > 0 (0 once dead),
+ *   Gram-Schmidt applies its column operations to dPhi.
+ * afqmc_pair_delta_E refuses tangent handles (STATE).  Synchronises.
+ * Errors: ARG, NOMEM, CUDA.
+ */
+afqmc_status afqmc_set_tangent(afqmc_handle h, const double* P, cudaStream_t stream);
+
+/* afqmc_energy_tangent -- per repeat r: e_mixed[r] = sum w Re E_L / sum w and
+ * de_mixed[r] = its d/dlambda; de_local [2][Nw] (or NULL): dE_L of every walker.
+ * Synchronises.  Errors: STATE (tangent mode off), CUDA. */
+afqmc_status afqmc_energy_tangent(afqmc_handle h, double* de_local, double* e_mixed,
+                                  double* de_mixed, cudaStream_t stream);
+
+/* afqmc_get_tangent_state -- d log w [Nw] of every walker.  Synchronises. */
+afqmc_status afqmc_get_tangent_state(afqmc_handle h, double* dlogw, cudaStream_t stream);
+
+/*
  * afqmc_delta_E_stats -- host-only statistics of Sec. II.B (no GPU needed).
  *   dE [n_meas][R] energy differences per measurement and repeat, taus [n_meas].
  *   mean_tau, se_tau [n_meas] (may be NULL): mean and standard error sd/sqrt(R) per tau.

@@ -50,6 +50,9 @@ SIGNATURES = {
     "afqmc_delta_E_stats": (ctypes.c_int, [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            VP, VP, VP]),
     "afqmc_reblock_error": (ctypes.c_double, [VP, ctypes.c_int]),
+    "afqmc_set_tangent": (ctypes.c_int, [VP, VP, VP]),
+    "afqmc_energy_tangent": (ctypes.c_int, [VP, VP, VP, VP, VP]),
+    "afqmc_get_tangent_state": (ctypes.c_int, [VP, VP, VP]),
     "afqmc_local_energy_static": (ctypes.c_int, [VP, VP, VP, VP, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, VP,
                                                  VP]),

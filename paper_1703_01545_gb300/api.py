@@ -209,6 +209,26 @@ class System:
         return dict(phi=phi[0] + 1j * phi[1], logO=lo[:nw] + 1j * lo[nw:],
                     w=w[:nw] + 1j * w[nw:], alive=al.astype(bool))
 
+    def set_tangent(self, P):
+        """Tangent mode along h1 -> h1 + lambda P (None switches it off)."""
+        Pm = None if P is None else np.ascontiguousarray(P, dtype=np.float64)
+        _check(_lib.load().afqmc_set_tangent(self.h, _ptr(Pm), _stream(None)), self.h,
+               "afqmc_set_tangent")
+
+    def energy_tangent(self):
+        """(E_mixed [R], dE_mixed/dlambda [R], dE_L/dlambda [Nw] complex)."""
+        de = np.empty(2 * self.n_walkers)
+        em, dm = np.empty(self.n_repeats), np.empty(self.n_repeats)
+        _check(_lib.load().afqmc_energy_tangent(self.h, _ptr(de), _ptr(em), _ptr(dm),
+                                                _stream(None)), self.h, "afqmc_energy_tangent")
+        return em, dm, de[:self.n_walkers] + 1j * de[self.n_walkers:]
+
+    def tangent_state(self):
+        d = np.empty(self.n_walkers)
+        _check(_lib.load().afqmc_get_tangent_state(self.h, _ptr(d), _stream(None)), self.h,
+               "afqmc_get_tangent_state")
+        return d
+
     def set_walkers(self, phi, w=None):
         phi = np.asarray(phi)
         p = np.ascontiguousarray(np.stack([phi.real, phi.imag]), dtype=np.float64)

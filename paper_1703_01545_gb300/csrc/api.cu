@@ -69,6 +69,9 @@ void free_ctx(Ctx* h) {
       if (op->lo) cudaFree(op->lo);
       delete op;
     }
+  for (double* b : {h->Bneg, h->dexpK, h->htilP, h->dphi, h->dphi2, h->dtheta, h->drhobar, h->dU,
+                    h->dAvhs, h->dlogO, h->dlogw, h->daux, h->deloc, h->desum})
+    if (b) cudaFree(b);
   for (float* b : {h->Avhs32, h->phi32, h->expK32, h->Ltil32, h->theta32, h->LtT})
     if (b) cudaFree(b);
   if (h->d_tc_err) cudaFree(h->d_tc_err);
@@ -181,8 +184,41 @@ afqmc_status check_tc(Ctx* h) {
 
 afqmc_status step_launch_mixed(Ctx* h, const double* fields_t, cudaStream_t s);
 
+// One FP64 step of the walkers and their tangents along h1 -> h1 + lambda P.
+afqmc_status step_launch_tangent(Ctx* h, const double* fields_t, cudaStream_t s) {
+  const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
+  const int64_t NM = (int64_t)N * M;
+  AFQ_CK(afq::gemm_tn_f64(X, 2 * Nw, (int)NM, 1.0, h->Ltil, NM, 0, h->theta, NM, 0, 0.0,
+                          h->rhobar, X, 0, 1, s, afq::GEMM_FORCE_BIAS));
+  AFQ_CK(afq::gemm_tn_f64(X, 2 * Nw, (int)NM, 1.0, h->Ltil, NM, 0, h->dtheta, NM, 0, 0.0,
+                          h->drhobar, X, 0, 1, s, afq::GEMM_FORCE_BIAS));
+  AFQ_CK(afq::launch_fields_tan(*h, fields_t, s));
+  AFQ_CK(afq::gemm_tn_f64((int)h->P, 2 * Nw, X, 1.0, h->Lt, X, 0, h->U, X, 0, 0.0, h->Avhs,
+                          h->P, 0, 1, s, afq::GEMM_VHS));
+  AFQ_CK(afq::gemm_tn_f64((int)h->P, 2 * Nw, X, 1.0, h->Lt, X, 0, h->dU, X, 0, 0.0, h->dAvhs,
+                          h->P, 0, 1, s, afq::GEMM_VHS));
+  const int cols = 2 * Nw * N;
+  AFQ_CK(afq::gemm_tn_f64(M, cols, M, 1.0, h->expK, M, 0, h->phi, M, 0, 0.0, h->phi2, M, 0, 1, s,
+                          afq::GEMM_ONEBODY));
+  AFQ_CK(afq::gemm_tn_f64(M, cols, M, 1.0, h->dexpK, M, 0, h->phi, M, 0, 0.0, h->dphi2, M, 0, 1, s,
+                          afq::GEMM_ONEBODY));
+  AFQ_CK(afq::gemm_tn_f64(M, cols, M, 1.0, h->expK, M, 0, h->dphi, M, 0, 1.0, h->dphi2, M, 0, 1, s,
+                          afq::GEMM_ONEBODY));
+  AFQ_CK(afq::launch_taylor_tan(*h, s));
+  AFQ_CK(afq::gemm_tn_f64(M, cols, M, 1.0, h->expK, M, 0, h->phi2, M, 0, 0.0, h->theta, M, 0, 1, s,
+                          afq::GEMM_ONEBODY));
+  AFQ_CK(afq::gemm_tn_f64(M, cols, M, 1.0, h->dexpK, M, 0, h->phi2, M, 0, 0.0, h->dtheta, M, 0, 1, s,
+                          afq::GEMM_ONEBODY));
+  AFQ_CK(afq::gemm_tn_f64(M, cols, M, 1.0, h->expK, M, 0, h->dphi2, M, 0, 1.0, h->dtheta, M, 0, 1, s,
+                          afq::GEMM_ONEBODY));
+  AFQ_CK(afq::launch_overlap_tan(*h, afq::OV_UPDATE, s));
+  AFQ_CK(afq::launch_step_advance(*h, s));
+  return AFQMC_OK;
+}
+
 // One propagation step of every walker of system h (Eqs. 3-5, 8-9, 11, hybrid weight).
 afqmc_status step_launch(Ctx* h, const double* fields_t, cudaStream_t s) {
+  if (h->tangent_on) return step_launch_tangent(h, fields_t, s);
   if (h->opt.precision == AFQMC_BF16X3) return step_launch_mixed(h, fields_t, s);
   const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
   const int64_t NM = (int64_t)N * M;
@@ -218,6 +254,11 @@ afqmc_status overlap_launch(Ctx* h, const double* src, int mode, cudaStream_t s)
 }
 
 afqmc_status ortho_launch(Ctx* h, cudaStream_t s) {
+  if (h->tangent_on) {
+    AFQ_CK(afq::launch_mgs_tan(*h, s));
+    AFQ_CK(afq::launch_overlap_tan(*h, afq::OV_REFRESH, s));
+    return AFQMC_OK;
+  }
   if (h->theta32 && afq::fast_walker_kernels_ok(*h)) {
     AFQ_CK(afq::launch_mgs_warp(*h, s));
   } else {
@@ -319,6 +360,7 @@ afqmc_status afqmc_setup(afqmc_handle* out, const double* h1_in, const double* L
   AFQ_ALLOC(h->htil, NM);
   AFQ_ALLOC(h->psi, NM);
   AFQ_ALLOC(h->expK, (int64_t)M * M);
+  AFQ_ALLOC(h->Bneg, (int64_t)M * M);
   AFQ_ALLOC(h->rho_mf, X);
   AFQ_ALLOC(h->phi, 2 * Nw * NM);
   AFQ_ALLOC(h->phi2, 2 * Nw * NM);
@@ -412,6 +454,7 @@ afqmc_status afqmc_setup(afqmc_handle* out, const double* h1_in, const double* L
     std::swap(E0, E1);
   }
   AFQ_SCK(cudaMemcpyAsync(h->expK, E0, sizeof(double) * M * M, cudaMemcpyDeviceToDevice, s));
+  AFQ_SCK(cudaMemcpyAsync(h->Bneg, Kb, sizeof(double) * M * M, cudaMemcpyDeviceToDevice, s));
   // walkers = trial, w = 1; trial energy E_T = E_L(psi_T)
   AFQ_SCK(afq::launch_broadcast_walkers(h->psi, h->phi, (int)Nw, (int)NM, s));
   AFQ_SCK(afq::launch_init_weights(h->w, h->alive, nullptr, (int)Nw, s));
@@ -605,6 +648,150 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_fail(h, "afqmc_time_kernel", e);
   *ms = (double)t / reps;
+  return AFQMC_OK;
+}
+
+// C = X Y for n x n row-major matrices through the TN kernel (Y transposed into Yt first).
+afqmc_status gemm_nn(Ctx* h, int n, double alpha, const double* Xm, const double* Ym, double* Yt,
+                     double* C, cudaStream_t s) {
+  AFQ_CK(afq::launch_transpose(Ym, Yt, n, n, s));
+  AFQ_CK(afq::gemm_tn_f64(n, n, n, alpha, Yt, n, 0, Xm, n, 0, 0.0, C, n, 0, 1, s));
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_set_tangent(afqmc_handle h, const double* P, cudaStream_t s) {
+  if (!h) return AFQMC_ERR_ARG;
+  if (!P) {
+    h->tangent_on = false;
+    return AFQMC_OK;
+  }
+  if (h->opt.precision != AFQMC_FP64 || h->opt.mode != AFQMC_PHASELESS)
+    return set_err(h, AFQMC_ERR_ARG, "tangent mode needs the FP64 phaseless path");
+  if (!afq::tangent_fits(*h)) return set_err(h, AFQMC_ERR_ARG, "tangent kernels exceed shared memory");
+  const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
+  const int64_t NM = (int64_t)N * M, n2 = 2 * (int64_t)M;
+  afqmc_status st;
+  if (!h->dphi) {
+    if ((st = dalloc(h, &h->dexpK, (size_t)M * M)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->htilP, (size_t)NM)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->dphi, 2 * (size_t)Nw * NM)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->dphi2, 2 * (size_t)Nw * NM)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->dtheta, 2 * (size_t)Nw * NM)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->drhobar, 2 * (size_t)Nw * X)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->dU, 2 * (size_t)Nw * X)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->dAvhs, 2 * (size_t)Nw * h->P)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->dlogO, 2 * (size_t)Nw)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->dlogw, (size_t)Nw)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->daux, 4 * (size_t)Nw)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->deloc, 2 * (size_t)Nw)) != AFQMC_OK) return st;
+    if ((st = dalloc(h, &h->desum, 4 * (size_t)h->R)) != AFQMC_OK) return st;
+  }
+  AFQ_CK(afq::prepare_tangent_kernels(*h));
+  // Z = [[B, dB], [0, B]], B = -dt K / 2, dB = -dt P / 2; exp(Z) upper-right block = dE
+  double *Z = nullptr, *E0 = nullptr, *E1 = nullptr, *Yt = nullptr, *dn = nullptr, *dP = nullptr,
+         *dE = nullptr;
+  auto cleanup = [&]() {
+    for (double* p : {Z, E0, E1, Yt, dn, dP, dE})
+      if (p) cudaFree(p);
+  };
+  const size_t zz = (size_t)n2 * n2;
+  if (dalloc(h, &Z, zz) != AFQMC_OK || dalloc(h, &E0, zz) != AFQMC_OK || dalloc(h, &E1, zz) != AFQMC_OK ||
+      dalloc(h, &Yt, zz) != AFQMC_OK || dalloc(h, &dn, 1) != AFQMC_OK || dalloc(h, &dP, (size_t)M * M) != AFQMC_OK ||
+      dalloc(h, &dE, 1) != AFQMC_OK) {
+    cleanup();
+    return AFQMC_ERR_NOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(dP, P, sizeof(double) * M * M, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Z, 0, sizeof(double) * zz, s);
+  for (int r = 0; r < M && e == cudaSuccess; ++r) {
+    e = cudaMemcpyAsync(Z + r * n2, h->Bneg + (int64_t)r * M, sizeof(double) * M, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Z + (r + M) * n2 + M, h->Bneg + (int64_t)r * M, sizeof(double) * M,
+                          cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(Z + r * n2 + M, dP + (int64_t)r * M, sizeof(double) * M, cudaMemcpyDeviceToDevice, s);
+  }
+  // dB = -dt/2 P in the upper-right block
+  if (e == cudaSuccess) {
+    // scale the upper-right block in place: reuse the GEMM with alpha on an identity is wasteful;
+    // a plain copy of -dt/2 P is built on the host side of this call instead
+    std::vector<double> hp((size_t)M * M);
+    e = cudaMemcpyAsync(hp.data(), dP, sizeof(double) * M * M, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (double& v : hp) v *= -0.5 * h->opt.dt;
+    for (int r = 0; r < M && e == cudaSuccess; ++r)
+      e = cudaMemcpy(Z + r * n2 + M, hp.data() + (size_t)r * M, sizeof(double) * M, cudaMemcpyHostToDevice);
+  }
+  double nrm = 0;
+  if (e == cudaSuccess) e = afq::launch_norm1(Z, (int)n2, dn, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nrm, dn, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(h, "afqmc_set_tangent", e);
+  }
+  int sq = 0;
+  while (nrm / std::ldexp(1.0, sq) > 0.5) ++sq;
+  const double sc = std::ldexp(1.0, -sq);
+  e = cudaMemsetAsync(E0, 0, sizeof(double) * zz, s);
+  if (e == cudaSuccess) e = afq::launch_add_identity(E0, (int)n2, 1.0, s);
+  for (int k = 20; k >= 1 && e == cudaSuccess; --k) {
+    if (gemm_nn(h, (int)n2, sc / k, Z, E0, Yt, E1, s) != AFQMC_OK) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = afq::launch_add_identity(E1, (int)n2, 1.0, s);
+    std::swap(E0, E1);
+  }
+  for (int q = 0; q < sq && e == cudaSuccess; ++q) {
+    if (gemm_nn(h, (int)n2, 1.0, E0, E0, Yt, E1, s) != AFQMC_OK) e = cudaErrorUnknown;
+    std::swap(E0, E1);
+  }
+  for (int r = 0; r < M && e == cudaSuccess; ++r)
+    e = cudaMemcpyAsync(h->dexpK + (int64_t)r * M, E0 + r * n2 + M, sizeof(double) * M,
+                        cudaMemcpyDeviceToDevice, s);
+  // Psi^T P rows and dE_T = sum_s tr(P P_s)
+  if (e == cudaSuccess) e = afq::gemm_tn_f64(M, N, M, 1.0, dP, M, 0, h->psi, M, 0, 0.0, h->htilP, M, 0, 1, s);
+  if (e == cudaSuccess) e = afq::launch_rho_mf(h->htilP, h->psi, dE, 1, (int)NM, s);
+  double det = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&det, dE, sizeof(double), cudaMemcpyDeviceToHost, s);
+  for (double* b : {h->dphi, h->dtheta})
+    if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, sizeof(double) * 2 * Nw * NM, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->dlogO, 0, sizeof(double) * 2 * Nw, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->dlogw, 0, sizeof(double) * Nw, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(h, "afqmc_set_tangent", e);
+  h->de_trial = det;
+  h->tangent_on = true;
+  // consistent Theta / log O / tangents of the current walkers
+  AFQ_CK(afq::launch_overlap_tan(*h, afq::OV_REFRESH, s));
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_energy_tangent(afqmc_handle h, double* de_local, double* e_mixed,
+                                  double* de_mixed, cudaStream_t s) {
+  if (!h) return AFQMC_ERR_ARG;
+  if (!h->tangent_on) return set_err(h, AFQMC_ERR_STATE, "tangent mode is not enabled");
+  AFQ_CK(afq::launch_energy_tan(*h, s));
+  if (de_local) AFQ_CK(cudaMemcpyAsync(de_local, h->deloc, sizeof(double) * 2 * h->Nw, cudaMemcpyDefault, s));
+  AFQ_CK(afq::launch_mixed_sum_tan(*h, h->desum, s));
+  std::vector<double> es(4 * (size_t)h->R);
+  AFQ_CK(cudaMemcpyAsync(es.data(), h->desum, sizeof(double) * es.size(), cudaMemcpyDeviceToHost, s));
+  AFQ_CK(cudaStreamSynchronize(s));
+  std::vector<double> em(h->R), dm(h->R);
+  for (int r = 0; r < h->R; ++r) {
+    const double num = es[4 * r], den = es[4 * r + 1], dnum = es[4 * r + 2], dden = es[4 * r + 3];
+    em[r] = den != 0 ? num / den : NAN;
+    dm[r] = den != 0 ? (dnum - em[r] * dden) / den : NAN;
+  }
+  if (e_mixed) AFQ_CK(cudaMemcpy(e_mixed, em.data(), sizeof(double) * h->R, cudaMemcpyDefault));
+  if (de_mixed) AFQ_CK(cudaMemcpy(de_mixed, dm.data(), sizeof(double) * h->R, cudaMemcpyDefault));
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_get_tangent_state(afqmc_handle h, double* dlogw, cudaStream_t s) {
+  if (!h || !dlogw) return AFQMC_ERR_ARG;
+  if (!h->tangent_on) return set_err(h, AFQMC_ERR_STATE, "tangent mode is not enabled");
+  AFQ_CK(cudaMemcpyAsync(dlogw, h->dlogw, sizeof(double) * h->Nw, cudaMemcpyDefault, s));
+  AFQ_CK(cudaStreamSynchronize(s));
   return AFQMC_OK;
 }
 

@@ -62,6 +62,16 @@ struct Ctx {
   // autotuned variants (autotune.cpp); -1 = not tuned, use the default
   int tune_energy_wb = -1;    // walkers per CTA of the FP32 exchange kernel: 2, 4 or 8
   int tune_taylor_smem = -1;  // 1: A_w staged in shared memory, 0: read through L1
+  // tangent mode (tangent.cu): derivative along h1 -> h1 + lambda P, FP64 path only
+  bool tangent_on = false;
+  double* Bneg = nullptr;     // [M][M]  -dt K / 2 (kept from setup)
+  double* dexpK = nullptr;    // [M][M]  Frechet derivative of exp(-dt K/2) along -dt P/2
+  double* htilP = nullptr;    // [N][M]  rows of Psi_s^T P
+  double de_trial = 0.0;      // dE_T/dlambda = sum_s tr(P Psi_s Psi_s^T)
+  double *dphi = nullptr, *dphi2 = nullptr, *dtheta = nullptr;   // [2][Nw][N][M]
+  double *drhobar = nullptr, *dU = nullptr;                      // [2][Nw][X]
+  double* dAvhs = nullptr;    // [2][Nw][P]
+  double *dlogO = nullptr, *dlogw = nullptr, *daux = nullptr, *deloc = nullptr, *desum = nullptr;
   // pair-run graph cache (owned; see pair.cu)
   void* pair_cache = nullptr;
   uint64_t uid = 0;           // unique per handle, so a cached graph never outlives its partner
@@ -128,6 +138,15 @@ cudaError_t prepare_fast_walker_kernels(const Ctx& c);
 cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaStream_t s);
 cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s);
 cudaError_t launch_fields_mixed(const Ctx& c, const double* fields, cudaStream_t s);
+// tangent mode (tangent.cu)
+bool tangent_fits(const Ctx& c);
+cudaError_t prepare_tangent_kernels(const Ctx& c);
+cudaError_t launch_fields_tan(const Ctx& c, const double* fields, cudaStream_t s);
+cudaError_t launch_taylor_tan(const Ctx& c, cudaStream_t s);
+cudaError_t launch_overlap_tan(const Ctx& c, int mode, cudaStream_t s);
+cudaError_t launch_mgs_tan(const Ctx& c, cudaStream_t s);
+cudaError_t launch_energy_tan(const Ctx& c, cudaStream_t s);
+cudaError_t launch_mixed_sum_tan(const Ctx& c, double* out, cudaStream_t s);
 inline int pad64(int k) { return (k + 63) / 64 * 64; }
 
 enum OverlapMode { OV_REFRESH = 0, OV_UPDATE = 1 };

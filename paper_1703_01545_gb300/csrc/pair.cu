@@ -70,6 +70,8 @@ extern "C" afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n
       A->opt.precision != B->opt.precision)
     return fail(A, B, AFQMC_ERR_ARG, "pair handles differ in seed, walkers, repeats, dt, mode or walker offset");
   if (A->step != B->step) return fail(A, B, AFQMC_ERR_STATE, "pair handles are at different steps");
+  if (A->tangent_on || B->tangent_on)
+    return fail(A, B, AFQMC_ERR_STATE, "tangent mode runs through afqmc_propagate, not the pair graph");
   if (energy_every < 1 || mgs_every < 1 || energy_every % mgs_every != 0 || n_steps < 0 ||
       n_steps % energy_every != 0)
     return fail(A, B, AFQMC_ERR_ARG, "need energy_every % mgs_every == 0 and n_steps % energy_every == 0");
