@@ -229,6 +229,32 @@ afqmc_status afqmc_energy_tangent(afqmc_handle h, double* de_local, double* e_mi
 afqmc_status afqmc_get_tangent_state(afqmc_handle h, double* dlogw, cudaStream_t stream);
 
 /*
+ * afqmc_adjoint_run -- reverse-mode (adjoint) derivative of one run's mixed energy with
+ * respect to every entry of h1 (Eq. 1), with the fields and the trial held fixed: the paper
+ * has no derivative.  Runs n_steps FP64 phaseless steps of the handle's walkers (Eqs. 3-5,
+ * 8-9, 11 and the hybrid weight of Sec. II.D), orthonormalising after every step t with
+ * (t + 1) % mgs_every == 0 (0: never) and measuring after every step with
+ * (t + 1) % energy_every == 0, t counted from the first step of this call, and returns
+ *   *e_mixed = mean over the measurements of sum_k w_k Re E_L,k / sum_k w_k  (Eqs. 7, 10),
+ *   dE_dh1 [M][M] row-major (host or device) = dE/dh1_ij, the M^2 entries taken as
+ *   independent (contracting with a symmetric P gives the tangent-mode derivative along P).
+ * The forward pass keeps the walker state (Phi, log O, w, alive) every `checkpoint` steps;
+ * the reverse pass recomputes one segment at a time from its checkpoint, so device memory
+ * grows as (n_steps / checkpoint + checkpoint) walker states.  fields: as afqmc_propagate
+ * ([n_steps][Nw][X], host or device) or NULL for the Philox stream from the handle's current
+ * step.  The handle ends in the state after the n_steps steps (step counter advanced), as if
+ * afqmc_propagate and afqmc_orthonormalise had run.  Walkers that die get no adjoint flow
+ * past the step that killed them (the derivative of the branch that is taken).
+ * Requires precision AFQMC_FP64, mode AFQMC_PHASELESS, n_repeats == 1, tangent mode off,
+ * 1 <= energy_every <= n_steps, checkpoint >= 1.  Synchronises.
+ * Errors: ARG, STATE (tangent mode on), NOMEM, NUMERIC (no live walker at a measurement),
+ * CUDA.
+ */
+afqmc_status afqmc_adjoint_run(afqmc_handle h, int n_steps, const double* fields, int mgs_every,
+                               int energy_every, int checkpoint, double* e_mixed,
+                               double* dE_dh1, cudaStream_t stream);
+
+/*
  * afqmc_delta_E_stats -- host-only statistics of Sec. II.B (no GPU needed).
  *   dE [n_meas][R] energy differences per measurement and repeat, taus [n_meas].
  *   mean_tau, se_tau [n_meas] (may be NULL): mean and standard error sd/sqrt(R) per tau.

@@ -229,6 +229,23 @@ class System:
                "afqmc_get_tangent_state")
         return d
 
+    def adjoint_run(self, n_steps, fields=None, mgs_every=5, energy_every=5, checkpoint=0):
+        """(E, dE/dh1 [M, M]) of an n_steps FP64 run by the library's reverse mode: E is the
+        mean over the measurements (every energy_every steps) of sum w Re E_L / sum w, the
+        gradient takes the M^2 entries of h1 as independent.  checkpoint=0 picks about
+        sqrt(n_steps) steps per checkpoint segment.  The walkers end after the run."""
+        if checkpoint <= 0:
+            checkpoint = max(1, int(round(np.sqrt(n_steps))))
+        fp = None
+        if fields is not None:
+            fp = np.ascontiguousarray(fields, dtype=np.float64)
+        e = np.empty(1)
+        g = np.empty((self.M, self.M))
+        _check(_lib.load().afqmc_adjoint_run(self.h, int(n_steps), _ptr(fp), int(mgs_every),
+                                             int(energy_every), int(checkpoint), _ptr(e), _ptr(g),
+                                             _stream(None)), self.h, "afqmc_adjoint_run")
+        return float(e[0]), g
+
     def set_walkers(self, phi, w=None):
         phi = np.asarray(phi)
         p = np.ascontiguousarray(np.stack([phi.real, phi.imag]), dtype=np.float64)

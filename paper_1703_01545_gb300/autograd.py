@@ -1,9 +1,13 @@
-"""torch.autograd wrapper of the tangent-mode derivative.
+"""torch.autograd wrappers of the library's derivatives of a run's mixed energy.
 
 ``mixed_energy(lam, ...)`` runs the FP64 propagation of one system with h1 + lam P on a
 fixed field realisation and returns the run's mixed energy (the mean of the per-measurement
 estimates of Eq. 7); its backward pass uses dE/dlambda from the library's tangent mode, so
 torch.autograd.grad gives the exact derivative of that estimate along P.
+
+``mixed_energy_h1(h1, ...)`` returns the same estimate as a function of the whole h1 tensor;
+its backward pass is the library's checkpointed reverse mode (one forward run, one reverse
+sweep), giving dE/dh1 for all M^2 entries at once.
 """
 import numpy as np
 import torch
@@ -75,3 +79,36 @@ def mixed_energy_grad_h1(h1, L, trial, n_up, n_dn, fields=None, dt=0.01, n_walke
             else:   # direction E_ij + E_ji: split equally over the symmetric pair
                 grad[i, j] = grad[j, i] = 0.5 * g
     return grad
+
+
+class _MixedEnergyH1(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, h1, L, trial, n_up, n_dn, fields, dt, n_walkers, n_steps, mgs_every,
+                energy_every, seed, checkpoint):
+        hv = h1.detach().to("cpu", torch.float64).numpy()
+        s = System(hv, L, trial, n_up, n_dn, dt=dt, n_walkers=n_walkers, seed=seed,
+                   precision=FP64)
+        try:
+            E, G = s.adjoint_run(n_steps, fields, mgs_every=mgs_every, energy_every=energy_every,
+                                 checkpoint=checkpoint)
+        finally:
+            s.close()
+        ctx.save_for_backward(torch.from_numpy(G).to(device=h1.device, dtype=h1.dtype))
+        return torch.tensor(E, dtype=h1.dtype, device=h1.device)
+
+    @staticmethod
+    def backward(ctx, grad):
+        (G,) = ctx.saved_tensors
+        return (grad * G,) + (None,) * 12
+
+
+def mixed_energy_h1(h1, L, trial, n_up, n_dn, fields=None, dt=0.01, n_walkers=128, n_steps=20,
+                    mgs_every=5, energy_every=5, seed=1, checkpoint=0):
+    """Mixed energy of a run as a differentiable function of the h1 tensor [M, M] (float64).
+    The gradient treats the M^2 entries as independent; checkpoint=0 picks about
+    sqrt(n_steps) steps per recomputed segment."""
+    return _MixedEnergyH1.apply(h1, np.asarray(L, float), np.asarray(trial, float), int(n_up),
+                                int(n_dn),
+                                None if fields is None else np.ascontiguousarray(fields, float),
+                                float(dt), int(n_walkers), int(n_steps), int(mgs_every),
+                                int(energy_every), int(seed), int(checkpoint))

@@ -287,6 +287,7 @@ afqmc_status check_opts(const afqmc_options* o, std::string& why) {
 
 namespace afq {
 afqmc_status pair_step(Ctx* h, cudaStream_t s) { return step_launch(h, nullptr, s); }
+afqmc_status run_step(Ctx* h, const double* fields_t, cudaStream_t s) { return step_launch(h, fields_t, s); }
 afqmc_status pair_ortho(Ctx* h, cudaStream_t s) { return ortho_launch(h, s); }
 afqmc_status pair_energy(Ctx* h, cudaStream_t s) { return energy_launch(h, s); }
 afqmc_status pair_check(Ctx* h) { return check_tc(h); }
@@ -659,6 +660,81 @@ afqmc_status gemm_nn(Ctx* h, int n, double alpha, const double* Xm, const double
   return AFQMC_OK;
 }
 
+}  // extern "C"
+
+namespace afq {
+// out = L_exp(B, scale * dir), B = -dt K / 2: the Frechet derivative of the matrix exponential
+// at B along scale * dir, read off the upper-right block of exp([[B, D], [0, B]]) (Taylor
+// series of order 20 with scaling and squaring, as at setup).  The direction is scaled down
+// to the norm of B first and the result scaled back (the map is linear in D), so the block
+// matrix needs no more squarings than B itself.  dir, out: device [M][M].
+afqmc_status frechet_expm(Ctx* h, const double* dir, double scale, double* out, cudaStream_t s) {
+  const int M = h->M, n2 = 2 * M;
+  const size_t zz = (size_t)n2 * n2;
+  double *Z = nullptr, *E0 = nullptr, *E1 = nullptr, *Yt = nullptr, *dn = nullptr;
+  auto cleanup = [&]() {
+    for (double* p : {Z, E0, E1, Yt, dn})
+      if (p) cudaFree(p);
+  };
+  if (dalloc(h, &Z, zz) != AFQMC_OK || dalloc(h, &E0, zz) != AFQMC_OK || dalloc(h, &E1, zz) != AFQMC_OK ||
+      dalloc(h, &Yt, zz) != AFQMC_OK || dalloc(h, &dn, 3) != AFQMC_OK) {
+    cleanup();
+    return AFQMC_ERR_NOMEM;
+  }
+  double nrm[3] = {0, 0, 0};
+  cudaError_t e = launch_norm1(dir, M, dn, s);
+  if (e == cudaSuccess) e = launch_norm1(h->Bneg, M, dn + 1, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nrm, dn, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(h, "frechet_expm", e);
+  }
+  const double nd = std::fabs(scale) * nrm[0], nb = nrm[1];
+  if (!std::isfinite(nd)) {
+    cleanup();
+    return set_err(h, AFQMC_ERR_NUMERIC, "non-finite direction for the exponential's derivative");
+  }
+  if (nd == 0.0) {
+    e = cudaMemsetAsync(out, 0, sizeof(double) * M * M, s);
+    cleanup();
+    return e == cudaSuccess ? AFQMC_OK : cuda_fail(h, "frechet_expm", e);
+  }
+  const double eps = (nb > 0.0 && nd > nb) ? nb / nd : 1.0;
+  e = cudaMemsetAsync(Z, 0, sizeof(double) * zz, s);
+  if (e == cudaSuccess) e = place_block(Z, n2, 0, 0, h->Bneg, M, 1.0, s);
+  if (e == cudaSuccess) e = place_block(Z, n2, M, M, h->Bneg, M, 1.0, s);
+  if (e == cudaSuccess) e = place_block(Z, n2, 0, M, dir, M, scale * eps, s);
+  if (e == cudaSuccess) e = launch_norm1(Z, n2, dn + 2, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nrm + 2, dn + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(h, "frechet_expm", e);
+  }
+  int sq = 0;
+  while (nrm[2] / std::ldexp(1.0, sq) > 0.5) ++sq;
+  const double sc = std::ldexp(1.0, -sq);
+  e = cudaMemsetAsync(E0, 0, sizeof(double) * zz, s);
+  if (e == cudaSuccess) e = launch_add_identity(E0, n2, 1.0, s);
+  for (int k = 20; k >= 1 && e == cudaSuccess; --k) {
+    if (gemm_nn(h, n2, sc / k, Z, E0, Yt, E1, s) != AFQMC_OK) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = launch_add_identity(E1, n2, 1.0, s);
+    std::swap(E0, E1);
+  }
+  for (int q = 0; q < sq && e == cudaSuccess; ++q) {
+    if (gemm_nn(h, n2, 1.0, E0, E0, Yt, E1, s) != AFQMC_OK) e = cudaErrorUnknown;
+    std::swap(E0, E1);
+  }
+  if (e == cudaSuccess) e = take_block(E0, n2, 0, M, out, M, 1.0 / eps, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cleanup();
+  return e == cudaSuccess ? AFQMC_OK : cuda_fail(h, "frechet_expm", e);
+}
+}  // namespace afq
+
+extern "C" {
+
 afqmc_status afqmc_set_tangent(afqmc_handle h, const double* P, cudaStream_t s) {
   if (!h) return AFQMC_ERR_ARG;
   if (!P) {
@@ -669,7 +745,7 @@ afqmc_status afqmc_set_tangent(afqmc_handle h, const double* P, cudaStream_t s) 
     return set_err(h, AFQMC_ERR_ARG, "tangent mode needs the FP64 phaseless path");
   if (!afq::tangent_fits(*h)) return set_err(h, AFQMC_ERR_ARG, "tangent kernels exceed shared memory");
   const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
-  const int64_t NM = (int64_t)N * M, n2 = 2 * (int64_t)M;
+  const int64_t NM = (int64_t)N * M;
   afqmc_status st;
   if (!h->dphi) {
     if ((st = dalloc(h, &h->dexpK, (size_t)M * M)) != AFQMC_OK) return st;
@@ -687,66 +763,26 @@ afqmc_status afqmc_set_tangent(afqmc_handle h, const double* P, cudaStream_t s) 
     if ((st = dalloc(h, &h->desum, 4 * (size_t)h->R)) != AFQMC_OK) return st;
   }
   AFQ_CK(afq::prepare_tangent_kernels(*h));
-  // Z = [[B, dB], [0, B]], B = -dt K / 2, dB = -dt P / 2; exp(Z) upper-right block = dE
-  double *Z = nullptr, *E0 = nullptr, *E1 = nullptr, *Yt = nullptr, *dn = nullptr, *dP = nullptr,
-         *dE = nullptr;
-  auto cleanup = [&]() {
-    for (double* p : {Z, E0, E1, Yt, dn, dP, dE})
-      if (p) cudaFree(p);
-  };
-  const size_t zz = (size_t)n2 * n2;
-  if (dalloc(h, &Z, zz) != AFQMC_OK || dalloc(h, &E0, zz) != AFQMC_OK || dalloc(h, &E1, zz) != AFQMC_OK ||
-      dalloc(h, &Yt, zz) != AFQMC_OK || dalloc(h, &dn, 1) != AFQMC_OK || dalloc(h, &dP, (size_t)M * M) != AFQMC_OK ||
-      dalloc(h, &dE, 1) != AFQMC_OK) {
-    cleanup();
+  double *dP = nullptr, *dE = nullptr;
+  if (dalloc(h, &dP, (size_t)M * M) != AFQMC_OK || dalloc(h, &dE, 1) != AFQMC_OK) {
+    if (dP) cudaFree(dP);
     return AFQMC_ERR_NOMEM;
   }
+  auto cleanup = [&]() {
+    cudaFree(dP);
+    cudaFree(dE);
+  };
   cudaError_t e = cudaMemcpyAsync(dP, P, sizeof(double) * M * M, cudaMemcpyDefault, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(Z, 0, sizeof(double) * zz, s);
-  for (int r = 0; r < M && e == cudaSuccess; ++r) {
-    e = cudaMemcpyAsync(Z + r * n2, h->Bneg + (int64_t)r * M, sizeof(double) * M, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(Z + (r + M) * n2 + M, h->Bneg + (int64_t)r * M, sizeof(double) * M,
-                          cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(Z + r * n2 + M, dP + (int64_t)r * M, sizeof(double) * M, cudaMemcpyDeviceToDevice, s);
-  }
-  // dB = -dt/2 P in the upper-right block
-  if (e == cudaSuccess) {
-    // scale the upper-right block in place: reuse the GEMM with alpha on an identity is wasteful;
-    // a plain copy of -dt/2 P is built on the host side of this call instead
-    std::vector<double> hp((size_t)M * M);
-    e = cudaMemcpyAsync(hp.data(), dP, sizeof(double) * M * M, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    for (double& v : hp) v *= -0.5 * h->opt.dt;
-    for (int r = 0; r < M && e == cudaSuccess; ++r)
-      e = cudaMemcpy(Z + r * n2 + M, hp.data() + (size_t)r * M, sizeof(double) * M, cudaMemcpyHostToDevice);
-  }
-  double nrm = 0;
-  if (e == cudaSuccess) e = afq::launch_norm1(Z, (int)n2, dn, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&nrm, dn, sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cleanup();
     return cuda_fail(h, "afqmc_set_tangent", e);
   }
-  int sq = 0;
-  while (nrm / std::ldexp(1.0, sq) > 0.5) ++sq;
-  const double sc = std::ldexp(1.0, -sq);
-  e = cudaMemsetAsync(E0, 0, sizeof(double) * zz, s);
-  if (e == cudaSuccess) e = afq::launch_add_identity(E0, (int)n2, 1.0, s);
-  for (int k = 20; k >= 1 && e == cudaSuccess; --k) {
-    if (gemm_nn(h, (int)n2, sc / k, Z, E0, Yt, E1, s) != AFQMC_OK) e = cudaErrorUnknown;
-    if (e == cudaSuccess) e = afq::launch_add_identity(E1, (int)n2, 1.0, s);
-    std::swap(E0, E1);
+  // d exp(B) along dB = -dt P / 2
+  afqmc_status fs = afq::frechet_expm(h, dP, -0.5 * h->opt.dt, h->dexpK, s);
+  if (fs != AFQMC_OK) {
+    cleanup();
+    return fs;
   }
-  for (int q = 0; q < sq && e == cudaSuccess; ++q) {
-    if (gemm_nn(h, (int)n2, 1.0, E0, E0, Yt, E1, s) != AFQMC_OK) e = cudaErrorUnknown;
-    std::swap(E0, E1);
-  }
-  for (int r = 0; r < M && e == cudaSuccess; ++r)
-    e = cudaMemcpyAsync(h->dexpK + (int64_t)r * M, E0 + r * n2 + M, sizeof(double) * M,
-                        cudaMemcpyDeviceToDevice, s);
   // Psi^T P rows and dE_T = sum_s tr(P P_s)
   if (e == cudaSuccess) e = afq::gemm_tn_f64(M, N, M, 1.0, dP, M, 0, h->psi, M, 0, 0.0, h->htilP, M, 0, 1, s);
   if (e == cudaSuccess) e = afq::launch_rho_mf(h->htilP, h->psi, dE, 1, (int)NM, s);

@@ -147,6 +147,42 @@ cudaError_t launch_overlap_tan(const Ctx& c, int mode, cudaStream_t s);
 cudaError_t launch_mgs_tan(const Ctx& c, cudaStream_t s);
 cudaError_t launch_energy_tan(const Ctx& c, cudaStream_t s);
 cudaError_t launch_mixed_sum_tan(const Ctx& c, double* out, cudaStream_t s);
+// reverse mode (adjoint_kernels.cu): see those kernels for the adjoint of each step piece
+bool adjoint_fits(const Ctx& c);
+cudaError_t prepare_adjoint_kernels(const Ctx& c);
+cudaError_t adj_inv_overlap(const Ctx& c, const double* phi, double* Y, double* logO, double* theta,
+                            const int* mask, cudaStream_t s);
+cudaError_t adj_rbar(const Ctx& c, const double* logO_new, const double* logO_old, const int* still,
+                     double* lwbar, double* rbar, cudaStream_t s);
+cudaError_t adj_mask(const Ctx& c, double* pb, const int* still, cudaStream_t s);
+cudaError_t adj_logdet(const Ctx& c, double* pb, const double* Y, const double* rbar, double sgn,
+                       cudaStream_t s);
+cudaError_t adj_taylor(const Ctx& c, const double* phi1, double* pbar, double* terms, double* Abar,
+                       double* phi2, const int* mask, cudaStream_t s);
+cudaError_t adj_outer(const Ctx& c, const double* Xm, const double* Ym, const int* mask, double* Ebar,
+                      cudaStream_t s);
+cudaError_t adj_fields(const Ctx& c, const double* fields, const double* S, const double* rbar,
+                       const double* lwbar, double* rbb, const int* mask, cudaStream_t s);
+cudaError_t adj_overlap(const Ctx& c, const double* phi, const double* Y, const double* thb,
+                        double* pb, const int* mask, cudaStream_t s);
+cudaError_t adj_mgs(const Ctx& c, const double* Q, const double* phi3, double* pb, const int* alive,
+                    cudaStream_t s);
+cudaError_t adj_energy(const Ctx& c, const double* theta, const double* ebar, double* thb,
+                       double* eloc, const int* mask, cudaStream_t s);
+cudaError_t adj_meas_weights(const Ctx& c, double* ebar, double inv_meas, cudaStream_t s);
+cudaError_t adj_meas_finish(const Ctx& c, const double* eloc, const double* ebar, double* lwbar,
+                            double* e_acc, double n_meas, cudaStream_t s);
+cudaError_t adj_theta_avg(const Ctx& c, const double* theta, const double* ebar, double* avg,
+                          cudaStream_t s);
+cudaError_t adj_h1bar(const Ctx& c, const double* Lx, double alpha, const double* avg, double* out,
+                      cudaStream_t s);
+cudaError_t place_block(double* Z, int ldz, int r0, int c0, const double* src, int M, double alpha,
+                        cudaStream_t s);
+cudaError_t take_block(const double* Z, int ldz, int r0, int c0, double* dst, int M, double alpha,
+                       cudaStream_t s);
+cudaError_t set_step(const Ctx& c, unsigned long long v, cudaStream_t s);
+// out = L_exp(-dt K/2, scale * dir), the exponential's Frechet derivative (api.cu)
+afqmc_status frechet_expm(Ctx* h, const double* dir, double scale, double* out, cudaStream_t s);
 inline int pad64(int k) { return (k + 63) / 64 * 64; }
 
 enum OverlapMode { OV_REFRESH = 0, OV_UPDATE = 1 };
