@@ -154,6 +154,7 @@ afqmc_status adjoint_body(Ctx* h, Arena& ar, int n_steps, const double* fields, 
   double* e_acc = ar.get<double>(1);
   double* LtilT = ar.get<double>((size_t)NM * X);
   double* Ebar = ar.get<double>(MM);
+  double* part = ar.get<double>((size_t)afq::kOuterSlices * MM);
   double* avg = ar.get<double>(NM);
   double* LE = ar.get<double>(MM);
   double* h1bar = ar.get<double>(MM);
@@ -216,13 +217,13 @@ afqmc_status adjoint_body(Ctx* h, Arena& ar, int n_steps, const double* fields, 
       ADJ_CK(afq::adj_inv_overlap(c, phi3, Y1, logO_new, nullptr, still, s));
       ADJ_CK(afq::adj_rbar(c, logO_new, tp.logO, still, lwbar, rbar, s));
       ADJ_CK(afq::adj_logdet(c, phibar, Y1, rbar, 1.0, s));
-      ADJ_CK(afq::adj_outer(c, phibar, c.phi2, still, Ebar, s));
+      ADJ_CK(afq::adj_outer(c, phibar, c.phi2, still, part, Ebar, s));
       ADJ_CK(afq::gemm_tn_f64(M, cols, M, 1.0, c.expK, M, 0, phibar, M, 0, 0.0, pbA, M, 0, 1, s,
                               afq::GEMM_ONEBODY));
       ADJ_CK(afq::gemm_tn_f64(M, cols, M, 1.0, c.expK, M, 0, tp.phi, M, 0, 0.0, phi1, M, 0, 1, s,
                               afq::GEMM_ONEBODY));
       ADJ_CK(afq::adj_taylor(c, phi1, pbA, terms, Abar, c.phi2, still, s));
-      ADJ_CK(afq::adj_outer(c, pbA, tp.phi, still, Ebar, s));
+      ADJ_CK(afq::adj_outer(c, pbA, tp.phi, still, part, Ebar, s));
       ADJ_CK(afq::gemm_tn_f64(M, cols, M, 1.0, c.expK, M, 0, pbA, M, 0, 0.0, phibar, M, 0, 1, s,
                               afq::GEMM_ONEBODY));
       // S[(p,w)][g] = sum_ij L_g,ij Abar[(p,w)][ij]

@@ -361,12 +361,14 @@ __global__ void __launch_bounds__(kT) k_taylor_rev(const double* __restrict__ ph
 }
 
 // ---------------------------------------------------------------------------
-// Ebar[i][j] += sum_rows Re(X[row][i] conj(Y[row][j])), rows = (plane-free) walker columns.
-// X, Y planar [2][R][M]; each CTA reduces a 32 x 32 tile over a slice of rows, then atomics.
+// Ebar[i][j] += sum_rows Re(X[row][i] conj(Y[row][j])), rows = (walker, orbital) columns.
+// X, Y planar [2][rows][M]; each CTA reduces a 32 x 32 tile over one slice of rows into
+// its own partial, and k_outer_sum adds the slices in a fixed order (no atomics, so a
+// recomputed pass reproduces the sum bit for bit).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_outer_re(const double* __restrict__ Xm, const double* __restrict__ Ym,
                                                   const int* __restrict__ mask, int64_t rows,
-                                                  int N, int M, double* __restrict__ Ebar) {
+                                                  int N, int M, double* __restrict__ part) {
   __shared__ double xs[2][32][33], ys[2][32][33];
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -395,10 +397,19 @@ __global__ void __launch_bounds__(256) k_outer_re(const double* __restrict__ Xm,
     }
     __syncthreads();
   }
+  double* pz = part + (int64_t)blockIdx.z * M * M;
   for (int q = 0; q < 4; ++q) {
     const int i = i0 + tx, j = j0 + ty + 8 * q;
-    if (i < M && j < M) atomicAdd(Ebar + (int64_t)i * M + j, acc[q]);
+    if (i < M && j < M) pz[(int64_t)i * M + j] = acc[q];
   }
+}
+
+__global__ void k_outer_sum(const double* __restrict__ part, int nz, int MM, double* __restrict__ Ebar) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= MM) return;
+  double s = Ebar[e];
+  for (int z = 0; z < nz; ++z) s += part[(int64_t)z * MM + e];
+  Ebar[e] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -870,13 +881,18 @@ cudaError_t adj_taylor(const Ctx& c, const double* phi1, double* pbar, double* t
                                                     c.N, c.Nw, c.P, c.opt.taylor_order);
   return cudaGetLastError();
 }
-cudaError_t adj_outer(const Ctx& c, const double* Xm, const double* Ym, const int* mask, double* Ebar,
-                      cudaStream_t s) {
+cudaError_t adj_outer(const Ctx& c, const double* Xm, const double* Ym, const int* mask, double* part,
+                      double* Ebar, cudaStream_t s) {
   const int64_t rows = (int64_t)c.Nw * c.N;
   const int tiles = ((c.M + 31) / 32) * ((c.M + 31) / 32);
   int zs = (int)std::min<int64_t>((rows + 31) / 32, std::max(1, 2 * 152 / tiles));
-  dim3 grid((c.M + 31) / 32, (c.M + 31) / 32, zs < 1 ? 1 : zs);
-  k_outer_re<<<grid, 256, 0, s>>>(Xm, Ym, mask, rows, c.N, c.M, Ebar);
+  zs = std::max(1, std::min(zs, kOuterSlices));
+  dim3 grid((c.M + 31) / 32, (c.M + 31) / 32, zs);
+  k_outer_re<<<grid, 256, 0, s>>>(Xm, Ym, mask, rows, c.N, c.M, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int MM = c.M * c.M;
+  k_outer_sum<<<(MM + 255) / 256, 256, 0, s>>>(part, zs, MM, Ebar);
   return cudaGetLastError();
 }
 cudaError_t adj_fields(const Ctx& c, const double* fields, const double* S, const double* rbar,

@@ -159,8 +159,9 @@ cudaError_t adj_logdet(const Ctx& c, double* pb, const double* Y, const double* 
                        cudaStream_t s);
 cudaError_t adj_taylor(const Ctx& c, const double* phi1, double* pbar, double* terms, double* Abar,
                        double* phi2, const int* mask, cudaStream_t s);
-cudaError_t adj_outer(const Ctx& c, const double* Xm, const double* Ym, const int* mask, double* Ebar,
-                      cudaStream_t s);
+constexpr int kOuterSlices = 64;   // row slices of the Ebar outer product; part: [64][M][M]
+cudaError_t adj_outer(const Ctx& c, const double* Xm, const double* Ym, const int* mask, double* part,
+                      double* Ebar, cudaStream_t s);
 cudaError_t adj_fields(const Ctx& c, const double* fields, const double* S, const double* rbar,
                        const double* lwbar, double* rbb, const int* mask, cudaStream_t s);
 cudaError_t adj_overlap(const Ctx& c, const double* phi, const double* Y, const double* thb,
