@@ -3,6 +3,7 @@
 // the small dense linear algebra (N_s <= 16) synchronises with __syncwarp only.  The
 // arithmetic (overlaps, determinants, ratios, weights, Gram-Schmidt) is FP64 as in the
 // reference kernels; only Theta = Phi O^{-1} is formed in FP32 here.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cuda_bf16.h>
@@ -32,22 +33,27 @@ struct FastOvArgs {
   double log_shift;
 };
 
-// One CTA (256 threads) per walker.  Shared: phi [2][N][M] (FP64), per spin the augmented
-// matrix [O | I] as [2][ns][2 ns] (FP64).
+// One CTA (256 threads) per walker.  Shared: phi [2][N][M] (FP64), per spin the overlap
+// matrix inverted in place (re and im [16][32], FP64), FP32 copies of phi and the inverses.
+// ROWS: elimination rows per lane, ceil(ns / (32 / ns)) for the larger spin block (2, 4 or 8);
+// the multipliers of those rows are held in registers.
+template <int ROWS>
 __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   extern __shared__ double smo[];
   const int wk = blockIdx.x, tid = threadIdx.x, M = a.M, N = a.N, NM = N * M;
   const int lane = tid & 31, warp = tid >> 5;
   double* pr = smo;            // [N][M]
   double* pi = pr + NM;        // [N][M]
-  double* aug = pi + NM;       // spin s at aug + s * 2 * 16 * 32: re [16][32], im [16][32]
+  double* aug = pi + NM;       // O_s then O_s^{-1}: spin s at aug + s * 2 * 16 * 32, re/im [16][32]
   // FP32 copies for Theta: converting once here keeps double->float conversions (which run
   // on the FP64 pipe) off the Theta loop
   float* pfr = reinterpret_cast<float*>(aug + 2 * 2 * kNsMax * 32);  // [N][M]
   float* pfi = pfr + NM;
   float* invf = pfi + NM;      // spin s at invf + s * 2 * 16 * 16: re [16][16], im [16][16]
-  __shared__ double s_ld[2][2];
+  __shared__ double s_det[2][2];   // per spin: determinant mantissa (re, im) ...
+  __shared__ int s_dexp[2];        // ... and its power-of-two exponent
   __shared__ int s_bad[2];
+  __shared__ int s_piv[2][kNsMax];
   const bool live = a.alive[wk] != 0;
   const bool upd = (a.mode == OV_UPDATE) && live;
   const double* src = upd ? a.src : a.phi;
@@ -59,17 +65,17 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     pfr[e] = (float)xr;
     pfi[e] = (float)xi;
   }
-  if (tid < 2) { s_ld[tid][0] = 0.0; s_ld[tid][1] = 0.0; s_bad[tid] = 0; }
+  if (tid < 2) { s_det[tid][0] = 1.0; s_det[tid][1] = 0.0; s_dexp[tid] = 0; s_bad[tid] = 0; }
   __syncthreads();
   // O_s[a][b] = sum_i psi[n0+a][i] phi[n0+b][i]; 4 threads per entry, shuffle-combined
   const int nu = a.n_up, nd = N - nu, nn = nu * nu + nd * nd;
   for (int base = 0; base < nn * 4; base += blockDim.x) {
     const int q = base + tid, ent = q >> 2, part = q & 3;
     double re = 0.0, im = 0.0;
-    int sp = 0, r = 0, c = 0, ns = nu;
+    int sp = 0, r = 0, c = 0;
     if (ent < nn) {
       if (ent < nu * nu) { r = ent / nu; c = ent % nu; }
-      else { sp = 1; ns = nd; const int e2 = ent - nu * nu; r = e2 / nd; c = e2 % nd; }
+      else { sp = 1; const int e2 = ent - nu * nu; r = e2 / nd; c = e2 % nd; }
       const int n0 = sp ? nu : 0;
       const double* ps = a.psi + (int64_t)(n0 + r) * M;
       const double* fr = pr + (n0 + c) * M;
@@ -89,98 +95,106 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
       double* ai = ar + kNsMax * 32;
       ar[r * 32 + c] = re;
       ai[r * 32 + c] = im;
-      ar[r * 32 + ns + c] = (r == c) ? 1.0 : 0.0;
-      ai[r * 32 + ns + c] = 0.0;
     }
   }
   __syncthreads();
-  // warp-synchronous Gauss-Jordan with partial pivoting on [O | I] (ns x 2ns): warp sp
-  // handles spin sp; lane l owns column l % 2ns and rows l / 2ns, l / 2ns + RS, ... so all
-  // lanes work.  The determinant is the product of the pivots (times the swap signs), kept
-  // as a complex number with a separate power-of-two exponent; one log at the end.
+  // warp-synchronous in-place Gauss-Jordan inversion with partial (row) pivoting: warp sp
+  // handles spin sp; lane l owns column l % ns and rows l / ns, l / ns + RS, ... (RS = 32 / ns).
+  // Every FP64 warp instruction occupies the FP64 pipe whatever its active lanes, so the
+  // per-pivot scalar work is kept short and runs in all lanes: the pivot is chosen on an
+  // integer magnitude key (the high word of |re| or |im|, monotone in the magnitude), the
+  // determinant is the product of the pivots renormalised by an exact power of two built from
+  // its exponent bits, and the row inverse uses one reciprocal.  Each complex update of the
+  // elimination is 4 FP64 fused multiply-adds.
   if (warp < 2) {
     const int sp = warp, ns = sp ? nd : nu;
     if (ns > 0) {
       double* ar = aug + sp * 2 * kNsMax * 32;
       double* ai = ar + kNsMax * 32;
-      const int w2 = 2 * ns, RS = 32 / w2 > 0 ? 32 / w2 : 1;  // row stride between a lane's rows
-      const int c = lane % w2, r0 = lane / w2;
-      const bool active = lane < RS * w2;
+      const int RS = 32 / ns;                 // rows per pass (ns <= 16, so RS >= 2)
+      const int c = lane % ns, r0 = lane / ns;
+      const bool active = r0 < RS;
       double dr = 1.0, di = 0.0;
       int dexp = 0;
       bool bad = false;
       for (int k = 0; k < ns; ++k) {
-        // pivot choice by magnitude only: FP32 compare, warp argmax (lowest row on ties)
-        float m2 = -1.f;
+        unsigned key = 0u;
         if (lane >= k && lane < ns) {
-          const float xr = (float)ar[lane * 32 + k], xi = (float)ai[lane * 32 + k];
-          m2 = xr * xr + xi * xi;
+          const unsigned hr = (unsigned)__double2hiint(ar[lane * 32 + k]) & 0x7fffffffu;
+          const unsigned hi = (unsigned)__double2hiint(ai[lane * 32 + k]) & 0x7fffffffu;
+          key = hr > hi ? hr : hi;
         }
         int p = lane;
         for (int o = 16; o > 0; o >>= 1) {
-          const float om = __shfl_xor_sync(0xffffffffu, m2, o);
+          const unsigned ok = __shfl_xor_sync(0xffffffffu, key, o);
           const int op = __shfl_xor_sync(0xffffffffu, p, o);
-          if (om > m2 || (om == m2 && op < p)) { m2 = om; p = op; }
+          if (ok > key || (ok == key && op < p)) { key = ok; p = op; }
         }
-        if (!(m2 > 0.f) || !isfinite(m2)) {
-          // tiny pivots that FP32 cannot resolve: fall back to the FP64 scan
-          double best = -1.0;
-          p = k;
-          for (int r = k; r < ns; ++r) {
-            const double d2 = ar[r * 32 + k] * ar[r * 32 + k] + ai[r * 32 + k] * ai[r * 32 + k];
-            if (d2 > best) { best = d2; p = r; }
-          }
-          if (!(best > 0.0) || !isfinite(best)) { bad = true; break; }
+        // zero, subnormal-only or non-finite column: singular for this kernel
+        if (key < 0x00100000u || key >= 0x7ff00000u) { bad = true; break; }
+        if (lane == 0) s_piv[sp][k] = p;
+        if (p != k && lane < ns) {
+          double t = ar[k * 32 + lane]; ar[k * 32 + lane] = ar[p * 32 + lane]; ar[p * 32 + lane] = t;
+          t = ai[k * 32 + lane]; ai[k * 32 + lane] = ai[p * 32 + lane]; ai[p * 32 + lane] = t;
         }
         __syncwarp();
-        if (p != k && active && r0 == 0) {
-          double t = ar[k * 32 + c]; ar[k * 32 + c] = ar[p * 32 + c]; ar[p * 32 + c] = t;
-          t = ai[k * 32 + c]; ai[k * 32 + c] = ai[p * 32 + c]; ai[p * 32 + c] = t;
-        }
-        __syncwarp();
-        cplx inv = {0.0, 0.0};
-        if (lane == 0) {
-          const double vr = ar[k * 32 + k], vi = ai[k * 32 + k];
-          const cplx d = cmul({dr, di}, {vr, vi});
-          int e2;
-          const double mag = frexp(fmax(fabs(d.re), fabs(d.im)), &e2);
-          (void)mag;
-          dr = ldexp(d.re, -e2);
-          di = ldexp(d.im, -e2);
-          dexp += e2;
-          if (p != k) { dr = -dr; di = -di; }
-          inv = cinv({vr, vi});
-        }
-        inv.re = __shfl_sync(0xffffffffu, inv.re, 0);
-        inv.im = __shfl_sync(0xffffffffu, inv.im, 0);
-        __syncwarp();
-        if (active && r0 == 0) {
-          const cplx v = cmul({ar[k * 32 + c], ai[k * 32 + c]}, inv);
-          ar[k * 32 + c] = v.re;
-          ai[k * 32 + c] = v.im;
-        }
-        __syncwarp();
-        if (active) {
-          const double kr = ar[k * 32 + c], ki = ai[k * 32 + c];
-          for (int r = r0; r < ns; r += RS) {
-            if (r == k) continue;
-            const double fr = ar[r * 32 + k], fi = ai[r * 32 + k];
-            // column k itself is read (fr, fi) by other lanes of this row: update it last
-            if (c == k) continue;
-            ar[r * 32 + c] -= fr * kr - fi * ki;
-            ai[r * 32 + c] -= fr * ki + fi * kr;
+        const double vr = ar[k * 32 + k], vi = ai[k * 32 + k];
+        {
+          const double tr = fma(dr, vr, -di * vi);
+          di = fma(dr, vi, di * vr);
+          dr = (p != k) ? -tr : tr;
+          if (p != k) di = -di;
+          const int e1 = (__double2hiint(dr) >> 20) & 0x7ff, e2 = (__double2hiint(di) >> 20) & 0x7ff;
+          const int eh = e1 > e2 ? e1 : e2;
+          if (eh > 0 && eh < 2046) {
+            const double sc = __hiloint2double((2046 - eh) << 20, 0);   // 2^(1023 - eh), exact
+            dr *= sc;
+            di *= sc;
+            dexp += eh - 1023;
           }
         }
+        const double rinv = __drcp_rn(fma(vr, vr, vi * vi));
+        const double ir = vr * rinv, ii = -vi * rinv;          // 1 / pivot
         __syncwarp();
-        if (active && c == k)
-          for (int r = r0; r < ns; r += RS)
-            if (r != k) { ar[r * 32 + k] = 0.0; ai[r * 32 + k] = 0.0; }
+        if (lane < ns) {                                       // row k *= 1/pivot, A[k][k] = 1/pivot
+          const double xr = ar[k * 32 + lane], xi = ai[k * 32 + lane];
+          ar[k * 32 + lane] = (lane == k) ? ir : fma(xr, ir, -xi * ii);
+          ai[k * 32 + lane] = (lane == k) ? ii : fma(xr, ii, xi * ir);
+        }
+        __syncwarp();
+        double fr[ROWS], fi[ROWS];
+        const double kr = ar[k * 32 + c], ki = ai[k * 32 + c];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+          const int r = r0 + q * RS;
+          fr[q] = (active && r < ns) ? ar[r * 32 + k] : 0.0;
+          fi[q] = (active && r < ns) ? ai[r * 32 + k] : 0.0;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {                // A[r][c] -= A[r][k] A[k][c]; column k
+          const int r = r0 + q * RS;                           // becomes -A[r][k] / pivot
+          if (active && r < ns && r != k) {
+            const double xr = (c == k) ? 0.0 : ar[r * 32 + c], xi = (c == k) ? 0.0 : ai[r * 32 + c];
+            ar[r * 32 + c] = fma(-fr[q], kr, fma(fi[q], ki, xr));
+            ai[r * 32 + c] = fma(-fr[q], ki, fma(-fi[q], kr, xi));
+          }
+        }
         __syncwarp();
       }
+      // undo the row interchanges on the inverse's columns, last interchange first
+      if (!bad && lane < ns)
+        for (int k = ns - 1; k >= 0; --k) {
+          const int p = s_piv[sp][k];
+          if (p != k) {
+            double t = ar[lane * 32 + k]; ar[lane * 32 + k] = ar[lane * 32 + p]; ar[lane * 32 + p] = t;
+            t = ai[lane * 32 + k]; ai[lane * 32 + k] = ai[lane * 32 + p]; ai[lane * 32 + p] = t;
+          }
+        }
       if (lane == 0) {
-        // log det = log(d) + dexp ln 2
-        s_ld[sp][0] = 0.5 * log(dr * dr + di * di) + dexp * M_LN2;
-        s_ld[sp][1] = atan2(di, dr);
+        s_det[sp][0] = dr;
+        s_det[sp][1] = di;
+        s_dexp[sp] = dexp;
         s_bad[sp] = bad ? 1 : 0;
       }
     }
@@ -193,8 +207,8 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     else { sp = 1; ns = nd; r = (e - nu * nu) / nd; c = (e - nu * nu) % nd; }
     const double* ar = aug + sp * 2 * kNsMax * 32;
     float* fr = invf + sp * 2 * kNsMax * kNsMax;
-    fr[r * kNsMax + c] = (float)ar[r * 32 + ns + c];
-    fr[kNsMax * kNsMax + r * kNsMax + c] = (float)ar[kNsMax * 32 + r * 32 + ns + c];
+    fr[r * kNsMax + c] = (float)ar[r * 32 + c];
+    fr[kNsMax * kNsMax + r * kNsMax + c] = (float)ar[kNsMax * 32 + r * 32 + c];
   }
   __syncthreads();
   // Theta_s = Phi_s O_s^{-1} in FP32; FP32 copy and split bf16 force-bias operand
@@ -226,7 +240,11 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     }
   }
   if (tid != 0) return;
-  const double ld_re = s_ld[0][0] + s_ld[1][0], ld_im = s_ld[0][1] + s_ld[1][1];
+  // log det O = log(d_up d_dn) + (e_up + e_dn) ln 2: one log and one atan2 per walker
+  const double d0r = s_det[0][0], d0i = s_det[0][1], d1r = s_det[1][0], d1i = s_det[1][1];
+  const double pr_ = fma(d0r, d1r, -d0i * d1i), pi_ = fma(d0r, d1i, d0i * d1r);
+  const double ld_re = 0.5 * log(fma(pr_, pr_, pi_ * pi_)) + (s_dexp[0] + s_dexp[1]) * M_LN2;
+  const double ld_im = atan2(pi_, pr_);
   if (bad || !isfinite(ld_re) || !isfinite(ld_im)) {
     atomicAdd(a.flags, 1);
     if (upd || a.mode == OV_REFRESH) {
@@ -340,9 +358,10 @@ cudaError_t prepare_fast_walker_kernels(const Ctx& c) {
   static size_t have_o = 0, have_m = 0;
   cudaError_t e;
   if (smem_fast_overlap(c) > have_o) {
-    if ((e = cudaFuncSetAttribute(k_overlap_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_fast_overlap(c))) != cudaSuccess)
-      return e;
+    for (auto* f : {k_overlap_fast<2>, k_overlap_fast<4>, k_overlap_fast<8>})
+      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_fast_overlap(c))) != cudaSuccess)
+        return e;
     have_o = smem_fast_overlap(c);
   }
   if (smem_mgs_warp(c) > have_m) {
@@ -362,7 +381,12 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
   a.M = c.M; a.N = c.N; a.n_up = c.n_up; a.Nw = c.Nw; a.mode = mode;
   a.free_proj = c.opt.mode == AFQMC_FREE;
   a.log_shift = -c.opt.dt * (c.c_mf - c.e_trial);
-  k_overlap_fast<<<c.Nw, 256, smem_fast_overlap(c), s>>>(a);
+  auto rows = [](int ns) { return ns > 0 ? (ns + 32 / ns - 1) / (32 / ns) : 0; };
+  const int need = std::max(rows(c.n_up), rows(c.N - c.n_up));
+  const size_t sm = smem_fast_overlap(c);
+  if (need <= 2) k_overlap_fast<2><<<c.Nw, 256, sm, s>>>(a);
+  else if (need <= 4) k_overlap_fast<4><<<c.Nw, 256, sm, s>>>(a);
+  else k_overlap_fast<8><<<c.Nw, 256, sm, s>>>(a);
   return cudaGetLastError();
 }
 
