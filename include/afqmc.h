@@ -80,7 +80,9 @@ typedef struct {
   double e_trial;     /* E_T = E_L(psi_T), the trial (HF) energy used as the energy shift   */
   double c_mf;        /* C = -1/2 sum_g <rho_g>_T^2, scalar of the one-body part H_1        */
   int n_alive;        /* live walkers (synchronises the stream)                             */
-  int tuned_energy_walkers_per_cta; /* autotuned exchange-kernel variant, -1 if not tuned    */
+  int tuned_energy_walkers_per_cta; /* local-energy kernel of the split-precision step: 0 =
+                                       tensor cores, 2/4/8 = FP32 kernel with that many walkers
+                                       per CTA, -1 = not tuned (tensor cores where supported) */
   int tuned_taylor_smem;            /* autotuned Taylor variant (1: A in shared memory), -1 */
 } afqmc_info;
 
@@ -280,6 +282,17 @@ enum { AFQMC_K_VHS = 0, AFQMC_K_FORCE_BIAS = 1, AFQMC_K_TAYLOR = 2, AFQMC_K_EXCH
        AFQMC_K_OVERLAP = 4 };
 afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms,
                                cudaStream_t stream);
+
+/*
+ * afqmc_select_kernel -- testing and benchmarking aid (no counterpart in the paper): fixes
+ * the variant of a tunable kernel of the split-precision step, overriding the autotuner.
+ *   which AFQMC_K_EXCHANGE: variant 0 = tensor-core local energy, 2 / 4 / 8 = FP32 kernel
+ *                           with that many walkers per CTA;
+ *   which AFQMC_K_TAYLOR:   variant 0 = A read through L1, 1 = A staged in shared memory.
+ * The choice shows in afqmc_get_info.  Errors: ARG (FP64 handle, unknown kernel, or a
+ * variant this shape does not support).
+ */
+afqmc_status afqmc_select_kernel(afqmc_handle h, int which, int variant);
 
 /*
  * afqmc_local_energy_static -- local energies E_L of the walkers phi, like

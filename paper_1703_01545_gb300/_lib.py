@@ -53,6 +53,7 @@ SIGNATURES = {
     "afqmc_set_tangent": (ctypes.c_int, [VP, VP, VP]),
     "afqmc_energy_tangent": (ctypes.c_int, [VP, VP, VP, VP, VP]),
     "afqmc_get_tangent_state": (ctypes.c_int, [VP, VP, VP]),
+    "afqmc_select_kernel": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int]),
     "afqmc_adjoint_run": (ctypes.c_int, [VP, ctypes.c_int, VP, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, VP, VP, VP]),
     "afqmc_local_energy_static": (ctypes.c_int, [VP, VP, VP, VP, ctypes.c_int, ctypes.c_int,

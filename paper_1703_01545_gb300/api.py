@@ -229,6 +229,12 @@ class System:
                "afqmc_get_tangent_state")
         return d
 
+    def select_kernel(self, which, variant):
+        """Fix a tunable kernel's variant (K_EXCHANGE: 0 tensor cores, 2/4/8 FP32 walkers per
+        CTA; K_TAYLOR: 0 L1, 1 shared memory), overriding the autotuner."""
+        _check(_lib.load().afqmc_select_kernel(self.h, int(which), int(variant)), self.h,
+               "afqmc_select_kernel")
+
     def adjoint_run(self, n_steps, fields=None, mgs_every=5, energy_every=5, checkpoint=0):
         """(E, dE/dh1 [M, M]) of an n_steps FP64 run by the library's reverse mode: E is the
         mean over the measurements (every energy_every steps) of sum w Re E_L / sum w, the

@@ -75,6 +75,17 @@ void free_ctx(Ctx* h) {
   for (float* b : {h->Avhs32, h->phi32, h->expK32, h->Ltil32, h->theta32, h->LtT})
     if (b) cudaFree(b);
   if (h->d_tc_err) cudaFree(h->d_tc_err);
+  if (h->etc) {
+    for (afq::TcOperand* op : {h->etc->A, h->etc->B})
+      if (op) {
+        if (op->hi) cudaFree(op->hi);
+        if (op->lo) cudaFree(op->lo);
+        delete op;
+      }
+    if (h->etc->part) cudaFree(h->etc->part);
+    delete h->etc;
+    h->etc = nullptr;
+  }
 }
 
 afqmc_status overlap_launch(Ctx* h, const double* src, int mode, cudaStream_t s);
@@ -134,6 +145,32 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   if (e == cudaSuccess && overlap_launch(h, nullptr, afq::OV_REFRESH, s) != AFQMC_OK)
     e = cudaErrorUnknown;
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Avhs32, 0, sizeof(float) * 2 * (size_t)Nw * MM, s);
+  if (e == cudaSuccess && afq::energy_tc_np(*h) > 0) {
+    // tensor-core local energy: operands in the padded (g, n') / (w, re/im, n') row layouts
+    const int np = afq::energy_tc_np(*h);
+    e = afq::prepare_energy_tc_kernels();
+    if (e == cudaSuccess) {
+      h->etc = new afq::EnergyTc();
+      h->etc->NP = np;
+      int ra = 0, rb = 0;
+      afq::energy_tc_sizes(*h, np, &ra, &rb, &h->etc->Kp, &h->etc->RT, &h->etc->NwP);
+      h->etc->A = new afq::TcOperand();
+      h->etc->B = new afq::TcOperand();
+      h->etc->A->rows = ra;
+      h->etc->B->rows = rb;
+      const size_t ka = (size_t)ra * h->etc->Kp, kb = (size_t)rb * h->etc->Kp;
+      if (dalloc(h, &h->etc->A->hi, ka) != AFQMC_OK || dalloc(h, &h->etc->A->lo, ka) != AFQMC_OK ||
+          dalloc(h, &h->etc->B->hi, kb) != AFQMC_OK || dalloc(h, &h->etc->B->lo, kb) != AFQMC_OK ||
+          dalloc(h, &h->etc->part, 2 * (size_t)h->etc->RT * h->etc->NwP) != AFQMC_OK) {
+        if (own) {
+          cudaStreamSynchronize(s);
+          cudaFree(tmp);
+        }
+        return AFQMC_ERR_NOMEM;
+      }
+      e = afq::energy_tc_init(*h, *h->etc, s);
+    }
+  }
   if (e == cudaSuccess && h->opt.autotune)
     e = afq::autotune_mixed(*h, h->opt.autotune_cache, s);
   if (own) {
@@ -166,7 +203,11 @@ afqmc_status step_launch_mixed(Ctx* h, const double* fields_t, cudaStream_t s) {
 
 afqmc_status energy_launch(Ctx* h, cudaStream_t s) {
   if (h->opt.precision == AFQMC_BF16X3) {
-    AFQ_CK(afq::launch_energy_tiled(*h, h->theta32, h->LtT, s));
+    if (h->etc && h->tune_energy_wb <= 0) {
+      AFQ_CK(afq::launch_energy_tc(*h, s));
+    } else {
+      AFQ_CK(afq::launch_energy_tiled(*h, h->theta32, h->LtT, s));
+    }
   } else {
     AFQ_CK(afq::launch_energy(*h, s));
   }
@@ -634,6 +675,7 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
         if (h->phi32) return afq::launch_taylor_f32_best(*h, h->phi32, h->Avhs32, s);
         return afq::launch_taylor(*h, h->phi2, s);
       default:
+        if (h->etc && h->tune_energy_wb <= 0) return afq::launch_energy_tc(*h, s);
         if (h->LtT) return afq::launch_energy_tiled(*h, h->theta32, h->LtT, s);
         return afq::launch_energy(*h, s);
     }
@@ -829,6 +871,26 @@ afqmc_status afqmc_get_tangent_state(afqmc_handle h, double* dlogw, cudaStream_t
   AFQ_CK(cudaMemcpyAsync(dlogw, h->dlogw, sizeof(double) * h->Nw, cudaMemcpyDefault, s));
   AFQ_CK(cudaStreamSynchronize(s));
   return AFQMC_OK;
+}
+
+afqmc_status afqmc_select_kernel(afqmc_handle h, int which, int variant) {
+  if (!h) return AFQMC_ERR_ARG;
+  if (h->opt.precision != AFQMC_BF16X3) return set_err(h, AFQMC_ERR_ARG, "FP64 handles have no variants");
+  if (which == AFQMC_K_EXCHANGE) {
+    const bool ok = variant == 0 ? h->etc != nullptr
+                                 : (variant == 2 || variant == 4 || variant == 8) &&
+                                       afq::energy_variant_ok(*h, variant);
+    if (!ok) return set_err(h, AFQMC_ERR_ARG, "local-energy variant unsupported for this shape");
+    h->tune_energy_wb = variant;
+    return AFQMC_OK;
+  }
+  if (which == AFQMC_K_TAYLOR) {
+    if ((variant != 0 && variant != 1) || !afq::taylor_variant_ok(*h, variant))
+      return set_err(h, AFQMC_ERR_ARG, "Taylor variant unsupported for this shape");
+    h->tune_taylor_smem = variant;
+    return AFQMC_OK;
+  }
+  return set_err(h, AFQMC_ERR_ARG, "no variants for this kernel");
 }
 
 afqmc_status afqmc_test_gemm(int impl, int Md, int Nd, int K, const double* A, const double* B,

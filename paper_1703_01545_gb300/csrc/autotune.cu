@@ -82,7 +82,7 @@ float time_variant(F launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
 cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto cache = load(cache_path);
-  const std::string ke = key_of(c, "energy_wb"), kt = key_of(c, "taylor_smem");
+  const std::string ke = key_of(c, "energy_v2"), kt = key_of(c, "taylor_smem");
   bool dirty = false;
   cudaEvent_t e0, e1;
   cudaError_t err = cudaEventCreate(&e0);
@@ -92,14 +92,17 @@ cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s) {
     cudaEventDestroy(e0);
     return err;
   }
-  if (cache.count(ke) && energy_variant_ok(c, cache[ke])) {
+  if (cache.count(ke) && (cache[ke] == 0 ? c.etc != nullptr : energy_variant_ok(c, cache[ke]))) {
     c.tune_energy_wb = cache[ke];
   } else {
     float best = 1e30f;
-    for (int wb : {2, 4, 8}) {
-      if (!energy_variant_ok(c, wb)) continue;
-      const float t = time_variant([&]() { return launch_energy_tiled(c, c.theta32, c.LtT, s, -1, wb); },
-                                   s, e0, e1);
+    for (int wb : {0, 2, 4, 8}) {   // 0: tensor-core kernel
+      if (wb == 0 ? c.etc == nullptr : !energy_variant_ok(c, wb)) continue;
+      const float t = time_variant(
+          [&]() {
+            return wb == 0 ? launch_energy_tc(c, s) : launch_energy_tiled(c, c.theta32, c.LtT, s, -1, wb);
+          },
+          s, e0, e1);
       if (t < best) { best = t; c.tune_energy_wb = wb; }
     }
     cache[ke] = c.tune_energy_wb;

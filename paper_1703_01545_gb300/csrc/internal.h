@@ -14,6 +14,14 @@ namespace afq {
 inline int64_t packed_size(int M) { return (int64_t)M * (M + 1) / 2; }
 
 struct Workspace;
+struct TcOperand;
+// tensor-core local energy of the split-precision step (energy_tc.cu)
+struct EnergyTc {
+  TcOperand* A = nullptr;     // rows (g, n') of Psi^T L_g, spin blocks padded to NP / 2
+  TcOperand* B = nullptr;     // rows (w, re/im, n') of Theta
+  float* part = nullptr;      // [RT][2][NwP] partial two-body energies per row tile
+  int NP = 0, Kp = 0, RT = 0, NwP = 0;
+};
 
 struct Ctx {
   int M = 0, X = 0, n_up = 0, n_dn = 0, N = 0, Nw = 0, R = 1;
@@ -59,8 +67,9 @@ struct Ctx {
   float* theta32 = nullptr;   // [2][Nw][N][M]  Theta in FP32 (split-precision mode)
   float* LtT = nullptr;       // [X][M][NPT]    Psi_s^T L_g transposed, spin-padded (FP32)
   int* d_tc_err = nullptr;    // set by a tensor-core kernel whose bounded wait expired
+  EnergyTc* etc = nullptr;    // tensor-core local energy (null when the shape is unsupported)
   // autotuned variants (autotune.cpp); -1 = not tuned, use the default
-  int tune_energy_wb = -1;    // walkers per CTA of the FP32 exchange kernel: 2, 4 or 8
+  int tune_energy_wb = -1;    // local energy: 0 tensor cores, else walkers per CTA of the FP32 kernel (2, 4, 8)
   int tune_taylor_smem = -1;  // 1: A_w staged in shared memory, 0: read through L1
   // tangent mode (tangent.cu): derivative along h1 -> h1 + lambda P, FP64 path only
   bool tangent_on = false;
@@ -129,6 +138,12 @@ bool energy_variant_ok(const Ctx& c, int wb);
 bool taylor_variant_ok(const Ctx& c, int use_smem);
 cudaError_t launch_taylor_f32_variant(const Ctx& c, float* phi32, const float* A32, cudaStream_t s,
                                       int use_smem);
+// tensor-core local energy (energy_tc.cu)
+int energy_tc_np(const Ctx& c);   // padded orbitals per Cholesky vector (8, 16, 32) or 0
+cudaError_t prepare_energy_tc_kernels();
+void energy_tc_sizes(const Ctx& c, int NP, int* rows_A, int* rows_B, int* Kp, int* RT, int* NwP);
+cudaError_t energy_tc_init(const Ctx& c, EnergyTc& et, cudaStream_t s);
+cudaError_t launch_energy_tc(const Ctx& c, cudaStream_t s, int n_walkers = -1);
 // runtime autotuner (autotune.cpp): times the variants on the handle's buffers at setup
 cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s);
 cudaError_t launch_taylor_f32_best(const Ctx& c, float* phi32, const float* A32, cudaStream_t s);
