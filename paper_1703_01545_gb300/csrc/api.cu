@@ -88,7 +88,8 @@ void free_ctx(Ctx* h) {
   }
 }
 
-afqmc_status overlap_launch(Ctx* h, const double* src, int mode, cudaStream_t s);
+afqmc_status overlap_launch(Ctx* h, const double* src, int mode, cudaStream_t s,
+                            const float* src32 = nullptr);
 
 // Allocate a split operand of `rows` logical rows (padded to whole TMA boxes, zero-filled)
 // and K = Kp columns, and encode its tensor maps.
@@ -114,6 +115,7 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   AFQ_CK(afq::prepare_mixed_kernels(*h));
   AFQ_CK(afq::prepare_mixed_kernels2(*h));
   AFQ_CK(afq::prepare_fast_walker_kernels(*h));
+  AFQ_CK(afq::prepare_propagate_f32());
   if ((st = make_operand(h, &h->tc_L, (int)MM, X, s)) != AFQMC_OK) return st;
   if ((st = make_operand(h, &h->tc_Ltil, X, (int)NM, s)) != AFQMC_OK) return st;
   if ((st = make_operand(h, &h->tc_U, 2 * Nw, X, s)) != AFQMC_OK) return st;
@@ -192,10 +194,17 @@ afqmc_status step_launch_mixed(Ctx* h, const double* fields_t, cudaStream_t s) {
   }
   AFQ_CK(afq::launch_fields_mixed(*h, fields_t, s));
   AFQ_CK(afq::gemm_bf16x3(*h->tc_L, *h->tc_U, (int)MM, 2 * Nw, 1.0f, h->Avhs32, MM, h->d_tc_err, s));
-  AFQ_CK(afq::gemm_f32_from_f64(M, 2 * Nw * N, M, 1.0f, h->expK32, M, h->phi, M, h->phi32, M, s));
-  AFQ_CK(afq::launch_taylor_f32_best(*h, h->phi32, h->Avhs32, s));
-  AFQ_CK(afq::gemm_f32_to_f64(M, 2 * Nw * N, M, 1.0f, h->expK32, M, h->phi32, M, h->theta, M, s));
-  afqmc_status os = overlap_launch(h, h->theta, afq::OV_UPDATE, s);
+  const float* p32 = nullptr;
+  if (afq::fused_propagation(*h)) {
+    // Phi' (FP64 into theta, FP32 into phi32) in one kernel
+    AFQ_CK(afq::launch_propagate_f32(*h, h->theta, h->phi32, s));
+    p32 = h->phi32;
+  } else {
+    AFQ_CK(afq::gemm_f32_from_f64(M, 2 * Nw * N, M, 1.0f, h->expK32, M, h->phi, M, h->phi32, M, s));
+    AFQ_CK(afq::launch_taylor_f32_best(*h, h->phi32, h->Avhs32, s));
+    AFQ_CK(afq::gemm_f32_to_f64(M, 2 * Nw * N, M, 1.0f, h->expK32, M, h->phi32, M, h->theta, M, s));
+  }
+  afqmc_status os = overlap_launch(h, h->theta, afq::OV_UPDATE, s, p32);
   if (os != AFQMC_OK) return os;
   AFQ_CK(afq::launch_step_advance(*h, s));
   return AFQMC_OK;
@@ -285,9 +294,10 @@ afqmc_status step_launch(Ctx* h, const double* fields_t, cudaStream_t s) {
 }
 
 // Overlap / Theta / weight kernel: the warp-synchronous variant in split-precision mode.
-afqmc_status overlap_launch(Ctx* h, const double* src, int mode, cudaStream_t s) {
+afqmc_status overlap_launch(Ctx* h, const double* src, int mode, cudaStream_t s,
+                            const float* src32) {
   if (h->theta32 && h->tc_Theta && afq::fast_walker_kernels_ok(*h)) {
-    AFQ_CK(afq::launch_overlap_fast(*h, src, mode, s));
+    AFQ_CK(afq::launch_overlap_fast(*h, src, mode, s, src32));
   } else {
     AFQ_CK(afq::launch_overlap(*h, src, mode, s));
   }
@@ -671,7 +681,8 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
         if (h->theta32 && h->tc_Theta && afq::fast_walker_kernels_ok(*h))
           return afq::launch_overlap_fast(*h, nullptr, afq::OV_REFRESH, s);
         return afq::launch_overlap(*h, nullptr, afq::OV_REFRESH, s);
-      case AFQMC_K_TAYLOR:
+      case AFQMC_K_TAYLOR:   // split precision: the fused propagator times its two one-body products too
+        if (h->phi32 && afq::fused_propagation(*h)) return afq::launch_propagate_f32(*h, h->theta, nullptr, s);
         if (h->phi32) return afq::launch_taylor_f32_best(*h, h->phi32, h->Avhs32, s);
         return afq::launch_taylor(*h, h->phi2, s);
       default:
@@ -885,7 +896,7 @@ afqmc_status afqmc_select_kernel(afqmc_handle h, int which, int variant) {
     return AFQMC_OK;
   }
   if (which == AFQMC_K_TAYLOR) {
-    if ((variant != 0 && variant != 1) || !afq::taylor_variant_ok(*h, variant))
+    if (variant < 0 || variant > 2 || !afq::taylor_variant_ok(*h, variant))
       return set_err(h, AFQMC_ERR_ARG, "Taylor variant unsupported for this shape");
     h->tune_taylor_smem = variant;
     return AFQMC_OK;

@@ -70,7 +70,7 @@ struct Ctx {
   EnergyTc* etc = nullptr;    // tensor-core local energy (null when the shape is unsupported)
   // autotuned variants (autotune.cpp); -1 = not tuned, use the default
   int tune_energy_wb = -1;    // local energy: 0 tensor cores, else walkers per CTA of the FP32 kernel (2, 4, 8)
-  int tune_taylor_smem = -1;  // 1: A_w staged in shared memory, 0: read through L1
+  int tune_taylor_smem = -1;  // propagation: 2 fused kernel; Taylor kernel with A in shared memory (1) or L1 (0)
   // tangent mode (tangent.cu): derivative along h1 -> h1 + lambda P, FP64 path only
   bool tangent_on = false;
   double* Bneg = nullptr;     // [M][M]  -dt K / 2 (kept from setup)
@@ -138,6 +138,15 @@ bool energy_variant_ok(const Ctx& c, int wb);
 bool taylor_variant_ok(const Ctx& c, int use_smem);
 cudaError_t launch_taylor_f32_variant(const Ctx& c, float* phi32, const float* A32, cudaStream_t s,
                                       int use_smem);
+// fused FP32 propagator e^{-dt K/2} e^A e^{-dt K/2} of the split-precision step (propagate_f32.cu)
+bool propagate_f32_ok(const Ctx& c);
+cudaError_t prepare_propagate_f32();
+cudaError_t launch_propagate_f32(const Ctx& c, double* out, float* out32, cudaStream_t s);
+// the split-precision step propagates with the fused kernel (variant 2, the default when the
+// shape allows it) or with two FP32 GEMMs around a Taylor kernel (variants 0 and 1)
+inline bool fused_propagation(const Ctx& c) {
+  return (c.tune_taylor_smem == 2 || c.tune_taylor_smem < 0) && propagate_f32_ok(c);
+}
 // tensor-core local energy (energy_tc.cu)
 int energy_tc_np(const Ctx& c);   // padded orbitals per Cholesky vector (8, 16, 32) or 0
 cudaError_t prepare_energy_tc_kernels();
@@ -150,7 +159,8 @@ cudaError_t launch_taylor_f32_best(const Ctx& c, float* phi32, const float* A32,
 // latency-oriented FP64 walker kernels of the split-precision step (walker_fast.cu)
 bool fast_walker_kernels_ok(const Ctx& c);
 cudaError_t prepare_fast_walker_kernels(const Ctx& c);
-cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaStream_t s);
+cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaStream_t s,
+                                const float* src32 = nullptr);
 cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s);
 cudaError_t launch_fields_mixed(const Ctx& c, const double* fields, cudaStream_t s);
 // tangent mode (tangent.cu)

@@ -694,7 +694,9 @@ cudaError_t launch_energy_tiled(const Ctx& c, const float* theta32, const float*
 }
 
 bool energy_variant_ok(const Ctx& c, int wb) { return energy_wb_ok(c, wb); }
-bool taylor_variant_ok(const Ctx& c, int use_smem) { return use_smem ? taylor_smem_ok(c) : true; }
+bool taylor_variant_ok(const Ctx& c, int v) {
+  return v == 2 ? propagate_f32_ok(c) : v == 1 ? taylor_smem_ok(c) : true;
+}
 
 cudaError_t launch_taylor_f32_variant(const Ctx& c, float* phi32, const float* A32, cudaStream_t s,
                                       int use_smem) {

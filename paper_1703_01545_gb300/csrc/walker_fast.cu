@@ -18,6 +18,7 @@ constexpr int kNsMax = 16;   // spin block size handled by the warp Gauss-Jordan
 
 struct FastOvArgs {
   const double* src;  // [2][Nw][N][M]  (propagated walkers in update mode)
+  const float* src32; // the same in FP32 (update mode, may be null): no conversions needed
   double* phi;
   float* theta32;
   __nv_bfloat16* op_hi;
@@ -58,12 +59,13 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   const bool upd = (a.mode == OV_UPDATE) && live;
   const double* src = upd ? a.src : a.phi;
   const int64_t plane = (int64_t)a.Nw * NM, wbase = (int64_t)wk * NM;
+  const bool f32 = upd && a.src32 != nullptr;
   for (int e = tid; e < NM; e += blockDim.x) {
     const double xr = src[wbase + e], xi = src[plane + wbase + e];
     pr[e] = xr;
     pi[e] = xi;
-    pfr[e] = (float)xr;
-    pfi[e] = (float)xi;
+    pfr[e] = f32 ? a.src32[wbase + e] : (float)xr;
+    pfi[e] = f32 ? a.src32[plane + wbase + e] : (float)xi;
   }
   if (tid < 2) { s_det[tid][0] = 1.0; s_det[tid][1] = 0.0; s_dexp[tid] = 0; s_bad[tid] = 0; }
   __syncthreads();
@@ -373,9 +375,11 @@ cudaError_t prepare_fast_walker_kernels(const Ctx& c) {
   return cudaSuccess;
 }
 
-cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaStream_t s) {
+cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaStream_t s,
+                                const float* src32) {
   FastOvArgs a;
-  a.src = src; a.phi = c.phi; a.theta32 = c.theta32;
+  a.src = src;
+  a.src32 = src32; a.phi = c.phi; a.theta32 = c.theta32;
   a.op_hi = c.tc_Theta->hi; a.op_lo = c.tc_Theta->lo; a.Kp = c.tc_Theta->Kp;
   a.psi = c.psi; a.logO = c.logO; a.w = c.w; a.alive = c.alive; a.aux = c.aux; a.flags = c.d_flags;
   a.M = c.M; a.N = c.N; a.n_up = c.n_up; a.Nw = c.Nw; a.mode = mode;
