@@ -53,6 +53,8 @@ def _measured_bf16_peak():
 
 
 BF16_PEAK_TFLOPS = _measured_bf16_peak()
+# FP32 SIMT peak derived from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def parse():
@@ -65,6 +67,9 @@ def parse():
     ap.add_argument("--coupling", default="moderate", choices=["literal", "moderate"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune-cache", default=None,
+                    help="kernel-variant cache file: read if present, else written after tuning "
+                         "(lets a profiled run reuse the choices of an unprofiled one)")
     ap.add_argument("--kernel", choices=["vhs", "force_bias", "taylor", "energy", "overlap"],
                     help="profiling aid: set up the workload, take one step, then launch only "
                          "this kernel --reps times (no JSON line)")
@@ -218,7 +223,8 @@ def run_kernel(args, wl):
     d = systems(wl, args.coupling)[0]
     nw = args.walkers or wl["n_walkers"]
     A = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=wl["dt"], n_walkers=nw,
-                   precision={"fp64": afq.FP64, "bf16x3": afq.BF16X3}[args.precision])
+                   precision={"fp64": afq.FP64, "bf16x3": afq.BF16X3}[args.precision],
+                   autotune_cache=args.autotune_cache)
     A.propagate(1)
     which = {"vhs": afq.K_VHS, "force_bias": afq.K_FORCE_BIAS, "taylor": afq.K_TAYLOR,
              "energy": afq.K_EXCHANGE, "overlap": afq.K_OVERLAP}[args.kernel]
@@ -246,7 +252,8 @@ def run_ours(args, wl, rank, world, local_rank):
 
     def make(d, prec):
         return afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt, n_walkers=nw,
-                          seed=1, n_repeats=R, walker_offset=rank * nw, precision=prec_id[prec])
+                          seed=1, n_repeats=R, walker_offset=rank * nw, precision=prec_id[prec],
+                          autotune_cache=args.autotune_cache)
 
     def timed(prec, coupling, clocks=None):
         dA, dB = systems(wl, coupling)
@@ -316,18 +323,50 @@ def run_ours(args, wl, rank, world, local_rank):
                        "ms_per_launch": vhs_ms,
                        "traffic": tr["dram_bytes_per_launch"] if tr else None,
                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, kernel timed alone)"}
-        # time-dominant kernel of the split-precision step: the FP64 overlap / inverse / det
+        # time-dominant kernel of the split-precision step: the fused FP32 propagator
+        # e^{-dt K/2} e^A e^{-dt K/2} (largest share in the launch list); its algorithmic work is
+        # `order` complex products A T plus two real-by-complex one-body products per walker
+        order = 6
+        p_ms = afq.afqmc_time_kernel(A.h, afq.K_TAYLOR, 5, stream.cuda_stream)
+        pflops = (8.0 * order + 8.0) * M * M * N * nw
+        ach = pflops / (p_ms / 1e3) / 1e12
+        trp = traffic_for("propagate_f32.cu", "propagate_f32_C2")
+        roofline = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP32_PEAK_TFLOPS,
+                    "traffic": trp["dram_bytes_per_launch"] if trp else None,
+                    "kernel": "k_propagate_f32 (fused one-body half steps + Taylor exponential, "
+                              "FP32; largest share of the split-precision step)",
+                    "algorithmic_flops_per_launch": pflops, "ms_per_launch": p_ms,
+                    "peak_source": "derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+        # the FP64 overlap / Gauss-Jordan inverse / log det kernel (second share)
         o_ms = afq.afqmc_time_kernel(A.h, afq.K_OVERLAP, 5, stream.cuda_stream)
         oflops = (4.0 * M * N2 + 8.0 * (nu ** 3 + nd ** 3)) * nw   # FP64: Psi^T Phi, Gauss-Jordan
-        ach = oflops / (o_ms / 1e3) / 1e12
         tro = traffic_for("walker_fast.cu", "overlap_fast_C2")
-        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS,
-                    "traffic": tro["dram_bytes_per_launch"] if tro else None,
-                    "kernel": "k_overlap_fast (FP64 overlap, Gauss-Jordan inverse, log det; "
-                              "largest share of the split-precision step)",
-                    "algorithmic_flops_per_launch": oflops, "ms_per_launch": o_ms,
-                    "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe table)"}
+        roofline["overlap_fp64"] = {
+            "bound": "alu", "achieved": oflops / (o_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": oflops / (o_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+            "traffic": tro["dram_bytes_per_launch"] if tro else None,
+            "kernel": "k_overlap_fast (refresh form: FP64 overlap, Gauss-Jordan inverse, log det)",
+            "algorithmic_flops_per_launch": oflops, "ms_per_launch": o_ms,
+            "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe table)"}
+        # the tensor-core local energy: split-BF16 GEMM of Psi^T L_g Theta over (g, w) with the
+        # exchange reduction in the epilogue; MMA work counts the orbital padding to P2 per spin
+        e_ms = afq.afqmc_time_kernel(A.h, afq.K_EXCHANGE, 5, stream.cuda_stream)
+        p2 = 4
+        while p2 < max(nu, nd):
+            p2 *= 2
+        NPp, Kp = 2 * p2, (M + 63) // 64 * 64
+        eflops = 3.0 * 2.0 * (X * NPp) * (2 * NPp * nw) * Kp
+        useful_e = 2.0 * X * (nu * nu + nd * nd) * M * 2 * nw
+        tre = traffic_for("energy_tc.cu", "energy_tc_C2")
+        roofline["energy_tc"] = {
+            "bound": "tensor", "achieved": eflops / (e_ms / 1e3) / 1e12, "peak": BF16_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": eflops / (e_ms / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
+            "traffic": tre["dram_bytes_per_launch"] if tre else None,
+            "kernel": "k_energy_B + k_energy_tc + k_energy_tc_reduce (split-BF16 tcgen05 local energy)",
+            "algorithmic_flops_per_launch": eflops, "useful_flops_per_launch": useful_e,
+            "ms_per_launch": e_ms,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, kernel timed alone)"}
     contraction["frac"] = contraction["achieved"] / contraction["peak"]
     roofline["contraction_vhs"] = contraction
     main["A"].close()

@@ -72,7 +72,7 @@ void free_ctx(Ctx* h) {
   for (double* b : {h->Bneg, h->dexpK, h->htilP, h->dphi, h->dphi2, h->dtheta, h->drhobar, h->dU,
                     h->dAvhs, h->dlogO, h->dlogw, h->daux, h->deloc, h->desum})
     if (b) cudaFree(b);
-  for (float* b : {h->Avhs32, h->phi32, h->expK32, h->Ltil32, h->theta32, h->LtT})
+  for (float* b : {h->Avhs32, h->phi32, h->expK32, h->Ltil32, h->theta32, h->LtT, h->psi32h, h->psi32l})
     if (b) cudaFree(b);
   if (h->d_tc_err) cudaFree(h->d_tc_err);
   if (h->etc) {
@@ -127,6 +127,8 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   if ((st = dalloc(h, &h->d_tc_err, 1)) != AFQMC_OK) return st;
   if ((st = dalloc(h, &h->theta32, 2 * (size_t)Nw * NM)) != AFQMC_OK) return st;
   if ((st = dalloc(h, &h->LtT, (size_t)afq::LtT_size(*h))) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->psi32h, (size_t)NM)) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->psi32l, (size_t)NM)) != AFQMC_OK) return st;
   AFQ_CK(cudaMemsetAsync(h->d_tc_err, 0, sizeof(int), s));
   // L as rows ij with g contiguous: transpose [X][M*M] -> [M*M][X] through phi2 (large enough
   // only when 2*Nw*N*M >= X*M*M; otherwise a temporary)
@@ -143,6 +145,7 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   if (e == cudaSuccess) e = afq::to_float(h->expK, h->expK32, MM, s);
   if (e == cudaSuccess) e = afq::to_float(h->Ltil, h->Ltil32, (int64_t)X * NM, s);
   if (e == cudaSuccess) e = afq::build_LtT(*h, h->LtT, s);
+  if (e == cudaSuccess) e = afq::split_f32(h->psi, h->psi32h, h->psi32l, NM, s);
   // Theta of the current walkers in FP32 and as the split force-bias operand
   if (e == cudaSuccess && overlap_launch(h, nullptr, afq::OV_REFRESH, s) != AFQMC_OK)
     e = cudaErrorUnknown;

@@ -66,6 +66,7 @@ struct Ctx {
   float* Ltil32 = nullptr;    // [X][N][M]
   float* theta32 = nullptr;   // [2][Nw][N][M]  Theta in FP32 (split-precision mode)
   float* LtT = nullptr;       // [X][M][NPT]    Psi_s^T L_g transposed, spin-padded (FP32)
+  float *psi32h = nullptr, *psi32l = nullptr;   // [N][M]  psi = psi32h + psi32l (FP32 pair)
   int* d_tc_err = nullptr;    // set by a tensor-core kernel whose bounded wait expired
   EnergyTc* etc = nullptr;    // tensor-core local energy (null when the shape is unsupported)
   // autotuned variants (autotune.cpp); -1 = not tuned, use the default
@@ -129,6 +130,8 @@ cudaError_t gemm_f32_to_f64(int Md, int Nd, int Kd, float alpha, const float* A,
 cudaError_t launch_taylor_f32(const Ctx& c, float* phi32, const float* A32, cudaStream_t s);
 cudaError_t launch_energy_f32(const Ctx& c, const float* Ltil32, cudaStream_t s, int n_walkers = -1);
 cudaError_t to_float(const double* in, float* out, int64_t n, cudaStream_t s);
+// hi = fl32(in), lo = fl32(in - hi)
+cudaError_t split_f32(const double* in, float* hi, float* lo, int64_t n, cudaStream_t s);
 cudaError_t prepare_mixed_kernels2(const Ctx& c);
 cudaError_t build_LtT(const Ctx& c, float* LtT, cudaStream_t s);
 int64_t LtT_size(const Ctx& c);

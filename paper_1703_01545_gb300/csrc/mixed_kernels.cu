@@ -307,6 +307,22 @@ cudaError_t launch_energy_f32(const Ctx& c, const float* Ltil32, cudaStream_t s,
   return cudaGetLastError();
 }
 
+__global__ void k_split_f32(const double* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo,
+                            int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float h = (float)in[e];
+    hi[e] = h;
+    lo[e] = (float)(in[e] - (double)h);
+  }
+}
+
+cudaError_t split_f32(const double* in, float* hi, float* lo, int64_t n, cudaStream_t s) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+  k_split_f32<<<grid, 256, 0, s>>>(in, hi, lo, n);
+  return cudaGetLastError();
+}
+
 cudaError_t to_float(const double* in, float* out, int64_t n, cudaStream_t s) {
   int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 64);
   if (grid < 1) grid = 1;

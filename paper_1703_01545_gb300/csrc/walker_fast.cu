@@ -18,7 +18,10 @@ constexpr int kNsMax = 16;   // spin block size handled by the warp Gauss-Jordan
 
 struct FastOvArgs {
   const double* src;  // [2][Nw][N][M]  (propagated walkers in update mode)
-  const float* src32; // the same in FP32 (update mode, may be null): no conversions needed
+  const float* src32; // the same in FP32 (update mode, may be null): no conversions needed,
+                      // and the overlap is summed in double-float FP32 arithmetic
+  const float* psih;  // psi = psih + psil (FP32 pair, [N][M])
+  const float* psil;
   double* phi;
   float* theta32;
   __nv_bfloat16* op_hi;
@@ -36,6 +39,18 @@ struct FastOvArgs {
 
 // One CTA (256 threads) per walker.  Shared: phi [2][N][M] (FP64), per spin the overlap
 // matrix inverted in place (re and im [16][32], FP64), FP32 copies of phi and the inverses.
+// s + c += (h + l) x for FP32 h, l, x with the product and the addition error-free (Dekker
+// product through FMA, Knuth two-sum); the intrinsics keep the compiler from contracting them.
+__device__ __forceinline__ void df_acc(float& s, float& c, float h, float l, float x) {
+  const float p = __fmul_rn(h, x);
+  const float e = __fmaf_rn(h, x, -p);                  // h x - p, exactly
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));   // s + p - t
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(l, x, e)));
+}
+
 // ROWS: elimination rows per lane, ceil(ns / (32 / ns)) for the larger spin block (2, 4 or 8);
 // the multipliers of those rows are held in registers.
 template <int ROWS>
@@ -79,13 +94,32 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
       if (ent < nu * nu) { r = ent / nu; c = ent % nu; }
       else { sp = 1; const int e2 = ent - nu * nu; r = e2 / nd; c = e2 % nd; }
       const int n0 = sp ? nu : 0;
-      const double* ps = a.psi + (int64_t)(n0 + r) * M;
-      const double* fr = pr + (n0 + c) * M;
-      const double* fi = pi + (n0 + c) * M;
-      for (int i = part; i < M; i += 4) {
-        const double p = __ldg(ps + i);
-        re = fma(p, fr[i], re);
-        im = fma(p, fi[i], im);
+      if (f32) {
+        // phi is exactly representable in FP32 here: each term psi*phi is formed exactly as
+        // (psih*phi rounded) + (its FMA residual) + psil*phi and summed as an unevaluated pair
+        // (s, c) with error-free additions, ~2^-46 relative to sum |terms|; the FP64 pipe
+        // sees only the final conversions
+        const float* hs = a.psih + (int64_t)(n0 + r) * M;
+        const float* ls = a.psil + (int64_t)(n0 + r) * M;
+        const float* xr = pfr + (n0 + c) * M;
+        const float* xi = pfi + (n0 + c) * M;
+        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+        for (int i = part; i < M; i += 4) {
+          const float h = __ldg(hs + i), l = __ldg(ls + i);
+          df_acc(sr, cr, h, l, xr[i]);
+          df_acc(si, ci, h, l, xi[i]);
+        }
+        re = (double)sr + (double)cr;
+        im = (double)si + (double)ci;
+      } else {
+        const double* ps = a.psi + (int64_t)(n0 + r) * M;
+        const double* fr = pr + (n0 + c) * M;
+        const double* fi = pi + (n0 + c) * M;
+        for (int i = part; i < M; i += 4) {
+          const double p = __ldg(ps + i);
+          re = fma(p, fr[i], re);
+          im = fma(p, fi[i], im);
+        }
       }
     }
     re += __shfl_xor_sync(0xffffffffu, re, 1);
@@ -379,7 +413,9 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
                                 const float* src32) {
   FastOvArgs a;
   a.src = src;
-  a.src32 = src32; a.phi = c.phi; a.theta32 = c.theta32;
+  a.src32 = c.psi32h ? src32 : nullptr;
+  a.psih = c.psi32h;
+  a.psil = c.psi32l; a.phi = c.phi; a.theta32 = c.theta32;
   a.op_hi = c.tc_Theta->hi; a.op_lo = c.tc_Theta->lo; a.Kp = c.tc_Theta->Kp;
   a.psi = c.psi; a.logO = c.logO; a.w = c.w; a.alive = c.alive; a.aux = c.aux; a.flags = c.d_flags;
   a.M = c.M; a.N = c.N; a.n_up = c.n_up; a.Nw = c.Nw; a.mode = mode;
