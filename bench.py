@@ -323,21 +323,40 @@ def run_ours(args, wl, rank, world, local_rank):
                        "ms_per_launch": vhs_ms,
                        "traffic": tr["dram_bytes_per_launch"] if tr else None,
                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, kernel timed alone)"}
-        # time-dominant kernel of the split-precision step: the fused FP32 propagator
-        # e^{-dt K/2} e^A e^{-dt K/2} (largest share in the launch list); its algorithmic work is
-        # `order` complex products A T plus two real-by-complex one-body products per walker
+        # time-dominant kernel of the split-precision step: the propagator
+        # e^{-dt K/2} e^A e^{-dt K/2} (largest share in the launch list) in the variant the
+        # autotuner chose; its algorithmic work is `order` complex products A T plus two
+        # real-by-complex one-body products per walker
         order = 6
+        pv = A.info().tuned_taylor_smem
         p_ms = afq.afqmc_time_kernel(A.h, afq.K_TAYLOR, 5, stream.cuda_stream)
         pflops = (8.0 * order + 8.0) * M * M * N * nw
-        ach = pflops / (p_ms / 1e3) / 1e12
-        trp = traffic_for("propagate_f32.cu", "propagate_f32_C2")
-        roofline = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP32_PEAK_TFLOPS,
-                    "traffic": trp["dram_bytes_per_launch"] if trp else None,
-                    "kernel": "k_propagate_f32 (fused one-body half steps + Taylor exponential, "
-                              "FP32; largest share of the split-precision step)",
-                    "algorithmic_flops_per_launch": pflops, "ms_per_launch": p_ms,
-                    "peak_source": "derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+        if pv == 3:
+            # tensor cores: per walker (order + 2) rounds of 3 split-BF16 MMAs, M = 128 rows
+            # ([A_re; A_im] or E - I over 64 padded orbitals), N = 2 pad8(N), K = 64
+            nb = 2 * ((N + 7) // 8 * 8)
+            mflops = nw * (order + 2) * 3.0 * 2.0 * 128 * nb * 64
+            roofline = {"bound": "tensor", "achieved": mflops / (p_ms / 1e3) / 1e12,
+                        "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": mflops / (p_ms / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
+                        "kernel": "k_propagate_tc (split-BF16 tcgen05 one-body + Taylor rounds; "
+                                  "largest share of the split-precision step)",
+                        "algorithmic_flops_per_launch": mflops, "useful_flops_per_launch": pflops,
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, kernel timed alone)"}
+            trp = traffic_for("propagate_tc.cu", "propagate_tc_C2")
+        else:
+            name = {2: "k_propagate_f32 (fused one-body half steps + Taylor exponential, FP32"}.get(
+                pv, "k_gemm_tn_f32 + k_taylor_f32 + k_gemm_tn_f32 (FP32")
+            ach = pflops / (p_ms / 1e3) / 1e12
+            roofline = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": ach / FP32_PEAK_TFLOPS,
+                        "kernel": name + "; largest share of the split-precision step)",
+                        "algorithmic_flops_per_launch": pflops,
+                        "peak_source": "derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+            trp = traffic_for("propagate_f32.cu", "propagate_f32_C2") if pv == 2 else None
+        roofline["ms_per_launch"] = p_ms
+        roofline["traffic"] = trp["dram_bytes_per_launch"] if trp else None
+        roofline["variant"] = pv
         # the FP64 overlap / Gauss-Jordan inverse / log det kernel (second share)
         o_ms = afq.afqmc_time_kernel(A.h, afq.K_OVERLAP, 5, stream.cuda_stream)
         oflops = (4.0 * M * N2 + 8.0 * (nu ** 3 + nd ** 3)) * nw   # FP64: Psi^T Phi, Gauss-Jordan

@@ -116,6 +116,7 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   AFQ_CK(afq::prepare_mixed_kernels2(*h));
   AFQ_CK(afq::prepare_fast_walker_kernels(*h));
   AFQ_CK(afq::prepare_propagate_f32());
+  AFQ_CK(afq::prepare_propagate_tc());
   if ((st = make_operand(h, &h->tc_L, (int)MM, X, s)) != AFQMC_OK) return st;
   if ((st = make_operand(h, &h->tc_Ltil, X, (int)NM, s)) != AFQMC_OK) return st;
   if ((st = make_operand(h, &h->tc_U, 2 * Nw, X, s)) != AFQMC_OK) return st;
@@ -197,17 +198,10 @@ afqmc_status step_launch_mixed(Ctx* h, const double* fields_t, cudaStream_t s) {
   }
   AFQ_CK(afq::launch_fields_mixed(*h, fields_t, s));
   AFQ_CK(afq::gemm_bf16x3(*h->tc_L, *h->tc_U, (int)MM, 2 * Nw, 1.0f, h->Avhs32, MM, h->d_tc_err, s));
-  const float* p32 = nullptr;
-  if (afq::fused_propagation(*h)) {
-    // Phi' (FP64 into theta, FP32 into phi32) in one kernel
-    AFQ_CK(afq::launch_propagate_f32(*h, h->theta, h->phi32, s));
-    p32 = h->phi32;
-  } else {
-    AFQ_CK(afq::gemm_f32_from_f64(M, 2 * Nw * N, M, 1.0f, h->expK32, M, h->phi, M, h->phi32, M, s));
-    AFQ_CK(afq::launch_taylor_f32_best(*h, h->phi32, h->Avhs32, s));
-    AFQ_CK(afq::gemm_f32_to_f64(M, 2 * Nw * N, M, 1.0f, h->expK32, M, h->phi32, M, h->theta, M, s));
-  }
-  afqmc_status os = overlap_launch(h, h->theta, afq::OV_UPDATE, s, p32);
+  // Phi' = e^{-dt K/2} e^A e^{-dt K/2} Phi into theta (FP64); variants 2, 3 also into phi32 (FP32)
+  const int pv = afq::propagation_variant(*h);
+  AFQ_CK(afq::launch_propagation(*h, pv, h->theta, h->phi32, s));
+  afqmc_status os = overlap_launch(h, h->theta, afq::OV_UPDATE, s, pv >= 2 ? h->phi32 : nullptr);
   if (os != AFQMC_OK) return os;
   AFQ_CK(afq::launch_step_advance(*h, s));
   return AFQMC_OK;
@@ -685,8 +679,7 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
           return afq::launch_overlap_fast(*h, nullptr, afq::OV_REFRESH, s);
         return afq::launch_overlap(*h, nullptr, afq::OV_REFRESH, s);
       case AFQMC_K_TAYLOR:   // split precision: the fused propagator times its two one-body products too
-        if (h->phi32 && afq::fused_propagation(*h)) return afq::launch_propagate_f32(*h, h->theta, nullptr, s);
-        if (h->phi32) return afq::launch_taylor_f32_best(*h, h->phi32, h->Avhs32, s);
+        if (h->phi32) return afq::launch_propagation(*h, afq::propagation_variant(*h), h->theta, nullptr, s);
         return afq::launch_taylor(*h, h->phi2, s);
       default:
         if (h->etc && h->tune_energy_wb <= 0) return afq::launch_energy_tc(*h, s);
@@ -899,7 +892,7 @@ afqmc_status afqmc_select_kernel(afqmc_handle h, int which, int variant) {
     return AFQMC_OK;
   }
   if (which == AFQMC_K_TAYLOR) {
-    if (variant < 0 || variant > 2 || !afq::taylor_variant_ok(*h, variant))
+    if (variant < 0 || variant > 3 || !afq::taylor_variant_ok(*h, variant))
       return set_err(h, AFQMC_ERR_ARG, "Taylor variant unsupported for this shape");
     h->tune_taylor_smem = variant;
     return AFQMC_OK;

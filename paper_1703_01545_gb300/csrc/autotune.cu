@@ -112,20 +112,13 @@ cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s) {
     c.tune_taylor_smem = cache[kt];
   } else {
     float best = 1e30f;
-    // the whole one-body + Taylor propagation: fused kernel (2) or GEMM, Taylor (1, 0), GEMM;
+    // the whole one-body + Taylor propagation: tensor-core (3) or fused FP32 kernel (2), or
+    // GEMM, Taylor (1, 0), GEMM;
     // every variant writes only scratch (phi32, the FP64 theta buffer)
-    const int M = c.M, cols = 2 * c.Nw * c.N;
-    for (int v : {2, 1, 0}) {
+    for (int v : {3, 2, 1, 0}) {
       if (!taylor_variant_ok(c, v)) continue;
-      const float t = time_variant(
-          [&]() {
-            if (v == 2) return launch_propagate_f32(c, c.theta, c.phi32, s);
-            cudaError_t e = gemm_f32_from_f64(M, cols, M, 1.0f, c.expK32, M, c.phi, M, c.phi32, M, s);
-            if (e == cudaSuccess) e = launch_taylor_f32_variant(c, c.phi32, c.Avhs32, s, v);
-            if (e == cudaSuccess) e = gemm_f32_to_f64(M, cols, M, 1.0f, c.expK32, M, c.phi32, M, c.theta, M, s);
-            return e;
-          },
-          s, e0, e1);
+      const float t = time_variant([&]() { return launch_propagation(c, v, c.theta, c.phi32, s); },
+                                   s, e0, e1);
       if (t < best) { best = t; c.tune_taylor_smem = v; }
     }
     cache[kt] = c.tune_taylor_smem;

@@ -145,11 +145,17 @@ cudaError_t launch_taylor_f32_variant(const Ctx& c, float* phi32, const float* A
 bool propagate_f32_ok(const Ctx& c);
 cudaError_t prepare_propagate_f32();
 cudaError_t launch_propagate_f32(const Ctx& c, double* out, float* out32, cudaStream_t s);
-// the split-precision step propagates with the fused kernel (variant 2, the default when the
-// shape allows it) or with two FP32 GEMMs around a Taylor kernel (variants 0 and 1)
-inline bool fused_propagation(const Ctx& c) {
-  return (c.tune_taylor_smem == 2 || c.tune_taylor_smem < 0) && propagate_f32_ok(c);
-}
+// tensor-core propagator (propagate_tc.cu), M <= 64 and N <= 16
+bool propagate_tc_ok(const Ctx& c);
+cudaError_t prepare_propagate_tc();
+cudaError_t launch_propagate_tc(const Ctx& c, double* out, float* out32, cudaStream_t s);
+// Propagation variants of the split-precision step: 3 tensor-core kernel, 2 fused FP32 kernel,
+// 1 / 0 two FP32 GEMMs around a Taylor kernel with A in shared memory / through L1.  The
+// effective variant is the tuned one, else the first the shape supports in that order.
+int propagation_variant(const Ctx& c);
+// Phi' of every walker from c.phi and c.Avhs32 into out (FP64); variants 2 and 3 also write
+// the FP32 copy out32 (may be null), variants 0 and 1 use c.phi32 as scratch
+cudaError_t launch_propagation(const Ctx& c, int variant, double* out, float* out32, cudaStream_t s);
 // tensor-core local energy (energy_tc.cu)
 int energy_tc_np(const Ctx& c);   // padded orbitals per Cholesky vector (8, 16, 32) or 0
 cudaError_t prepare_energy_tc_kernels();

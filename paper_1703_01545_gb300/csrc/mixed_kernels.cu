@@ -711,7 +711,23 @@ cudaError_t launch_energy_tiled(const Ctx& c, const float* theta32, const float*
 
 bool energy_variant_ok(const Ctx& c, int wb) { return energy_wb_ok(c, wb); }
 bool taylor_variant_ok(const Ctx& c, int v) {
-  return v == 2 ? propagate_f32_ok(c) : v == 1 ? taylor_smem_ok(c) : true;
+  return v == 3 ? propagate_tc_ok(c) : v == 2 ? propagate_f32_ok(c) : v == 1 ? taylor_smem_ok(c) : v == 0;
+}
+
+int propagation_variant(const Ctx& c) {
+  if (c.tune_taylor_smem >= 0 && taylor_variant_ok(c, c.tune_taylor_smem)) return c.tune_taylor_smem;
+  for (int v : {3, 2, 1}) if (taylor_variant_ok(c, v)) return v;
+  return 0;
+}
+
+cudaError_t launch_propagation(const Ctx& c, int variant, double* out, float* out32, cudaStream_t s) {
+  if (variant == 3) return launch_propagate_tc(c, out, out32, s);
+  if (variant == 2) return launch_propagate_f32(c, out, out32, s);
+  const int M = c.M, cols = 2 * c.Nw * c.N;
+  cudaError_t e = gemm_f32_from_f64(M, cols, M, 1.0f, c.expK32, M, c.phi, M, c.phi32, M, s);
+  if (e == cudaSuccess) e = launch_taylor_f32_variant(c, c.phi32, c.Avhs32, s, variant);
+  if (e == cudaSuccess) e = gemm_f32_to_f64(M, cols, M, 1.0f, c.expK32, M, c.phi32, M, out, M, s);
+  return e;
 }
 
 cudaError_t launch_taylor_f32_variant(const Ctx& c, float* phi32, const float* A32, cudaStream_t s,

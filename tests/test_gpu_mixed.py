@@ -105,7 +105,7 @@ def test_autotuner_picks_valid_variants_and_persists(tmp_path):
                     precision=afq.BF16X3, autotune_cache=str(cache))
     info = s2.info()
     assert info.tuned_energy_walkers_per_cta in (0, 2, 4, 8)
-    assert info.tuned_taylor_smem in (0, 1, 2)
+    assert info.tuned_taylor_smem in (0, 1, 2, 3)
     text = cache.read_text()
     assert "energy_v2:M64X320u8d8w512" in text and "propagate_v2" in text
     s2.close()

@@ -46,3 +46,38 @@ def test_fused_propagator_matches_three_launch_form(cfg, which, coupling, nw):
     scale = np.abs(ref["phi"][live]).max()
     assert np.abs(fused["phi"][live] - ref["phi"][live]).max() < 1e-4 * scale
     np.testing.assert_allclose(fused["w"].real[live], ref["w"].real[live], rtol=1e-4)
+
+
+@pytest.mark.parametrize("cfg,which,coupling,nw", [
+    ("C1", "A", 1.0, 33),            # M = 8 padded to 64, N = 4 padded to 8
+    ("C1", "B", 1.0, 470),           # N = 3; more walkers than resident CTAs (persistent loop)
+    ("C2", "A", "moderate", 301),    # M = 64, N = 16
+    ("C2", "B", "moderate", 64),     # N = 15
+])
+def test_tensor_core_propagator_matches_fp32(cfg, which, coupling, nw):
+    """Variant 3 (split-BF16 tcgen05 rounds) against the FP32 fused kernel: the Taylor products
+    carry ~2^-16 relative error of |A| |T| per step, so after 5 steps the walkers agree to
+    ~1e-4 of their size."""
+    afq = need_gpu()
+    d = system_data(cfg, which, coupling)
+    dt = CONFIGS[cfg]["dt"]
+    fields = explicit_fields(5, nw, d["X"], seed=6)
+    tc, info = run(afq, d, nw, dt, fields, 3)
+    assert info.tuned_taylor_smem == 3
+    ref, _ = run(afq, d, nw, dt, fields, 2)
+    live = tc["alive"] & ref["alive"]
+    assert live.sum() >= nw - 2
+    scale = np.abs(ref["phi"][live]).max()
+    err = np.abs(tc["phi"][live] - ref["phi"][live]).max() / scale
+    assert err < 5e-4, err
+    np.testing.assert_allclose(tc["w"].real[live], ref["w"].real[live], rtol=2e-3)
+
+
+def test_tensor_core_propagator_refuses_large_shapes():
+    afq = need_gpu()
+    d = system_data("C5", "A", "moderate")
+    s = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=0.005, n_walkers=8,
+                   precision=afq.BF16X3, autotune=False)
+    with pytest.raises(RuntimeError):
+        s.select_kernel(afq.K_TAYLOR, 3)
+    s.close()
