@@ -168,32 +168,36 @@ __global__ void __launch_bounds__(128, 3)
   };
 
   for (int w = blockIdx.x; w < Nw; w += gridDim.x) {
-    // [A_re; A_im] rows: thread tid = operand row r, A row i = r mod 64
-    {
-      const int i = tid & 63;
-      const float* src = Av + (tid < 64 ? 0 : (int64_t)Nw * MM) + (int64_t)w * MM + (int64_t)i * M;
+    // [A_re; A_im] rows r (A row i = r mod 64), 4 consecutive j per item: a warp reads two
+    // whole rows per instruction (coalesced) and stores 8-byte halves of swizzled chunks
+    for (int e = tid; e < 128 * 16; e += 128) {
+      const int r = e >> 4, j0 = (e & 15) * 4, i = r & 63;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < M && j0 < M)
+        v = __ldg(reinterpret_cast<const float4*>(Av + (r < 64 ? 0 : (int64_t)Nw * MM) +
+                                                  (int64_t)w * MM + (int64_t)i * M + j0));
+      const float x[4] = {v.x, v.y, v.z, v.w};
+      uint32_t h[2], l[2];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        float x[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int j = 8 * c + q;
-          x[q] = (i < M && j < M) ? __ldg(src + j) : 0.f;
-        }
-        uint4 h, l;
-        split8(x, h, l);
-        *reinterpret_cast<uint4*>(smem + Lay::A_HI + sw128_off(tid, 8 * c)) = h;
-        *reinterpret_cast<uint4*>(smem + Lay::A_LO + sw128_off(tid, 8 * c)) = l;
+      for (int q = 0; q < 2; ++q) {
+        const __nv_bfloat16 a0 = __float2bfloat16_rn(x[2 * q]), a1 = __float2bfloat16_rn(x[2 * q + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * q] - __bfloat162float(a0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * q + 1] - __bfloat162float(a1));
+        h[q] = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(a1) << 16);
+        l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
       }
+      *reinterpret_cast<uint2*>(smem + Lay::A_HI + sw128_off(r, j0)) = make_uint2(h[0], h[1]);
+      *reinterpret_cast<uint2*>(smem + Lay::A_LO + sw128_off(r, j0)) = make_uint2(l[0], l[1]);
     }
+    // the walker, coalesced into the staging buffer as [p][b][i] (64 floats per column)
+    for (int e = tid; e < 2 * NPAD * 64; e += 128) {
+      const int pp = e / (NPAD * 64), bb = (e / 64) % NPAD, i = e % 64;
+      S[e] = (bb < N && i < M) ? (float)phi_in[(int64_t)pp * plane + ((int64_t)w * N + bb) * M + i] : 0.f;
+    }
+    __syncthreads();
     float X[EPT], Ssum[EPT], T[EPT];
-    const bool col = b < N;
-    const int64_t gbase = (int64_t)p * plane + ((int64_t)w * N + b) * M;
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int i = i0 + q;
-      X[q] = (col && i < M) ? (float)phi_in[gbase + i] : 0.f;
-    }
+    for (int q = 0; q < EPT; ++q) X[q] = S[nrow * 64 + i0 + q];
     // Phi1 = Phi + (E - I) Phi
     write_b(X);
     if (!mma_round(true)) break;
@@ -223,12 +227,17 @@ __global__ void __launch_bounds__(128, 3)
     write_b(Ssum);
     if (!mma_round(true)) break;
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int i = i0 + q;
-      if (col && i < M) {
-        const float v = Ssum[q] + S[i * SST + p * NPAD + b];
-        phi_out[gbase + i] = (double)v;
-        if (phi_out32) phi_out32[gbase + i] = v;
+    for (int q = 0; q < EPT; ++q) X[q] = Ssum[q] + S[(i0 + q) * SST + p * NPAD + b];
+    __syncthreads();   // every thread has read the accumulator rows from S
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) S[nrow * 64 + i0 + q] = X[q];
+    __syncthreads();
+    for (int e = tid; e < 2 * NPAD * 64; e += 128) {   // coalesced write of the walker
+      const int pp = e / (NPAD * 64), bb = (e / 64) % NPAD, i = e % 64;
+      if (bb < N && i < M) {
+        const int64_t g = (int64_t)pp * plane + ((int64_t)w * N + bb) * M + i;
+        phi_out[g] = (double)S[e];
+        if (phi_out32) phi_out32[g] = S[e];
       }
     }
     __syncthreads();   // S and the operands are reused by the next walker
