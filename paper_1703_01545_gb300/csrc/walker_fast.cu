@@ -51,6 +51,15 @@ __device__ __forceinline__ void df_acc(float& s, float& c, float h, float l, flo
   c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(l, x, e)));
 }
 
+// (s, c) += (s2, c2) for unevaluated FP32 pairs, the leading sum error-free (two-sum)
+__device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
+  const float t = __fadd_rn(s, s2);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, c2));
+}
+
 // ROWS: elimination rows per lane, ceil(ns / (32 / ns)) for the larger spin block (2, 4 or 8);
 // the multipliers of those rows are held in registers.
 template <int ROWS>
@@ -89,6 +98,7 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   for (int base = 0; base < nn * 4; base += blockDim.x) {
     const int q = base + tid, ent = q >> 2, part = q & 3;
     double re = 0.0, im = 0.0;
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;   // FP32-pair partial sums (update mode)
     int sp = 0, r = 0, c = 0;
     if (ent < nn) {
       if (ent < nu * nu) { r = ent / nu; c = ent % nu; }
@@ -103,14 +113,11 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         const float* ls = a.psil + (int64_t)(n0 + r) * M;
         const float* xr = pfr + (n0 + c) * M;
         const float* xi = pfi + (n0 + c) * M;
-        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
         for (int i = part; i < M; i += 4) {
           const float h = __ldg(hs + i), l = __ldg(ls + i);
           df_acc(sr, cr, h, l, xr[i]);
           df_acc(si, ci, h, l, xi[i]);
         }
-        re = (double)sr + (double)cr;
-        im = (double)si + (double)ci;
       } else {
         const double* ps = a.psi + (int64_t)(n0 + r) * M;
         const double* fr = pr + (n0 + c) * M;
@@ -122,10 +129,24 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         }
       }
     }
-    re += __shfl_xor_sync(0xffffffffu, re, 1);
-    im += __shfl_xor_sync(0xffffffffu, im, 1);
-    re += __shfl_xor_sync(0xffffffffu, re, 2);
-    im += __shfl_xor_sync(0xffffffffu, im, 2);
+    // combine the 4 partial sums of each entry (every lane takes part in the shuffles)
+    if (f32) {
+      // FP32 pairs with error-free additions: the FP64 pipe sees one conversion per component
+#pragma unroll
+      for (int o = 1; o <= 2; o <<= 1) {
+        const float s2r = __shfl_xor_sync(0xffffffffu, sr, o), c2r = __shfl_xor_sync(0xffffffffu, cr, o);
+        const float s2i = __shfl_xor_sync(0xffffffffu, si, o), c2i = __shfl_xor_sync(0xffffffffu, ci, o);
+        df_add(sr, cr, s2r, c2r);
+        df_add(si, ci, s2i, c2i);
+      }
+      re = (double)sr + (double)cr;
+      im = (double)si + (double)ci;
+    } else {
+      re += __shfl_xor_sync(0xffffffffu, re, 1);
+      im += __shfl_xor_sync(0xffffffffu, im, 1);
+      re += __shfl_xor_sync(0xffffffffu, re, 2);
+      im += __shfl_xor_sync(0xffffffffu, im, 2);
+    }
     if (ent < nn && part == 0) {
       double* ar = aug + sp * 2 * kNsMax * 32;
       double* ai = ar + kNsMax * 32;
@@ -142,7 +163,103 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   // determinant is the product of the pivots renormalised by an exact power of two built from
   // its exponent bits, and the row inverse uses one reciprocal.  Each complex update of the
   // elimination is 4 FP64 fused multiply-adds.
-  if (warp < 2) {
+  if (nu <= 8 && nd <= 8) {
+    // both spin blocks in warp 0, 16 lanes each: every FP64 instruction of the per-pivot work
+    // (determinant update, reciprocal, row scale) serves both spins
+    if (warp == 0) {
+      const int h = lane >> 4, l16 = lane & 15, ns = h ? nd : nu;
+      double* ar = aug + h * 2 * kNsMax * 32;
+      double* ai = ar + kNsMax * 32;
+      const int nsd = ns > 0 ? ns : 1, RS = 16 / nsd;
+      const int c = l16 % nsd, r0 = l16 / nsd;
+      const bool active = ns > 0 && r0 < RS;
+      const int kmax = nu > nd ? nu : nd;
+      double dr = 1.0, di = 0.0;
+      int dexp = 0;
+      bool bad = false;
+      for (int k = 0; k < kmax; ++k) {
+        const bool live = k < ns && !bad;
+        unsigned key = 0u;
+        if (live && l16 >= k && l16 < ns) {
+          const unsigned hr = (unsigned)__double2hiint(ar[l16 * 32 + k]) & 0x7fffffffu;
+          const unsigned hi = (unsigned)__double2hiint(ai[l16 * 32 + k]) & 0x7fffffffu;
+          key = hr > hi ? hr : hi;
+        }
+        int p = l16;
+        for (int o = 8; o > 0; o >>= 1) {   // within the 16-lane half
+          const unsigned ok = __shfl_xor_sync(0xffffffffu, key, o);
+          const int op = __shfl_xor_sync(0xffffffffu, p, o);
+          if (ok > key || (ok == key && op < p)) { key = ok; p = op; }
+        }
+        if (live && (key < 0x00100000u || key >= 0x7ff00000u)) bad = true;
+        const bool go = live && !bad;
+        if (go && l16 == 0) s_piv[h][k] = p;
+        if (go && p != k && l16 < ns) {
+          double t = ar[k * 32 + l16]; ar[k * 32 + l16] = ar[p * 32 + l16]; ar[p * 32 + l16] = t;
+          t = ai[k * 32 + l16]; ai[k * 32 + l16] = ai[p * 32 + l16]; ai[p * 32 + l16] = t;
+        }
+        __syncwarp();
+        const double vr = go ? ar[k * 32 + k] : 1.0, vi = go ? ai[k * 32 + k] : 0.0;
+        {
+          const double tr = fma(dr, vr, -di * vi);
+          double ti = fma(dr, vi, di * vr);
+          double trr = tr;
+          if (go && p != k) { trr = -tr; ti = -ti; }
+          if (go) { dr = trr; di = ti; }
+          const int e1 = (__double2hiint(dr) >> 20) & 0x7ff, e2 = (__double2hiint(di) >> 20) & 0x7ff;
+          const int eh = e1 > e2 ? e1 : e2;
+          if (eh > 0 && eh < 2046) {
+            const double sc = __hiloint2double((2046 - eh) << 20, 0);   // 2^(1023 - eh), exact
+            dr *= sc;
+            di *= sc;
+            dexp += eh - 1023;
+          }
+        }
+        const double rinv = __drcp_rn(fma(vr, vr, vi * vi));
+        const double ir = vr * rinv, ii = -vi * rinv;
+        __syncwarp();
+        if (go && l16 < ns) {
+          const double xr = ar[k * 32 + l16], xi = ai[k * 32 + l16];
+          ar[k * 32 + l16] = (l16 == k) ? ir : fma(xr, ir, -xi * ii);
+          ai[k * 32 + l16] = (l16 == k) ? ii : fma(xr, ii, xi * ir);
+        }
+        __syncwarp();
+        double fr[4], fi[4];
+        const double kr = go ? ar[k * 32 + c] : 0.0, ki = go ? ai[k * 32 + c] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = r0 + q * RS;
+          fr[q] = (go && active && r < ns) ? ar[r * 32 + k] : 0.0;
+          fi[q] = (go && active && r < ns) ? ai[r * 32 + k] : 0.0;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = r0 + q * RS;
+          if (go && active && r < ns && r != k) {
+            const double xr = (c == k) ? 0.0 : ar[r * 32 + c], xi = (c == k) ? 0.0 : ai[r * 32 + c];
+            ar[r * 32 + c] = fma(-fr[q], kr, fma(fi[q], ki, xr));
+            ai[r * 32 + c] = fma(-fr[q], ki, fma(-fi[q], kr, xi));
+          }
+        }
+        __syncwarp();
+      }
+      if (!bad && l16 < ns)
+        for (int k = ns - 1; k >= 0; --k) {
+          const int p = s_piv[h][k];
+          if (p != k) {
+            double t = ar[l16 * 32 + k]; ar[l16 * 32 + k] = ar[l16 * 32 + p]; ar[l16 * 32 + p] = t;
+            t = ai[l16 * 32 + k]; ai[l16 * 32 + k] = ai[l16 * 32 + p]; ai[l16 * 32 + p] = t;
+          }
+        }
+      if (l16 == 0 && ns > 0) {
+        s_det[h][0] = dr;
+        s_det[h][1] = di;
+        s_dexp[h] = dexp;
+        s_bad[h] = bad ? 1 : 0;
+      }
+    }
+  } else if (warp < 2) {
     const int sp = warp, ns = sp ? nd : nu;
     if (ns > 0) {
       double* ar = aug + sp * 2 * kNsMax * 32;
