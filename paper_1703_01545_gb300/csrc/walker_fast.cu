@@ -442,54 +442,64 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
 // removed one at a time (warp-shuffle inner products), then normalised.  FP64.
 __global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const int* __restrict__ alive,
                                                  int M, int N, int n_up, int Nw) {
+  // one warp per walker (two walkers per CTA): lanes 0-15 orthonormalise the spin-up block,
+  // lanes 16-31 the spin-down block, so every FP64 instruction serves both spins; dots reduce
+  // over 16 lanes.  Columns in order, each projected on the finished ones (modified
+  // Gram-Schmidt), then normalised; all arithmetic FP64.
   extern __shared__ double smg[];
-  const int wk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, sp = tid >> 5;
-  if (!alive[wk]) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wk = blockIdx.x * 2 + warp;
+  if (wk >= Nw || !alive[wk]) return;
   const int NM = N * M;
-  double* vr = smg;
-  double* vi = smg + NM;
+  double* vr = smg + (int64_t)warp * 2 * NM;
+  double* vi = vr + NM;
   const int64_t plane = (int64_t)Nw * NM, base = (int64_t)wk * NM;
-  for (int e = tid; e < NM; e += blockDim.x) {
+  for (int e = lane; e < NM; e += 32) {
     vr[e] = phi[base + e];
     vi[e] = phi[plane + base + e];
   }
-  __syncthreads();
-  const int n0 = sp == 0 ? 0 : n_up, n1 = sp == 0 ? n_up : N;
-  for (int j = n0; j < n1; ++j) {
-    double* xr = vr + j * M;
-    double* xi = vi + j * M;
-    for (int q = n0; q < j; ++q) {
-      const double* qr = vr + q * M;
-      const double* qi = vi + q * M;
+  __syncwarp();
+  const int h = lane >> 4, l16 = lane & 15;
+  const int n0 = h ? n_up : 0, ns = h ? N - n_up : n_up, nmax = n_up > N - n_up ? n_up : N - n_up;
+  for (int j = 0; j < nmax; ++j) {
+    const bool col = j < ns;
+    double* xr = vr + (n0 + (col ? j : 0)) * M;
+    double* xi = vi + (n0 + (col ? j : 0)) * M;
+    for (int q = 0; q < j; ++q) {
+      const double* qr = vr + (n0 + q) * M;
+      const double* qi = vi + (n0 + q) * M;
       double s0 = 0, s1 = 0;
-      for (int i = lane; i < M; i += 32) {
-        s0 += qr[i] * xr[i] + qi[i] * xi[i];
-        s1 += qr[i] * xi[i] - qi[i] * xr[i];
-      }
-      for (int o = 16; o > 0; o >>= 1) {
+      if (col)
+        for (int i = l16; i < M; i += 16) {
+          s0 += qr[i] * xr[i] + qi[i] * xi[i];
+          s1 += qr[i] * xi[i] - qi[i] * xr[i];
+        }
+      for (int o = 8; o > 0; o >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       }
-      for (int i = lane; i < M; i += 32) {
-        const double u = xr[i] - (s0 * qr[i] - s1 * qi[i]);
-        const double v = xi[i] - (s0 * qi[i] + s1 * qr[i]);
-        xr[i] = u;
-        xi[i] = v;
-      }
+      if (col)
+        for (int i = l16; i < M; i += 16) {
+          const double u = xr[i] - (s0 * qr[i] - s1 * qi[i]);
+          const double v = xi[i] - (s0 * qi[i] + s1 * qr[i]);
+          xr[i] = u;
+          xi[i] = v;
+        }
       __syncwarp();
     }
-    double s = 0;
-    for (int i = lane; i < M; i += 32) s += xr[i] * xr[i] + xi[i] * xi[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const double inv = 1.0 / sqrt(s);
-    for (int i = lane; i < M; i += 32) {
-      xr[i] *= inv;
-      xi[i] *= inv;
-    }
+    double sn = 0;
+    if (col)
+      for (int i = l16; i < M; i += 16) sn += xr[i] * xr[i] + xi[i] * xi[i];
+    for (int o = 8; o > 0; o >>= 1) sn += __shfl_xor_sync(0xffffffffu, sn, o);
+    const double inv = col ? 1.0 / sqrt(sn) : 0.0;
+    if (col)
+      for (int i = l16; i < M; i += 16) {
+        xr[i] *= inv;
+        xi[i] *= inv;
+      }
     __syncwarp();
   }
-  __syncthreads();
-  for (int e = tid; e < NM; e += blockDim.x) {
+  for (int e = lane; e < NM; e += 32) {
     phi[base + e] = vr[e];
     phi[plane + base + e] = vi[e];
   }
@@ -499,12 +509,13 @@ size_t smem_fast_overlap(const Ctx& c) {
   return sizeof(double) * (2 * (size_t)c.N * c.M + 2 * 2 * kNsMax * 32) +
          sizeof(float) * (2 * (size_t)c.N * c.M + 2 * 2 * kNsMax * kNsMax);
 }
-size_t smem_mgs_warp(const Ctx& c) { return sizeof(double) * 2 * (size_t)c.N * c.M; }
+size_t smem_mgs_warp(const Ctx& c) { return sizeof(double) * 4 * (size_t)c.N * c.M; }   // two walkers
 
 }  // namespace
 
 bool fast_walker_kernels_ok(const Ctx& c) {
-  return c.n_up <= kNsMax && c.N - c.n_up <= kNsMax && smem_fast_overlap(c) <= 200 * 1024;
+  return c.n_up <= kNsMax && c.N - c.n_up <= kNsMax && smem_fast_overlap(c) <= 200 * 1024 &&
+         smem_mgs_warp(c) <= 200 * 1024;
 }
 
 cudaError_t prepare_fast_walker_kernels(const Ctx& c) {
@@ -548,7 +559,7 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
 }
 
 cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s) {
-  k_mgs_warp<<<c.Nw, 64, smem_mgs_warp(c), s>>>(c.phi, c.alive, c.M, c.N, c.n_up, c.Nw);
+  k_mgs_warp<<<(c.Nw + 1) / 2, 64, smem_mgs_warp(c), s>>>(c.phi, c.alive, c.M, c.N, c.n_up, c.Nw);
   return cudaGetLastError();
 }
 
@@ -583,21 +594,23 @@ __device__ __forceinline__ void put_split(__nv_bfloat16* hi, __nv_bfloat16* lo, 
 }
 
 __global__ void __launch_bounds__(128) k_fields_mixed(FieldArgsM a) {
-  __shared__ double red[4 * 4 + 4];
+  __shared__ float2 red[4][4];   // per warp: the 4 sums as FP32 pairs
   const int wk = blockIdx.x, X = a.X;
   const uint32_t t = (uint32_t)(*a.step);
   const int64_t row = (int64_t)wk * X, plane = (int64_t)a.Nw * X;
   const int64_t o0 = (int64_t)wk * a.Kp, o1 = (int64_t)(a.Nw + wk) * a.Kp;
-  double acc[4] = {0, 0, 0, 0};
+  // sum c_g rho_g (re, im), x.xbar - xbar^2/2 (re, im): FP32 terms summed as unevaluated FP32
+  // pairs (error-free additions), converted to FP64 once per walker, so the thin FP64 pipe only
+  // sees the final sums
+  float ps[4] = {0.f, 0.f, 0.f, 0.f}, pc[4] = {0.f, 0.f, 0.f, 0.f};
   const int npair = (X + 1) / 2;
   for (int j = threadIdx.x; j < npair; j += blockDim.x) {
     float z[2];
     if (a.fields == nullptr) {
       const uint4 r = philox4x32_10(make_uint4((uint32_t)j, a.k0 + (uint32_t)wk, t, 0u), a.key);
-      const uint64_t hi64 = ((uint64_t)r.y << 32) | r.x;
-      const uint64_t lo64 = ((uint64_t)r.w << 32) | r.z;
-      const float u1 = (float)((double)((hi64 >> 11) + 1ull) * 0x1p-53);
-      const float u2 = (float)((double)(lo64 >> 11) * 0x1p-53);
+      // the top 24 bits of the 53-bit uniforms (their FP32 roundings up to one unit)
+      const float u1 = (float)((r.y >> 8) + 1u) * 0x1p-24f;
+      const float u2 = (float)(r.w >> 8) * 0x1p-24f;
       const float rad = sqrtf(-2.0f * logf(u1));
       float sn, cs;
       sincospif(2.0f * u2, &sn, &cs);
@@ -632,13 +645,27 @@ __global__ void __launch_bounds__(128) k_fields_mixed(FieldArgsM a) {
       f0 += x * xb_re - 0.5f * (xb_re * xb_re - xb_im * xb_im);
       f1 += x * xb_im - xb_re * xb_im;
     }
-    acc[0] += s0;
-    acc[1] += s1;
-    acc[2] += f0;
-    acc[3] += f1;
+    df_add(ps[0], pc[0], s0, 0.f);
+    df_add(ps[1], pc[1], s1, 0.f);
+    df_add(ps[2], pc[2], f0, 0.f);
+    df_add(ps[3], pc[3], f1, 0.f);
   }
-  block_sum<4>(acc, red);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    for (int o = 16; o > 0; o >>= 1) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, ps[q], o), c2 = __shfl_xor_sync(0xffffffffu, pc[q], o);
+      df_add(ps[q], pc[q], s2, c2);
+    }
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[wid][q] = make_float2(ps[q], pc[q]);
+  __syncthreads();
   if (threadIdx.x == 0) {
+    double acc[4] = {0, 0, 0, 0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += (double)red[w][q].x + (double)red[w][q].y;
     double* o = a.aux + 4 * (int64_t)wk;
     o[0] = (double)a.sqrt_dt * acc[1];
     o[1] = -(double)a.sqrt_dt * acc[0];
