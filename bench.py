@@ -280,7 +280,8 @@ def run_ours(args, wl, rank, world, local_rank):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
         alive = [A.info().n_alive, B.info().n_alive]
-        return dict(ms=ms, res=res, alive=alive, clocks=ck, A=A, B=B, dA=dA)
+        return dict(ms=ms, res=res, alive=alive, clocks=ck, A=A, B=B, dA=dA,
+                    graph_kernels=afq.pair_graph_kernels(A))
 
     main = timed(args.precision, args.coupling, ClockSampler(torch.cuda.current_device()))
     ms = main["ms"]
@@ -451,11 +452,8 @@ def run_ours(args, wl, rank, world, local_rank):
         cpu = {"value": n_s * STEPS_PER_BLOCK / ts, "unit": "walker-steps/s", "cores": blas_threads(),
                "kind": "oracle",
                "sample": f"{n_s} pair indices x {STEPS_PER_BLOCK} steps + MGS + energy, both systems"}
-    # per system and block: 5 steps x (force bias, fields, V_HS, 2 one-body, Taylor, overlap,
-    # step counter) + MGS + overlap refresh + energy + per-repeat sum; the split-precision step
-    # adds the two operand splits; one measurement counter per block
-    per_step = 8 if args.precision == "fp64" else 10
-    per_block = 2 * (STEPS_PER_BLOCK * per_step + 2 + 2) + 1
+    # kernel nodes of the captured measurement block (both systems), replayed once per block
+    per_block = main["graph_kernels"]
     if rank == 0:
         line = {
             "metric": "correlated-pair walker-steps/s", "value": value, "unit": "walker-steps/s",

@@ -208,6 +208,15 @@ afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n_steps,
                                 double* tau_at_min, cudaStream_t stream);
 
 /*
+ * afqmc_pair_graph_kernels -- instrumentation, no counterpart in the paper.  *n_kernels =
+ * the kernel launches in one measurement block of the pair graph that afqmc_pair_delta_E
+ * captured and cached on A (A as its first handle): energy_every steps of both systems,
+ * their orthonormalisations and measurement.  0 when no graph is cached.  Host only; does
+ * not synchronise.  Errors: ARG (null pointer), CUDA.
+ */
+afqmc_status afqmc_pair_graph_kernels(afqmc_handle A, int* n_kernels);
+
+/*
  * afqmc_set_tangent -- tangent-mode (forward) derivative along a one-body perturbation
  * h1 -> h1 + lambda P of Eq. 1, with the fields and the trial held fixed: the paper has no
  * derivative; this gives d/dlambda of the mixed estimate of Eq. 7 (with Eq. 10) along one

@@ -120,6 +120,13 @@ def afqmc_pair_delta_E(A, B, n_steps, energy_every, mgs_every, tau_eq, e_series=
     return code
 
 
+def afqmc_pair_graph_kernels(A):
+    """Kernel launches in one measurement block of the pair graph cached on handle A."""
+    n = ctypes.c_int(0)
+    _check(_lib.load().afqmc_pair_graph_kernels(A, ctypes.byref(n)), A, "afqmc_pair_graph_kernels")
+    return n.value
+
+
 def afqmc_delta_E_stats(dE, taus, tau_eq):
     """Host statistics; returns (mean_tau, se_tau, (mean, se, tau_at_min))."""
     dE = np.ascontiguousarray(dE, dtype=np.float64)
@@ -260,6 +267,11 @@ class System:
             w = np.asarray(w)
             wp = np.ascontiguousarray(np.stack([w.real, w.imag]), dtype=np.float64)
         afqmc_set_walkers(self.h, p, wp)
+
+
+def pair_graph_kernels(A: System):
+    """Kernel launches per measurement block of the last pair run with A as its first system."""
+    return afqmc_pair_graph_kernels(A.h)
 
 
 def pair_delta_E(A: System, B: System, n_steps, energy_every=5, mgs_every=5, tau_eq=0.0,

@@ -69,6 +69,7 @@ void free_ctx(Ctx* h) {
       if (op->lo) cudaFree(op->lo);
       delete op;
     }
+  if (h->ovdet) cudaFree(h->ovdet);
   for (double* b : {h->Bneg, h->dexpK, h->htilP, h->dphi, h->dphi2, h->dtheta, h->drhobar, h->dU,
                     h->dAvhs, h->dlogO, h->dlogw, h->daux, h->deloc, h->desum})
     if (b) cudaFree(b);
@@ -130,6 +131,7 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   if ((st = dalloc(h, &h->LtT, (size_t)afq::LtT_size(*h))) != AFQMC_OK) return st;
   if ((st = dalloc(h, &h->psi32h, (size_t)NM)) != AFQMC_OK) return st;
   if ((st = dalloc(h, &h->psi32l, (size_t)NM)) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->ovdet, 8 * (size_t)Nw)) != AFQMC_OK) return st;
   AFQ_CK(cudaMemsetAsync(h->d_tc_err, 0, sizeof(int), s));
   // L as rows ij with g contiguous: transpose [X][M*M] -> [M*M][X] through phi2 (large enough
   // only when 2*Nw*N*M >= X*M*M; otherwise a temporary)

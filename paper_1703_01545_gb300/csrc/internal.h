@@ -67,6 +67,7 @@ struct Ctx {
   float* theta32 = nullptr;   // [2][Nw][N][M]  Theta in FP32 (split-precision mode)
   float* LtT = nullptr;       // [X][M][NPT]    Psi_s^T L_g transposed, spin-padded (FP32)
   float *psi32h = nullptr, *psi32l = nullptr;   // [N][M]  psi = psi32h + psi32l (FP32 pair)
+  double* ovdet = nullptr;    // [Nw][8]  per-walker determinant factors between the overlap kernels
   int* d_tc_err = nullptr;    // set by a tensor-core kernel whose bounded wait expired
   EnergyTc* etc = nullptr;    // tensor-core local energy (null when the shape is unsupported)
   // autotuned variants (autotune.cpp); -1 = not tuned, use the default

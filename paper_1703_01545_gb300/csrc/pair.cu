@@ -31,6 +31,7 @@ struct Res {
   cudaGraphExec_t exec = nullptr;
   double* series = nullptr;
   int* meas = nullptr;
+  int n_kernels = 0;   // kernel nodes of the captured graph
   ~Res() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -133,6 +134,15 @@ extern "C" afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n
                                             cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
     }
     AFQ_PCK(cudaGraphInstantiate(&r->exec, r->graph, 0));
+    size_t n_nodes = 0;
+    AFQ_PCK(cudaGraphGetNodes(r->graph, nullptr, &n_nodes));
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    if (n_nodes) AFQ_PCK(cudaGraphGetNodes(r->graph, nodes.data(), &n_nodes));
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      AFQ_PCK(cudaGraphNodeGetType(nd, &ty));
+      if (ty == cudaGraphNodeTypeKernel) ++r->n_kernels;
+    }
   }
   cudaStream_t cs = s;
   if (n_meas > 0) {
@@ -183,5 +193,12 @@ extern "C" afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n
   for (int a : alA) na += a != 0;
   for (int b : alB) nb += b != 0;
   if (na == 0 || nb == 0) return fail(A, B, AFQMC_ERR_NUMERIC, "every walker of a system is dead");
+  return AFQMC_OK;
+}
+
+extern "C" afqmc_status afqmc_pair_graph_kernels(afqmc_handle A, int* n_kernels) {
+  if (!A || !n_kernels) return AFQMC_ERR_ARG;
+  const Res* r = static_cast<const Res*>(A->pair_cache);
+  *n_kernels = r ? r->n_kernels : 0;
   return AFQMC_OK;
 }

@@ -33,6 +33,8 @@ struct FastOvArgs {
   int* alive;
   const double* aux;
   int* flags;
+  double* det;        // [Nw][8]: per spin the determinant mantissa (re, im), the summed
+                      // power-of-two exponent, the singular flag (k_overlap_fast -> k_overlap_weights)
   int M, N, n_up, Nw, mode, free_proj;
   double log_shift;
 };
@@ -86,8 +88,14 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   const bool f32 = upd && a.src32 != nullptr;
   for (int e = tid; e < NM; e += blockDim.x) {
     const double xr = src[wbase + e], xi = src[plane + wbase + e];
-    pr[e] = xr;
-    pi[e] = xi;
+    if (upd) {                  // the propagated walker becomes the walker: no dependence on O
+      a.phi[wbase + e] = xr;
+      a.phi[plane + wbase + e] = xi;
+    }
+    if (!f32) {                 // the FP64 copy feeds only the FP64 overlap sums
+      pr[e] = xr;
+      pi[e] = xi;
+    }
     pfr[e] = f32 ? a.src32[wbase + e] : (float)xr;
     pfi[e] = f32 ? a.src32[plane + wbase + e] : (float)xi;
   }
@@ -139,19 +147,22 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         df_add(sr, cr, s2r, c2r);
         df_add(si, ci, s2i, c2i);
       }
-      re = (double)sr + (double)cr;
-      im = (double)si + (double)ci;
+      // every lane of the entry holds the combined pair; part 0 converts the real sum and
+      // part 1 the imaginary one, so each lane issues 2 conversions and 1 add
+      const bool odd = part & 1;
+      const double v = (double)(odd ? si : sr) + (double)(odd ? ci : cr);
+      if (ent < nn && part < 2) aug[sp * 2 * kNsMax * 32 + (odd ? kNsMax * 32 : 0) + r * 32 + c] = v;
     } else {
       re += __shfl_xor_sync(0xffffffffu, re, 1);
       im += __shfl_xor_sync(0xffffffffu, im, 1);
       re += __shfl_xor_sync(0xffffffffu, re, 2);
       im += __shfl_xor_sync(0xffffffffu, im, 2);
-    }
-    if (ent < nn && part == 0) {
-      double* ar = aug + sp * 2 * kNsMax * 32;
-      double* ai = ar + kNsMax * 32;
-      ar[r * 32 + c] = re;
-      ai[r * 32 + c] = im;
+      if (ent < nn && part == 0) {
+        double* ar = aug + sp * 2 * kNsMax * 32;
+        double* ai = ar + kNsMax * 32;
+        ar[r * 32 + c] = re;
+        ai[r * 32 + c] = im;
+      }
     }
   }
   __syncthreads();
@@ -387,16 +398,28 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     a.op_lo[r0] = __float2bfloat16_rn(re - __bfloat162float(h0));
     a.op_hi[r1] = h1;
     a.op_lo[r1] = __float2bfloat16_rn(im - __bfloat162float(h1));
-    if (upd) {
-      a.phi[gi] = pr[e];
-      a.phi[plane + gi] = pi[e];
-    }
   }
-  if (tid != 0) return;
-  // log det O = log(d_up d_dn) + (e_up + e_dn) ln 2: one log and one atan2 per walker
-  const double d0r = s_det[0][0], d0i = s_det[0][1], d1r = s_det[1][0], d1i = s_det[1][1];
+  // the per-walker scalar work (a log, an atan2, the weight update) runs in k_overlap_weights,
+  // one thread per walker: here it would occupy the FP64 pipe for a whole warp per walker
+  if (tid < 6) {
+    double v = bad ? 1.0 : 0.0;
+    if (tid < 4) v = s_det[tid >> 1][tid & 1];
+    else if (tid == 4) v = (double)(s_dexp[0] + s_dexp[1]);
+    a.det[8 * (int64_t)wk + tid] = v;
+  }
+}
+
+// Per walker, after k_overlap_fast: log det O, the overlap ratio and the weight update.
+__global__ void __launch_bounds__(32) k_overlap_weights(FastOvArgs a) {
+  const int wk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (wk >= a.Nw) return;
+  const bool upd = (a.mode == OV_UPDATE) && a.alive[wk] != 0;
+  const double* dt = a.det + 8 * (int64_t)wk;
+  const bool bad = dt[5] != 0.0;
+  // log det O = log(d_up d_dn) + (e_up + e_dn) ln 2
+  const double d0r = dt[0], d0i = dt[1], d1r = dt[2], d1i = dt[3];
   const double pr_ = fma(d0r, d1r, -d0i * d1i), pi_ = fma(d0r, d1i, d0i * d1r);
-  const double ld_re = 0.5 * log(fma(pr_, pr_, pi_ * pi_)) + (s_dexp[0] + s_dexp[1]) * M_LN2;
+  const double ld_re = 0.5 * log(fma(pr_, pr_, pi_ * pi_)) + dt[4] * M_LN2;
   const double ld_im = atan2(pi_, pr_);
   if (bad || !isfinite(ld_re) || !isfinite(ld_im)) {
     atomicAdd(a.flags, 1);
@@ -546,6 +569,7 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
   a.psil = c.psi32l; a.phi = c.phi; a.theta32 = c.theta32;
   a.op_hi = c.tc_Theta->hi; a.op_lo = c.tc_Theta->lo; a.Kp = c.tc_Theta->Kp;
   a.psi = c.psi; a.logO = c.logO; a.w = c.w; a.alive = c.alive; a.aux = c.aux; a.flags = c.d_flags;
+  a.det = c.ovdet;
   a.M = c.M; a.N = c.N; a.n_up = c.n_up; a.Nw = c.Nw; a.mode = mode;
   a.free_proj = c.opt.mode == AFQMC_FREE;
   a.log_shift = -c.opt.dt * (c.c_mf - c.e_trial);
@@ -555,6 +579,8 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
   if (need <= 2) k_overlap_fast<2><<<c.Nw, 256, sm, s>>>(a);
   else if (need <= 4) k_overlap_fast<4><<<c.Nw, 256, sm, s>>>(a);
   else k_overlap_fast<8><<<c.Nw, 256, sm, s>>>(a);
+  // one warp per CTA: the FP64 chain of each warp gets an SM's FP64 pipe to itself
+  k_overlap_weights<<<(c.Nw + 31) / 32, 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 
