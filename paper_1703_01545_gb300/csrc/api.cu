@@ -70,6 +70,7 @@ void free_ctx(Ctx* h) {
       delete op;
     }
   if (h->ovdet) cudaFree(h->ovdet);
+  if (h->emI_pk) cudaFree(h->emI_pk);
   for (double* b : {h->Bneg, h->dexpK, h->htilP, h->dphi, h->dphi2, h->dtheta, h->drhobar, h->dU,
                     h->dAvhs, h->dlogO, h->dlogw, h->daux, h->deloc, h->desum})
     if (b) cudaFree(b);
@@ -149,6 +150,10 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   if (e == cudaSuccess) e = afq::to_float(h->Ltil, h->Ltil32, (int64_t)X * NM, s);
   if (e == cudaSuccess) e = afq::build_LtT(*h, h->LtT, s);
   if (e == cudaSuccess) e = afq::split_f32(h->psi, h->psi32h, h->psi32l, NM, s);
+  if (e == cudaSuccess && afq::propagate_tc_ok(*h)) {
+    if (dalloc(h, &h->emI_pk, 64 * 64) != AFQMC_OK) return AFQMC_ERR_NOMEM;
+    e = afq::pack_propagate_tc(*h, h->emI_pk, s);
+  }
   // Theta of the current walkers in FP32 and as the split force-bias operand
   if (e == cudaSuccess && overlap_launch(h, nullptr, afq::OV_REFRESH, s) != AFQMC_OK)
     e = cudaErrorUnknown;

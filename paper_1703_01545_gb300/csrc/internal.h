@@ -68,6 +68,7 @@ struct Ctx {
   float* LtT = nullptr;       // [X][M][NPT]    Psi_s^T L_g transposed, spin-padded (FP32)
   float *psi32h = nullptr, *psi32l = nullptr;   // [N][M]  psi = psi32h + psi32l (FP32 pair)
   double* ovdet = nullptr;    // [Nw][8]  per-walker determinant factors between the overlap kernels
+  uint32_t* emI_pk = nullptr; // [64][64] e^{-dt K/2} - I as split-bf16 words (tensor-core propagator)
   int* d_tc_err = nullptr;    // set by a tensor-core kernel whose bounded wait expired
   EnergyTc* etc = nullptr;    // tensor-core local energy (null when the shape is unsupported)
   // autotuned variants (autotune.cpp); -1 = not tuned, use the default
@@ -149,6 +150,7 @@ cudaError_t launch_propagate_f32(const Ctx& c, double* out, float* out32, cudaSt
 // tensor-core propagator (propagate_tc.cu), M <= 64 and N <= 16
 bool propagate_tc_ok(const Ctx& c);
 cudaError_t prepare_propagate_tc();
+cudaError_t pack_propagate_tc(const Ctx& c, uint32_t* emI_pk, cudaStream_t s);
 cudaError_t launch_propagate_tc(const Ctx& c, double* out, float* out32, cudaStream_t s);
 // Propagation variants of the split-precision step: 3 tensor-core kernel, 2 fused FP32 kernel,
 // 1 / 0 two FP32 GEMMs around a Taylor kernel with A in shared memory / through L1.  The

@@ -41,21 +41,6 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int k) {
   return (uint32_t)(r * 128 + ((((k >> 3) ^ r) & 7) << 4) + ((k & 7) << 1));
 }
 
-// split 8 FP32 values into bf16 hi / lo chunks (16 bytes each)
-__device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const __nv_bfloat16 a = __float2bfloat16_rn(x[2 * q]), b = __float2bfloat16_rn(x[2 * q + 1]);
-    const __nv_bfloat16 c = __float2bfloat16_rn(x[2 * q] - __bfloat162float(a));
-    const __nv_bfloat16 d = __float2bfloat16_rn(x[2 * q + 1] - __bfloat162float(b));
-    h[q] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-    l[q] = (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(d) << 16);
-  }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
 struct PLayout {
   static constexpr int A_HI = 0;                 // [-A_im; A_re; A_im]: 192 rows, K = j
   static constexpr int A_LO = A_HI + 24576;
@@ -70,7 +55,7 @@ struct PLayout {
 
 __global__ void __launch_bounds__(128, 3)
     k_propagate_tc(const double* __restrict__ phi_in, const float* __restrict__ Av,
-                   const double* __restrict__ expK, double* __restrict__ phi_out,
+                   const uint32_t* __restrict__ emI_pk, double* __restrict__ phi_out,
                    float* __restrict__ phi_out32, int M, int N, int Nw, int order, int* err,
                    uint64_t wait_ns) {
   using Lay = PLayout;
@@ -101,24 +86,14 @@ __global__ void __launch_bounds__(128, 3)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's TMEM lanes
-  // [E - I; E - I] into tensor memory, once per CTA: lane tid holds row i of E - I (zero
-  // outside M x M), 16 K values per pair of 8-column stores
+  // [E - I; E - I] into tensor memory, once per CTA: lane tid holds row i (the split-bf16 words
+  // packed at setup: 32 hi words, then 32 lo words)
 #pragma unroll 1
   for (int cc = 0; cc < 4; ++cc) {
-    uint32_t vh[8], vl[8];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      float x[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int j = 16 * cc + 8 * c + q;
-        x[q] = (i < M && j < M) ? (float)(expK[(int64_t)i * M + j] - (i == j ? 1.0 : 0.0)) : 0.f;
-      }
-      uint4 h, l;
-      split8(x, h, l);
-      vh[4 * c] = h.x; vh[4 * c + 1] = h.y; vh[4 * c + 2] = h.z; vh[4 * c + 3] = h.w;
-      vl[4 * c] = l.x; vl[4 * c + 1] = l.y; vl[4 * c + 2] = l.z; vl[4 * c + 3] = l.w;
-    }
+    const uint4* src = reinterpret_cast<const uint4*>(emI_pk + i * 64 + 8 * cc);
+    const uint4 h0 = __ldg(src), h1 = __ldg(src + 1), l0 = __ldg(src + 8), l1 = __ldg(src + 9);
+    const uint32_t vh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+    const uint32_t vl[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
     tmem_st8(tl + Lay::T_EHI + 8 * cc, vh);
     tmem_st8(tl + Lay::T_ELO + 8 * cc, vl);
   }
@@ -286,7 +261,31 @@ __global__ void __launch_bounds__(128, 3)
                  : "memory");
 }
 
+// emI_pk[r][c]: row r of e^{-dt K/2} - I (formed in FP64, rounded to FP32, zero outside M x M)
+// split into bf16 hi + lo; words 0..31 hold hi pairs (k = 2c, 2c + 1), words 32..63 lo pairs
+__global__ void k_pack_emI(const double* __restrict__ expK, int M, uint32_t* __restrict__ out) {
+  const int r = blockIdx.x, c = threadIdx.x;   // 64 x 32
+  float x[2];
+  for (int q = 0; q < 2; ++q) {
+    const int j = 2 * c + q;
+    x[q] = (r < M && j < M) ? (float)(expK[(int64_t)r * M + j] - (r == j ? 1.0 : 0.0)) : 0.f;
+  }
+  uint16_t h[2], l[2];
+  for (int q = 0; q < 2; ++q) {
+    const __nv_bfloat16 hb = __float2bfloat16_rn(x[q]);
+    h[q] = __bfloat16_as_ushort(hb);
+    l[q] = __bfloat16_as_ushort(__float2bfloat16_rn(x[q] - __bfloat162float(hb)));
+  }
+  out[r * 64 + c] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+  out[r * 64 + 32 + c] = (uint32_t)l[0] | ((uint32_t)l[1] << 16);
+}
+
 }  // namespace
+
+cudaError_t pack_propagate_tc(const Ctx& c, uint32_t* emI_pk, cudaStream_t s) {
+  k_pack_emI<<<64, 32, 0, s>>>(c.expK, c.M, emI_pk);
+  return cudaGetLastError();
+}
 
 bool propagate_tc_ok(const Ctx& c) {
   return c.M <= 64 && c.M % 4 == 0 && c.N <= 16 && c.N >= 1;
@@ -301,7 +300,8 @@ cudaError_t prepare_propagate_tc() {
 cudaError_t launch_propagate_tc(const Ctx& c, double* out, float* out32, cudaStream_t s) {
   if (!propagate_tc_ok(c)) return cudaErrorInvalidValue;
   const int grid = std::min(c.Nw, 152 * 3);
-  k_propagate_tc<<<grid, 128, PLayout::SMEM_BYTES, s>>>(c.phi, c.Avhs32, c.expK, out, out32, c.M, c.N,
+  if (!c.emI_pk) return cudaErrorInvalidValue;
+  k_propagate_tc<<<grid, 128, PLayout::SMEM_BYTES, s>>>(c.phi, c.Avhs32, c.emI_pk, out, out32, c.M, c.N,
                                                         c.Nw, c.opt.taylor_order, c.d_tc_err, kPWaitNs);
   return cudaGetLastError();
 }

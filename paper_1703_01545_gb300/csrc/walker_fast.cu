@@ -15,6 +15,8 @@ namespace afq {
 namespace {
 
 constexpr int kNsMax = 16;   // spin block size handled by the warp Gauss-Jordan
+constexpr int kLd = 24;      // row stride (doubles) of the in-place inverse: the elimination's
+                             // accesses (2 rows x 8 columns per spin) fall in distinct banks
 
 struct FastOvArgs {
   const double* src;  // [2][Nw][N][M]  (propagated walkers in update mode)
@@ -36,11 +38,10 @@ struct FastOvArgs {
   double* det;        // [Nw][8]: per spin the determinant mantissa (re, im), the summed
                       // power-of-two exponent, the singular flag (k_overlap_fast -> k_overlap_weights)
   int M, N, n_up, Nw, mode, free_proj;
+  int fp64_copy;      // 1: Phi also staged in FP64 shared memory (every mode but the FP32 update)
   double log_shift;
 };
 
-// One CTA (256 threads) per walker.  Shared: phi [2][N][M] (FP64), per spin the overlap
-// matrix inverted in place (re and im [16][32], FP64), FP32 copies of phi and the inverses.
 // s + c += (h + l) x for FP32 h, l, x with the product and the addition error-free (Dekker
 // product through FMA, Knuth two-sum); the intrinsics keep the compiler from contracting them.
 __device__ __forceinline__ void df_acc(float& s, float& c, float h, float l, float x) {
@@ -62,6 +63,9 @@ __device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
   c = __fadd_rn(c, __fadd_rn(err, c2));
 }
 
+// One CTA (128 or 256 threads) per walker.  Shared: phi [2][N][M] in FP64 (not in the FP32 update),
+// per spin the overlap matrix inverted in place (re and im [16][kLd], FP64), FP32 copies of
+// phi and the inverses.
 // ROWS: elimination rows per lane, ceil(ns / (32 / ns)) for the larger spin block (2, 4 or 8);
 // the multipliers of those rows are held in registers.
 template <int ROWS>
@@ -69,12 +73,13 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   extern __shared__ double smo[];
   const int wk = blockIdx.x, tid = threadIdx.x, M = a.M, N = a.N, NM = N * M;
   const int lane = tid & 31, warp = tid >> 5;
-  double* pr = smo;            // [N][M]
+  double* pr = smo;            // [N][M] (only when a.fp64_copy: the FP64 overlap sums)
   double* pi = pr + NM;        // [N][M]
-  double* aug = pi + NM;       // O_s then O_s^{-1}: spin s at aug + s * 2 * 16 * 32, re/im [16][32]
+  double* aug = a.fp64_copy ? pi + NM : smo;   // O_s then O_s^{-1}: spin s at aug + s * 2 * 16 * kLd,
+                                               // re/im [16][kLd]
   // FP32 copies for Theta: converting once here keeps double->float conversions (which run
   // on the FP64 pipe) off the Theta loop
-  float* pfr = reinterpret_cast<float*>(aug + 2 * 2 * kNsMax * 32);  // [N][M]
+  float* pfr = reinterpret_cast<float*>(aug + 2 * 2 * kNsMax * kLd);  // [N][M]
   float* pfi = pfr + NM;
   float* invf = pfi + NM;      // spin s at invf + s * 2 * 16 * 16: re [16][16], im [16][16]
   __shared__ double s_det[2][2];   // per spin: determinant mantissa (re, im) ...
@@ -82,6 +87,9 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   __shared__ int s_bad[2];
   __shared__ int s_piv[2][kNsMax];
   const bool live = a.alive[wk] != 0;
+  // a dead walker keeps its Phi, so its overlap, Theta and operand rows do not change: the
+  // update skips it (k_overlap_weights too)
+  if (a.mode == OV_UPDATE && !live) return;
   const bool upd = (a.mode == OV_UPDATE) && live;
   const double* src = upd ? a.src : a.phi;
   const int64_t plane = (int64_t)a.Nw * NM, wbase = (int64_t)wk * NM;
@@ -151,17 +159,17 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
       // part 1 the imaginary one, so each lane issues 2 conversions and 1 add
       const bool odd = part & 1;
       const double v = (double)(odd ? si : sr) + (double)(odd ? ci : cr);
-      if (ent < nn && part < 2) aug[sp * 2 * kNsMax * 32 + (odd ? kNsMax * 32 : 0) + r * 32 + c] = v;
+      if (ent < nn && part < 2) aug[sp * 2 * kNsMax * kLd + (odd ? kNsMax * kLd : 0) + r * kLd + c] = v;
     } else {
       re += __shfl_xor_sync(0xffffffffu, re, 1);
       im += __shfl_xor_sync(0xffffffffu, im, 1);
       re += __shfl_xor_sync(0xffffffffu, re, 2);
       im += __shfl_xor_sync(0xffffffffu, im, 2);
       if (ent < nn && part == 0) {
-        double* ar = aug + sp * 2 * kNsMax * 32;
-        double* ai = ar + kNsMax * 32;
-        ar[r * 32 + c] = re;
-        ai[r * 32 + c] = im;
+        double* ar = aug + sp * 2 * kNsMax * kLd;
+        double* ai = ar + kNsMax * kLd;
+        ar[r * kLd + c] = re;
+        ai[r * kLd + c] = im;
       }
     }
   }
@@ -179,8 +187,8 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     // (determinant update, reciprocal, row scale) serves both spins
     if (warp == 0) {
       const int h = lane >> 4, l16 = lane & 15, ns = h ? nd : nu;
-      double* ar = aug + h * 2 * kNsMax * 32;
-      double* ai = ar + kNsMax * 32;
+      double* ar = aug + h * 2 * kNsMax * kLd;
+      double* ai = ar + kNsMax * kLd;
       const int nsd = ns > 0 ? ns : 1, RS = 16 / nsd;
       const int c = l16 % nsd, r0 = l16 / nsd;
       const bool active = ns > 0 && r0 < RS;
@@ -192,8 +200,8 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         const bool live = k < ns && !bad;
         unsigned key = 0u;
         if (live && l16 >= k && l16 < ns) {
-          const unsigned hr = (unsigned)__double2hiint(ar[l16 * 32 + k]) & 0x7fffffffu;
-          const unsigned hi = (unsigned)__double2hiint(ai[l16 * 32 + k]) & 0x7fffffffu;
+          const unsigned hr = (unsigned)__double2hiint(ar[l16 * kLd + k]) & 0x7fffffffu;
+          const unsigned hi = (unsigned)__double2hiint(ai[l16 * kLd + k]) & 0x7fffffffu;
           key = hr > hi ? hr : hi;
         }
         int p = l16;
@@ -206,11 +214,11 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         const bool go = live && !bad;
         if (go && l16 == 0) s_piv[h][k] = p;
         if (go && p != k && l16 < ns) {
-          double t = ar[k * 32 + l16]; ar[k * 32 + l16] = ar[p * 32 + l16]; ar[p * 32 + l16] = t;
-          t = ai[k * 32 + l16]; ai[k * 32 + l16] = ai[p * 32 + l16]; ai[p * 32 + l16] = t;
+          double t = ar[k * kLd + l16]; ar[k * kLd + l16] = ar[p * kLd + l16]; ar[p * kLd + l16] = t;
+          t = ai[k * kLd + l16]; ai[k * kLd + l16] = ai[p * kLd + l16]; ai[p * kLd + l16] = t;
         }
         __syncwarp();
-        const double vr = go ? ar[k * 32 + k] : 1.0, vi = go ? ai[k * 32 + k] : 0.0;
+        const double vr = go ? ar[k * kLd + k] : 1.0, vi = go ? ai[k * kLd + k] : 0.0;
         {
           const double tr = fma(dr, vr, -di * vi);
           double ti = fma(dr, vi, di * vr);
@@ -230,27 +238,27 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         const double ir = vr * rinv, ii = -vi * rinv;
         __syncwarp();
         if (go && l16 < ns) {
-          const double xr = ar[k * 32 + l16], xi = ai[k * 32 + l16];
-          ar[k * 32 + l16] = (l16 == k) ? ir : fma(xr, ir, -xi * ii);
-          ai[k * 32 + l16] = (l16 == k) ? ii : fma(xr, ii, xi * ir);
+          const double xr = ar[k * kLd + l16], xi = ai[k * kLd + l16];
+          ar[k * kLd + l16] = (l16 == k) ? ir : fma(xr, ir, -xi * ii);
+          ai[k * kLd + l16] = (l16 == k) ? ii : fma(xr, ii, xi * ir);
         }
         __syncwarp();
         double fr[4], fi[4];
-        const double kr = go ? ar[k * 32 + c] : 0.0, ki = go ? ai[k * 32 + c] : 0.0;
+        const double kr = go ? ar[k * kLd + c] : 0.0, ki = go ? ai[k * kLd + c] : 0.0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int r = r0 + q * RS;
-          fr[q] = (go && active && r < ns) ? ar[r * 32 + k] : 0.0;
-          fi[q] = (go && active && r < ns) ? ai[r * 32 + k] : 0.0;
+          fr[q] = (go && active && r < ns) ? ar[r * kLd + k] : 0.0;
+          fi[q] = (go && active && r < ns) ? ai[r * kLd + k] : 0.0;
         }
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int r = r0 + q * RS;
           if (go && active && r < ns && r != k) {
-            const double xr = (c == k) ? 0.0 : ar[r * 32 + c], xi = (c == k) ? 0.0 : ai[r * 32 + c];
-            ar[r * 32 + c] = fma(-fr[q], kr, fma(fi[q], ki, xr));
-            ai[r * 32 + c] = fma(-fr[q], ki, fma(-fi[q], kr, xi));
+            const double xr = (c == k) ? 0.0 : ar[r * kLd + c], xi = (c == k) ? 0.0 : ai[r * kLd + c];
+            ar[r * kLd + c] = fma(-fr[q], kr, fma(fi[q], ki, xr));
+            ai[r * kLd + c] = fma(-fr[q], ki, fma(-fi[q], kr, xi));
           }
         }
         __syncwarp();
@@ -259,8 +267,8 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         for (int k = ns - 1; k >= 0; --k) {
           const int p = s_piv[h][k];
           if (p != k) {
-            double t = ar[l16 * 32 + k]; ar[l16 * 32 + k] = ar[l16 * 32 + p]; ar[l16 * 32 + p] = t;
-            t = ai[l16 * 32 + k]; ai[l16 * 32 + k] = ai[l16 * 32 + p]; ai[l16 * 32 + p] = t;
+            double t = ar[l16 * kLd + k]; ar[l16 * kLd + k] = ar[l16 * kLd + p]; ar[l16 * kLd + p] = t;
+            t = ai[l16 * kLd + k]; ai[l16 * kLd + k] = ai[l16 * kLd + p]; ai[l16 * kLd + p] = t;
           }
         }
       if (l16 == 0 && ns > 0) {
@@ -273,8 +281,8 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   } else if (warp < 2) {
     const int sp = warp, ns = sp ? nd : nu;
     if (ns > 0) {
-      double* ar = aug + sp * 2 * kNsMax * 32;
-      double* ai = ar + kNsMax * 32;
+      double* ar = aug + sp * 2 * kNsMax * kLd;
+      double* ai = ar + kNsMax * kLd;
       const int RS = 32 / ns;                 // rows per pass (ns <= 16, so RS >= 2)
       const int c = lane % ns, r0 = lane / ns;
       const bool active = r0 < RS;
@@ -284,8 +292,8 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
       for (int k = 0; k < ns; ++k) {
         unsigned key = 0u;
         if (lane >= k && lane < ns) {
-          const unsigned hr = (unsigned)__double2hiint(ar[lane * 32 + k]) & 0x7fffffffu;
-          const unsigned hi = (unsigned)__double2hiint(ai[lane * 32 + k]) & 0x7fffffffu;
+          const unsigned hr = (unsigned)__double2hiint(ar[lane * kLd + k]) & 0x7fffffffu;
+          const unsigned hi = (unsigned)__double2hiint(ai[lane * kLd + k]) & 0x7fffffffu;
           key = hr > hi ? hr : hi;
         }
         int p = lane;
@@ -298,11 +306,11 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         if (key < 0x00100000u || key >= 0x7ff00000u) { bad = true; break; }
         if (lane == 0) s_piv[sp][k] = p;
         if (p != k && lane < ns) {
-          double t = ar[k * 32 + lane]; ar[k * 32 + lane] = ar[p * 32 + lane]; ar[p * 32 + lane] = t;
-          t = ai[k * 32 + lane]; ai[k * 32 + lane] = ai[p * 32 + lane]; ai[p * 32 + lane] = t;
+          double t = ar[k * kLd + lane]; ar[k * kLd + lane] = ar[p * kLd + lane]; ar[p * kLd + lane] = t;
+          t = ai[k * kLd + lane]; ai[k * kLd + lane] = ai[p * kLd + lane]; ai[p * kLd + lane] = t;
         }
         __syncwarp();
-        const double vr = ar[k * 32 + k], vi = ai[k * 32 + k];
+        const double vr = ar[k * kLd + k], vi = ai[k * kLd + k];
         {
           const double tr = fma(dr, vr, -di * vi);
           di = fma(dr, vi, di * vr);
@@ -321,27 +329,27 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         const double ir = vr * rinv, ii = -vi * rinv;          // 1 / pivot
         __syncwarp();
         if (lane < ns) {                                       // row k *= 1/pivot, A[k][k] = 1/pivot
-          const double xr = ar[k * 32 + lane], xi = ai[k * 32 + lane];
-          ar[k * 32 + lane] = (lane == k) ? ir : fma(xr, ir, -xi * ii);
-          ai[k * 32 + lane] = (lane == k) ? ii : fma(xr, ii, xi * ir);
+          const double xr = ar[k * kLd + lane], xi = ai[k * kLd + lane];
+          ar[k * kLd + lane] = (lane == k) ? ir : fma(xr, ir, -xi * ii);
+          ai[k * kLd + lane] = (lane == k) ? ii : fma(xr, ii, xi * ir);
         }
         __syncwarp();
         double fr[ROWS], fi[ROWS];
-        const double kr = ar[k * 32 + c], ki = ai[k * 32 + c];
+        const double kr = ar[k * kLd + c], ki = ai[k * kLd + c];
 #pragma unroll
         for (int q = 0; q < ROWS; ++q) {
           const int r = r0 + q * RS;
-          fr[q] = (active && r < ns) ? ar[r * 32 + k] : 0.0;
-          fi[q] = (active && r < ns) ? ai[r * 32 + k] : 0.0;
+          fr[q] = (active && r < ns) ? ar[r * kLd + k] : 0.0;
+          fi[q] = (active && r < ns) ? ai[r * kLd + k] : 0.0;
         }
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < ROWS; ++q) {                // A[r][c] -= A[r][k] A[k][c]; column k
           const int r = r0 + q * RS;                           // becomes -A[r][k] / pivot
           if (active && r < ns && r != k) {
-            const double xr = (c == k) ? 0.0 : ar[r * 32 + c], xi = (c == k) ? 0.0 : ai[r * 32 + c];
-            ar[r * 32 + c] = fma(-fr[q], kr, fma(fi[q], ki, xr));
-            ai[r * 32 + c] = fma(-fr[q], ki, fma(-fi[q], kr, xi));
+            const double xr = (c == k) ? 0.0 : ar[r * kLd + c], xi = (c == k) ? 0.0 : ai[r * kLd + c];
+            ar[r * kLd + c] = fma(-fr[q], kr, fma(fi[q], ki, xr));
+            ai[r * kLd + c] = fma(-fr[q], ki, fma(-fi[q], kr, xi));
           }
         }
         __syncwarp();
@@ -351,8 +359,8 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         for (int k = ns - 1; k >= 0; --k) {
           const int p = s_piv[sp][k];
           if (p != k) {
-            double t = ar[lane * 32 + k]; ar[lane * 32 + k] = ar[lane * 32 + p]; ar[lane * 32 + p] = t;
-            t = ai[lane * 32 + k]; ai[lane * 32 + k] = ai[lane * 32 + p]; ai[lane * 32 + p] = t;
+            double t = ar[lane * kLd + k]; ar[lane * kLd + k] = ar[lane * kLd + p]; ar[lane * kLd + p] = t;
+            t = ai[lane * kLd + k]; ai[lane * kLd + k] = ai[lane * kLd + p]; ai[lane * kLd + p] = t;
           }
         }
       if (lane == 0) {
@@ -369,10 +377,10 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     int sp = 0, r, c, ns = nu;
     if (e < nu * nu) { r = e / nu; c = e % nu; }
     else { sp = 1; ns = nd; r = (e - nu * nu) / nd; c = (e - nu * nu) % nd; }
-    const double* ar = aug + sp * 2 * kNsMax * 32;
+    const double* ar = aug + sp * 2 * kNsMax * kLd;
     float* fr = invf + sp * 2 * kNsMax * kNsMax;
-    fr[r * kNsMax + c] = (float)ar[r * 32 + c];
-    fr[kNsMax * kNsMax + r * kNsMax + c] = (float)ar[kNsMax * 32 + r * 32 + c];
+    fr[r * kNsMax + c] = (float)ar[r * kLd + c];
+    fr[kNsMax * kNsMax + r * kNsMax + c] = (float)ar[kNsMax * kLd + r * kLd + c];
   }
   __syncthreads();
   // Theta_s = Phi_s O_s^{-1} in FP32; FP32 copy and split bf16 force-bias operand
@@ -414,6 +422,7 @@ __global__ void __launch_bounds__(32) k_overlap_weights(FastOvArgs a) {
   const int wk = blockIdx.x * blockDim.x + threadIdx.x;
   if (wk >= a.Nw) return;
   const bool upd = (a.mode == OV_UPDATE) && a.alive[wk] != 0;
+  if (a.mode == OV_UPDATE && !upd) return;
   const double* dt = a.det + 8 * (int64_t)wk;
   const bool bad = dt[5] != 0.0;
   // log det O = log(d_up d_dn) + (e_up + e_dn) ln 2
@@ -528,8 +537,8 @@ __global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const
   }
 }
 
-size_t smem_fast_overlap(const Ctx& c) {
-  return sizeof(double) * (2 * (size_t)c.N * c.M + 2 * 2 * kNsMax * 32) +
+size_t smem_fast_overlap(const Ctx& c, bool fp64_copy = true) {
+  return sizeof(double) * ((fp64_copy ? 2 * (size_t)c.N * c.M : 0) + 2 * 2 * kNsMax * kLd) +
          sizeof(float) * (2 * (size_t)c.N * c.M + 2 * 2 * kNsMax * kNsMax);
 }
 size_t smem_mgs_warp(const Ctx& c) { return sizeof(double) * 4 * (size_t)c.N * c.M; }   // two walkers
@@ -573,12 +582,16 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
   a.M = c.M; a.N = c.N; a.n_up = c.n_up; a.Nw = c.Nw; a.mode = mode;
   a.free_proj = c.opt.mode == AFQMC_FREE;
   a.log_shift = -c.opt.dt * (c.c_mf - c.e_trial);
+  a.fp64_copy = !(mode == OV_UPDATE && a.src32 != nullptr);
   auto rows = [](int ns) { return ns > 0 ? (ns + 32 / ns - 1) / (32 / ns) : 0; };
   const int need = std::max(rows(c.n_up), rows(c.N - c.n_up));
-  const size_t sm = smem_fast_overlap(c);
-  if (need <= 2) k_overlap_fast<2><<<c.Nw, 256, sm, s>>>(a);
-  else if (need <= 4) k_overlap_fast<4><<<c.Nw, 256, sm, s>>>(a);
-  else k_overlap_fast<8><<<c.Nw, 256, sm, s>>>(a);
+  const size_t sm = smem_fast_overlap(c, a.fp64_copy != 0);
+  // the FP32 update (FP32-pair sums, smaller shared footprint) runs more CTAs of 128 threads
+  // per SM, so more Gauss-Jordan warps overlap; the FP64 sums of the other modes use 256
+  const int nt = a.fp64_copy ? 256 : 128;
+  if (need <= 2) k_overlap_fast<2><<<c.Nw, nt, sm, s>>>(a);
+  else if (need <= 4) k_overlap_fast<4><<<c.Nw, nt, sm, s>>>(a);
+  else k_overlap_fast<8><<<c.Nw, nt, sm, s>>>(a);
   // one warp per CTA: the FP64 chain of each warp gets an SM's FP64 pipe to itself
   k_overlap_weights<<<(c.Nw + 31) / 32, 32, 0, s>>>(a);
   return cudaGetLastError();
