@@ -63,12 +63,106 @@ __device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
   c = __fadd_rn(c, __fadd_rn(err, c2));
 }
 
+// LU factorisation with partial (row) pivoting of one spin block, P O = L U, in FP64 by W
+// lanes of a warp (W = 16: both halves of the warp factorise one block each, in step; W = 32:
+// one block per warp).  Pivot k interchanges whole rows, scales row k right of the diagonal by
+// 1 / pivot (U is unit upper triangular), stores 1 / pivot on the diagonal and updates the
+// trailing block; L, with the pivots as its diagonal, is left below the diagonal.  The pivots
+// and the determinant are those of Gauss-Jordan elimination with the same pivoting.  Every
+// FP64 warp instruction occupies the FP64 pipe whatever its active lanes, so the per-pivot
+// scalar work is short and runs in all lanes: the pivot is chosen on an integer magnitude key
+// (the high word of |re| or |im|, monotone in the magnitude), the determinant is the product
+// of the pivots renormalised by an exact power of two built from its exponent bits, the row
+// scale uses one reciprocal, and row blocks of the trailing update that no lane needs are
+// skipped.  Each complex update is 4 FP64 fused multiply-adds.  Lane l owns column l % ns and
+// rows l / ns + q (W / ns), q < Q.  kmax: the larger block of the warp (uniform loop bound).
+template <int W, int Q>
+__device__ __forceinline__ void lu_block(double* __restrict__ ar, double* __restrict__ ai, int l,
+                                         int ns, int kmax, int* __restrict__ piv, double& dr,
+                                         double& di, int& dexp, bool& bad) {
+  const int nsd = ns > 0 ? ns : 1, RS = W / nsd;
+  const int c = l % nsd, r0 = l / nsd;
+  const bool active = ns > 0 && r0 < RS;
+  dr = 1.0;
+  di = 0.0;
+  dexp = 0;
+  bad = false;
+  for (int k = 0; k < kmax; ++k) {
+    const bool live = k < ns && !bad;
+    unsigned key = 0u;
+    if (live && l >= k && l < ns) {
+      const unsigned hr = (unsigned)__double2hiint(ar[l * kLd + k]) & 0x7fffffffu;
+      const unsigned hi = (unsigned)__double2hiint(ai[l * kLd + k]) & 0x7fffffffu;
+      key = hr > hi ? hr : hi;
+    }
+    int p = l;
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) {
+      const unsigned ok = __shfl_xor_sync(0xffffffffu, key, o);
+      const int op = __shfl_xor_sync(0xffffffffu, p, o);
+      if (ok > key || (ok == key && op < p)) { key = ok; p = op; }
+    }
+    // zero, subnormal-only or non-finite column: singular for this kernel
+    if (live && (key < 0x00100000u || key >= 0x7ff00000u)) bad = true;
+    const bool go = live && !bad;
+    if (go && l == 0) piv[k] = p;
+    if (go && p != k && l < ns) {
+      double t = ar[k * kLd + l]; ar[k * kLd + l] = ar[p * kLd + l]; ar[p * kLd + l] = t;
+      t = ai[k * kLd + l]; ai[k * kLd + l] = ai[p * kLd + l]; ai[p * kLd + l] = t;
+    }
+    __syncwarp();
+    const double vr = go ? ar[k * kLd + k] : 1.0, vi = go ? ai[k * kLd + k] : 0.0;
+    {
+      const double tr = fma(dr, vr, -di * vi);
+      double ti = fma(dr, vi, di * vr);
+      double trr = tr;
+      if (go && p != k) { trr = -tr; ti = -ti; }
+      if (go) { dr = trr; di = ti; }
+      const int e1 = (__double2hiint(dr) >> 20) & 0x7ff, e2 = (__double2hiint(di) >> 20) & 0x7ff;
+      const int eh = e1 > e2 ? e1 : e2;
+      if (eh > 0 && eh < 2046) {
+        const double sc = __hiloint2double((2046 - eh) << 20, 0);   // 2^(1023 - eh), exact
+        dr *= sc;
+        di *= sc;
+        dexp += eh - 1023;
+      }
+    }
+    const double rinv = __drcp_rn(fma(vr, vr, vi * vi));
+    const double ir = vr * rinv, ii = -vi * rinv;          // 1 / pivot
+    __syncwarp();
+    if (go && l >= k && l < ns) {
+      const double xr = ar[k * kLd + l], xi = ai[k * kLd + l];
+      ar[k * kLd + l] = (l == k) ? ir : fma(xr, ir, -xi * ii);
+      ai[k * kLd + l] = (l == k) ? ii : fma(xr, ii, xi * ir);
+    }
+    __syncwarp();
+    // A[r][c] -= A[r][k] U[k][c] for r, c > k: column k and row k are not written, so no
+    // synchronisation separates these reads from the update
+    const bool colk = go && active && c > k;
+    const int qf = colk ? max(0, (k + 1 - r0 + RS - 1) / RS) : Q;
+    const int q0 = __reduce_min_sync(0xffffffffu, qf);
+    const double kr = colk ? ar[k * kLd + c] : 0.0, ki = colk ? ai[k * kLd + c] : 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      if (q >= q0) {
+        const int r = r0 + q * RS;
+        if (colk && r < ns && r > k) {
+          const double fr = ar[r * kLd + k], fi = ai[r * kLd + k];
+          ar[r * kLd + c] = fma(-fr, kr, fma(fi, ki, ar[r * kLd + c]));
+          ai[r * kLd + c] = fma(-fr, ki, fma(-fi, kr, ai[r * kLd + c]));
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // One CTA (128 or 256 threads) per walker.  Shared: phi [2][N][M] in FP64 (not in the FP32 update),
 // per spin the overlap matrix inverted in place (re and im [16][kLd], FP64), FP32 copies of
 // phi and the inverses.
-// ROWS: elimination rows per lane, ceil(ns / (32 / ns)) for the larger spin block (2, 4 or 8);
-// the multipliers of those rows are held in registers.
-template <int ROWS>
+// NSM: the larger spin block is at most 8 (both blocks factorised by warp 0, 16 lanes each) or
+// 16 (one warp per block, ROWS = ceil(ns / (32 / ns)) rows per lane, 4 or 8).
+template <int ROWS, int NSM>
 __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   extern __shared__ double smo[];
   const int wk = blockIdx.x, tid = threadIdx.x, M = a.M, N = a.N, NM = N * M;
@@ -86,6 +180,7 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   __shared__ int s_dexp[2];        // ... and its power-of-two exponent
   __shared__ int s_bad[2];
   __shared__ int s_piv[2][kNsMax];
+  __shared__ unsigned long long s_perm[2];   // row j of P O_s is row (s_perm >> 4 j) & 15 of O_s
   const bool live = a.alive[wk] != 0;
   // a dead walker keeps its Phi, so its overlap, Theta and operand rows do not change: the
   // update skips it (k_overlap_weights too)
@@ -174,104 +269,15 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     }
   }
   __syncthreads();
-  // warp-synchronous in-place Gauss-Jordan inversion with partial (row) pivoting: warp sp
-  // handles spin sp; lane l owns column l % ns and rows l / ns, l / ns + RS, ... (RS = 32 / ns).
-  // Every FP64 warp instruction occupies the FP64 pipe whatever its active lanes, so the
-  // per-pivot scalar work is kept short and runs in all lanes: the pivot is chosen on an
-  // integer magnitude key (the high word of |re| or |im|, monotone in the magnitude), the
-  // determinant is the product of the pivots renormalised by an exact power of two built from
-  // its exponent bits, and the row inverse uses one reciprocal.  Each complex update of the
-  // elimination is 4 FP64 fused multiply-adds.
-  if (nu <= 8 && nd <= 8) {
-    // both spin blocks in warp 0, 16 lanes each: every FP64 instruction of the per-pivot work
-    // (determinant update, reciprocal, row scale) serves both spins
-    if (warp == 0) {
+  if (NSM == 8) {
+    if (warp == 0) {   // both spin blocks, 16 lanes each
       const int h = lane >> 4, l16 = lane & 15, ns = h ? nd : nu;
       double* ar = aug + h * 2 * kNsMax * kLd;
-      double* ai = ar + kNsMax * kLd;
-      const int nsd = ns > 0 ? ns : 1, RS = 16 / nsd;
-      const int c = l16 % nsd, r0 = l16 / nsd;
-      const bool active = ns > 0 && r0 < RS;
-      const int kmax = nu > nd ? nu : nd;
-      double dr = 1.0, di = 0.0;
-      int dexp = 0;
-      bool bad = false;
-      for (int k = 0; k < kmax; ++k) {
-        const bool live = k < ns && !bad;
-        unsigned key = 0u;
-        if (live && l16 >= k && l16 < ns) {
-          const unsigned hr = (unsigned)__double2hiint(ar[l16 * kLd + k]) & 0x7fffffffu;
-          const unsigned hi = (unsigned)__double2hiint(ai[l16 * kLd + k]) & 0x7fffffffu;
-          key = hr > hi ? hr : hi;
-        }
-        int p = l16;
-        for (int o = 8; o > 0; o >>= 1) {   // within the 16-lane half
-          const unsigned ok = __shfl_xor_sync(0xffffffffu, key, o);
-          const int op = __shfl_xor_sync(0xffffffffu, p, o);
-          if (ok > key || (ok == key && op < p)) { key = ok; p = op; }
-        }
-        if (live && (key < 0x00100000u || key >= 0x7ff00000u)) bad = true;
-        const bool go = live && !bad;
-        if (go && l16 == 0) s_piv[h][k] = p;
-        if (go && p != k && l16 < ns) {
-          double t = ar[k * kLd + l16]; ar[k * kLd + l16] = ar[p * kLd + l16]; ar[p * kLd + l16] = t;
-          t = ai[k * kLd + l16]; ai[k * kLd + l16] = ai[p * kLd + l16]; ai[p * kLd + l16] = t;
-        }
-        __syncwarp();
-        const double vr = go ? ar[k * kLd + k] : 1.0, vi = go ? ai[k * kLd + k] : 0.0;
-        {
-          const double tr = fma(dr, vr, -di * vi);
-          double ti = fma(dr, vi, di * vr);
-          double trr = tr;
-          if (go && p != k) { trr = -tr; ti = -ti; }
-          if (go) { dr = trr; di = ti; }
-          const int e1 = (__double2hiint(dr) >> 20) & 0x7ff, e2 = (__double2hiint(di) >> 20) & 0x7ff;
-          const int eh = e1 > e2 ? e1 : e2;
-          if (eh > 0 && eh < 2046) {
-            const double sc = __hiloint2double((2046 - eh) << 20, 0);   // 2^(1023 - eh), exact
-            dr *= sc;
-            di *= sc;
-            dexp += eh - 1023;
-          }
-        }
-        const double rinv = __drcp_rn(fma(vr, vr, vi * vi));
-        const double ir = vr * rinv, ii = -vi * rinv;
-        __syncwarp();
-        if (go && l16 < ns) {
-          const double xr = ar[k * kLd + l16], xi = ai[k * kLd + l16];
-          ar[k * kLd + l16] = (l16 == k) ? ir : fma(xr, ir, -xi * ii);
-          ai[k * kLd + l16] = (l16 == k) ? ii : fma(xr, ii, xi * ir);
-        }
-        __syncwarp();
-        double fr[4], fi[4];
-        const double kr = go ? ar[k * kLd + c] : 0.0, ki = go ? ai[k * kLd + c] : 0.0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int r = r0 + q * RS;
-          fr[q] = (go && active && r < ns) ? ar[r * kLd + k] : 0.0;
-          fi[q] = (go && active && r < ns) ? ai[r * kLd + k] : 0.0;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int r = r0 + q * RS;
-          if (go && active && r < ns && r != k) {
-            const double xr = (c == k) ? 0.0 : ar[r * kLd + c], xi = (c == k) ? 0.0 : ai[r * kLd + c];
-            ar[r * kLd + c] = fma(-fr[q], kr, fma(fi[q], ki, xr));
-            ai[r * kLd + c] = fma(-fr[q], ki, fma(-fi[q], kr, xi));
-          }
-        }
-        __syncwarp();
-      }
-      if (!bad && l16 < ns)
-        for (int k = ns - 1; k >= 0; --k) {
-          const int p = s_piv[h][k];
-          if (p != k) {
-            double t = ar[l16 * kLd + k]; ar[l16 * kLd + k] = ar[l16 * kLd + p]; ar[l16 * kLd + p] = t;
-            t = ai[l16 * kLd + k]; ai[l16 * kLd + k] = ai[l16 * kLd + p]; ai[l16 * kLd + p] = t;
-          }
-        }
-      if (l16 == 0 && ns > 0) {
+      double dr, di;
+      int dexp;
+      bool bad;
+      lu_block<16, 4>(ar, ar + kNsMax * kLd, l16, ns, nu > nd ? nu : nd, s_piv[h], dr, di, dexp, bad);
+      if (l16 == 0) {
         s_det[h][0] = dr;
         s_det[h][1] = di;
         s_dexp[h] = dexp;
@@ -280,123 +286,45 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     }
   } else if (warp < 2) {
     const int sp = warp, ns = sp ? nd : nu;
-    if (ns > 0) {
-      double* ar = aug + sp * 2 * kNsMax * kLd;
-      double* ai = ar + kNsMax * kLd;
-      const int RS = 32 / ns;                 // rows per pass (ns <= 16, so RS >= 2)
-      const int c = lane % ns, r0 = lane / ns;
-      const bool active = r0 < RS;
-      double dr = 1.0, di = 0.0;
-      int dexp = 0;
-      bool bad = false;
-      for (int k = 0; k < ns; ++k) {
-        unsigned key = 0u;
-        if (lane >= k && lane < ns) {
-          const unsigned hr = (unsigned)__double2hiint(ar[lane * kLd + k]) & 0x7fffffffu;
-          const unsigned hi = (unsigned)__double2hiint(ai[lane * kLd + k]) & 0x7fffffffu;
-          key = hr > hi ? hr : hi;
-        }
-        int p = lane;
-        for (int o = 16; o > 0; o >>= 1) {
-          const unsigned ok = __shfl_xor_sync(0xffffffffu, key, o);
-          const int op = __shfl_xor_sync(0xffffffffu, p, o);
-          if (ok > key || (ok == key && op < p)) { key = ok; p = op; }
-        }
-        // zero, subnormal-only or non-finite column: singular for this kernel
-        if (key < 0x00100000u || key >= 0x7ff00000u) { bad = true; break; }
-        if (lane == 0) s_piv[sp][k] = p;
-        if (p != k && lane < ns) {
-          double t = ar[k * kLd + lane]; ar[k * kLd + lane] = ar[p * kLd + lane]; ar[p * kLd + lane] = t;
-          t = ai[k * kLd + lane]; ai[k * kLd + lane] = ai[p * kLd + lane]; ai[p * kLd + lane] = t;
-        }
-        __syncwarp();
-        const double vr = ar[k * kLd + k], vi = ai[k * kLd + k];
-        {
-          const double tr = fma(dr, vr, -di * vi);
-          di = fma(dr, vi, di * vr);
-          dr = (p != k) ? -tr : tr;
-          if (p != k) di = -di;
-          const int e1 = (__double2hiint(dr) >> 20) & 0x7ff, e2 = (__double2hiint(di) >> 20) & 0x7ff;
-          const int eh = e1 > e2 ? e1 : e2;
-          if (eh > 0 && eh < 2046) {
-            const double sc = __hiloint2double((2046 - eh) << 20, 0);   // 2^(1023 - eh), exact
-            dr *= sc;
-            di *= sc;
-            dexp += eh - 1023;
-          }
-        }
-        const double rinv = __drcp_rn(fma(vr, vr, vi * vi));
-        const double ir = vr * rinv, ii = -vi * rinv;          // 1 / pivot
-        __syncwarp();
-        if (lane < ns) {                                       // row k *= 1/pivot, A[k][k] = 1/pivot
-          const double xr = ar[k * kLd + lane], xi = ai[k * kLd + lane];
-          ar[k * kLd + lane] = (lane == k) ? ir : fma(xr, ir, -xi * ii);
-          ai[k * kLd + lane] = (lane == k) ? ii : fma(xr, ii, xi * ir);
-        }
-        __syncwarp();
-        double fr[ROWS], fi[ROWS];
-        const double kr = ar[k * kLd + c], ki = ai[k * kLd + c];
-#pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-          const int r = r0 + q * RS;
-          fr[q] = (active && r < ns) ? ar[r * kLd + k] : 0.0;
-          fi[q] = (active && r < ns) ? ai[r * kLd + k] : 0.0;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < ROWS; ++q) {                // A[r][c] -= A[r][k] A[k][c]; column k
-          const int r = r0 + q * RS;                           // becomes -A[r][k] / pivot
-          if (active && r < ns && r != k) {
-            const double xr = (c == k) ? 0.0 : ar[r * kLd + c], xi = (c == k) ? 0.0 : ai[r * kLd + c];
-            ar[r * kLd + c] = fma(-fr[q], kr, fma(fi[q], ki, xr));
-            ai[r * kLd + c] = fma(-fr[q], ki, fma(-fi[q], kr, xi));
-          }
-        }
-        __syncwarp();
-      }
-      // undo the row interchanges on the inverse's columns, last interchange first
-      if (!bad && lane < ns)
-        for (int k = ns - 1; k >= 0; --k) {
-          const int p = s_piv[sp][k];
-          if (p != k) {
-            double t = ar[lane * kLd + k]; ar[lane * kLd + k] = ar[lane * kLd + p]; ar[lane * kLd + p] = t;
-            t = ai[lane * kLd + k]; ai[lane * kLd + k] = ai[lane * kLd + p]; ai[lane * kLd + p] = t;
-          }
-        }
-      if (lane == 0) {
-        s_det[sp][0] = dr;
-        s_det[sp][1] = di;
-        s_dexp[sp] = dexp;
-        s_bad[sp] = bad ? 1 : 0;
-      }
+    double* ar = aug + sp * 2 * kNsMax * kLd;
+    double dr, di;
+    int dexp;
+    bool bad;
+    lu_block<32, ROWS>(ar, ar + kNsMax * kLd, lane, ns, ns, s_piv[sp], dr, di, dexp, bad);
+    if (lane == 0) {
+      s_det[sp][0] = dr;
+      s_det[sp][1] = di;
+      s_dexp[sp] = dexp;
+      s_bad[sp] = bad ? 1 : 0;
     }
   }
   __syncthreads();
   const bool bad = s_bad[0] || s_bad[1];
-  for (int e = tid; e < nn; e += blockDim.x) {   // O^{-1} blocks to FP32, once
-    int sp = 0, r, c, ns = nu;
+  if (tid < 2) {   // P from the interchanges, in order, as 4-bit row indices
+    const int ns = tid ? nd : nu;
+    unsigned long long pw = 0xfedcba9876543210ull;
+    if (!bad)
+      for (int k = 0; k < ns; ++k) {
+        const int p = s_piv[tid][k];
+        const unsigned long long a = (pw >> (4 * k)) & 15ull, b = (pw >> (4 * p)) & 15ull;
+        pw ^= ((a ^ b) << (4 * k)) | ((a ^ b) << (4 * p));
+      }
+    s_perm[tid] = pw;
+  }
+  for (int e = tid; e < nn; e += blockDim.x) {   // the factors (and 1/pivot) to FP32, once
+    int sp = 0, r, c;
     if (e < nu * nu) { r = e / nu; c = e % nu; }
-    else { sp = 1; ns = nd; r = (e - nu * nu) / nd; c = (e - nu * nu) % nd; }
+    else { sp = 1; r = (e - nu * nu) / nd; c = (e - nu * nu) % nd; }
     const double* ar = aug + sp * 2 * kNsMax * kLd;
     float* fr = invf + sp * 2 * kNsMax * kNsMax;
     fr[r * kNsMax + c] = (float)ar[r * kLd + c];
     fr[kNsMax * kNsMax + r * kNsMax + c] = (float)ar[kNsMax * kLd + r * kLd + c];
   }
   __syncthreads();
-  // Theta_s = Phi_s O_s^{-1} in FP32; FP32 copy and split bf16 force-bias operand
-  for (int e = tid; e < NM; e += blockDim.x) {
-    const int n = e / M, i = e % M;
-    const int sp = n < nu ? 0 : 1, ns = sp ? nd : nu, n0 = sp ? nu : 0, b = n - n0;
-    const float* fr = invf + sp * 2 * kNsMax * kNsMax;
-    const float* fi = fr + kNsMax * kNsMax;
-    float re = 0.f, im = 0.f;
-    if (!bad)
-      for (int c = 0; c < ns; ++c) {
-        const float xr = pfr[(n0 + c) * M + i], xi = pfi[(n0 + c) * M + i];
-        const float orr = fr[c * kNsMax + b], oi = fi[c * kNsMax + b];
-        re = fmaf(xr, orr, fmaf(-xi, oi, re));
-        im = fmaf(xr, oi, fmaf(xi, orr, im));
-      }
+  // Theta_s = Phi_s O_s^{-1} = ((Phi_s U^{-1}) L^{-1}) P, one orbital row i of one spin per
+  // thread, in FP32: y U = phi_i (U unit upper), z L = y (L lower, 1/pivot on the diagonal),
+  // theta_i[perm[j]] = z_j.  Written as the FP32 copy and the split bf16 force-bias operand.
+  auto put = [&](int e, float re, float im) {
     const int64_t gi = wbase + e;
     a.theta32[gi] = re;
     a.theta32[plane + gi] = im;
@@ -406,6 +334,50 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     a.op_lo[r0] = __float2bfloat16_rn(re - __bfloat162float(h0));
     a.op_hi[r1] = h1;
     a.op_lo[r1] = __float2bfloat16_rn(im - __bfloat162float(h1));
+  };
+  if (bad) {
+    for (int e = tid; e < NM; e += blockDim.x) put(e, 0.f, 0.f);
+  } else {
+    for (int t = tid; t < 2 * M; t += blockDim.x) {
+      const int sp = t / M, i = t - sp * M, ns = sp ? nd : nu, n0 = sp ? nu : 0;
+      const float* Lr = invf + sp * 2 * kNsMax * kNsMax;
+      const float* Li = Lr + kNsMax * kNsMax;
+      float yr[NSM], yi[NSM];
+#pragma unroll
+      for (int j = 0; j < NSM; ++j) {
+        yr[j] = j < ns ? pfr[(n0 + j) * M + i] : 0.f;
+        yi[j] = j < ns ? pfi[(n0 + j) * M + i] : 0.f;
+      }
+#pragma unroll
+      for (int j = 1; j < NSM; ++j)
+        if (j < ns) {
+#pragma unroll
+          for (int k = 0; k < j; ++k) {
+            const float ur = Lr[k * kNsMax + j], ui = Li[k * kNsMax + j];
+            yr[j] = fmaf(-yr[k], ur, fmaf(yi[k], ui, yr[j]));
+            yi[j] = fmaf(-yr[k], ui, fmaf(-yi[k], ur, yi[j]));
+          }
+        }
+#pragma unroll
+      for (int j = NSM - 1; j >= 0; --j)
+        if (j < ns) {
+          float tr = yr[j], ti = yi[j];
+#pragma unroll
+          for (int k = j + 1; k < NSM; ++k)
+            if (k < ns) {
+              const float lr = Lr[k * kNsMax + j], li = Li[k * kNsMax + j];
+              tr = fmaf(-yr[k], lr, fmaf(yi[k], li, tr));
+              ti = fmaf(-yr[k], li, fmaf(-yi[k], lr, ti));
+            }
+          const float pr_ = Lr[j * kNsMax + j], pi_ = Li[j * kNsMax + j];
+          yr[j] = fmaf(tr, pr_, -ti * pi_);
+          yi[j] = fmaf(tr, pi_, ti * pr_);
+        }
+      const unsigned long long pw = s_perm[sp];
+#pragma unroll
+      for (int j = 0; j < NSM; ++j)
+        if (j < ns) put((n0 + (int)((pw >> (4 * j)) & 15ull)) * M + i, yr[j], yi[j]);
+    }
   }
   // the per-walker scalar work (a log, an atan2, the weight update) runs in k_overlap_weights,
   // one thread per walker: here it would occupy the FP64 pipe for a whole warp per walker
@@ -554,7 +526,7 @@ cudaError_t prepare_fast_walker_kernels(const Ctx& c) {
   static size_t have_o = 0, have_m = 0;
   cudaError_t e;
   if (smem_fast_overlap(c) > have_o) {
-    for (auto* f : {k_overlap_fast<2>, k_overlap_fast<4>, k_overlap_fast<8>})
+    for (auto* f : {k_overlap_fast<4, 8>, k_overlap_fast<4, 16>, k_overlap_fast<8, 16>})
       if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem_fast_overlap(c))) != cudaSuccess)
         return e;
@@ -584,14 +556,15 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
   a.log_shift = -c.opt.dt * (c.c_mf - c.e_trial);
   a.fp64_copy = !(mode == OV_UPDATE && a.src32 != nullptr);
   auto rows = [](int ns) { return ns > 0 ? (ns + 32 / ns - 1) / (32 / ns) : 0; };
+  const int nmax = std::max(c.n_up, c.N - c.n_up);
   const int need = std::max(rows(c.n_up), rows(c.N - c.n_up));
   const size_t sm = smem_fast_overlap(c, a.fp64_copy != 0);
   // the FP32 update (FP32-pair sums, smaller shared footprint) runs more CTAs of 128 threads
   // per SM, so more Gauss-Jordan warps overlap; the FP64 sums of the other modes use 256
   const int nt = a.fp64_copy ? 256 : 128;
-  if (need <= 2) k_overlap_fast<2><<<c.Nw, nt, sm, s>>>(a);
-  else if (need <= 4) k_overlap_fast<4><<<c.Nw, nt, sm, s>>>(a);
-  else k_overlap_fast<8><<<c.Nw, nt, sm, s>>>(a);
+  if (nmax <= 8) k_overlap_fast<4, 8><<<c.Nw, nt, sm, s>>>(a);
+  else if (need <= 4) k_overlap_fast<4, 16><<<c.Nw, nt, sm, s>>>(a);
+  else k_overlap_fast<8, 16><<<c.Nw, nt, sm, s>>>(a);
   // one warp per CTA: the FP64 chain of each warp gets an SM's FP64 pipe to itself
   k_overlap_weights<<<(c.Nw + 31) / 32, 32, 0, s>>>(a);
   return cudaGetLastError();
