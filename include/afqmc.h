@@ -167,8 +167,9 @@ afqmc_status afqmc_propagate(afqmc_handle h, int n_steps, const double* fields,
                              cudaStream_t stream);
 
 /* afqmc_orthonormalise -- Sec. II.D: modified Gram-Schmidt of each spin block of
- * every live walker (columns in order), then log <psi_T|phi> is recomputed.  The
- * weights are unchanged.  Errors: CUDA. */
+ * every live walker (columns in order), Phi -> Phi R^{-1}; log <psi_T|phi> follows
+ * (recomputed, or in AFQMC_BF16X3 mode lowered by log det R = sum_j log R_jj; Theta =
+ * Phi (Psi_T^T Phi)^{-1} is unchanged by it).  The weights are unchanged.  Errors: CUDA. */
 afqmc_status afqmc_orthonormalise(afqmc_handle h, cudaStream_t stream);
 
 /*

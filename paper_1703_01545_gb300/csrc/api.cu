@@ -314,6 +314,12 @@ afqmc_status ortho_launch(Ctx* h, cudaStream_t s) {
     AFQ_CK(afq::launch_overlap_tan(*h, afq::OV_REFRESH, s));
     return AFQMC_OK;
   }
+  if (h->theta32 && h->tc_Theta && afq::fast_walker_kernels_ok(*h)) {
+    // Gram-Schmidt is Phi -> Phi R^{-1}: Theta is unchanged and log O drops by log det R, so the
+    // kernel updates log O from its column norms and no overlap recomputation follows
+    AFQ_CK(afq::launch_mgs_warp(*h, s, true));
+    return AFQMC_OK;
+  }
   if (h->theta32 && afq::fast_walker_kernels_ok(*h)) {
     AFQ_CK(afq::launch_mgs_warp(*h, s));
   } else {

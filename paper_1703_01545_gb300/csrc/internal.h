@@ -173,7 +173,8 @@ bool fast_walker_kernels_ok(const Ctx& c);
 cudaError_t prepare_fast_walker_kernels(const Ctx& c);
 cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaStream_t s,
                                 const float* src32 = nullptr);
-cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s);
+// update_logO: subtract log det R (the column norms) from log O instead of recomputing it
+cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s, bool update_logO = false);
 cudaError_t launch_fields_mixed(const Ctx& c, const double* fields, cudaStream_t s);
 // tangent mode (tangent.cu)
 bool tangent_fits(const Ctx& c);

@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(32) k_overlap_weights(FastOvArgs a) {
 // Modified Gram-Schmidt, one warp per spin block: columns in order, each projection
 // removed one at a time (warp-shuffle inner products), then normalised.  FP64.
 __global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const int* __restrict__ alive,
-                                                 int M, int N, int n_up, int Nw) {
+                                                 double* __restrict__ logO, int M, int N, int n_up, int Nw) {
   // one warp per walker (two walkers per CTA): lanes 0-15 orthonormalise the spin-up block,
   // lanes 16-31 the spin-down block, so every FP64 instruction serves both spins; dots reduce
   // over 16 lanes.  Columns in order, each projected on the finished ones (modified
@@ -465,6 +465,7 @@ __global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const
   __syncwarp();
   const int h = lane >> 4, l16 = lane & 15;
   const int n0 = h ? n_up : 0, ns = h ? N - n_up : n_up, nmax = n_up > N - n_up ? n_up : N - n_up;
+  double my_sn = 1.0;   // lane j of each half: squared norm of column j before normalisation
   for (int j = 0; j < nmax; ++j) {
     const bool col = j < ns;
     double* xr = vr + (n0 + (col ? j : 0)) * M;
@@ -495,6 +496,7 @@ __global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const
     if (col)
       for (int i = l16; i < M; i += 16) sn += xr[i] * xr[i] + xi[i] * xi[i];
     for (int o = 8; o > 0; o >>= 1) sn += __shfl_xor_sync(0xffffffffu, sn, o);
+    if (col && l16 == j) my_sn = sn;
     const double inv = col ? 1.0 / sqrt(sn) : 0.0;
     if (col)
       for (int i = l16; i < M; i += 16) {
@@ -506,6 +508,13 @@ __global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const
   for (int e = lane; e < NM; e += 32) {
     phi[base + e] = vr[e];
     phi[plane + base + e] = vi[e];
+  }
+  // Phi -> Phi R^{-1} with R upper triangular, diag(R) = the column norms: log <psi_T|phi>
+  // drops by sum_j log R_jj (real), and Theta = Phi (Psi^T Phi)^{-1} is unchanged
+  if (logO) {
+    double v = l16 < ns ? 0.5 * log(my_sn) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) logO[wk] -= v;
   }
 }
 
@@ -570,8 +579,9 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s) {
-  k_mgs_warp<<<(c.Nw + 1) / 2, 64, smem_mgs_warp(c), s>>>(c.phi, c.alive, c.M, c.N, c.n_up, c.Nw);
+cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s, bool update_logO) {
+  k_mgs_warp<<<(c.Nw + 1) / 2, 64, smem_mgs_warp(c), s>>>(c.phi, c.alive, update_logO ? c.logO : nullptr,
+                                                         c.M, c.N, c.n_up, c.Nw);
   return cudaGetLastError();
 }
 
