@@ -288,11 +288,14 @@ afqmc_status afqmc_delta_E_stats(const double* dE, const double* taus, int n_mea
  * (force-bias contraction), AFQMC_K_TAYLOR (Taylor exponential, on scratch memory),
  * AFQMC_K_EXCHANGE (local-energy kernel), AFQMC_K_OVERLAP (overlap / inverse / log det /
  * Theta kernel in its refresh form, which recomputes the same values from the current
- * walkers).  None of them changes the walkers.
+ * walkers), AFQMC_K_OVERLAP_UPDATE (AFQMC_BF16X3 only, ERR_ARG otherwise: the same kernel in
+ * the form each propagation step runs, FP32-pair overlap sums from the FP32 walkers, without
+ * the weight update; one refresh afterwards restores Theta and log O).  None of them changes
+ * the walkers or the weights.
  * Synchronises the stream.  Errors: ARG, CUDA.
  */
 enum { AFQMC_K_VHS = 0, AFQMC_K_FORCE_BIAS = 1, AFQMC_K_TAYLOR = 2, AFQMC_K_EXCHANGE = 3,
-       AFQMC_K_OVERLAP = 4 };
+       AFQMC_K_OVERLAP = 4, AFQMC_K_OVERLAP_UPDATE = 5 };
 afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms,
                                cudaStream_t stream);
 

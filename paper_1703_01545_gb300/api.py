@@ -139,7 +139,7 @@ def afqmc_delta_E_stats(dE, taus, tau_eq):
     return mt, st, tuple(est)
 
 
-K_VHS, K_FORCE_BIAS, K_TAYLOR, K_EXCHANGE, K_OVERLAP = 0, 1, 2, 3, 4
+K_VHS, K_FORCE_BIAS, K_TAYLOR, K_EXCHANGE, K_OVERLAP, K_OVERLAP_UPDATE = 0, 1, 2, 3, 4, 5
 
 
 def afqmc_time_kernel(h, which, reps, stream=None):

@@ -667,7 +667,12 @@ afqmc_status afqmc_energy(afqmc_handle h, double* e_local, double* e_mixed, doub
 }
 
 afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, cudaStream_t s) {
-  if (!h || !ms || reps < 1 || which < 0 || which > 4) return AFQMC_ERR_ARG;
+  if (!h || !ms || reps < 1 || which < 0 || which > 5) return AFQMC_ERR_ARG;
+  const bool fast_ov = h->theta32 && h->tc_Theta && h->phi32 && afq::fast_walker_kernels_ok(*h);
+  if (which == AFQMC_K_OVERLAP_UPDATE && !fast_ov) {
+    h->err = "AFQMC_K_OVERLAP_UPDATE times the split-precision overlap kernel only";
+    return AFQMC_ERR_ARG;
+  }
   const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
   const int64_t NM = (int64_t)N * M;
   cudaEvent_t e0, e1;
@@ -687,6 +692,8 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
                                   h->d_tc_err, s);
         return afq::gemm_tn_f64(X, 2 * Nw, (int)NM, 1.0, h->Ltil, NM, 0, h->theta, NM, 0, 0.0,
                                 h->rhobar, X, 0, 1, s, afq::GEMM_FORCE_BIAS);
+      case AFQMC_K_OVERLAP_UPDATE:   // Phi <- Phi (unchanged), Theta from the FP32 walkers
+        return afq::launch_overlap_fast(*h, h->phi, afq::OV_UPDATE, s, h->phi32, false);
       case AFQMC_K_OVERLAP:
         if (h->theta32 && h->tc_Theta && afq::fast_walker_kernels_ok(*h))
           return afq::launch_overlap_fast(*h, nullptr, afq::OV_REFRESH, s);
@@ -707,6 +714,10 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   float t = 0;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  // the update form took Theta from the FP32 walkers, which Gram-Schmidt leaves stale
+  if (e == cudaSuccess && which == AFQMC_K_OVERLAP_UPDATE)
+    e = afq::launch_overlap_fast(*h, nullptr, afq::OV_REFRESH, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_fail(h, "afqmc_time_kernel", e);

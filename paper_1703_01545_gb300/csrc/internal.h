@@ -171,8 +171,9 @@ cudaError_t launch_taylor_f32_best(const Ctx& c, float* phi32, const float* A32,
 // latency-oriented FP64 walker kernels of the split-precision step (walker_fast.cu)
 bool fast_walker_kernels_ok(const Ctx& c);
 cudaError_t prepare_fast_walker_kernels(const Ctx& c);
+// with_weights = false launches the overlap kernel without the per-walker weight kernel
 cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaStream_t s,
-                                const float* src32 = nullptr);
+                                const float* src32 = nullptr, bool with_weights = true);
 // update_logO: subtract log det R (the column norms) from log O instead of recomputing it
 cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s, bool update_logO = false);
 cudaError_t launch_fields_mixed(const Ctx& c, const double* fields, cudaStream_t s);

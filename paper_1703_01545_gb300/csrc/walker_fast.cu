@@ -551,7 +551,7 @@ cudaError_t prepare_fast_walker_kernels(const Ctx& c) {
 }
 
 cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaStream_t s,
-                                const float* src32) {
+                                const float* src32, bool with_weights) {
   FastOvArgs a;
   a.src = src;
   a.src32 = c.psi32h ? src32 : nullptr;
@@ -575,7 +575,7 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
   else if (need <= 4) k_overlap_fast<4, 16><<<c.Nw, nt, sm, s>>>(a);
   else k_overlap_fast<8, 16><<<c.Nw, nt, sm, s>>>(a);
   // one warp per CTA: the FP64 chain of each warp gets an SM's FP64 pipe to itself
-  k_overlap_weights<<<(c.Nw + 31) / 32, 32, 0, s>>>(a);
+  if (with_weights) k_overlap_weights<<<(c.Nw + 31) / 32, 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 

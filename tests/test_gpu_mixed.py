@@ -120,3 +120,54 @@ def test_autotuner_picks_valid_variants_and_persists(tmp_path):
                     precision=afq.FP64)
     assert s4.info().tuned_energy_walkers_per_cta == -1
     s4.close()
+
+
+def test_gram_schmidt_log_overlap_update_matches_recomputation():
+    """Split path: Gram-Schmidt lowers log O by sum_j log R_jj (Sec. II.D; Phi -> Phi R^{-1}) instead
+    of recomputing the overlaps.  A refresh (the timing call's refresh form recomputes log O and
+    Theta from the walkers in FP64) must land on the same values."""
+    afq = need_gpu()
+    d = system_data("C2", "B", "moderate")
+    nw = 64
+    g = gpu_sys(afq, d, nw, CONFIGS["C2"]["dt"], afq.BF16X3)
+    g.propagate(5, explicit_fields(5, nw, d["X"], seed=21))
+    g.orthonormalise()
+    before = g.state()
+    _, em0, _ = g.energy()
+    afq.afqmc_time_kernel(g.h, afq.K_OVERLAP, 1)
+    after = g.state()
+    _, em1, _ = g.energy()
+    g.close()
+    live = before["alive"]
+    assert live.sum() >= nw - 2
+    assert np.abs(after["logO"].real - before["logO"].real)[live].max() < 1e-10
+    dphase = np.angle(np.exp(1j * (after["logO"].imag - before["logO"].imag)))
+    assert np.abs(dphase[live]).max() < 1e-10
+    assert abs(em1[0] - em0[0]) < 1e-6 * abs(em0[0])
+
+
+def test_kernel_timing_leaves_the_walkers_unchanged():
+    afq = need_gpu()
+    d = system_data("C2", "B", "moderate")
+    nw = 64
+    g = gpu_sys(afq, d, nw, CONFIGS["C2"]["dt"], afq.BF16X3)
+    g.propagate(5, explicit_fields(5, nw, d["X"], seed=22))
+    g.orthonormalise()
+    before = g.state()
+    _, em0, _ = g.energy()
+    for k in (afq.K_VHS, afq.K_FORCE_BIAS, afq.K_TAYLOR, afq.K_EXCHANGE, afq.K_OVERLAP,
+              afq.K_OVERLAP_UPDATE):
+        assert afq.afqmc_time_kernel(g.h, k, 2) > 0
+    after = g.state()
+    _, em1, _ = g.energy()
+    g.close()
+    assert np.array_equal(after["phi"], before["phi"])
+    assert np.array_equal(after["w"], before["w"])
+    assert np.array_equal(after["alive"], before["alive"])
+    live = before["alive"]
+    assert np.abs(after["logO"].real - before["logO"].real)[live].max() < 1e-10
+    assert abs(em1[0] - em0[0]) < 1e-6 * abs(em0[0])
+    f = gpu_sys(afq, d, 8, CONFIGS["C2"]["dt"], afq.FP64)
+    with pytest.raises(RuntimeError):
+        afq.afqmc_time_kernel(f.h, afq.K_OVERLAP_UPDATE, 1)
+    f.close()
