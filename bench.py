@@ -70,7 +70,8 @@ def parse():
     ap.add_argument("--autotune-cache", default=None,
                     help="kernel-variant cache file: read if present, else written after tuning "
                          "(lets a profiled run reuse the choices of an unprofiled one)")
-    ap.add_argument("--kernel", choices=["vhs", "force_bias", "taylor", "energy", "overlap"],
+    ap.add_argument("--kernel", choices=["vhs", "force_bias", "taylor", "energy", "overlap",
+                                         "overlap_update"],
                     help="profiling aid: set up the workload, take one step, then launch only "
                          "this kernel --reps times (no JSON line)")
     ap.add_argument("--walkers", type=int, default=None, help="override walkers per system")
@@ -227,7 +228,8 @@ def run_kernel(args, wl):
                    autotune_cache=args.autotune_cache)
     A.propagate(1)
     which = {"vhs": afq.K_VHS, "force_bias": afq.K_FORCE_BIAS, "taylor": afq.K_TAYLOR,
-             "energy": afq.K_EXCHANGE, "overlap": afq.K_OVERLAP}[args.kernel]
+             "energy": afq.K_EXCHANGE, "overlap": afq.K_OVERLAP,
+             "overlap_update": afq.K_OVERLAP_UPDATE}[args.kernel]
     ms = afq.afqmc_time_kernel(A.h, which, args.reps)
     torch.cuda.synchronize()
     print(f"{args.kernel}: {ms:.3f} ms per launch ({nw} walkers)")
