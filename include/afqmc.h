@@ -342,7 +342,8 @@ afqmc_status afqmc_local_energy_static(const double* h1, const double* L, const 
  * contraction kernels on given operands, C[n][m] = alpha sum_k A[m][k] B[n][k] with
  * A [Md][K], B [Nd][K] (row-major float64, host or device) and C [Nd][Md].
  * impl 0: FP64 kernel; impl 1: split-BF16 tensor-core kernel (hi/lo operands, three MMAs
- * per product, FP32 accumulation); impl 2: self-test of the tensor-core kernel's bounded
+ * per product, FP32 accumulation; the persistent 128 x 256-tile form from 2 x 152 tiles on,
+ * as for V_HS); impl 2: self-test of the tensor-core kernel's bounded
  * waits -- its TMA producer issues nothing, so the first wait expires after 20 ms and the
  * call must return TIMEOUT with the CUDA context still usable.  Allocates temporary
  * device memory; synchronises.

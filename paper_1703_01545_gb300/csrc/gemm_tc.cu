@@ -149,6 +149,156 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                  : "memory");
 }
 
+// Persistent variant for large outputs (the V_HS contraction): 128 x 256 tiles, grid = one CTA
+// per SM looping over tiles, 6 warps.
+//   warp 4 / lane 0  TMA producer over all of the CTA's tiles (2-stage ring of 96 KB stages)
+//   warp 5 / lane 0  MMA issuer: tile i accumulates into TMEM buffer i & 1 (2 x 256 columns),
+//                    commits "tile full" for the epilogue and waits for "tile empty" before it
+//                    reuses a buffer
+//   warps 0..3       epilogue: drain buffer i & 1 (warp w reads TMEM lanes 32 w ..) while the
+//                    MMAs of tile i + 1 run, then arrive on "tile empty"
+// Tiles run m-fastest, so consecutive CTAs share B tiles.  Every wait is bounded as above.
+constexpr int PBN = 256, PSTAGES = 2, PTHREADS = 192;
+struct PLayoutG {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = PBN * BK * 2;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int BAR_OFFSET = PSTAGES * STAGE_BYTES;
+  static constexpr int SMEM_BYTES = BAR_OFFSET + 256 + 1024;
+};
+
+__global__ void __launch_bounds__(PTHREADS, 1)
+    k_gemm_bf16x3_tc_persist(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                             const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                             int Md, int Nd, int nkb, float alpha, float* __restrict__ C, int64_t ldc,
+                             int* err, uint64_t wait_ns) {
+  using Lay = PLayoutG;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lay::BAR_OFFSET);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * PSTAGES + 5);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + PSTAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * PSTAGES), tempty0 = smem_u32(bars + 2 * PSTAGES + 2);
+  const uint32_t done = smem_u32(bars + 2 * PSTAGES + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = (Md + BM - 1) / BM, ntiles = mt * ((Nd + PBN - 1) / PBN);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PSTAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 128);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      // ---- TMA producer ----
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int m0 = (t % mt) * BM, n0 = (t / mt) * PBN;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % PSTAGES, use = g / PSTAGES;
+          if (g >= PSTAGES && !mbar_wait(empty0 + 8 * s, (use - 1) & 1, err, wait_ns)) { ok = false; break; }
+          const uint32_t st = smem_u32(smem + s * Lay::STAGE_BYTES);
+          const uint32_t fb = full0 + 8 * s;
+          mbar_expect_tx(fb, Lay::STAGE_BYTES);
+          tma_load_2d(st, &tmAh, fb, kb * BK, m0);
+          tma_load_2d(st + Lay::A_BYTES, &tmAl, fb, kb * BK, m0);
+          const uint32_t bh = st + 2 * Lay::A_BYTES, bl = bh + Lay::B_BYTES;
+          tma_load_2d(bh, &tmBh, fb, kb * BK, n0);
+          tma_load_2d(bh + Lay::B_BYTES / 2, &tmBh, fb, kb * BK, n0 + PBN / 2);
+          tma_load_2d(bl, &tmBl, fb, kb * BK, n0);
+          tma_load_2d(bl + Lay::B_BYTES / 2, &tmBl, fb, kb * BK, n0 + PBN / 2);
+        }
+      }
+      // every issued stage must have landed before the CTA may exit
+      for (int q = (g > PSTAGES ? g - PSTAGES : 0); q < g; ++q)
+        mbar_wait(full0 + 8 * (q % PSTAGES), (q / PSTAGES) & 1, err, wait_ns);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      const uint32_t idesc = idesc_bf16<PBN>();
+      int g = 0, i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        const int b = i & 1;
+        if (i >= 2 && !mbar_wait(tempty0 + 8 * b, ((i >> 1) - 1) & 1, err, wait_ns)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(b * PBN);
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % PSTAGES, use = g / PSTAGES;
+          if (!mbar_wait(full0 + 8 * s, use & 1, err, wait_ns)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = smem_u32(smem + s * Lay::STAGE_BYTES);
+          const uint64_t ah = sw128_desc(st), al = sw128_desc(st + Lay::A_BYTES);
+          const uint64_t bh = sw128_desc(st + 2 * Lay::A_BYTES);
+          const uint64_t bl = sw128_desc(st + 2 * Lay::A_BYTES + Lay::B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t dk = (uint64_t)((kk * 32) >> 4);
+            mma_bf16(d, ah + dk, bh + dk, idesc, (kb | kk) != 0);
+            mma_bf16(d, ah + dk, bl + dk, idesc, 1u);
+            mma_bf16(d, al + dk, bh + dk, idesc, 1u);
+          }
+          mma_commit(empty0 + 8 * s);
+        }
+        if (ok) mma_commit(tfull0 + 8 * b);
+      }
+      mma_commit(done);   // arrives once every issued MMA has completed
+    }
+  } else {
+    // ---- epilogue: warp w drains TMEM lanes 32 w .. 32 w + 31 (output rows m) ----
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int b = i & 1, m0 = (t % mt) * BM, n0 = (t / mt) * PBN;
+      const bool ok = mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, err, wait_ns);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!__all_sync(0xffffffffu, ok)) break;
+      const int m = m0 + warp * 32 + lane;
+      for (int c0 = 0; c0 < PBN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * PBN + c0), v);
+        if (m < Md) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + c0 + j;
+            if (n < Nd) C[(int64_t)n * ldc + m] = alpha * __uint_as_float(v[j]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(tempty0 + 8 * b);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(done, 0, err, wait_ns);   // no MMA may still write TMEM
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                 : "memory");
+}
+
 // ---- operand preparation ----
 
 // split rows of a float64 matrix into bf16 hi/lo, K padded with zeros:
@@ -238,6 +388,16 @@ cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, 
                         float* C, int64_t ldc, int* err, cudaStream_t s) {
   if (A.Kp != B.Kp || Md > A.rows || Nd > B.rows) return cudaErrorInvalidValue;
   if (Md <= 0 || Nd <= 0) return cudaSuccess;
+  // at least two 128 x 256 tiles per SM: the persistent kernel, whose epilogue overlaps the
+  // next tile's MMAs; B tiles of 256 rows stay inside the operand's padded rows (a multiple of
+  // 256 here), or read the TMA fill value beyond them
+  const int64_t tiles = (int64_t)((Md + BM - 1) / BM) * ((Nd + PBN - 1) / PBN);
+  if (tiles >= 2 * 152 && B.rows % PBN == 0) {
+    const int grid = (int)std::min<int64_t>(tiles, 152);
+    k_gemm_bf16x3_tc_persist<<<grid, PTHREADS, PLayoutG::SMEM_BYTES, s>>>(
+        A.map_hi, A.map_lo, B.map_hi, B.map_lo, Md, Nd, A.Kp / BK, alpha, C, ldc, err, kWaitLimitNs);
+    return cudaGetLastError();
+  }
   return launch_tc<128, 3, float>(A, B, Md, Nd, alpha, C, ldc, err, s);
 }
 
@@ -268,6 +428,9 @@ cudaError_t prepare_tc_kernels() {
     if (st == cudaSuccess)
       st = cudaFuncSetAttribute(k_gemm_bf16x3_tc<128, 3, double>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM_BYTES);
+    if (st == cudaSuccess)
+      st = cudaFuncSetAttribute(k_gemm_bf16x3_tc_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                PLayoutG::SMEM_BYTES);
   });
   return st;
 }

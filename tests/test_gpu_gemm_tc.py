@@ -15,8 +15,10 @@ from gpu_util import need_gpu
 
 pytestmark = pytest.mark.gpu
 
+# the last two have >= 2 x 152 output tiles of 128 x 256, so they run the persistent kernel
+# (the V_HS shape of the 64-orbital workload, and a ragged one)
 SHAPES = [(320, 4096, 1024), (4096, 512, 320), (70, 140, 100), (24, 256, 24), (128, 128, 64),
-          (1000, 300, 950)]
+          (1000, 300, 950), (4096, 4096, 320), (4000, 2560, 200)]
 
 
 def run(lib, impl, A, B, alpha=1.0):
