@@ -1,8 +1,8 @@
-// Latency-oriented FP64 walker kernels for the split-precision step: overlap /
-// Gauss-Jordan / weight update and modified Gram-Schmidt with one warp per spin block, so
-// the small dense linear algebra (N_s <= 16) synchronises with __syncwarp only.  The
-// arithmetic (overlaps, determinants, ratios, weights, Gram-Schmidt) is FP64 as in the
-// reference kernels; only Theta = Phi O^{-1} is formed in FP32 here.
+// Latency-oriented FP64 walker kernels for the split-precision step: overlap / LU / weight
+// update and modified Gram-Schmidt with the small dense linear algebra (N_s <= 16) in one
+// warp, synchronised with __syncwarp only.  Overlaps (FP64, or FP32 pairs when Phi is
+// FP32-exact), determinants, ratios, weights and Gram-Schmidt are FP64; Theta = Phi O^{-1}
+// is formed in FP32.  Also the fields kernel of the split-precision step.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -14,9 +14,10 @@
 namespace afq {
 namespace {
 
-constexpr int kNsMax = 16;   // spin block size handled by the warp Gauss-Jordan
-constexpr int kLd = 24;      // row stride (doubles) of the in-place inverse: the elimination's
-                             // accesses (2 rows x 8 columns per spin) fall in distinct banks
+constexpr int kNsMax = 16;   // spin block size handled by the warp LU
+constexpr int kPad = 4;      // column padding (elements) of the shared copies of Phi
+constexpr int kLd = 24;      // row stride (doubles) of the in-place LU factors: the trailing
+                             // updates' accesses (2 rows x 8 columns per spin) fall in distinct banks
 
 struct FastOvArgs {
   const double* src;  // [2][Nw][N][M]  (propagated walkers in update mode)
@@ -157,25 +158,28 @@ __device__ __forceinline__ void lu_block(double* __restrict__ ar, double* __rest
   }
 }
 
-// One CTA (128 or 256 threads) per walker.  Shared: phi [2][N][M] in FP64 (not in the FP32 update),
-// per spin the overlap matrix inverted in place (re and im [16][kLd], FP64), FP32 copies of
-// phi and the inverses.
+// One CTA (128 or 256 threads) per walker.  Shared: phi [2][N][M + kPad] in FP64 (not in the
+// FP32 update), per spin the overlap matrix factorised in place (re and im [16][kLd], FP64),
+// FP32 copies of phi and of the factors.
 // NSM: the larger spin block is at most 8 (both blocks factorised by warp 0, 16 lanes each) or
 // 16 (one warp per block, ROWS = ceil(ns / (32 / ns)) rows per lane, 4 or 8).
 template <int ROWS, int NSM>
 __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   extern __shared__ double smo[];
   const int wk = blockIdx.x, tid = threadIdx.x, M = a.M, N = a.N, NM = N * M;
+  // shared copies of Phi keep each column M + 4 apart: the overlap sums read 8 columns per
+  // warp, which then fall in distinct banks
+  const int MP = M + kPad, NMP = N * MP;
   const int lane = tid & 31, warp = tid >> 5;
-  double* pr = smo;            // [N][M] (only when a.fp64_copy: the FP64 overlap sums)
-  double* pi = pr + NM;        // [N][M]
-  double* aug = a.fp64_copy ? pi + NM : smo;   // O_s then O_s^{-1}: spin s at aug + s * 2 * 16 * kLd,
+  double* pr = smo;            // [N][MP] (only when a.fp64_copy: the FP64 overlap sums)
+  double* pi = pr + NMP;       // [N][MP]
+  double* aug = a.fp64_copy ? pi + NMP : smo;   // O_s then O_s^{-1}: spin s at aug + s * 2 * 16 * kLd,
                                                // re/im [16][kLd]
   // FP32 copies for Theta: converting once here keeps double->float conversions (which run
   // on the FP64 pipe) off the Theta loop
-  float* pfr = reinterpret_cast<float*>(aug + 2 * 2 * kNsMax * kLd);  // [N][M]
-  float* pfi = pfr + NM;
-  float* invf = pfi + NM;      // spin s at invf + s * 2 * 16 * 16: re [16][16], im [16][16]
+  float* pfr = reinterpret_cast<float*>(aug + 2 * 2 * kNsMax * kLd);  // [N][MP]
+  float* pfi = pfr + NMP;
+  float* invf = pfi + NMP;     // spin s at invf + s * 2 * 16 * 16: re [16][16], im [16][16]
   __shared__ double s_det[2][2];   // per spin: determinant mantissa (re, im) ...
   __shared__ int s_dexp[2];        // ... and its power-of-two exponent
   __shared__ int s_bad[2];
@@ -191,16 +195,17 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   const bool f32 = upd && a.src32 != nullptr;
   for (int e = tid; e < NM; e += blockDim.x) {
     const double xr = src[wbase + e], xi = src[plane + wbase + e];
+    const int es = e + (e / M) * kPad;   // (n, i) in the padded layout
     if (upd) {                  // the propagated walker becomes the walker: no dependence on O
       a.phi[wbase + e] = xr;
       a.phi[plane + wbase + e] = xi;
     }
     if (!f32) {                 // the FP64 copy feeds only the FP64 overlap sums
-      pr[e] = xr;
-      pi[e] = xi;
+      pr[es] = xr;
+      pi[es] = xi;
     }
-    pfr[e] = f32 ? a.src32[wbase + e] : (float)xr;
-    pfi[e] = f32 ? a.src32[plane + wbase + e] : (float)xi;
+    pfr[es] = f32 ? a.src32[wbase + e] : (float)xr;
+    pfi[es] = f32 ? a.src32[plane + wbase + e] : (float)xi;
   }
   if (tid < 2) { s_det[tid][0] = 1.0; s_det[tid][1] = 0.0; s_dexp[tid] = 0; s_bad[tid] = 0; }
   __syncthreads();
@@ -222,8 +227,8 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         // sees only the final conversions
         const float* hs = a.psih + (int64_t)(n0 + r) * M;
         const float* ls = a.psil + (int64_t)(n0 + r) * M;
-        const float* xr = pfr + (n0 + c) * M;
-        const float* xi = pfi + (n0 + c) * M;
+        const float* xr = pfr + (n0 + c) * MP;
+        const float* xi = pfi + (n0 + c) * MP;
         for (int i = part; i < M; i += 4) {
           const float h = __ldg(hs + i), l = __ldg(ls + i);
           df_acc(sr, cr, h, l, xr[i]);
@@ -231,8 +236,8 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
         }
       } else {
         const double* ps = a.psi + (int64_t)(n0 + r) * M;
-        const double* fr = pr + (n0 + c) * M;
-        const double* fi = pi + (n0 + c) * M;
+        const double* fr = pr + (n0 + c) * MP;
+        const double* fi = pi + (n0 + c) * MP;
         for (int i = part; i < M; i += 4) {
           const double p = __ldg(ps + i);
           re = fma(p, fr[i], re);
@@ -345,8 +350,8 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
       float yr[NSM], yi[NSM];
 #pragma unroll
       for (int j = 0; j < NSM; ++j) {
-        yr[j] = j < ns ? pfr[(n0 + j) * M + i] : 0.f;
-        yi[j] = j < ns ? pfi[(n0 + j) * M + i] : 0.f;
+        yr[j] = j < ns ? pfr[(n0 + j) * MP + i] : 0.f;
+        yi[j] = j < ns ? pfi[(n0 + j) * MP + i] : 0.f;
       }
 #pragma unroll
       for (int j = 1; j < NSM; ++j)
@@ -519,8 +524,9 @@ __global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const
 }
 
 size_t smem_fast_overlap(const Ctx& c, bool fp64_copy = true) {
-  return sizeof(double) * ((fp64_copy ? 2 * (size_t)c.N * c.M : 0) + 2 * 2 * kNsMax * kLd) +
-         sizeof(float) * (2 * (size_t)c.N * c.M + 2 * 2 * kNsMax * kNsMax);
+  const size_t nmp = (size_t)c.N * (c.M + kPad);
+  return sizeof(double) * ((fp64_copy ? 2 * nmp : 0) + 2 * 2 * kNsMax * kLd) +
+         sizeof(float) * (2 * nmp + 2 * 2 * kNsMax * kNsMax);
 }
 size_t smem_mgs_warp(const Ctx& c) { return sizeof(double) * 4 * (size_t)c.N * c.M; }   // two walkers
 
@@ -569,7 +575,7 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
   const int need = std::max(rows(c.n_up), rows(c.N - c.n_up));
   const size_t sm = smem_fast_overlap(c, a.fp64_copy != 0);
   // the FP32 update (FP32-pair sums, smaller shared footprint) runs more CTAs of 128 threads
-  // per SM, so more Gauss-Jordan warps overlap; the FP64 sums of the other modes use 256
+  // per SM, so more LU warps overlap; the FP64 sums of the other modes use 256
   const int nt = a.fp64_copy ? 256 : 128;
   if (nmax <= 8) k_overlap_fast<4, 8><<<c.Nw, nt, sm, s>>>(a);
   else if (need <= 4) k_overlap_fast<4, 16><<<c.Nw, nt, sm, s>>>(a);
