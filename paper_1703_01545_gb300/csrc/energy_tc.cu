@@ -27,27 +27,31 @@ namespace {
 
 using namespace tc;
 
-constexpr int EBM = 128, EBN = 256, EBK = 64, ETHREADS = 128;
+constexpr int EBM = 128, EBN = 256, EBK = 64;
 constexpr uint64_t kEWaitNs = 2000000000ull;
 
 __host__ __device__ constexpr int cols_per_group(int NP) { return 2 * NP > 32 ? 2 * NP : 32; }
 
-// One stage (A and B of one 64-wide k slice); the epilogue reuses it as its staging buffer
-// once every MMA has completed, so a CTA needs ~97 KB and two CTAs (2 x 256 TMEM columns)
-// share an SM.
+// One operand stage (A and B of one 64-wide k slice: the next tile's load and MMAs hide behind
+// the current tile's epilogue), the epilogue's staging rows (per warp 32 rows x (CW + 1)) and
+// the per-tile partial sums of the two tiles in flight: 131-163 KB, one CTA per SM, whose two
+// TMEM accumulators take all 512 columns.  8 epilogue warps: two per TMEM lane quadrant, each
+// taking half of the tile's column groups.
+constexpr int ESTAGES = 1, EWARPS = 8, EPTHREADS = 32 * (EWARPS + 2);
 template <int NP>
 struct ELayout {
   static constexpr int A_BYTES = EBM * EBK * 2;                 // one of hi / lo
   static constexpr int B_BYTES = EBN * EBK * 2;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int CW = cols_per_group(NP);                 // TMEM columns staged per step
-  static constexpr int STG_BYTES = 4 * 32 * (CW + 1) * 4;       // per warp 32 rows x (CW + 1)
+  static constexpr int STG_OFFSET = ESTAGES * STAGE_BYTES;
+  static constexpr int STG_BYTES = EWARPS * 32 * (CW + 1) * 4;
   static constexpr int WPT = EBN / (2 * NP);                    // walkers per tile
-  static constexpr int RED_OFFSET = STAGE_BYTES;
-  static constexpr int RED_BYTES = 4 * WPT * 2 * 4;
+  static constexpr int RED_OFFSET = STG_OFFSET + STG_BYTES;
+  static constexpr int RED_BYTES = 2 * 4 * WPT * 2 * 4;
   static constexpr int BAR_OFFSET = (RED_OFFSET + RED_BYTES + 7) & ~7;
-  static constexpr int SMEM_BYTES = BAR_OFFSET + 64 + 1024;     // 3 barriers, TMEM slot, alignment
-  static_assert(STG_BYTES <= STAGE_BYTES, "staging must fit in the operand stage");
+  static constexpr int SMEM_BYTES = BAR_OFFSET + 128 + 1024;    // 9 barriers, flag, TMEM slot, alignment
+  static_assert(SMEM_BYTES <= 232448, "one CTA must fit an SM's shared memory");
 };
 
 // Operand row r = (unit, n') of a spin-padded block: orbital index or -1 for a padding row.
@@ -89,43 +93,53 @@ __global__ void k_energy_B(const float* __restrict__ th, int Nw, int N, int M, i
   }
 }
 
-// ---------------------------------------------------------------------------
-// One 128 x 256 tile of T per CTA (4 warps): warp 0 / lane 0 issues the TMA loads of the
-// k slices (A hi/lo: one 128-row box each; B hi/lo: two 128-row boxes each) into the single
-// stage, warp 1 / lane 0 issues 4 x 3 tcgen05.mma (K = 16, N = 256) per slice into TMEM and
-// commits; all warps then run the epilogue on their 32 TMEM lanes (= rows (g, a)).
+// Persistent CTAs (one per SM) over the (row tile, column tile) pairs, m-fastest, 10 warps:
+//   warp 8 / lane 0  TMA producer
+//   warp 9 / lane 0  MMA issuer: per 64-wide k slice 4 x 3 tcgen05.mma (K = 16, N = 256) into
+//                    TMEM buffer i & 1 of the CTA's i-th tile, then "tile full"
+//   warps 0..7       epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows (g, a)) of buffer
+//                    i & 1, column groups of half w / 4, while the next tile's load and MMAs
+//                    run; "tile empty" once the rows are read; the 8 warps meet at a named
+//                    barrier to add their partial sums
 // part[(tile_row * 2 + re/im) * NwP + w] = sum over the tile's g of E2(g, w).
-// Every mbarrier wait is bounded; on expiry *err is set, the CTA drains what it issued,
-// frees its TMEM and writes zeros.
-// ---------------------------------------------------------------------------
+// Every mbarrier wait is bounded; on expiry *err is set, the epilogue warps stop together
+// (a shared flag read after their barrier), the CTA drains what it issued and frees its TMEM.
 template <int NP>
-__global__ void __launch_bounds__(ETHREADS, 1)
+__global__ void __launch_bounds__(EPTHREADS, 1)
     k_energy_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                 const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                int nkb, float* __restrict__ part, int NwP, int* err, uint64_t wait_ns) {
+                int nkb, int RT, int CT, float* __restrict__ part, int NwP, int* err,
+                uint64_t wait_ns) {
   using Lay = ELayout<NP>;
   constexpr int CW = Lay::CW, WPT = Lay::WPT, P2 = NP / 2, WPG = CW / (2 * NP);
   extern __shared__ uint8_t esm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(esm_raw) + 1023) &
                                              ~uintptr_t(1023));
+  float* stg = reinterpret_cast<float*>(smem + Lay::STG_OFFSET);
   float* red = reinterpret_cast<float*>(smem + Lay::RED_OFFSET);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lay::BAR_OFFSET);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
-  const uint32_t full = smem_u32(bars), empty = smem_u32(bars + 1), done = smem_u32(bars + 2);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(bars + 9);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + 2);
+  const uint32_t tfull0 = smem_u32(bars + 4), tempty0 = smem_u32(bars + 6), done = smem_u32(bars + 8);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * EBM, n0 = blockIdx.y * EBN;
+  const int ntiles = RT * CT;
 
-  for (int e = threadIdx.x; e < 4 * WPT * 2; e += ETHREADS) red[e] = 0.f;
   if (threadIdx.x == 0) {
-    mbar_init(full, 1);
-    mbar_init(empty, 1);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(full0 + 8 * q, 1);
+      mbar_init(empty0 + 8 * q, 1);
+      mbar_init(tfull0 + 8 * q, 1);
+      mbar_init(tempty0 + 8 * q, 32 * EWARPS);
+    }
     mbar_init(done, 1);
+    *s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"((uint32_t)EBN)
+                 "r"(512u)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -133,117 +147,155 @@ __global__ void __launch_bounds__(ETHREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t st = smem_u32(smem);
 
-  if (warp == 0 && lane == 0) {
-    // ---- TMA producer: slice kb reuses the stage after the MMAs of slice kb-1 released it ----
-    int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      if (kb > 0 && !mbar_wait(empty, (kb - 1) & 1, err, wait_ns)) break;
-      mbar_expect_tx(full, Lay::STAGE_BYTES);
-      const int kx = kb * EBK;
-      tma_load_2d(st, &tmAh, full, kx, m0);
-      tma_load_2d(st + Lay::A_BYTES, &tmAl, full, kx, m0);
-      const uint32_t bh = st + 2 * Lay::A_BYTES, bl = bh + Lay::B_BYTES;
-      tma_load_2d(bh, &tmBh, full, kx, n0);
-      tma_load_2d(bh + Lay::B_BYTES / 2, &tmBh, full, kx, n0 + EBN / 2);
-      tma_load_2d(bl, &tmBl, full, kx, n0);
-      tma_load_2d(bl + Lay::B_BYTES / 2, &tmBl, full, kx, n0 + EBN / 2);
-      issued = kb + 1;
+  if (warp == EWARPS) {
+    if (lane == 0) {
+      // ---- TMA producer ----
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int m0 = (t % RT) * EBM, n0 = (t / RT) * EBN;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % ESTAGES, use = g / ESTAGES;
+          if (g >= ESTAGES && !mbar_wait(empty0 + 8 * s, (use - 1) & 1, err, wait_ns)) { ok = false; break; }
+          const uint32_t st = smem_u32(smem + s * Lay::STAGE_BYTES), fb = full0 + 8 * s;
+          const int kx = kb * EBK;
+          mbar_expect_tx(fb, Lay::STAGE_BYTES);
+          tma_load_2d(st, &tmAh, fb, kx, m0);
+          tma_load_2d(st + Lay::A_BYTES, &tmAl, fb, kx, m0);
+          const uint32_t bh = st + 2 * Lay::A_BYTES, bl = bh + Lay::B_BYTES;
+          tma_load_2d(bh, &tmBh, fb, kx, n0);
+          tma_load_2d(bh + Lay::B_BYTES / 2, &tmBh, fb, kx, n0 + EBN / 2);
+          tma_load_2d(bl, &tmBl, fb, kx, n0);
+          tma_load_2d(bl + Lay::B_BYTES / 2, &tmBl, fb, kx, n0 + EBN / 2);
+        }
+      }
+      // every issued stage must have landed before the CTA may exit
+      for (int q = (g > ESTAGES ? g - ESTAGES : 0); q < g; ++q)
+        mbar_wait(full0 + 8 * (q % ESTAGES), (q / ESTAGES) & 1, err, wait_ns);
     }
-    // drain: the last issued slice must have landed before the CTA may exit
-    if (issued > 0) mbar_wait(full, (issued - 1) & 1, err, wait_ns);
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer ----
-    const uint32_t idesc = idesc_bf16<EBN>();
-    for (int kb = 0; kb < nkb; ++kb) {
-      if (!mbar_wait(full, kb & 1, err, wait_ns)) break;
+  } else if (warp == EWARPS + 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      const uint32_t idesc = idesc_bf16<EBN>();
+      int g = 0, i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        const int b = i & 1;
+        if (i >= 2 && !mbar_wait(tempty0 + 8 * b, ((i >> 1) - 1) & 1, err, wait_ns)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(b * EBN);
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % ESTAGES, use = g / ESTAGES;
+          if (!mbar_wait(full0 + 8 * s, use & 1, err, wait_ns)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = smem_u32(smem + s * Lay::STAGE_BYTES);
+          const uint64_t ah = sw128_desc(st), al = sw128_desc(st + Lay::A_BYTES);
+          const uint64_t bh = sw128_desc(st + 2 * Lay::A_BYTES);
+          const uint64_t bl = sw128_desc(st + 2 * Lay::A_BYTES + Lay::B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < EBK / 16; ++kk) {
+            const uint64_t dk = (uint64_t)((kk * 32) >> 4);   // 16 bf16 = 32 bytes inside the atom
+            mma_bf16(d, ah + dk, bh + dk, idesc, (kb | kk) != 0);
+            mma_bf16(d, ah + dk, bl + dk, idesc, 1u);
+            mma_bf16(d, al + dk, bh + dk, idesc, 1u);
+          }
+          mma_commit(empty0 + 8 * s);
+        }
+        if (ok) mma_commit(tfull0 + 8 * b);
+      }
+      mma_commit(done);   // arrives once every issued MMA has completed
+    }
+  } else {
+    // ---- epilogue ----
+    constexpr int NG = EBN / CW, NGH = NG / 2;   // column groups per tile, per half
+    float* S = stg + warp * 32 * (CW + 1);
+    const int quad = warp & 3, half = warp >> 2;
+    const int a = lane % NP, gl = lane / NP, s0 = a < P2 ? 0 : P2;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int b = i & 1;
+      float* rb = red + b * (4 * WPT * 2);
+      const bool ok = mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, err, wait_ns);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint64_t ah = sw128_desc(st), al = sw128_desc(st + Lay::A_BYTES);
-      const uint64_t bh = sw128_desc(st + 2 * Lay::A_BYTES);
-      const uint64_t bl = sw128_desc(st + 2 * Lay::A_BYTES + Lay::B_BYTES);
+      if (__all_sync(0xffffffffu, ok)) {
+        for (int gg = 0; gg < NGH; ++gg) {
+          const int grp = half * NGH + gg;
+          float rowv[CW];   // this lane's row (g, a) of the group: its own T[a][.]
 #pragma unroll
-      for (int kk = 0; kk < EBK / 16; ++kk) {
-        const uint64_t dk = (uint64_t)((kk * 32) >> 4);   // 16 bf16 = 32 bytes inside the atom
-        mma_bf16(tmem, ah + dk, bh + dk, idesc, (kb | kk) != 0);
-        mma_bf16(tmem, ah + dk, bl + dk, idesc, 1u);
-        mma_bf16(tmem, al + dk, bh + dk, idesc, 1u);
+          for (int h = 0; h < CW / 32; ++h) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * EBN + grp * CW + 32 * h), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              rowv[32 * h + j] = __uint_as_float(v[j]);
+              S[lane * (CW + 1) + 32 * h + j] = rowv[32 * h + j];
+            }
+          }
+          __syncwarp();
+#pragma unroll
+          for (int wi = 0; wi < WPG; ++wi) {
+            const int cb = wi * 2 * NP;
+            const float* colp = S + gl * NP * (CW + 1) + cb + a;        // T[.][a]
+            float exr = 0.f, exi = 0.f, dr = 0.f, di = 0.f;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+              // T[a][j] of the lane's spin block only (j in [s0, s0 + P2)); the diagonal
+              if (j >= s0 && j < s0 + P2) {
+                const float tr = rowv[cb + j], ti = rowv[cb + NP + j];
+                const float ur = colp[j * (CW + 1)], ui = colp[j * (CW + 1) + NP];
+                exr = fmaf(tr, ur, fmaf(-ti, ui, exr));
+                exi = fmaf(tr, ui, fmaf(ti, ur, exi));
+              }
+              if (j == a) { dr = rowv[cb + j]; di = rowv[cb + NP + j]; }
+            }
+#pragma unroll
+            for (int o = NP / 2; o > 0; o >>= 1) {                     // sums over the g block
+              exr += __shfl_xor_sync(0xffffffffu, exr, o);
+              exi += __shfl_xor_sync(0xffffffffu, exi, o);
+              dr += __shfl_xor_sync(0xffffffffu, dr, o);
+              di += __shfl_xor_sync(0xffffffffu, di, o);
+            }
+            float er = a == 0 ? 0.5f * (dr * dr - di * di - exr) : 0.f;
+            float ei = a == 0 ? 0.5f * (2.f * dr * di - exi) : 0.f;
+#pragma unroll
+            for (int o = NP; o < 32; o <<= 1) {                        // over the warp's g blocks
+              er += __shfl_xor_sync(0xffffffffu, er, o);
+              ei += __shfl_xor_sync(0xffffffffu, ei, o);
+            }
+            if (lane == 0) {
+              rb[(quad * WPT + grp * WPG + wi) * 2] = er;
+              rb[(quad * WPT + grp * WPG + wi) * 2 + 1] = ei;
+            }
+          }
+          __syncwarp();
+        }
+      } else if (lane == 0) {
+        *s_fail = 1;
       }
-      mma_commit(empty);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(tempty0 + 8 * b);
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * EWARPS) : "memory");   // the epilogue warps
+      if (*s_fail) break;
+      if (threadIdx.x < WPT) {
+        const int w = (t / RT) * WPT + threadIdx.x, rt = t % RT;
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          sr += rb[(q * WPT + threadIdx.x) * 2];
+          si += rb[(q * WPT + threadIdx.x) * 2 + 1];
+        }
+        part[(int64_t)(2 * rt) * NwP + w] = sr;
+        part[(int64_t)(2 * rt + 1) * NwP + w] = si;
+      }
     }
-    mma_commit(done);   // also on an early exit: arrives once the issued MMAs are complete
   }
-  __syncwarp();
-
-  // ---- epilogue ----
-  const bool ok = mbar_wait(done, 0, err, 2 * wait_ns);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncwarp();
-  // the operand stage is free once every MMA has completed: stage TMEM rows there
-  float* S = reinterpret_cast<float*>(smem) + warp * 32 * (CW + 1);
-  const int a = lane % NP, gl = lane / NP, s0 = a < P2 ? 0 : P2;
-  if (__all_sync(0xffffffffu, ok && *(volatile int*)err == 0)) {
-    for (int grp = 0; grp < EBN / CW; ++grp) {
-#pragma unroll
-      for (int h = 0; h < CW / 32; ++h) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(grp * CW + 32 * h), v);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) S[lane * (CW + 1) + 32 * h + j] = __uint_as_float(v[j]);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int wi = 0; wi < WPG; ++wi) {
-        const int cb = wi * 2 * NP;
-        const float* rowp = S + lane * (CW + 1) + cb;               // T[a][.] (re, then im)
-        const float* colp = S + gl * NP * (CW + 1) + cb + a;        // T[.][a]
-        float exr = 0.f, exi = 0.f;
-#pragma unroll
-        for (int j = 0; j < P2; ++j) {
-          const int b = s0 + j;
-          const float tr = rowp[b], ti = rowp[NP + b];
-          const float ur = colp[b * (CW + 1)], ui = colp[b * (CW + 1) + NP];
-          exr = fmaf(tr, ur, fmaf(-ti, ui, exr));
-          exi = fmaf(tr, ui, fmaf(ti, ur, exi));
-        }
-        float dr = rowp[a], di = rowp[NP + a];
-#pragma unroll
-        for (int o = NP / 2; o > 0; o >>= 1) {                     // sums over the g block
-          exr += __shfl_xor_sync(0xffffffffu, exr, o);
-          exi += __shfl_xor_sync(0xffffffffu, exi, o);
-          dr += __shfl_xor_sync(0xffffffffu, dr, o);
-          di += __shfl_xor_sync(0xffffffffu, di, o);
-        }
-        float er = a == 0 ? 0.5f * (dr * dr - di * di - exr) : 0.f;
-        float ei = a == 0 ? 0.5f * (2.f * dr * di - exi) : 0.f;
-#pragma unroll
-        for (int o = NP; o < 32; o <<= 1) {                        // over the warp's g blocks
-          er += __shfl_xor_sync(0xffffffffu, er, o);
-          ei += __shfl_xor_sync(0xffffffffu, ei, o);
-        }
-        if (lane == 0) {
-          red[(warp * WPT + grp * WPG + wi) * 2] = er;
-          red[(warp * WPT + grp * WPG + wi) * 2 + 1] = ei;
-        }
-      }
-      __syncwarp();
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (threadIdx.x < WPT) {
-    const int t = threadIdx.x, w = blockIdx.y * WPT + t;
-    float sr = 0.f, si = 0.f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      sr += red[(q * WPT + t) * 2];
-      si += red[(q * WPT + t) * 2 + 1];
-    }
-    part[(int64_t)(2 * blockIdx.x) * NwP + w] = sr;
-    part[(int64_t)(2 * blockIdx.x + 1) * NwP + w] = si;
-  }
+  if (threadIdx.x == 0) mbar_wait(done, 0, err, wait_ns);   // no MMA may still write TMEM
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)EBN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
                  : "memory");
 }
 
@@ -289,10 +341,10 @@ cudaError_t launch_np(const Ctx& c, const EnergyTc& et, int n_walkers, cudaStrea
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int ct = (nw * 2 * NP + EBN - 1) / EBN;
-  dim3 grid(et.RT, ct);
-  k_energy_tc<NP><<<grid, ETHREADS, Lay::SMEM_BYTES, s>>>(et.A->map_hi, et.A->map_lo, et.B->map_hi,
-                                                         et.B->map_lo, et.Kp / EBK, et.part, et.NwP,
-                                                         c.d_tc_err, kEWaitNs);
+  const int grid = std::min(et.RT * ct, 152);
+  k_energy_tc<NP><<<grid, EPTHREADS, Lay::SMEM_BYTES, s>>>(et.A->map_hi, et.A->map_lo, et.B->map_hi,
+                                                          et.B->map_lo, et.Kp / EBK, et.RT, ct, et.part,
+                                                          et.NwP, c.d_tc_err, kEWaitNs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_energy_tc_reduce<<<(nw + 7) / 8, 256, 0, s>>>(et.part, et.RT, et.NwP, c.theta32, c.htil, c.eloc,
                                                  c.Nw, nw, NM);
