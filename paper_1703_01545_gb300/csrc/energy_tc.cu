@@ -299,6 +299,240 @@ __global__ void __launch_bounds__(EPTHREADS, 1)
                  : "memory");
 }
 
+// Single k slice (M <= 64): the column tile of Theta stays in shared memory while the CTA
+// runs a group of RG row tiles of Psi^T L_g through it, so the operand stream is one B tile
+// per group plus the small A tiles (the per-tile form re-reads B for every row tile).
+// Work item = (column tile, row group); each walker's partial sums over the group's row tiles
+// add up in the epilogue and part[(group * 2 + re/im) * NwP + w] receives them.  Warp roles as
+// in k_energy_tc (with bres_ewarps(NP) epilogue warps); shared memory: B (64 KB), 2 A stages
+// (32 KB each), staging, partials.
+// Epilogue warps of the B-resident form: four per TMEM lane quadrant (two for NP = 32, whose
+// staging rows are twice as wide).
+__host__ __device__ constexpr int bres_ewarps(int NP) { return NP == 32 ? 8 : 16; }
+
+template <int NP>
+struct EBLayout {
+  static constexpr int EW = bres_ewarps(NP), THREADS = 32 * (EW + 2);
+  static constexpr int A_BYTES = EBM * EBK * 2;                 // one of hi / lo
+  static constexpr int B_BYTES = EBN * EBK * 2;
+  static constexpr int A_OFFSET = 2 * B_BYTES;
+  static constexpr int A_STAGE = 2 * A_BYTES;
+  static constexpr int CW = cols_per_group(NP);
+  static constexpr int STG_OFFSET = A_OFFSET + 2 * A_STAGE;
+  static constexpr int STG_BYTES = EW * 32 * (CW + 1) * 4;
+  static constexpr int WPT = EBN / (2 * NP);
+  static constexpr int RED_OFFSET = STG_OFFSET + STG_BYTES;
+  static constexpr int RED_BYTES = 2 * 4 * WPT * 2 * 4;
+  static constexpr int BAR_OFFSET = (RED_OFFSET + RED_BYTES + 7) & ~7;
+  static constexpr int SMEM_BYTES = BAR_OFFSET + 128 + 1024;    // 11 barriers, flag, TMEM slot, alignment
+  static_assert(SMEM_BYTES <= 232448, "one CTA must fit an SM's shared memory");
+};
+
+template <int NP>
+__global__ void __launch_bounds__(EBLayout<NP>::THREADS, 1)
+    k_energy_tc_bres(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                     int RT, int CT, int RG, int NG, float* __restrict__ part, int NwP, int* err,
+                     uint64_t wait_ns) {
+  using Lay = EBLayout<NP>;
+  constexpr int CW = Lay::CW, WPT = Lay::WPT, P2 = NP / 2, WPG = CW / (2 * NP), EW = Lay::EW;
+  extern __shared__ uint8_t esm_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(esm_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  float* stg = reinterpret_cast<float*>(smem + Lay::STG_OFFSET);
+  float* red = reinterpret_cast<float*>(smem + Lay::RED_OFFSET);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lay::BAR_OFFSET);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(bars + 11);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12);
+  const uint32_t bfull = smem_u32(bars), bempty = smem_u32(bars + 1);
+  const uint32_t full0 = smem_u32(bars + 2), empty0 = smem_u32(bars + 4);
+  const uint32_t tfull0 = smem_u32(bars + 6), tempty0 = smem_u32(bars + 8), done = smem_u32(bars + 10);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nitems = CT * NG;
+  const uint32_t sbase = smem_u32(smem);
+
+  if (threadIdx.x == 0) {
+    mbar_init(bfull, 1);
+    mbar_init(bempty, 1);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(full0 + 8 * q, 1);
+      mbar_init(empty0 + 8 * q, 1);
+      mbar_init(tfull0 + 8 * q, 1);
+      mbar_init(tempty0 + 8 * q, 32 * EW);
+    }
+    mbar_init(done, 1);
+    *s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == EW) {
+    if (lane == 0) {
+      // ---- TMA producer: B once per item (after the previous item's MMAs), A per row tile ----
+      int ga = 0, j = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++j) {
+        const int ct = it / NG, rg = it % NG, n0 = ct * EBN;
+        const int r0 = rg * RG, r1 = min(RT, r0 + RG);
+        if (j > 0 && !mbar_wait(bempty, (j - 1) & 1, err, wait_ns)) break;
+        mbar_expect_tx(bfull, 2 * Lay::B_BYTES);
+        tma_load_2d(sbase, &tmBh, bfull, 0, n0);
+        tma_load_2d(sbase + Lay::B_BYTES / 2, &tmBh, bfull, 0, n0 + EBN / 2);
+        tma_load_2d(sbase + Lay::B_BYTES, &tmBl, bfull, 0, n0);
+        tma_load_2d(sbase + Lay::B_BYTES + Lay::B_BYTES / 2, &tmBl, bfull, 0, n0 + EBN / 2);
+        for (int rt = r0; rt < r1; ++rt, ++ga) {
+          const int s = ga & 1, use = ga >> 1;
+          if (ga >= 2 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1, err, wait_ns)) { ok = false; break; }
+          const uint32_t st = sbase + Lay::A_OFFSET + s * Lay::A_STAGE, fb = full0 + 8 * s;
+          mbar_expect_tx(fb, Lay::A_STAGE);
+          tma_load_2d(st, &tmAh, fb, 0, rt * EBM);
+          tma_load_2d(st + Lay::A_BYTES, &tmAl, fb, 0, rt * EBM);
+        }
+      }
+      // every issued copy must have landed before the CTA may exit
+      if (j > 0) mbar_wait(bfull, (j - 1) & 1, err, wait_ns);
+      for (int q = (ga > 2 ? ga - 2 : 0); q < ga; ++q)
+        mbar_wait(full0 + 8 * (q & 1), (q >> 1) & 1, err, wait_ns);
+    }
+  } else if (warp == EW + 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      const uint32_t idesc = idesc_bf16<EBN>();
+      const uint64_t bh = sw128_desc(sbase), bl = sw128_desc(sbase + Lay::B_BYTES);
+      int ga = 0, i = 0, j = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++j) {
+        const int rg = it % NG, r0 = rg * RG, r1 = min(RT, r0 + RG);
+        if (!mbar_wait(bfull, j & 1, err, wait_ns)) break;
+        for (int rt = r0; rt < r1; ++rt, ++ga, ++i) {
+          const int b = i & 1, s = ga & 1;
+          if (i >= 2 && !mbar_wait(tempty0 + 8 * b, ((i >> 1) - 1) & 1, err, wait_ns)) { ok = false; break; }
+          if (!mbar_wait(full0 + 8 * s, (ga >> 1) & 1, err, wait_ns)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = sbase + Lay::A_OFFSET + s * Lay::A_STAGE;
+          const uint64_t ah = sw128_desc(st), al = sw128_desc(st + Lay::A_BYTES);
+          const uint32_t d = tmem + (uint32_t)(b * EBN);
+#pragma unroll
+          for (int kk = 0; kk < EBK / 16; ++kk) {
+            const uint64_t dk = (uint64_t)((kk * 32) >> 4);
+            mma_bf16(d, ah + dk, bh + dk, idesc, kk != 0);
+            mma_bf16(d, ah + dk, bl + dk, idesc, 1u);
+            mma_bf16(d, al + dk, bh + dk, idesc, 1u);
+          }
+          mma_commit(empty0 + 8 * s);
+          mma_commit(tfull0 + 8 * b);
+        }
+        mma_commit(bempty);   // the item's MMAs are done with B once this arrives
+      }
+      mma_commit(done);
+    }
+  } else {
+    // ---- epilogue ----
+    constexpr int NPART = EW / 4, NGR = EBN / CW, NGH = NGR / NPART;   // column groups per warp
+    float* S = stg + warp * 32 * (CW + 1);
+    const int quad = warp & 3, half = warp >> 2;
+    const int a = lane % NP, gl = lane / NP, s0 = a < P2 ? 0 : P2;
+    int i = 0;
+    bool stop = false;
+    for (int it = blockIdx.x; it < nitems && !stop; it += gridDim.x) {
+      const int ct = it / NG, rg = it % NG, r0 = rg * RG, r1 = min(RT, r0 + RG);
+      float accr = 0.f, acci = 0.f;   // threads < WPT: walker ct * WPT + threadIdx.x
+      for (int rt = r0; rt < r1; ++rt, ++i) {
+        const int b = i & 1;
+        float* rb = red + b * (4 * WPT * 2);
+        const bool ok = mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, err, wait_ns);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (__all_sync(0xffffffffu, ok)) {
+          for (int gg = 0; gg < NGH; ++gg) {
+            const int grp = half * NGH + gg;
+            float rowv[CW];
+#pragma unroll
+            for (int h = 0; h < CW / 32; ++h) {
+              uint32_t v[32];
+              tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * EBN + grp * CW + 32 * h), v);
+#pragma unroll
+              for (int q = 0; q < 32; ++q) {
+                rowv[32 * h + q] = __uint_as_float(v[q]);
+                S[lane * (CW + 1) + 32 * h + q] = rowv[32 * h + q];
+              }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int wi = 0; wi < WPG; ++wi) {
+              const int cb = wi * 2 * NP;
+              const float* colp = S + gl * NP * (CW + 1) + cb + a;        // T[.][a]
+              float exr = 0.f, exi = 0.f, dr = 0.f, di = 0.f;
+#pragma unroll
+              for (int q = 0; q < NP; ++q) {
+                if (q >= s0 && q < s0 + P2) {
+                  const float tr = rowv[cb + q], ti = rowv[cb + NP + q];
+                  const float ur = colp[q * (CW + 1)], ui = colp[q * (CW + 1) + NP];
+                  exr = fmaf(tr, ur, fmaf(-ti, ui, exr));
+                  exi = fmaf(tr, ui, fmaf(ti, ur, exi));
+                }
+                if (q == a) { dr = rowv[cb + q]; di = rowv[cb + NP + q]; }
+              }
+#pragma unroll
+              for (int o = NP / 2; o > 0; o >>= 1) {
+                exr += __shfl_xor_sync(0xffffffffu, exr, o);
+                exi += __shfl_xor_sync(0xffffffffu, exi, o);
+                dr += __shfl_xor_sync(0xffffffffu, dr, o);
+                di += __shfl_xor_sync(0xffffffffu, di, o);
+              }
+              float er = a == 0 ? 0.5f * (dr * dr - di * di - exr) : 0.f;
+              float ei = a == 0 ? 0.5f * (2.f * dr * di - exi) : 0.f;
+#pragma unroll
+              for (int o = NP; o < 32; o <<= 1) {
+                er += __shfl_xor_sync(0xffffffffu, er, o);
+                ei += __shfl_xor_sync(0xffffffffu, ei, o);
+              }
+              if (lane == 0) {
+                rb[(quad * WPT + grp * WPG + wi) * 2] = er;
+                rb[(quad * WPT + grp * WPG + wi) * 2 + 1] = ei;
+              }
+            }
+            __syncwarp();
+          }
+        } else if (lane == 0) {
+          *s_fail = 1;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(tempty0 + 8 * b);
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");   // the epilogue warps
+        if (*s_fail) { stop = true; break; }
+        if (threadIdx.x < WPT)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            accr += rb[(q * WPT + threadIdx.x) * 2];
+            acci += rb[(q * WPT + threadIdx.x) * 2 + 1];
+          }
+      }
+      if (!stop && threadIdx.x < WPT) {
+        const int w = ct * WPT + threadIdx.x;
+        part[(int64_t)(2 * rg) * NwP + w] = accr;
+        part[(int64_t)(2 * rg + 1) * NwP + w] = acci;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(done, 0, err, wait_ns);   // no MMA may still write TMEM
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                 : "memory");
+}
+
 // eloc[w] = sum_e htil[e] Theta_w[e] (FP64) + sum over row tiles of part for the first nw of
 // the Nw walkers (one warp per walker;
 // every sum in a fixed order, so repeated evaluations agree bit for bit).
@@ -341,12 +575,24 @@ cudaError_t launch_np(const Ctx& c, const EnergyTc& et, int n_walkers, cudaStrea
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int ct = (nw * 2 * NP + EBN - 1) / EBN;
-  const int grid = std::min(et.RT * ct, 152);
-  k_energy_tc<NP><<<grid, EPTHREADS, Lay::SMEM_BYTES, s>>>(et.A->map_hi, et.A->map_lo, et.B->map_hi,
-                                                          et.B->map_lo, et.Kp / EBK, et.RT, ct, et.part,
-                                                          et.NwP, c.d_tc_err, kEWaitNs);
+  int nparts = et.RT;
+  if (et.Kp == EBK) {
+    // B-resident form: about six (column tile, row group) items per SM
+    const int ng = std::max(1, std::min(et.RT, (152 * 6 + ct - 1) / ct));
+    const int rg = (et.RT + ng - 1) / ng;
+    nparts = (et.RT + rg - 1) / rg;
+    const int grid = std::min(ct * nparts, 152);
+    k_energy_tc_bres<NP><<<grid, EBLayout<NP>::THREADS, EBLayout<NP>::SMEM_BYTES, s>>>(
+        et.A->map_hi, et.A->map_lo, et.B->map_hi, et.B->map_lo, et.RT, ct, rg, nparts, et.part, et.NwP,
+        c.d_tc_err, kEWaitNs);
+  } else {
+    const int grid = std::min(et.RT * ct, 152);
+    k_energy_tc<NP><<<grid, EPTHREADS, Lay::SMEM_BYTES, s>>>(et.A->map_hi, et.A->map_lo, et.B->map_hi,
+                                                            et.B->map_lo, et.Kp / EBK, et.RT, ct, et.part,
+                                                            et.NwP, c.d_tc_err, kEWaitNs);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_energy_tc_reduce<<<(nw + 7) / 8, 256, 0, s>>>(et.part, et.RT, et.NwP, c.theta32, c.htil, c.eloc,
+  k_energy_tc_reduce<<<(nw + 7) / 8, 256, 0, s>>>(et.part, nparts, et.NwP, c.theta32, c.htil, c.eloc,
                                                  c.Nw, nw, NM);
   return cudaGetLastError();
 }
@@ -369,6 +615,15 @@ cudaError_t prepare_energy_tc_kernels() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_energy_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              ELayout<32>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_energy_tc_bres<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             EBLayout<8>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_energy_tc_bres<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             EBLayout<16>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_energy_tc_bres<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             EBLayout<32>::SMEM_BYTES);
   return e;
 }
 
