@@ -523,6 +523,86 @@ __global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const
   }
 }
 
+// Register-resident modified Gram-Schmidt for M <= 64 and spin blocks of at most 8 (FP64):
+// one warp per walker (two per 64-thread CTA), lanes 0-15 the spin-up block, 16-31 the
+// spin-down block; lane l holds rows l + 16 r (r < 4) of every column of its block, so the
+// projections and norms read no shared memory (the block with fewer columns carries zero
+// columns).  Columns in order, each projected on the finished ones, then normalised; log O
+// drops by the log of the norms as in k_mgs_warp.
+__global__ void __launch_bounds__(64) k_mgs_reg(double* __restrict__ phi, const int* __restrict__ alive,
+                                               double* __restrict__ logO, int M, int N, int n_up, int Nw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wk = blockIdx.x * 2 + warp;
+  if (wk >= Nw || !alive[wk]) return;
+  const int h = lane >> 4, l16 = lane & 15;
+  const int n0 = h ? n_up : 0, ns = h ? N - n_up : n_up;
+  const int64_t NM = (int64_t)N * M, plane = (int64_t)Nw * NM, base = (int64_t)wk * NM;
+  double xr[8][4], xi[8][4];
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = l16 + 16 * r;
+      const bool ok = c < ns && i < M;
+      const int64_t g = base + (int64_t)(n0 + (ok ? c : 0)) * M + (ok ? i : 0);
+      xr[c][r] = ok ? phi[g] : 0.0;
+      xi[c][r] = ok ? phi[plane + g] : 0.0;
+    }
+  double my_sn = 1.0;   // lane j of each half: squared norm of column j before normalisation
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+#pragma unroll
+    for (int q = 0; q < j; ++q) {
+      double s0 = 0.0, s1 = 0.0;   // <q|x_j>
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        s0 = fma(xr[q][r], xr[j][r], fma(xi[q][r], xi[j][r], s0));
+        s1 = fma(xr[q][r], xi[j][r], fma(-xi[q][r], xr[j][r], s1));
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        // x_j -= <q|x_j> q: 4 fused multiply-adds per complex element
+        xr[j][r] = fma(-s0, xr[q][r], fma(s1, xi[q][r], xr[j][r]));
+        xi[j][r] = fma(-s0, xi[q][r], fma(-s1, xr[q][r], xi[j][r]));
+      }
+    }
+    double sn = 0.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) sn = fma(xr[j][r], xr[j][r], fma(xi[j][r], xi[j][r], sn));
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) sn += __shfl_xor_sync(0xffffffffu, sn, o);
+    const bool col = j < ns;
+    if (col && l16 == j) my_sn = sn;
+    const double inv = col ? rsqrt(sn) : 0.0;   // log O below uses sn itself
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      xr[j][r] *= inv;
+      xi[j][r] *= inv;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = l16 + 16 * r;
+      if (c < ns && i < M) {
+        const int64_t g = base + (int64_t)(n0 + c) * M + i;
+        phi[g] = xr[c][r];
+        phi[plane + g] = xi[c][r];
+      }
+    }
+  if (logO) {
+    double v = l16 < ns ? 0.5 * log(my_sn) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) logO[wk] -= v;
+  }
+}
+
 size_t smem_fast_overlap(const Ctx& c, bool fp64_copy = true) {
   const size_t nmp = (size_t)c.N * (c.M + kPad);
   return sizeof(double) * ((fp64_copy ? 2 * nmp : 0) + 2 * 2 * kNsMax * kLd) +
@@ -586,8 +666,11 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
 }
 
 cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s, bool update_logO) {
-  k_mgs_warp<<<(c.Nw + 1) / 2, 64, smem_mgs_warp(c), s>>>(c.phi, c.alive, update_logO ? c.logO : nullptr,
-                                                         c.M, c.N, c.n_up, c.Nw);
+  double* lo = update_logO ? c.logO : nullptr;
+  if (c.M <= 64 && c.n_up <= 8 && c.N - c.n_up <= 8)
+    k_mgs_reg<<<(c.Nw + 1) / 2, 64, 0, s>>>(c.phi, c.alive, lo, c.M, c.N, c.n_up, c.Nw);
+  else
+    k_mgs_warp<<<(c.Nw + 1) / 2, 64, smem_mgs_warp(c), s>>>(c.phi, c.alive, lo, c.M, c.N, c.n_up, c.Nw);
   return cudaGetLastError();
 }
 
