@@ -74,7 +74,8 @@ void free_ctx(Ctx* h) {
   for (double* b : {h->Bneg, h->dexpK, h->htilP, h->dphi, h->dphi2, h->dtheta, h->drhobar, h->dU,
                     h->dAvhs, h->dlogO, h->dlogw, h->daux, h->deloc, h->desum})
     if (b) cudaFree(b);
-  for (float* b : {h->Avhs32, h->phi32, h->expK32, h->Ltil32, h->theta32, h->LtT, h->psi32h, h->psi32l})
+  for (float* b : {h->Avhs32, h->phi32, h->expK32, h->Ltil32, h->theta32, h->LtT, h->psi32h, h->psi32l,
+                   h->rhobar32, h->rho_mf32})
     if (b) cudaFree(b);
   if (h->d_tc_err) cudaFree(h->d_tc_err);
   if (h->etc) {
@@ -133,6 +134,8 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   if ((st = dalloc(h, &h->psi32h, (size_t)NM)) != AFQMC_OK) return st;
   if ((st = dalloc(h, &h->psi32l, (size_t)NM)) != AFQMC_OK) return st;
   if ((st = dalloc(h, &h->ovdet, 8 * (size_t)Nw)) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->rhobar32, 2 * (size_t)Nw * X)) != AFQMC_OK) return st;
+  if ((st = dalloc(h, &h->rho_mf32, (size_t)X)) != AFQMC_OK) return st;
   AFQ_CK(cudaMemsetAsync(h->d_tc_err, 0, sizeof(int), s));
   // L as rows ij with g contiguous: transpose [X][M*M] -> [M*M][X] through phi2 (large enough
   // only when 2*Nw*N*M >= X*M*M; otherwise a temporary)
@@ -150,6 +153,7 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   if (e == cudaSuccess) e = afq::to_float(h->Ltil, h->Ltil32, (int64_t)X * NM, s);
   if (e == cudaSuccess) e = afq::build_LtT(*h, h->LtT, s);
   if (e == cudaSuccess) e = afq::split_f32(h->psi, h->psi32h, h->psi32l, NM, s);
+  if (e == cudaSuccess) e = afq::to_float(h->rho_mf, h->rho_mf32, X, s);
   if (e == cudaSuccess && afq::propagate_tc_ok(*h)) {
     if (dalloc(h, &h->emI_pk, 64 * 64) != AFQMC_OK) return AFQMC_ERR_NOMEM;
     e = afq::pack_propagate_tc(*h, h->emI_pk, s);
@@ -200,7 +204,7 @@ afqmc_status step_launch_mixed(Ctx* h, const double* fields_t, cudaStream_t s) {
   const int64_t MM = (int64_t)M * M;
   if (h->opt.mode == AFQMC_PHASELESS) {
     // the Theta operand was written by the last overlap kernel
-    AFQ_CK(afq::gemm_bf16x3(*h->tc_Ltil, *h->tc_Theta, X, 2 * Nw, 1.0f, h->rhobar, X,
+    AFQ_CK(afq::gemm_bf16x3(*h->tc_Ltil, *h->tc_Theta, X, 2 * Nw, 1.0f, h->rhobar32, X,
                             h->d_tc_err, s));
   }
   AFQ_CK(afq::launch_fields_mixed(*h, fields_t, s));
@@ -688,7 +692,7 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
                                 h->P, 0, 1, s, afq::GEMM_VHS);
       case AFQMC_K_FORCE_BIAS:
         if (h->tc_Ltil)
-          return afq::gemm_bf16x3(*h->tc_Ltil, *h->tc_Theta, X, 2 * Nw, 1.0f, h->rhobar, X,
+          return afq::gemm_bf16x3(*h->tc_Ltil, *h->tc_Theta, X, 2 * Nw, 1.0f, h->rhobar32, X,
                                   h->d_tc_err, s);
         return afq::gemm_tn_f64(X, 2 * Nw, (int)NM, 1.0, h->Ltil, NM, 0, h->theta, NM, 0, 0.0,
                                 h->rhobar, X, 0, 1, s, afq::GEMM_FORCE_BIAS);

@@ -69,6 +69,8 @@ struct Ctx {
   float *psi32h = nullptr, *psi32l = nullptr;   // [N][M]  psi = psi32h + psi32l (FP32 pair)
   double* ovdet = nullptr;    // [Nw][8]  per-walker determinant factors between the overlap kernels
   uint32_t* emI_pk = nullptr; // [64][64] e^{-dt K/2} - I as split-bf16 words (tensor-core propagator)
+  float* rhobar32 = nullptr;  // [2][Nw][X]  force bias of the split-precision step (FP32 GEMM output)
+  float* rho_mf32 = nullptr;  // [X]         <rho_g>_T in FP32
   int* d_tc_err = nullptr;    // set by a tensor-core kernel whose bounded wait expired
   EnergyTc* etc = nullptr;    // tensor-core local energy (null when the shape is unsupported)
   // autotuned variants (autotune.cpp); -1 = not tuned, use the default

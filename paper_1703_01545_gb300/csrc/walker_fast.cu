@@ -490,8 +490,8 @@ __global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const
       }
       if (col)
         for (int i = l16; i < M; i += 16) {
-          const double u = xr[i] - (s0 * qr[i] - s1 * qi[i]);
-          const double v = xi[i] - (s0 * qi[i] + s1 * qr[i]);
+          const double u = fma(-s0, qr[i], fma(s1, qi[i], xr[i]));
+          const double v = fma(-s0, qi[i], fma(-s1, qr[i], xi[i]));
           xr[i] = u;
           xi[i] = v;
         }
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(64) k_mgs_warp(double* __restrict__ phi, const
       for (int i = l16; i < M; i += 16) sn += xr[i] * xr[i] + xi[i] * xi[i];
     for (int o = 8; o > 0; o >>= 1) sn += __shfl_xor_sync(0xffffffffu, sn, o);
     if (col && l16 == j) my_sn = sn;
-    const double inv = col ? 1.0 / sqrt(sn) : 0.0;
+    const double inv = col ? rsqrt(sn) : 0.0;
     if (col)
       for (int i = l16; i < M; i += 16) {
         xr[i] *= inv;
@@ -684,8 +684,8 @@ namespace {
 // V_HS coefficients U = i sqrt(dt) c in FP32, written straight into the split bf16
 // operand of the tensor-core V_HS GEMM; the two scalar sums accumulate in FP64.
 struct FieldArgsM {
-  const double* rhobar;   // [2][Nw][X]
-  const double* rho_mf;   // [X]
+  const float* rhobar;    // [2][Nw][X]  (the FP32 output of the force-bias contraction)
+  const float* rho_mf;    // [X]
   const double* fields;   // [Nw][X] or null
   __nv_bfloat16* u_hi;    // [(p, w)][Kp]
   __nv_bfloat16* u_lo;
@@ -735,10 +735,10 @@ __global__ void __launch_bounds__(128) k_fields_mixed(FieldArgsM a) {
       if (g >= X) break;
       const float x = a.fields ? (float)a.fields[row + g] : z[q];
       float xb_re = 0.f, xb_im = 0.f;
-      const float rm = (float)a.rho_mf[g];
+      const float rm = a.rho_mf[g];
       if (!a.free_proj) {
-        xb_re = a.sqrt_dt * (float)a.rhobar[plane + row + g];
-        xb_im = -a.sqrt_dt * ((float)a.rhobar[row + g] - rm);
+        xb_re = a.sqrt_dt * a.rhobar[plane + row + g];
+        xb_im = -a.sqrt_dt * (a.rhobar[row + g] - rm);
         if (a.fb_cap > 0.f) {
           const float m2 = xb_re * xb_re + xb_im * xb_im;
           if (m2 > a.fb_cap * a.fb_cap) {
@@ -773,10 +773,14 @@ __global__ void __launch_bounds__(128) k_fields_mixed(FieldArgsM a) {
     for (int q = 0; q < 4; ++q) red[wid][q] = make_float2(ps[q], pc[q]);
   __syncthreads();
   if (threadIdx.x == 0) {
-    double acc[4] = {0, 0, 0, 0};
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+    // the warps' pairs added as FP32 pairs too; the FP64 pipe sees one add per sum
+    double acc[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += (double)red[w][q].x + (double)red[w][q].y;
+    for (int q = 0; q < 4; ++q) {
+      float s = red[0][q].x, c = red[0][q].y;
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) df_add(s, c, red[w][q].x, red[w][q].y);
+      acc[q] = (double)s + (double)c;
+    }
     double* o = a.aux + 4 * (int64_t)wk;
     o[0] = (double)a.sqrt_dt * acc[1];
     o[1] = -(double)a.sqrt_dt * acc[0];
@@ -789,7 +793,7 @@ __global__ void __launch_bounds__(128) k_fields_mixed(FieldArgsM a) {
 
 cudaError_t launch_fields_mixed(const Ctx& c, const double* fields, cudaStream_t s) {
   FieldArgsM a;
-  a.rhobar = c.rhobar; a.rho_mf = c.rho_mf; a.fields = fields;
+  a.rhobar = c.rhobar32; a.rho_mf = c.rho_mf32; a.fields = fields;
   a.u_hi = c.tc_U->hi; a.u_lo = c.tc_U->lo; a.Kp = c.tc_U->Kp; a.aux = c.aux; a.step = c.d_step;
   a.key = make_uint2((uint32_t)(c.opt.seed & 0xffffffffull), (uint32_t)(c.opt.seed >> 32));
   a.k0 = (uint32_t)c.opt.walker_offset;
