@@ -209,10 +209,12 @@ afqmc_status step_launch_mixed(Ctx* h, const double* fields_t, cudaStream_t s) {
   }
   AFQ_CK(afq::launch_fields_mixed(*h, fields_t, s));
   AFQ_CK(afq::gemm_bf16x3(*h->tc_L, *h->tc_U, (int)MM, 2 * Nw, 1.0f, h->Avhs32, MM, h->d_tc_err, s));
-  // Phi' = e^{-dt K/2} e^A e^{-dt K/2} Phi into theta (FP64); variants 2, 3 also into phi32 (FP32)
+  // Phi' = e^{-dt K/2} e^A e^{-dt K/2} Phi into theta (FP64; the tensor-core propagator writes
+  // the live walkers in place) and, variants 2 and 3, into phi32 (FP32)
   const int pv = afq::propagation_variant(*h);
-  AFQ_CK(afq::launch_propagation(*h, pv, h->theta, h->phi32, s));
-  afqmc_status os = overlap_launch(h, h->theta, afq::OV_UPDATE, s, pv >= 2 ? h->phi32 : nullptr);
+  double* pout = pv == 3 ? h->phi : h->theta;
+  AFQ_CK(afq::launch_propagation(*h, pv, pout, h->phi32, s));
+  afqmc_status os = overlap_launch(h, pout, afq::OV_UPDATE, s, pv >= 2 ? h->phi32 : nullptr);
   if (os != AFQMC_OK) return os;
   AFQ_CK(afq::launch_step_advance(*h, s));
   return AFQMC_OK;

@@ -54,10 +54,10 @@ struct PLayout {
 };
 
 __global__ void __launch_bounds__(128, 3)
-    k_propagate_tc(const double* __restrict__ phi_in, const float* __restrict__ Av,
-                   const uint32_t* __restrict__ emI_pk, double* __restrict__ phi_out,
-                   float* __restrict__ phi_out32, int M, int N, int Nw, int order, int* err,
-                   uint64_t wait_ns) {
+    k_propagate_tc(const double* phi_in, const float* __restrict__ Av,
+                   const uint32_t* __restrict__ emI_pk, double* phi_out,
+                   float* __restrict__ phi_out32, const int* __restrict__ alive, int M, int N,
+                   int Nw, int order, int* err, uint64_t wait_ns) {
   using Lay = PLayout;
   extern __shared__ uint8_t psm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(psm_raw) + 1023) &
@@ -158,6 +158,9 @@ __global__ void __launch_bounds__(128, 3)
   };
 
   for (int w = blockIdx.x; w < Nw; w += gridDim.x) {
+    // in place (phi_out == phi_in), dead walkers keep their Phi: each walker's inputs are read
+    // in full before any of its outputs is written
+    if (alive && !alive[w]) continue;
     // the next walker's A planes and Phi towards L2 while this one is propagated
     if (tid == 0 && w + (int)gridDim.x < Nw) {
       const int wn = w + gridDim.x;
@@ -296,12 +299,14 @@ cudaError_t prepare_propagate_tc() {
                               PLayout::SMEM_BYTES);
 }
 
-// Phi' of every walker from c.phi and c.Avhs32: out (FP64), out32 (FP32, may be null).
+// Phi' of every walker from c.phi and c.Avhs32: out (FP64), out32 (FP32, may be null).  With
+// out == c.phi the live walkers are propagated in place and the dead ones left as they are.
 cudaError_t launch_propagate_tc(const Ctx& c, double* out, float* out32, cudaStream_t s) {
   if (!propagate_tc_ok(c)) return cudaErrorInvalidValue;
   const int grid = std::min(c.Nw, 152 * 3);
   if (!c.emI_pk) return cudaErrorInvalidValue;
-  k_propagate_tc<<<grid, 128, PLayout::SMEM_BYTES, s>>>(c.phi, c.Avhs32, c.emI_pk, out, out32, c.M, c.N,
+  k_propagate_tc<<<grid, 128, PLayout::SMEM_BYTES, s>>>(c.phi, c.Avhs32, c.emI_pk, out, out32,
+                                                        out == c.phi ? c.alive : nullptr, c.M, c.N,
                                                         c.Nw, c.opt.taylor_order, c.d_tc_err, kPWaitNs);
   return cudaGetLastError();
 }

@@ -193,19 +193,27 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   const double* src = upd ? a.src : a.phi;
   const int64_t plane = (int64_t)a.Nw * NM, wbase = (int64_t)wk * NM;
   const bool f32 = upd && a.src32 != nullptr;
+  const bool inplace = upd && a.src == a.phi;   // the propagator already wrote Phi
   for (int e = tid; e < NM; e += blockDim.x) {
-    const double xr = src[wbase + e], xi = src[plane + wbase + e];
     const int es = e + (e / M) * kPad;   // (n, i) in the padded layout
-    if (upd) {                  // the propagated walker becomes the walker: no dependence on O
-      a.phi[wbase + e] = xr;
-      a.phi[plane + wbase + e] = xi;
-    }
-    if (!f32) {                 // the FP64 copy feeds only the FP64 overlap sums
-      pr[es] = xr;
+    if (f32) {
+      pfr[es] = a.src32[wbase + e];
+      pfi[es] = a.src32[plane + wbase + e];
+      if (!inplace) {            // the propagated walker becomes the walker: no dependence on O
+        a.phi[wbase + e] = src[wbase + e];
+        a.phi[plane + wbase + e] = src[plane + wbase + e];
+      }
+    } else {
+      const double xr = src[wbase + e], xi = src[plane + wbase + e];
+      if (upd && !inplace) {
+        a.phi[wbase + e] = xr;
+        a.phi[plane + wbase + e] = xi;
+      }
+      pr[es] = xr;               // the FP64 copy feeds the FP64 overlap sums
       pi[es] = xi;
+      pfr[es] = (float)xr;
+      pfi[es] = (float)xi;
     }
-    pfr[es] = f32 ? a.src32[wbase + e] : (float)xr;
-    pfi[es] = f32 ? a.src32[plane + wbase + e] : (float)xi;
   }
   if (tid < 2) { s_det[tid][0] = 1.0; s_det[tid][1] = 0.0; s_dexp[tid] = 0; s_bad[tid] = 0; }
   __syncthreads();
