@@ -237,18 +237,17 @@ __global__ void __launch_bounds__(EPTHREADS, 1)
           for (int wi = 0; wi < WPG; ++wi) {
             const int cb = wi * 2 * NP;
             const float* colp = S + gl * NP * (CW + 1) + cb + a;        // T[.][a]
-            float exr = 0.f, exi = 0.f, dr = 0.f, di = 0.f;
+            float exr = 0.f, exi = 0.f;
 #pragma unroll
-            for (int j = 0; j < NP; ++j) {
-              // T[a][j] of the lane's spin block only (j in [s0, s0 + P2)); the diagonal
-              if (j >= s0 && j < s0 + P2) {
-                const float tr = rowv[cb + j], ti = rowv[cb + NP + j];
-                const float ur = colp[j * (CW + 1)], ui = colp[j * (CW + 1) + NP];
-                exr = fmaf(tr, ur, fmaf(-ti, ui, exr));
-                exi = fmaf(tr, ui, fmaf(ti, ur, exi));
-              }
-              if (j == a) { dr = rowv[cb + j]; di = rowv[cb + NP + j]; }
+            for (int j = 0; j < P2; ++j) {
+              // T[a][s0 + j] T[s0 + j][a] over the lane's spin block
+              const float tr = s0 ? rowv[cb + P2 + j] : rowv[cb + j];
+              const float ti = s0 ? rowv[cb + NP + P2 + j] : rowv[cb + NP + j];
+              const float ur = colp[(s0 + j) * (CW + 1)], ui = colp[(s0 + j) * (CW + 1) + NP];
+              exr = fmaf(tr, ur, fmaf(-ti, ui, exr));
+              exi = fmaf(tr, ui, fmaf(ti, ur, exi));
             }
+            float dr = S[lane * (CW + 1) + cb + a], di = S[lane * (CW + 1) + cb + NP + a];   // T[a][a]
 #pragma unroll
             for (int o = NP / 2; o > 0; o >>= 1) {                     // sums over the g block
               exr += __shfl_xor_sync(0xffffffffu, exr, o);
@@ -471,17 +470,17 @@ __global__ void __launch_bounds__(EBLayout<NP>::THREADS, 1)
             for (int wi = 0; wi < WPG; ++wi) {
               const int cb = wi * 2 * NP;
               const float* colp = S + gl * NP * (CW + 1) + cb + a;        // T[.][a]
-              float exr = 0.f, exi = 0.f, dr = 0.f, di = 0.f;
+              float exr = 0.f, exi = 0.f;
 #pragma unroll
-              for (int q = 0; q < NP; ++q) {
-                if (q >= s0 && q < s0 + P2) {
-                  const float tr = rowv[cb + q], ti = rowv[cb + NP + q];
-                  const float ur = colp[q * (CW + 1)], ui = colp[q * (CW + 1) + NP];
-                  exr = fmaf(tr, ur, fmaf(-ti, ui, exr));
-                  exi = fmaf(tr, ui, fmaf(ti, ur, exi));
-                }
-                if (q == a) { dr = rowv[cb + q]; di = rowv[cb + NP + q]; }
+              for (int q = 0; q < P2; ++q) {
+                // T[a][s0 + q] T[s0 + q][a] over the lane's spin block
+                const float tr = s0 ? rowv[cb + P2 + q] : rowv[cb + q];
+                const float ti = s0 ? rowv[cb + NP + P2 + q] : rowv[cb + NP + q];
+                const float ur = colp[(s0 + q) * (CW + 1)], ui = colp[(s0 + q) * (CW + 1) + NP];
+                exr = fmaf(tr, ur, fmaf(-ti, ui, exr));
+                exi = fmaf(tr, ui, fmaf(ti, ur, exi));
               }
+              float dr = S[lane * (CW + 1) + cb + a], di = S[lane * (CW + 1) + cb + NP + a];   // T[a][a]
 #pragma unroll
               for (int o = NP / 2; o > 0; o >>= 1) {
                 exr += __shfl_xor_sync(0xffffffffu, exr, o);
