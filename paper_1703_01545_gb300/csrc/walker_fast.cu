@@ -16,8 +16,8 @@ namespace {
 
 constexpr int kNsMax = 16;   // spin block size handled by the warp LU
 constexpr int kPad = 4;      // column padding (elements) of the shared copies of Phi
-constexpr int kLd = 24;      // row stride (doubles) of the in-place LU factors: the trailing
-                             // updates' accesses (2 rows x 8 columns per spin) fall in distinct banks
+constexpr int kLd = 24;      // row stride (doubles) of the in-place LU factors of blocks above 8:
+                             // the trailing updates' accesses (2 rows per pass) fall in distinct banks
 
 struct FastOvArgs {
   const double* src;  // [2][Nw][N][M]  (propagated walkers in update mode)
@@ -77,7 +77,7 @@ __device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
 // scale uses one reciprocal, and row blocks of the trailing update that no lane needs are
 // skipped.  Each complex update is 4 FP64 fused multiply-adds.  Lane l owns column l % ns and
 // rows l / ns + q (W / ns), q < Q.  kmax: the larger block of the warp (uniform loop bound).
-template <int W, int Q>
+template <int W, int Q, int LD>
 __device__ __forceinline__ void lu_block(double* __restrict__ ar, double* __restrict__ ai, int l,
                                          int ns, int kmax, int* __restrict__ piv, double& dr,
                                          double& di, int& dexp, bool& bad) {
@@ -92,8 +92,8 @@ __device__ __forceinline__ void lu_block(double* __restrict__ ar, double* __rest
     const bool live = k < ns && !bad;
     unsigned key = 0u;
     if (live && l >= k && l < ns) {
-      const unsigned hr = (unsigned)__double2hiint(ar[l * kLd + k]) & 0x7fffffffu;
-      const unsigned hi = (unsigned)__double2hiint(ai[l * kLd + k]) & 0x7fffffffu;
+      const unsigned hr = (unsigned)__double2hiint(ar[l * LD + k]) & 0x7fffffffu;
+      const unsigned hi = (unsigned)__double2hiint(ai[l * LD + k]) & 0x7fffffffu;
       key = hr > hi ? hr : hi;
     }
     int p = l;
@@ -108,11 +108,11 @@ __device__ __forceinline__ void lu_block(double* __restrict__ ar, double* __rest
     const bool go = live && !bad;
     if (go && l == 0) piv[k] = p;
     if (go && p != k && l < ns) {
-      double t = ar[k * kLd + l]; ar[k * kLd + l] = ar[p * kLd + l]; ar[p * kLd + l] = t;
-      t = ai[k * kLd + l]; ai[k * kLd + l] = ai[p * kLd + l]; ai[p * kLd + l] = t;
+      double t = ar[k * LD + l]; ar[k * LD + l] = ar[p * LD + l]; ar[p * LD + l] = t;
+      t = ai[k * LD + l]; ai[k * LD + l] = ai[p * LD + l]; ai[p * LD + l] = t;
     }
     __syncwarp();
-    const double vr = go ? ar[k * kLd + k] : 1.0, vi = go ? ai[k * kLd + k] : 0.0;
+    const double vr = go ? ar[k * LD + k] : 1.0, vi = go ? ai[k * LD + k] : 0.0;
     {
       const double tr = fma(dr, vr, -di * vi);
       double ti = fma(dr, vi, di * vr);
@@ -132,9 +132,9 @@ __device__ __forceinline__ void lu_block(double* __restrict__ ar, double* __rest
     const double ir = vr * rinv, ii = -vi * rinv;          // 1 / pivot
     __syncwarp();
     if (go && l >= k && l < ns) {
-      const double xr = ar[k * kLd + l], xi = ai[k * kLd + l];
-      ar[k * kLd + l] = (l == k) ? ir : fma(xr, ir, -xi * ii);
-      ai[k * kLd + l] = (l == k) ? ii : fma(xr, ii, xi * ir);
+      const double xr = ar[k * LD + l], xi = ai[k * LD + l];
+      ar[k * LD + l] = (l == k) ? ir : fma(xr, ir, -xi * ii);
+      ai[k * LD + l] = (l == k) ? ii : fma(xr, ii, xi * ir);
     }
     __syncwarp();
     // A[r][c] -= A[r][k] U[k][c] for r, c > k: column k and row k are not written, so no
@@ -142,15 +142,15 @@ __device__ __forceinline__ void lu_block(double* __restrict__ ar, double* __rest
     const bool colk = go && active && c > k;
     const int qf = colk ? max(0, (k + 1 - r0 + RS - 1) / RS) : Q;
     const int q0 = __reduce_min_sync(0xffffffffu, qf);
-    const double kr = colk ? ar[k * kLd + c] : 0.0, ki = colk ? ai[k * kLd + c] : 0.0;
+    const double kr = colk ? ar[k * LD + c] : 0.0, ki = colk ? ai[k * LD + c] : 0.0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       if (q >= q0) {
         const int r = r0 + q * RS;
         if (colk && r < ns && r > k) {
-          const double fr = ar[r * kLd + k], fi = ai[r * kLd + k];
-          ar[r * kLd + c] = fma(-fr, kr, fma(fi, ki, ar[r * kLd + c]));
-          ai[r * kLd + c] = fma(-fr, ki, fma(-fi, kr, ai[r * kLd + c]));
+          const double fr = ar[r * LD + k], fi = ai[r * LD + k];
+          ar[r * LD + c] = fma(-fr, kr, fma(fi, ki, ar[r * LD + c]));
+          ai[r * LD + c] = fma(-fr, ki, fma(-fi, kr, ai[r * LD + c]));
         }
       }
     }
@@ -159,7 +159,7 @@ __device__ __forceinline__ void lu_block(double* __restrict__ ar, double* __rest
 }
 
 // One CTA (128 or 256 threads) per walker.  Shared: phi [2][N][M + kPad] in FP64 (not in the
-// FP32 update), per spin the overlap matrix factorised in place (re and im [16][kLd], FP64),
+// FP32 update), per spin the overlap matrix factorised in place (re and im [NSM][LDA], FP64),
 // FP32 copies of phi and of the factors.
 // NSM: the larger spin block is at most 8 (both blocks factorised by warp 0, 16 lanes each) or
 // 16 (one warp per block, ROWS = ceil(ns / (32 / ns)) rows per lane, 4 or 8).
@@ -170,14 +170,16 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   // shared copies of Phi keep each column M + 4 apart: the overlap sums read 8 columns per
   // warp, which then fall in distinct banks
   const int MP = M + kPad, NMP = N * MP;
+  // in-place factors of a spin block: NSM rows of LDA doubles per re / im plane; blocks of at
+  // most 8 use a stride of 8, which puts the two row sets of a 16-lane half in disjoint banks
+  constexpr int LDA = NSM == 8 ? 8 : kLd, PLN = NSM * LDA, SPB = 2 * PLN;
   const int lane = tid & 31, warp = tid >> 5;
   double* pr = smo;            // [N][MP] (only when a.fp64_copy: the FP64 overlap sums)
   double* pi = pr + NMP;       // [N][MP]
-  double* aug = a.fp64_copy ? pi + NMP : smo;   // O_s then O_s^{-1}: spin s at aug + s * 2 * 16 * kLd,
-                                               // re/im [16][kLd]
+  double* aug = a.fp64_copy ? pi + NMP : smo;   // LU factors: spin s at aug + s * SPB, re, im [NSM][LDA]
   // FP32 copies for Theta: converting once here keeps double->float conversions (which run
   // on the FP64 pipe) off the Theta loop
-  float* pfr = reinterpret_cast<float*>(aug + 2 * 2 * kNsMax * kLd);  // [N][MP]
+  float* pfr = reinterpret_cast<float*>(aug + 2 * SPB);  // [N][MP]
   float* pfi = pfr + NMP;
   float* invf = pfi + NMP;     // spin s at invf + s * 2 * 16 * 16: re [16][16], im [16][16]
   __shared__ double s_det[2][2];   // per spin: determinant mantissa (re, im) ...
@@ -267,17 +269,17 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
       // part 1 the imaginary one, so each lane issues 2 conversions and 1 add
       const bool odd = part & 1;
       const double v = (double)(odd ? si : sr) + (double)(odd ? ci : cr);
-      if (ent < nn && part < 2) aug[sp * 2 * kNsMax * kLd + (odd ? kNsMax * kLd : 0) + r * kLd + c] = v;
+      if (ent < nn && part < 2) aug[sp * SPB + (odd ? PLN : 0) + r * LDA + c] = v;
     } else {
       re += __shfl_xor_sync(0xffffffffu, re, 1);
       im += __shfl_xor_sync(0xffffffffu, im, 1);
       re += __shfl_xor_sync(0xffffffffu, re, 2);
       im += __shfl_xor_sync(0xffffffffu, im, 2);
       if (ent < nn && part == 0) {
-        double* ar = aug + sp * 2 * kNsMax * kLd;
-        double* ai = ar + kNsMax * kLd;
-        ar[r * kLd + c] = re;
-        ai[r * kLd + c] = im;
+        double* ar = aug + sp * SPB;
+        double* ai = ar + PLN;
+        ar[r * LDA + c] = re;
+        ai[r * LDA + c] = im;
       }
     }
   }
@@ -285,11 +287,11 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   if (NSM == 8) {
     if (warp == 0) {   // both spin blocks, 16 lanes each
       const int h = lane >> 4, l16 = lane & 15, ns = h ? nd : nu;
-      double* ar = aug + h * 2 * kNsMax * kLd;
+      double* ar = aug + h * SPB;
       double dr, di;
       int dexp;
       bool bad;
-      lu_block<16, 4>(ar, ar + kNsMax * kLd, l16, ns, nu > nd ? nu : nd, s_piv[h], dr, di, dexp, bad);
+      lu_block<16, 4, LDA>(ar, ar + PLN, l16, ns, nu > nd ? nu : nd, s_piv[h], dr, di, dexp, bad);
       if (l16 == 0) {
         s_det[h][0] = dr;
         s_det[h][1] = di;
@@ -299,11 +301,11 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     }
   } else if (warp < 2) {
     const int sp = warp, ns = sp ? nd : nu;
-    double* ar = aug + sp * 2 * kNsMax * kLd;
+    double* ar = aug + sp * SPB;
     double dr, di;
     int dexp;
     bool bad;
-    lu_block<32, ROWS>(ar, ar + kNsMax * kLd, lane, ns, ns, s_piv[sp], dr, di, dexp, bad);
+    lu_block<32, ROWS, LDA>(ar, ar + PLN, lane, ns, ns, s_piv[sp], dr, di, dexp, bad);
     if (lane == 0) {
       s_det[sp][0] = dr;
       s_det[sp][1] = di;
@@ -328,10 +330,10 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     int sp = 0, r, c;
     if (e < nu * nu) { r = e / nu; c = e % nu; }
     else { sp = 1; r = (e - nu * nu) / nd; c = (e - nu * nu) % nd; }
-    const double* ar = aug + sp * 2 * kNsMax * kLd;
+    const double* ar = aug + sp * SPB;
     float* fr = invf + sp * 2 * kNsMax * kNsMax;
-    fr[r * kNsMax + c] = (float)ar[r * kLd + c];
-    fr[kNsMax * kNsMax + r * kNsMax + c] = (float)ar[kNsMax * kLd + r * kLd + c];
+    fr[r * kNsMax + c] = (float)ar[r * LDA + c];
+    fr[kNsMax * kNsMax + r * kNsMax + c] = (float)ar[PLN + r * LDA + c];
   }
   __syncthreads();
   // Theta_s = Phi_s O_s^{-1} = ((Phi_s U^{-1}) L^{-1}) P, one orbital row i of one spin per
@@ -613,7 +615,9 @@ __global__ void __launch_bounds__(64) k_mgs_reg(double* __restrict__ phi, const 
 
 size_t smem_fast_overlap(const Ctx& c, bool fp64_copy = true) {
   const size_t nmp = (size_t)c.N * (c.M + kPad);
-  return sizeof(double) * ((fp64_copy ? 2 * nmp : 0) + 2 * 2 * kNsMax * kLd) +
+  const bool small = std::max(c.n_up, c.N - c.n_up) <= 8;   // the NSM = 8 factor layout
+  const size_t aug = small ? 2 * 2 * 8 * 8 : 2 * 2 * kNsMax * kLd;
+  return sizeof(double) * ((fp64_copy ? 2 * nmp : 0) + aug) +
          sizeof(float) * (2 * nmp + 2 * 2 * kNsMax * kNsMax);
 }
 size_t smem_mgs_warp(const Ctx& c) { return sizeof(double) * 4 * (size_t)c.N * c.M; }   // two walkers
