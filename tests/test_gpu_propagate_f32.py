@@ -81,3 +81,32 @@ def test_tensor_core_propagator_refuses_large_shapes():
     with pytest.raises(RuntimeError):
         s.select_kernel(afq.K_TAYLOR, 3)
     s.close()
+
+
+def test_dead_walkers_keep_their_state_with_in_place_propagation():
+    """The tensor-core propagator writes live walkers in place and skips dead ones (killed by the
+    cos cut, Sec. II.B): a dead walker's Phi and weight stay bit for bit as they were, and the
+    mixed energy stays finite."""
+    afq = need_gpu()
+    d = system_data("C1", "A")
+    nw = 64
+    s = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=0.1, n_walkers=nw,
+                   precision=afq.BF16X3, fb_cap=0.3, autotune=False)
+    s.select_kernel(afq.K_TAYLOR, 3)
+    fields = explicit_fields(30, nw, d["X"], seed=41)
+    s.propagate(20, fields[:20])
+    s.orthonormalise()
+    st1 = s.state()
+    dead = ~st1["alive"]
+    assert dead.any() and not dead.all()
+    s.propagate(10, fields[20:])
+    s.orthonormalise()
+    st2 = s.state()
+    _, em, _ = s.energy()
+    s.close()
+    assert np.array_equal(st2["phi"][dead], st1["phi"][dead])
+    assert np.array_equal(st2["w"][dead], st1["w"][dead])
+    assert not st2["alive"][dead].any()
+    assert np.all(np.isfinite(em))
+    live = st2["alive"]
+    assert np.abs(st2["phi"][live] - st1["phi"][live]).max() > 0
