@@ -252,14 +252,16 @@ def run_ours(args, wl, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     prec_id = {"fp64": afq.FP64, "bf16x3": afq.BF16X3}
 
-    def make(d, prec):
+    def make(d, prec, seed=1, independent=False):
         return afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt, n_walkers=nw,
-                          seed=1, n_repeats=R, walker_offset=rank * nw, precision=prec_id[prec],
-                          autotune_cache=args.autotune_cache)
+                          seed=seed, n_repeats=R, walker_offset=rank * nw, precision=prec_id[prec],
+                          autotune_cache=args.autotune_cache, independent_fields=independent)
 
-    def timed(prec, coupling, clocks=None):
+    def timed(prec, coupling, clocks=None, independent=False):
+        """Pair run; independent=True gives B its own field key (uncorrelated sampling)."""
         dA, dB = systems(wl, coupling)
-        A, B = make(dA, prec), make(dB, prec)
+        A = make(dA, prec, 1, independent)
+        B = make(dB, prec, 2 if independent else 1, independent)
         afq.pair_delta_E(A, B, W * STEPS_PER_BLOCK, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
                          raise_on_dead=False)
         torch.cuda.synchronize()
@@ -441,6 +443,21 @@ def run_ours(args, wl, rank, world, local_rank):
            "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
            "note": "setup of both systems from host arrays + pair run + energy series to host"}
 
+    # correlated against independent fields at the same workload and precision (Sec. III):
+    # GPU time to reach a given sigma_dE scales as sigma^2 * t
+    corr = None
+    if world == 1:
+        ri = timed(args.precision, args.coupling, independent=True)
+        ri["A"].close()
+        ri["B"].close()
+        sc, si = main["res"]["dE_sigma"], ri["res"]["dE_sigma"]
+        corr = {"dE_mean_correlated_Ha": main["res"]["dE_mean"], "dE_sigma_correlated_Ha": sc,
+                "dE_mean_independent_Ha": ri["res"]["dE_mean"], "dE_sigma_independent_Ha": si,
+                "ms_correlated": ms, "ms_independent": ri["ms"],
+                "gpu_time_ratio_at_equal_sigma": (si * si * ri["ms"]) / (sc * sc * ms)
+                if sc > 0 else None,
+                "repeats": R, "note": "independent: system B keyed by its own seed"}
+
     other = None
     if world == 1:
         oc = "literal" if args.coupling == "moderate" else "moderate"
@@ -471,7 +488,7 @@ def run_ours(args, wl, rank, world, local_rank):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clocks"],
             "gpu_launches": per_block * K, "alive_walkers": main["alive"],
-            "sigma_sqrt_t": comp, "other_coupling": other,
+            "sigma_sqrt_t": comp, "correlated_vs_independent": corr, "other_coupling": other,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

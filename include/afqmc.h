@@ -72,6 +72,10 @@ typedef struct {
                          handle's buffers and keep the fastest (default), 0 = defaults    */
   const char* autotune_cache; /* NULL, or a JSON file of tuned choices keyed by kernel and
                          shape; read at setup, rewritten when a new shape was timed        */
+  int independent_fields; /* 0 (default): afqmc_pair_delta_E requires equal seeds, so walker
+                         k of both systems draws the same fields (correlated sampling);
+                         1 on both handles of a pair: the seeds must differ and each system
+                         draws its own fields (the uncorrelated comparison of Sec. III)    */
 } afqmc_options;
 
 typedef struct {
@@ -91,7 +95,7 @@ typedef struct {
 
 /* Fill *o with dt = 0.01, n_walkers = 128, taylor_order = 6, FP64, phaseless,
  * n_repeats = 1, seed = 1, fb_cap = 1.0, walker_offset = 0, autotune = 1,
- * autotune_cache = NULL. */
+ * autotune_cache = NULL, independent_fields = 0. */
 void afqmc_default_options(afqmc_options* o);
 
 const char* afqmc_status_string(afqmc_status s);
@@ -193,7 +197,9 @@ afqmc_status afqmc_energy(afqmc_handle h, double* e_local, double* e_mixed, doub
  * (order: propagate, orthonormalise, measure).  One measurement block is captured
  * once as a CUDA graph and replayed.  Requirements: same seed, Nw, R, dt, mode and
  * step counter on both handles; the step counter a multiple of energy_every;
- * energy_every a multiple of mgs_every; n_steps a multiple of energy_every.
+ * energy_every a multiple of mgs_every; n_steps a multiple of energy_every.  With
+ * independent_fields = 1 on both handles the seeds must differ instead: each system then
+ * draws its own fields and the same statistics measure uncorrelated sampling.
  * Outputs (host or device, any may be NULL):
  *   e_series [n_meas][2][R]   E_A,r and E_B,r at each measurement
  *   dE_mean, dE_sigma, tau_at_min: mean and standard error (over the R repeats) of

@@ -266,8 +266,11 @@ def mixed_energy(sys: System, w, eloc, groups, n_repeats):
 
 def run_pair(sysA: System, sysB: System, n_walkers: int, n_steps: int, seed: int,
              energy_every: int = 5, mgs_every: int = 5, n_repeats: int = 1,
-             walker_index=None, fields=None, record_walkers=False):
+             walker_index=None, fields=None, record_walkers=False, seed_B=None):
     """Correlated pair run (Sec. II.B): walker k of A and walker k of B share x_{t,k,g}.
+
+    ``seed_B`` (optional) gives B its own key instead: the two systems then draw
+    independent fields, the uncorrelated sampling that Sec. III compares against.
 
     ``walker_index`` (default 0..Nw-1) gives the global pair index k of every walker
     propagated here, so a subset of a large population can be followed exactly.
@@ -276,7 +279,10 @@ def run_pair(sysA: System, sysB: System, n_walkers: int, n_steps: int, seed: int
     mixed energies for both systems and (optionally) per-walker records.
     Order within a step boundary: propagate, then MGS, then measure.
     """
-    systems = [s for s in (sysA, sysB) if s is not None]
+    keyed = [(s, sd) for s, sd in ((sysA, seed), (sysB, seed if seed_B is None else seed_B))
+             if s is not None]
+    systems = [s for s, _ in keyed]
+    seeds = [sd for _, sd in keyed]
     k = np.arange(n_walkers) if walker_index is None else np.asarray(walker_index)
     groups = repeat_groups(n_walkers, n_repeats)[k] if walker_index is None else \
         (k * n_repeats) // n_walkers
@@ -284,9 +290,9 @@ def run_pair(sysA: System, sysB: System, n_walkers: int, n_steps: int, seed: int
     out = dict(steps=[], E=[[] for _ in systems], W=[[] for _ in systems],
                records=[[] for _ in systems])
     for t in range(n_steps):
-        for s, wk in zip(systems, wks):
+        for s, wk, sd in zip(systems, wks, seeds):
             if fields is None:
-                x = gaussian_fields(seed, t, k, s.X)
+                x = gaussian_fields(sd, t, k, s.X)
             else:
                 x = fields[t][:, :s.X]
             propagate(s, wk, x)

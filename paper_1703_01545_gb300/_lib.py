@@ -16,7 +16,7 @@ class AfqmcOptions(ctypes.Structure):
                 ("mode", ctypes.c_int), ("n_repeats", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("fb_cap", ctypes.c_double),
                 ("walker_offset", ctypes.c_int64), ("autotune", ctypes.c_int),
-                ("autotune_cache", ctypes.c_char_p)]
+                ("autotune_cache", ctypes.c_char_p), ("independent_fields", ctypes.c_int)]
 
 
 class AfqmcInfo(ctypes.Structure):

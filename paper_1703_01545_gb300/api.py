@@ -159,7 +159,8 @@ class System:
 
     def __init__(self, h1, L, trial, n_up, n_dn, dt=0.01, n_walkers=128, taylor_order=6,
                  mode=PHASELESS, n_repeats=1, seed=1, fb_cap=1.0, walker_offset=0,
-                 precision=FP64, autotune=True, autotune_cache=None, stream=None):
+                 precision=FP64, autotune=True, autotune_cache=None, independent_fields=False,
+                 stream=None):
         h1 = np.ascontiguousarray(h1, dtype=np.float64)
         L = np.ascontiguousarray(L, dtype=np.float64)
         trial = np.ascontiguousarray(trial, dtype=np.float64)
@@ -172,6 +173,7 @@ class System:
         o.seed, o.fb_cap, o.walker_offset = int(seed), float(fb_cap), int(walker_offset)
         o.autotune = 1 if autotune else 0
         o.autotune_cache = autotune_cache.encode() if autotune_cache else None
+        o.independent_fields = 1 if independent_fields else 0
         self.opt = o
         self.h = afqmc_setup(h1, L, trial, self.M, self.X, self.n_up, self.n_dn, o, stream)
 

@@ -347,6 +347,10 @@ afqmc_status check_opts(const afqmc_options* o, std::string& why) {
     why = "walker_offset out of range";
     return AFQMC_ERR_ARG;
   }
+  if (o->independent_fields != 0 && o->independent_fields != 1) {
+    why = "independent_fields must be 0 or 1";
+    return AFQMC_ERR_ARG;
+  }
   return AFQMC_OK;
 }
 
@@ -375,6 +379,7 @@ void afqmc_default_options(afqmc_options* o) {
   o->walker_offset = 0;
   o->autotune = 1;
   o->autotune_cache = nullptr;
+  o->independent_fields = 0;
 }
 
 const char* afqmc_status_string(afqmc_status s) {

@@ -66,10 +66,18 @@ extern "C" afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n
                                            double* e_series, double* dE_mean, double* dE_sigma,
                                            double* tau_at_min, cudaStream_t s) {
   if (!A || !B || A == B) return fail(A, B, AFQMC_ERR_ARG, "need two distinct handles");
-  if (A->opt.seed != B->opt.seed || A->Nw != B->Nw || A->R != B->R || A->opt.dt != B->opt.dt ||
+  if (A->Nw != B->Nw || A->R != B->R || A->opt.dt != B->opt.dt ||
       A->opt.mode != B->opt.mode || A->opt.walker_offset != B->opt.walker_offset ||
       A->opt.precision != B->opt.precision)
-    return fail(A, B, AFQMC_ERR_ARG, "pair handles differ in seed, walkers, repeats, dt, mode or walker offset");
+    return fail(A, B, AFQMC_ERR_ARG, "pair handles differ in walkers, repeats, dt, mode, precision or walker offset");
+  // Correlated sampling shares one field stream (one key); the uncorrelated comparison
+  // needs two keys, so equal seeds there would silently correlate the pair.
+  if (A->opt.independent_fields != B->opt.independent_fields)
+    return fail(A, B, AFQMC_ERR_ARG, "pair handles differ in independent_fields");
+  if (!A->opt.independent_fields && A->opt.seed != B->opt.seed)
+    return fail(A, B, AFQMC_ERR_ARG, "correlated pair handles need the same seed");
+  if (A->opt.independent_fields && A->opt.seed == B->opt.seed)
+    return fail(A, B, AFQMC_ERR_ARG, "independent_fields needs different seeds");
   if (A->step != B->step) return fail(A, B, AFQMC_ERR_STATE, "pair handles are at different steps");
   if (A->tangent_on || B->tangent_on)
     return fail(A, B, AFQMC_ERR_STATE, "tangent mode runs through afqmc_propagate, not the pair graph");

@@ -20,9 +20,11 @@ def system_data(cfg, which, coupling=1.0):
     return build_system(**d)
 
 
-def pair(afq, d, nw, dt, seed=1, R=1, mode=0, fb_cap=1.0, taylor_order=6):
+def pair(afq, d, nw, dt, seed=1, R=1, mode=0, fb_cap=1.0, taylor_order=6,
+         independent_fields=False):
     g = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt, n_walkers=nw,
-                   seed=seed, n_repeats=R, mode=mode, fb_cap=fb_cap, taylor_order=taylor_order)
+                   seed=seed, n_repeats=R, mode=mode, fb_cap=fb_cap, taylor_order=taylor_order,
+                   independent_fields=independent_fields)
     o = orc.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt, fb_cap=fb_cap,
                    mode=orc.FREE if mode == 1 else orc.PHASELESS, taylor_order=taylor_order)
     return g, o

@@ -46,9 +46,9 @@ def test_struct_layout_matches_header(tmp_path):
         pytest.skip("no C compiler")
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "afqmc.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(afqmc_options),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(afqmc_options),'
                    ' offsetof(afqmc_options, seed), offsetof(afqmc_options, walker_offset),'
-                   ' offsetof(afqmc_options, autotune_cache),'
+                   ' offsetof(afqmc_options, autotune_cache), offsetof(afqmc_options, independent_fields),'
                    ' sizeof(afqmc_info), offsetof(afqmc_info, step), offsetof(afqmc_info, c_mf),'
                    ' offsetof(afqmc_info, n_alive), offsetof(afqmc_info, tuned_taylor_smem)); return 0;}\n')
     exe = tmp_path / "layout"
@@ -59,6 +59,7 @@ def test_struct_layout_matches_header(tmp_path):
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     O, I = _lib.AfqmcOptions, _lib.AfqmcInfo
     want = [ctypes.sizeof(O), O.seed.offset, O.walker_offset.offset, O.autotune_cache.offset,
+            O.independent_fields.offset,
             ctypes.sizeof(I), I.step.offset,
             I.c_mf.offset, I.n_alive.offset, I.tuned_taylor_smem.offset]
     assert got == want
@@ -68,6 +69,7 @@ def test_default_options_and_status_strings(lib):
     from paper_1703_01545_gb300 import afqmc_default_options
     o = afqmc_default_options()
     assert (o.dt, o.n_walkers, o.taylor_order, o.mode, o.n_repeats, o.fb_cap) == (0.01, 128, 6, 0, 1, 1.0)
+    assert o.independent_fields == 0
     for code in range(7):
         assert lib.afqmc_status_string(code)
 
@@ -97,6 +99,9 @@ def test_setup_rejects_bad_arguments_without_a_device(lib):
     assert call(opt=bad) == 1
     bad = afqmc_default_options()
     bad.precision = 7
+    assert call(opt=bad) == 1
+    bad = afqmc_default_options()
+    bad.independent_fields = 2
     assert call(opt=bad) == 1
     assert lib.afqmc_setup(None, None, None, None, 1, 1, 1, 0, None, None) == 1
     assert lib.afqmc_destroy(None) == 0

@@ -184,6 +184,31 @@ def test_pair_graph_matches_oracle(afq):
     gB.close()
 
 
+def test_pair_independent_fields_matches_oracle(afq):
+    """independent_fields = 1 on both handles: B draws from its own key (the uncorrelated
+    comparison of Sec. III); both systems follow the oracle run with seed_B.  A flag set on
+    one handle only, or a shared seed under the flag, is rejected before any work."""
+    cfg = CONFIGS["C1"]
+    dA, dB = system_data("C1", "A"), system_data("C1", "B")
+    nw, R, steps = 64, 4, 20
+    gA, oA = pair(afq, dA, nw, cfg["dt"], seed=5, R=R, independent_fields=True)
+    gB, oB = pair(afq, dB, nw, cfg["dt"], seed=6, R=R, independent_fields=True)
+    gC, _ = pair(afq, dB, nw, cfg["dt"], seed=5, R=R, independent_fields=True)
+    gD, _ = pair(afq, dB, nw, cfg["dt"], seed=6, R=R)
+    for other in (gC, gD):
+        with pytest.raises(afq.AfqmcError, match="invalid argument"):
+            afq.pair_delta_E(gA, other, steps, 5, 5)
+    res = afq.pair_delta_E(gA, gB, steps, 5, 5)
+    ref = orc.run_pair(oA, oB, nw, steps, seed=5, seed_B=6, n_repeats=R)
+    assert rel(res["E"][:, 0, :], ref["E"][0]) < TOL
+    assert rel(res["E"][:, 1, :], ref["E"][1]) < TOL
+    wkA, wkB = ref["walkers"]
+    compare_state(gA, wkA)
+    compare_state(gB, wkB)
+    for g in (gA, gB, gC, gD):
+        g.close()
+
+
 def test_identical_systems_exactly_zero_difference(afq):
     d = system_data("C1", "A")
     gA, _ = pair(afq, d, 64, 0.01, seed=2, R=4)

@@ -83,3 +83,19 @@ def test_correlated_sampling_reduces_error_of_difference():
     mu, su, _ = stats.delta_e_estimate(du, taus, 0.3)
     assert sc < 0.2 * su
     assert abs(mc - mu) < 3 * np.hypot(sc, su)     # same difference, smaller error
+
+
+def test_seed_B_draws_independent_fields_for_B_only():
+    """run_pair(seed_B=...) is the uncorrelated comparison: A follows its solo run on the
+    common key and B its solo run on its own key, bit for bit."""
+    sA, _ = c1("A", 0.01)
+    sB, _ = c1("B", 0.01)
+    nw, R, steps = 8, 2, 15
+    ind = afqmc.run_pair(sA, sB, nw, steps, seed=7, seed_B=8, n_repeats=R)
+    soloA = afqmc.run_pair(sA, None, nw, steps, seed=7, n_repeats=R)
+    soloB = afqmc.run_pair(sB, None, nw, steps, seed=8, n_repeats=R)
+    assert np.array_equal(ind["E"][0], soloA["E"][0])
+    assert np.array_equal(ind["E"][1], soloB["E"][0])
+    same = afqmc.run_pair(sA, sB, nw, steps, seed=7, n_repeats=R)
+    assert np.array_equal(same["E"][0], ind["E"][0])
+    assert not np.array_equal(same["E"][1], ind["E"][1])
