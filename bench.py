@@ -74,6 +74,10 @@ def parse():
                                          "overlap_update"],
                     help="profiling aid: set up the workload, take one step, then launch only "
                          "this kernel --reps times (no JSON line)")
+    ap.add_argument("--study", choices=["correlation"],
+                    help="correlation: sigma_dE of correlated against independent fields for "
+                         "6..192 walkers per repeat (one JSON line per population, no "
+                         "benchmark line)")
     ap.add_argument("--walkers", type=int, default=None, help="override walkers per system")
     ap.add_argument("--reps", type=int, default=2)
     return ap.parse_args()
@@ -234,6 +238,53 @@ def run_kernel(args, wl):
     torch.cuda.synchronize()
     print(f"{args.kernel}: {ms:.3f} ms per launch ({nw} walkers)")
     A.close()
+
+
+def run_study(args, wl):
+    """Efficiency of correlated sampling (Sec. III): for each population, the pair run with
+    shared fields and again with independent_fields (B keyed by its own seed), each started,
+    run once for --steps blocks to equilibrate and capture its graph, then run and timed for
+    --steps more blocks. Both runs at one population cost the same per step, so the GPU time
+    to reach a given sigma_dE scales with sigma^2 x t. One JSON line per population."""
+    import torch
+    import paper_1703_01545_gb300 as afq
+
+    afq.build()
+    dt, R = wl["dt"], wl["repeats"]
+    n_steps = args.steps * STEPS_PER_BLOCK
+    tau_eq = 0.25 * n_steps * dt
+    prec = {"fp64": afq.FP64, "bf16x3": afq.BF16X3}[args.precision]
+    dA, dB = systems(wl, args.coupling)
+    stream = torch.cuda.current_stream()
+    for per in (6, 12, 24, 48, 96, 192):
+        nw = per * R
+        row = {"study": "correlated_vs_independent", "workload": wl["cfg"],
+               "coupling": args.coupling, "precision": args.precision, "repeats": R,
+               "walkers_per_repeat": per, "walkers_per_system": nw,
+               "propagation_steps": n_steps, "tau_eq": tau_eq}
+        for key, indep in (("correlated", False), ("independent", True)):
+            hs = [afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt,
+                             n_walkers=nw, seed=seed, n_repeats=R, precision=prec,
+                             autotune_cache=args.autotune_cache, independent_fields=indep)
+                  for d, seed in ((dA, 1), (dB, 2 if indep else 1))]
+            afq.pair_delta_E(hs[0], hs[1], n_steps, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
+                             raise_on_dead=False)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            res = afq.pair_delta_E(hs[0], hs[1], n_steps, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
+                                   tau_eq=tau_eq, raise_on_dead=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[key] = {"dE_mean_Ha": res["dE_mean"], "dE_sigma_Ha": res["dE_sigma"],
+                        "ms": e0.elapsed_time(e1), "alive": [h.info().n_alive for h in hs]}
+            for h in hs:
+                h.close()
+        c, i = row["correlated"], row["independent"]
+        row["gpu_time_ratio_at_equal_sigma"] = (
+            (i["dE_sigma_Ha"] ** 2 * i["ms"]) / (c["dE_sigma_Ha"] ** 2 * c["ms"])
+            if c["dE_sigma_Ha"] > 0 else None)
+        print(json.dumps(row), flush=True)
 
 
 def run_ours(args, wl, rank, world, local_rank):
@@ -501,6 +552,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.kernel:
         run_kernel(args, wl)
+    elif args.study:
+        run_study(args, wl)
     elif args.impl == "reference":
         run_reference(args, wl, rank, world)
     else:
