@@ -1,6 +1,7 @@
 // C-ABI entry points: argument checking, device memory, the setup sequence, the
 // per-step kernel schedule, and the CUDA-graph driven correlated pair run.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -419,7 +420,7 @@ afqmc_status afqmc_setup(afqmc_handle* out, const double* h1_in, const double* L
   h->sqrt_dt = std::sqrt(opt->dt);
   cudaGetDevice(&h->device);
   {
-    static uint64_t next_uid = 0;
+    static std::atomic<uint64_t> next_uid{0};
     h->uid = ++next_uid;
   }
   const int64_t NM = (int64_t)N * M, Nw = h->Nw;

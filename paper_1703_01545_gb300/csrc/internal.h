@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units (not part of the ABI).
 #pragma once
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -12,6 +13,28 @@ namespace afq {
 // Packed upper triangle (i <= j) of a symmetric M x M matrix, row-major:
 // idx(i, j) = i*M - i*(i-1)/2 + (j - i).
 inline int64_t packed_size(int M) { return (int64_t)M * (M + 1) / 2; }
+
+// Dynamic shared-memory limits already raised on a group of kernels, kept per device (a
+// function attribute belongs to the device's context) and guarded for setups on several
+// threads.  raise(slot, bytes, set) calls set() when `bytes` is above what the slot allows on
+// the current device; limits only grow, so handles set up earlier keep valid launches.
+struct SmemLimits {
+  static constexpr int kDevices = 64, kSlots = 8;
+  std::mutex mu;
+  size_t have[kDevices][kSlots] = {};
+  template <class Set>
+  cudaError_t raise(int slot, size_t bytes, Set set) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool cached = dev >= 0 && dev < kDevices && slot >= 0 && slot < kSlots;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached && bytes <= have[dev][slot]) return cudaSuccess;
+    e = set();
+    if (e == cudaSuccess && cached) have[dev][slot] = bytes;
+    return e;
+  }
+};
 
 struct Workspace;
 struct TcOperand;

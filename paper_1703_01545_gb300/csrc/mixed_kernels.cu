@@ -256,23 +256,19 @@ size_t smem_energy_f32(const Ctx& c) {
 }
 
 cudaError_t prepare_mixed_kernels(const Ctx& c) {
-  static size_t have_t = 0, have_e = 0;
-  cudaError_t e;
+  static SmemLimits lim;
   const size_t st = smem_taylor_f32(c), se = smem_energy_f32(c);
-  if (st > have_t) {
-    for (auto f : {k_taylor_f32<1>, k_taylor_f32<2>, k_taylor_f32<4>})
-      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st)) !=
-          cudaSuccess)
-        return e;
-    have_t = st;
-  }
-  if (se > have_e) {
-    if ((e = cudaFuncSetAttribute(k_energy_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)se)) != cudaSuccess)
-      return e;
-    have_e = se;
-  }
-  return cudaSuccess;
+  cudaError_t e = lim.raise(0, st, [&] {
+    for (auto f : {k_taylor_f32<1>, k_taylor_f32<2>, k_taylor_f32<4>}) {
+      cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
+  return lim.raise(1, se, [&] {
+    return cudaFuncSetAttribute(k_energy_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
+  });
 }
 
 cudaError_t gemm_f32_from_f64(int Md, int Nd, int Kd, float alpha, const float* A, int64_t lda,
@@ -653,28 +649,25 @@ bool taylor_smem_ok(const Ctx& c) {
 }
 
 cudaError_t prepare_mixed_kernels2(const Ctx& c) {
-  static size_t have_e[3] = {0, 0, 0}, have_t = 0;
+  static SmemLimits lim;
   cudaError_t e;
   const int wbs[3] = {2, 4, 8};
   for (int q = 0; q < 3; ++q) {
     if (!energy_wb_ok(c, wbs[q])) continue;
     const size_t se = smem_energy_tiled(c, energy_gc(c, wbs[q]), wbs[q]);
-    if (se > have_e[q]) {
-      auto f = q == 0 ? k_energy_f32_tiled<2> : q == 1 ? k_energy_f32_tiled<4> : k_energy_f32_tiled<8>;
-      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se)) !=
-          cudaSuccess)
-        return e;
-      have_e[q] = se;
-    }
+    auto f = q == 0 ? k_energy_f32_tiled<2> : q == 1 ? k_energy_f32_tiled<4> : k_energy_f32_tiled<8>;
+    e = lim.raise(q, se, [&] {
+      return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
+    });
+    if (e != cudaSuccess) return e;
   }
   if (taylor_smem_ok(c)) {
     const size_t st = smem_taylor_smem(c);
-    if (st > have_t) {
-      if ((e = cudaFuncSetAttribute(k_taylor_f32_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)st)) != cudaSuccess)
-        return e;
-      have_t = st;
-    }
+    e = lim.raise(3, st, [&] {
+      return cudaFuncSetAttribute(k_taylor_f32_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)st);
+    });
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

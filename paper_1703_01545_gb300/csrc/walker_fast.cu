@@ -630,22 +630,19 @@ bool fast_walker_kernels_ok(const Ctx& c) {
 }
 
 cudaError_t prepare_fast_walker_kernels(const Ctx& c) {
-  static size_t have_o = 0, have_m = 0;
-  cudaError_t e;
-  if (smem_fast_overlap(c) > have_o) {
-    for (auto* f : {k_overlap_fast<4, 8>, k_overlap_fast<4, 16>, k_overlap_fast<8, 16>})
-      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem_fast_overlap(c))) != cudaSuccess)
-        return e;
-    have_o = smem_fast_overlap(c);
-  }
-  if (smem_mgs_warp(c) > have_m) {
-    if ((e = cudaFuncSetAttribute(k_mgs_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_mgs_warp(c))) != cudaSuccess)
-      return e;
-    have_m = smem_mgs_warp(c);
-  }
-  return cudaSuccess;
+  static SmemLimits lim;
+  const size_t so = smem_fast_overlap(c), sm = smem_mgs_warp(c);
+  cudaError_t e = lim.raise(0, so, [&] {
+    for (auto* f : {k_overlap_fast<4, 8>, k_overlap_fast<4, 16>, k_overlap_fast<8, 16>}) {
+      cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)so);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
+  return lim.raise(1, sm, [&] {
+    return cudaFuncSetAttribute(k_mgs_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  });
 }
 
 cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaStream_t s,

@@ -577,14 +577,14 @@ size_t smem_energy(const Ctx& c) {
   return sizeof(double) * (2 * (size_t)c.N * c.M + 2 * (size_t)G_CH * nn + 64);
 }
 
-// Raise a kernel's dynamic shared-memory limit to `bytes` if it is below (process-wide).
+// Raise a kernel's dynamic shared-memory limit on the current device to `bytes` if it is
+// below; `slot` names the kernel in the record of limits already set.
+SmemLimits g_fp64_limits;
 template <class F>
 cudaError_t ensure_smem(F* f, int slot, size_t bytes) {
-  static size_t have[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (bytes <= have[slot]) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) have[slot] = bytes;
-  return e;
+  return g_fp64_limits.raise(slot, bytes, [&] {
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  });
 }
 
 }  // namespace
