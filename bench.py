@@ -292,6 +292,8 @@ def run_ours(args, wl, rank, world, local_rank):
     import torch.distributed as dist
     import paper_1703_01545_gb300 as afq
 
+    from paper_1703_01545_gb300.replicas import walker_offset as replica_offset
+
     torch.cuda.set_device(local_rank)
     if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
@@ -305,7 +307,7 @@ def run_ours(args, wl, rank, world, local_rank):
 
     def make(d, prec, seed=1, independent=False):
         return afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt, n_walkers=nw,
-                          seed=seed, n_repeats=R, walker_offset=rank * nw, precision=prec_id[prec],
+                          seed=seed, n_repeats=R, walker_offset=replica_offset(rank, nw), precision=prec_id[prec],
                           autotune_cache=args.autotune_cache, independent_fields=independent)
 
     def timed(prec, coupling, clocks=None, independent=False):
@@ -340,6 +342,14 @@ def run_ours(args, wl, rank, world, local_rank):
 
     main = timed(args.precision, args.coupling, ClockSampler(torch.cuda.current_device()))
     ms = main["ms"]
+    # Delta E over the repeats of every replica (gathered after the timed region)
+    replicas = None
+    if world > 1:
+        from paper_1703_01545_gb300.replicas import gather_series, merged_delta_E
+        E_all = gather_series(main["res"]["E"])
+        m_, s_, t_ = merged_delta_E(E_all, main["res"]["taus"], tau_eq)
+        replicas = {"dE_mean_Ha": m_, "dE_sigma_Ha": s_, "tau_at_min": t_,
+                    "repeats": int(E_all.shape[2])}
     value = world * nw * n_steps / (ms / 1e3)
 
     # kernels timed alone on this stream with CUDA events: the path's time-dominant kernel
@@ -540,6 +550,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clocks"],
             "gpu_launches": per_block * K, "alive_walkers": main["alive"],
             "sigma_sqrt_t": comp, "correlated_vs_independent": corr, "other_coupling": other,
+            "replicas_dE": replicas,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
