@@ -136,6 +136,18 @@ afqmc_status afqmc_set_walkers(afqmc_handle h, const double* phi, const double* 
                                cudaStream_t stream);
 
 /*
+ * afqmc_set_step -- set the step counter t, the time index of the counter-based field
+ * stream x_{t,k,g} that the next propagation step draws from.  With afqmc_get_state and
+ * afqmc_set_walkers this resumes a run from a checkpoint: the state between steps is
+ * (Phi, w, t) for a given seed and walker offset, so a handle restored at a step right after
+ * an orthonormalisation continues along the same fields as the run that wrote it.  FP64
+ * handles then continue bit for bit, because log O and Theta are recomputed from Phi in both.
+ * Split-precision handles continue within rounding: they lower log O by log det R at
+ * orthonormalisation instead.  Asynchronous on the stream.  Errors: ARG (h NULL), CUDA.
+ */
+afqmc_status afqmc_set_step(afqmc_handle h, uint64_t step, cudaStream_t stream);
+
+/*
  * afqmc_get_state -- copy the population out.  Any output may be NULL.
  *   phi  [2][Nw][M][N]  walker determinants
  *   logO [2][Nw]        log <psi_T|phi_k> (branch of the imaginary part unspecified)

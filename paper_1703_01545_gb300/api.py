@@ -81,6 +81,10 @@ def afqmc_set_walkers(h, phi, w=None, stream=None):
            "afqmc_set_walkers")
 
 
+def afqmc_set_step(h, step, stream=None):
+    _check(_lib.load().afqmc_set_step(h, int(step), _stream(stream)), h, "afqmc_set_step")
+
+
 def afqmc_get_state(h, phi=None, logO=None, w=None, alive=None, stream=None):
     _check(_lib.load().afqmc_get_state(h, _ptr(phi), _ptr(logO), _ptr(w), _ptr(alive),
                                        _stream(stream)), h, "afqmc_get_state")
@@ -260,6 +264,21 @@ class System:
                                              int(energy_every), int(checkpoint), _ptr(e), _ptr(g),
                                              _stream(None)), self.h, "afqmc_adjoint_run")
         return float(e[0]), g
+
+    def checkpoint(self):
+        """Resumable state (walkers, weights, step counter and the run's identity); best
+        taken right after orthonormalise(). checkpoint.save / load write and read it."""
+        from . import checkpoint
+        st = self.state()
+        return checkpoint.make(self, st["phi"], st["w"], self.info().step)
+
+    def resume(self, ck):
+        """Continue from a checkpoint of a run with the same Hamiltonian and options: its
+        walkers and weights, and the step counter of the field stream."""
+        from . import checkpoint
+        checkpoint.check(ck, self)
+        self.set_walkers(ck["phi"], ck["w"])
+        afqmc_set_step(self.h, int(ck["step"]))
 
     def set_walkers(self, phi, w=None):
         phi = np.asarray(phi)

@@ -586,6 +586,13 @@ afqmc_status afqmc_set_walkers(afqmc_handle h, const double* phi, const double* 
   return AFQMC_OK;
 }
 
+afqmc_status afqmc_set_step(afqmc_handle h, uint64_t step, cudaStream_t s) {
+  if (!h) return AFQMC_ERR_ARG;
+  AFQ_CK(afq::set_step(*h, (unsigned long long)step, s));
+  h->step = step;
+  return AFQMC_OK;
+}
+
 afqmc_status afqmc_get_state(afqmc_handle h, double* phi, double* logO, double* w, int* alive,
                              cudaStream_t s) {
   if (!h) return AFQMC_ERR_ARG;
