@@ -1,0 +1,202 @@
+"""Planted mistakes in the oracle, each of which must fail at least one of its pins.
+
+Every mutant below is a plausible slip in writing the method down: a sign, a dropped term
+or factor, a transposed operand, a conjugation the paper does not have, an off-by-one
+order, a stale quantity after orthonormalisation. The mutant replaces one oracle function
+(module attribute, so the oracle's internal calls see it too), then the pins of
+test_oracle_pins.py and test_oracle_rng.py run cheapest first until one fails. The control
+case (no mutant) must pass them all, so the failures come from the mutants.
+"""
+import numpy as np
+import pytest
+
+import test_oracle_pins as P
+import test_oracle_rng as RNG
+from oracle import afqmc, philox
+
+ORIG = {n: getattr(afqmc, n) for n in ("force_bias", "green", "local_energy", "taylor_apply",
+                                       "step_determinant", "orthonormalise", "propagate",
+                                       "overlap", "modified_gram_schmidt")}
+ORIG_INIT = afqmc.System.__init__
+ORIG_BOX_MULLER = philox.box_muller
+
+PINS = [
+    ("overlap vs determinant expansion", lambda: P.test_overlap_is_many_body_overlap(2, 1)),
+    ("G as log-overlap derivative", lambda: P.test_green_function_is_log_overlap_derivative(2, 1)),
+    ("G invariants", P.test_green_function_invariants),
+    ("rhobar as log-overlap derivative", P.test_force_bias_is_log_overlap_derivative),
+    ("E_L vs FCI mixed estimate", lambda: P.test_local_energy_is_mixed_estimate_in_fci_space(2, 1)),
+    ("E_T vs HF", lambda: P.test_trial_energy_is_hartree_fock_energy(2, 1)),
+    ("one electron", P.test_one_electron_has_no_two_body_energy),
+    ("Taylor bound", P.test_taylor_error_bound),
+    ("MGS", lambda: P.test_modified_gram_schmidt(2, 2)),
+    ("Eq. 8 stationarity", P.test_force_bias_is_stationary_point_of_weight),
+    # after stationarity: its check of the capped values recomputes the uncapped bias itself
+    ("force-bias cap", P.test_force_bias_cap),
+    ("non-interacting closed form", P.test_non_interacting_limit_is_deterministic_closed_form),
+    ("normal moments", RNG.test_normal_moments),
+    ("quadrature, no shift", lambda: P.test_hs_propagator_and_force_bias_by_quadrature(0.0)),
+    ("quadrature, complex shift",
+     lambda: P.test_hs_propagator_and_force_bias_by_quadrature(0.4 - 0.7j)),
+    ("walker death", P.test_walker_death_is_permanent_and_freezes_determinant),
+]
+
+
+def _reinit(after):
+    """System.__init__ followed by `after(self)` (a slip in the derived one-body data)."""
+    def init(self, *a, **kw):
+        ORIG_INIT(self, *a, **kw)
+        after(self)
+    return init
+
+
+def _half_step(s, K):
+    lam, U = np.linalg.eigh(K)
+    return (U * np.exp(-0.5 * s.dt * lam)) @ U.T
+
+
+def _k_without_LL(s):
+    s.K = s.K + 0.5 * np.einsum("gik,gkj->ij", s.L, s.L)
+    s.expK = _half_step(s, s.K)
+
+
+def _k_mean_field_sign(s):
+    s.K = s.K - 2 * np.einsum("g,gij->ij", s.rho_mf, s.L)
+    s.expK = _half_step(s, s.K)
+
+
+def _full_step(s):
+    lam, U = np.linalg.eigh(s.K)
+    s.expK = (U * np.exp(-s.dt * lam)) @ U.T
+
+
+def _fb_no_mean_field(sys, G):
+    saved = sys.rho_mf
+    sys.rho_mf = np.zeros_like(saved)
+    try:
+        return ORIG["force_bias"](sys, G)
+    finally:
+        sys.rho_mf = saved
+
+
+def _fb_cap_componentwise(sys, G):
+    cap = sys.fb_cap
+    raw = -1j * sys.sqrt_dt * (afqmc.rhobar(sys, G) - sys.rho_mf[None, :])
+    if cap <= 0:
+        return raw
+    return np.clip(raw.real, -cap, cap) + 1j * np.clip(raw.imag, -cap, cap)
+
+
+def _parts(sys, phi):
+    G = afqmc.green(sys, phi)
+    e1 = sum(np.einsum("ij,wji->w", sys.h1, Gs) for Gs in G)
+    rb = afqmc.rhobar(sys, G)
+    return e1, 0.5 * np.sum(rb * rb, axis=1)
+
+
+def _eloc_no_half(sys, phi, chunk=0):
+    e = ORIG["local_energy"](sys, phi, chunk)
+    e1, _ = _parts(sys, phi)
+    return e1 + 2 * (e - e1)
+
+
+def _eloc_no_exchange(sys, phi, chunk=0):
+    e1, coul = _parts(sys, phi)
+    return e1 + coul
+
+
+def _eloc_exchange_sign(sys, phi, chunk=0):
+    e = ORIG["local_energy"](sys, phi, chunk)
+    e1, coul = _parts(sys, phi)
+    return e1 + coul + (e1 + coul - e)
+
+
+def _step_variant(kind):
+    def step(sys, phi, logO, x, xbar):
+        phi3, logO3, logR, logI = ORIG["step_determinant"](sys, phi, logO, x, xbar)
+        if kind == "conjugated xbar^2":
+            logI = logI + 0.5 * np.sum(xbar * xbar, axis=1) - 0.5 * np.sum(np.abs(xbar) ** 2, axis=1)
+        elif kind == "x.xbar sign":
+            logI = logI - 2 * np.sum(x * xbar, axis=1)
+        elif kind == "mean-field scalar dropped":
+            log_s = -1j * sys.sqrt_dt * ((x - xbar) @ sys.rho_mf)
+            logR, logI = logR - log_s, logI - log_s
+        elif kind == "energy shift sign":
+            logI = logI + 2 * sys.dt * (sys.C - sys.E_T)
+        return phi3, logO3, logR, logI
+    return step
+
+
+def _propagate_no_cos(sys, wk, x):
+    """The phaseless update without the max(0, cos dtheta) factor."""
+    if sys.mode != afqmc.PHASELESS:
+        return ORIG["propagate"](sys, wk, x)
+    live = wk.alive
+    if not np.any(live):
+        return
+    phi = wk.phi[live]
+    xs = np.asarray(x, dtype=np.float64)[live]
+    xbar = afqmc.force_bias(sys, afqmc.green(sys, phi))
+    phi3, logO_new, logR, logI = afqmc.step_determinant(sys, phi, wk.logO[live], xs, xbar)
+    idx = np.nonzero(live)[0]
+    wk.phi[idx] = phi3
+    wk.logO[idx] = logO_new
+    wk.w[idx] = (wk.w[live].real * np.exp(logI.real)).astype(np.complex128)
+
+
+def _ortho_stale_logO(sys, wk):
+    saved = wk.logO.copy()
+    ORIG["orthonormalise"](sys, wk)
+    wk.logO[:] = saved
+
+
+MUTANTS = {
+    "force bias sign": ("force_bias", lambda s, G: -ORIG["force_bias"](s, G)),
+    "force bias without <rho>_T": ("force_bias", _fb_no_mean_field),
+    "force bias without i": ("force_bias", lambda s, G: -1j * ORIG["force_bias"](s, G)),
+    "cap per component": ("force_bias", _fb_cap_componentwise),
+    "G transposed": ("green", lambda s, phi: [np.swapaxes(g, 1, 2) for g in ORIG["green"](s, phi)]),
+    "overlap of conj(Phi)": ("overlap", lambda s, phi: ORIG["overlap"](s, np.conj(phi))),
+    "E_L without 1/2": ("local_energy", _eloc_no_half),
+    "E_L without exchange": ("local_energy", _eloc_no_exchange),
+    "E_L exchange sign": ("local_energy", _eloc_exchange_sign),
+    "Taylor one order short": ("taylor_apply", lambda A, phi, n: ORIG["taylor_apply"](A, phi, n - 1)),
+    "xbar^2 conjugated": ("step_determinant", _step_variant("conjugated xbar^2")),
+    "x.xbar sign": ("step_determinant", _step_variant("x.xbar sign")),
+    "mean-field scalar dropped": ("step_determinant", _step_variant("mean-field scalar dropped")),
+    "energy shift sign": ("step_determinant", _step_variant("energy shift sign")),
+    "phaseless cos factor dropped": ("propagate", _propagate_no_cos),
+    "log O stale after MGS": ("orthonormalise", _ortho_stale_logO),
+    "MGS not normalised": ("modified_gram_schmidt", lambda q: 2.0 * ORIG["modified_gram_schmidt"](q)),
+    "K without -1/2 sum L L": ("__init__", _reinit(_k_without_LL)),
+    "K mean-field sign": ("__init__", _reinit(_k_mean_field_sign)),
+    "C sign": ("__init__", _reinit(lambda s: setattr(s, "C", -s.C))),
+    "full one-body step on each side": ("__init__", _reinit(_full_step)),
+    "Box-Muller radius without 2": ("box_muller",
+                                    lambda u1, u2: tuple(z / np.sqrt(2) for z in ORIG_BOX_MULLER(u1, u2))),
+}
+
+
+def first_failing_pin():
+    for name, pin in PINS:
+        try:
+            pin()
+        except Exception:   # an assertion, or a pin that cannot even run on the mutant
+            return name
+    return None
+
+
+def test_control_passes_every_pin():
+    assert first_failing_pin() is None
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(monkeypatch, mutant):
+    target, fn = MUTANTS[mutant]
+    if target == "__init__":
+        monkeypatch.setattr(afqmc.System, "__init__", fn)
+    elif target == "box_muller":
+        monkeypatch.setattr(philox, "box_muller", fn)
+    else:
+        monkeypatch.setattr(afqmc, target, fn)
+    assert first_failing_pin() is not None, f"no pin catches: {mutant}"
