@@ -8,16 +8,14 @@ tangent mode (itself pinned by central differences of whole runs), and one entry
 central difference. The unmutated source must pass them all. Slips that change only the
 antisymmetric part of dE/dh1 are not listed: h1 is symmetric, so no measurement sees them.
 """
-import importlib.util
-import os
 import types
 
 import pytest
 
 import test_oracle_adjoint as PA
-import oracle
+from mutation_util import compile_variant, mutate, oracle_source
 
-SRC = open(os.path.join(os.path.dirname(oracle.__file__), "adjoint.py")).read()
+SRC = oracle_source("adjoint.py")
 
 MUTANTS = {
     "cos-cut term sign": ("Rbar = lb * (1.0 - 1j * np.tan(th))",
@@ -49,15 +47,6 @@ PINS = [
 ]
 
 
-def compile_variant(src, tag):
-    name = f"oracle._adjoint_{tag}"
-    spec = importlib.util.spec_from_loader(name, loader=None)
-    mod = importlib.util.module_from_spec(spec)
-    mod.__package__ = "oracle"
-    exec(compile(src, f"<adjoint {tag}>", "exec"), mod.__dict__)
-    return mod
-
-
 def first_failing_pin(monkeypatch, mod: types.ModuleType):
     monkeypatch.setattr(PA, "adjoint", mod)
     for name, pin in PINS:
@@ -69,12 +58,11 @@ def first_failing_pin(monkeypatch, mod: types.ModuleType):
 
 
 def test_unmutated_source_passes_every_pin(monkeypatch):
-    assert first_failing_pin(monkeypatch, compile_variant(SRC, "control")) is None
+    assert first_failing_pin(monkeypatch, compile_variant(SRC, "adjoint_control")) is None
 
 
 @pytest.mark.parametrize("mutant", sorted(MUTANTS))
 def test_planted_mistake_fails_a_pin(monkeypatch, mutant):
     old, new = MUTANTS[mutant]
-    assert SRC.count(old) == 1, f"mutation site not found once: {old}"
-    mod = compile_variant(SRC.replace(old, new), "mutant")
+    mod = mutate(SRC, old, new, "adjoint_mutant")
     assert first_failing_pin(monkeypatch, mod) is not None, f"no pin catches: {mutant}"
