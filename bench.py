@@ -19,6 +19,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -177,18 +178,38 @@ def blas_threads():
     return os.cpu_count()
 
 
+def device_code_sha256(text):
+    """sha256 of a CUDA source's __global__ and __device__ functions (from the start of the
+    declaring line to the closing brace of the body), so that host-side edits in the same file
+    leave the recorded traffic of unchanged kernels valid."""
+    parts = []
+    for m in re.finditer(r"__(?:global|device)__", text):
+        brace, semi = text.find("{", m.end()), text.find(";", m.end())
+        if brace < 0 or 0 <= semi < brace:
+            continue    # a declaration or a __device__ variable
+        depth, i = 0, brace
+        while i < len(text):
+            depth += {"{": 1, "}": -1}.get(text[i], 0)
+            if depth == 0:
+                break
+            i += 1
+        parts.append(text[text.rfind("\n", 0, m.start()) + 1:i + 1])
+    return hashlib.sha256("\n".join(parts).encode()).hexdigest()
+
+
 def traffic_for(kernel_file, name):
-    """dram bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    """dram bytes per launch from the committed ncu summary, if the kernel is unchanged: the
+    file's device code hashes as it did when the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
         data = json.load(open(path))
         ent = data[name]
-        src = open(os.path.join(ROOT, "paper_1703_01545_gb300", "csrc", kernel_file), "rb").read()
-        if ent.get("source_sha256") != hashlib.sha256(src).hexdigest():
-            return None
-        return ent
+        src = open(os.path.join(ROOT, "paper_1703_01545_gb300", "csrc", kernel_file)).read()
+        if "device_sha256" in ent:
+            return ent if ent["device_sha256"] == device_code_sha256(src) else None
+        return ent if ent.get("source_sha256") == hashlib.sha256(src.encode()).hexdigest() else None
     except Exception:
         return None
 

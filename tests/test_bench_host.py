@@ -1,0 +1,36 @@
+"""Host logic of bench.py that needs no GPU: the device-code hash that decides whether a
+recorded ncu traffic figure still belongs to the kernel being timed."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+SRC = """
+#include <cuda_runtime.h>
+__device__ __align__(16) double g_table[4];
+static __device__ __forceinline__ float twice(float x) { return 2.0f * x; }
+__global__ void k_scale(float* y, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { y[i] = twice(y[i]); }
+}
+cudaError_t launch_scale(float* y, int n, cudaStream_t s) {
+  k_scale<<<(n + 255) / 256, 256, 0, s>>>(y, n);
+  return cudaGetLastError();
+}
+"""
+
+
+def test_host_edits_keep_the_device_hash():
+    h = bench.device_code_sha256(SRC)
+    host = SRC.replace("(n + 255) / 256, 256", "(n + 127) / 128, 128")
+    assert host != SRC and bench.device_code_sha256(host) == h
+
+
+def test_kernel_and_device_helper_edits_change_it():
+    h = bench.device_code_sha256(SRC)
+    for old, new in (("if (i < n)", "if (i <= n)"), ("2.0f * x", "3.0f * x")):
+        edited = SRC.replace(old, new)
+        assert edited != SRC and bench.device_code_sha256(edited) != h
