@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
     ap.add_argument("--coupling", default="moderate", choices=["literal", "moderate"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3"])
+    ap.add_argument("--mode", default="phaseless", choices=["phaseless", "free"],
+                    help="free: correlated free projection (x_bar = 0, complex weights)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune-cache", default=None,
                     help="kernel-variant cache file: read if present, else written after tuning "
@@ -280,13 +282,15 @@ def run_study(args, wl):
     for per in (6, 12, 24, 48, 96, 192):
         nw = per * R
         row = {"study": "correlated_vs_independent", "workload": wl["cfg"],
-               "coupling": args.coupling, "precision": args.precision, "repeats": R,
+               "coupling": args.coupling, "precision": args.precision, "mode": args.mode,
+               "repeats": R,
                "walkers_per_repeat": per, "walkers_per_system": nw,
                "propagation_steps": n_steps, "tau_eq": tau_eq}
         for key, indep in (("correlated", False), ("independent", True)):
             hs = [afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt,
                              n_walkers=nw, seed=seed, n_repeats=R, precision=prec,
-                             autotune_cache=args.autotune_cache, independent_fields=indep)
+                             autotune_cache=args.autotune_cache, independent_fields=indep,
+                             mode=afq.FREE if args.mode == "free" else afq.PHASELESS)
                   for d, seed in ((dA, 1), (dB, 2 if indep else 1))]
             afq.pair_delta_E(hs[0], hs[1], n_steps, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
                              raise_on_dead=False)
@@ -329,7 +333,8 @@ def run_ours(args, wl, rank, world, local_rank):
     def make(d, prec, seed=1, independent=False):
         return afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt, n_walkers=nw,
                           seed=seed, n_repeats=R, walker_offset=replica_offset(rank, nw), precision=prec_id[prec],
-                          autotune_cache=args.autotune_cache, independent_fields=independent)
+                          autotune_cache=args.autotune_cache, independent_fields=independent,
+                          mode=afq.FREE if args.mode == "free" else afq.PHASELESS)
 
     def timed(prec, coupling, clocks=None, independent=False):
         """Pair run; independent=True gives B its own field key (uncorrelated sampling)."""
@@ -565,6 +570,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "dtype": "f64" if args.precision == "fp64" else "bf16x3+f32 (f64 determinants/weights/MGS)",
             "data": "synthetic",
             "config": {"workload": wl["desc"], "coupling": args.coupling, "precision": args.precision,
+                       "mode": args.mode,
                        "step": "one measurement block (5 propagation steps + MGS + energy) of both systems",
                        "l2": "inputs larger than L2 (per-step working set ~0.5 GB)",
                        "parallelism": f"replicas x{world}"},
