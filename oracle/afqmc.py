@@ -266,11 +266,15 @@ def mixed_energy(sys: System, w, eloc, groups, n_repeats):
 
 def run_pair(sysA: System, sysB: System, n_walkers: int, n_steps: int, seed: int,
              energy_every: int = 5, mgs_every: int = 5, n_repeats: int = 1,
-             walker_index=None, fields=None, record_walkers=False, seed_B=None):
+             walker_index=None, fields=None, record_walkers=False, seed_B=None,
+             walkers=None, t0: int = 0):
     """Correlated pair run (Sec. II.B): walker k of A and walker k of B share x_{t,k,g}.
 
     ``seed_B`` (optional) gives B its own key instead: the two systems then draw
     independent fields, the uncorrelated sampling that Sec. III compares against.
+    ``walkers`` (optional) continues given populations, one per system, instead of starting
+    from the trials, and ``t0`` is the step index of the first field drawn (the fields of
+    step t0 + t; the Gram-Schmidt and measurement schedule counts from the start of the call).
 
     ``walker_index`` (default 0..Nw-1) gives the global pair index k of every walker
     propagated here, so a subset of a large population can be followed exactly.
@@ -286,13 +290,14 @@ def run_pair(sysA: System, sysB: System, n_walkers: int, n_steps: int, seed: int
     k = np.arange(n_walkers) if walker_index is None else np.asarray(walker_index)
     groups = repeat_groups(n_walkers, n_repeats)[k] if walker_index is None else \
         (k * n_repeats) // n_walkers
-    wks = [Walkers(s, k.size) for s in systems]
+    wks = [Walkers(s, k.size) for s in systems] if walkers is None else \
+        [w for w in walkers if w is not None]
     out = dict(steps=[], E=[[] for _ in systems], W=[[] for _ in systems],
                records=[[] for _ in systems])
     for t in range(n_steps):
         for s, wk, sd in zip(systems, wks, seeds):
             if fields is None:
-                x = gaussian_fields(sd, t, k, s.X)
+                x = gaussian_fields(sd, t0 + t, k, s.X)
             else:
                 x = fields[t][:, :s.X]
             propagate(s, wk, x)

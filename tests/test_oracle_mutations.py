@@ -10,14 +10,16 @@ case (no mutant) must pass them all, so the failures come from the mutants.
 import numpy as np
 import pytest
 
+import test_oracle_pes as PES
 import test_oracle_pins as P
 import test_oracle_rng as RNG
-from oracle import afqmc, philox
+from oracle import afqmc, pes, philox
 
 ORIG = {n: getattr(afqmc, n) for n in ("force_bias", "green", "local_energy", "taylor_apply",
                                        "step_determinant", "orthonormalise", "propagate",
                                        "overlap", "modified_gram_schmidt")}
 ORIG_INIT = afqmc.System.__init__
+ORIG_PES = {n: getattr(pes, n) for n in ("comb_select", "seed_secondary", "seed_columns")}
 ORIG_BOX_MULLER = philox.box_muller
 
 PINS = [
@@ -39,6 +41,12 @@ PINS = [
     ("quadrature, complex shift",
      lambda: P.test_hs_propagator_and_force_bias_by_quadrature(0.4 - 0.7j)),
     ("walker death", P.test_walker_death_is_permanent_and_freezes_determinant),
+    ("comb weight and dead walkers", PES.test_comb_keeps_the_total_weight_and_skips_dead_walkers),
+    ("comb expected copies", PES.test_comb_expected_copies_are_the_weight_shares),
+    ("comb within repeats", PES.test_population_control_stays_within_each_repeat),
+    ("seeding keeps the state", lambda: PES.test_seeding_keeps_the_represented_state(2)),
+    ("seeding an ion", lambda: PES.test_seeding_keeps_the_represented_state(1)),
+    ("seeding phase projection", PES.test_seeding_projects_the_phase_of_the_ratio),
 ]
 
 
@@ -144,6 +152,37 @@ def _propagate_no_cos(sys, wk, x):
     wk.w[idx] = (wk.w[live].real * np.exp(logI.real)).astype(np.complex128)
 
 
+def _comb_left(w, n_out, u):
+    """The comb taking the first walker whose running sum reaches the point (side='left'):
+    a dead walker sitting on a boundary can be chosen."""
+    w = np.asarray(w, dtype=np.float64)
+    W = float(w.sum())
+    points = (np.arange(n_out) + float(u)) * (W / n_out)
+    return np.minimum(np.searchsorted(np.cumsum(w), points, side="left"), w.size - 1), W / n_out
+
+
+def _seed_variant(kind):
+    def seed(sA, sB, wkA):
+        if kind == "inverted ratio":
+            phi = wkA.phi[:, :, pes.seed_columns(sA, sB)]
+            logR = wkA.logO - afqmc.overlap(sB, phi)
+            w = wkA.w.real * np.exp(logR.real) * np.maximum(0.0, np.cos(logR.imag))
+            return afqmc.Walkers(sB, phi.shape[0], phi=phi, w=np.where(wkA.alive, w, 0.0) + 0j)
+        wkB = ORIG_PES["seed_secondary"](sA, sB, wkA)
+        if kind == "phase not projected":
+            phi = wkB.phi
+            logR = afqmc.overlap(sB, phi) - wkA.logO
+            w = wkA.w.real * np.exp(logR.real)
+            return afqmc.Walkers(sB, phi.shape[0], phi=phi, w=w + 0j)
+        return wkB
+    return seed
+
+
+def _last_columns(sA, sB):
+    return (list(range(sA.n_up - sB.n_up, sA.n_up)) +
+            list(range(sA.N - sB.n_dn, sA.N)))
+
+
 def _ortho_stale_logO(sys, wk):
     saved = wk.logO.copy()
     ORIG["orthonormalise"](sys, wk)
@@ -172,6 +211,10 @@ MUTANTS = {
     "K mean-field sign": ("__init__", _reinit(_k_mean_field_sign)),
     "C sign": ("__init__", _reinit(lambda s: setattr(s, "C", -s.C))),
     "full one-body step on each side": ("__init__", _reinit(_full_step)),
+    "comb picks on the left of a point": ("pes.comb_select", _comb_left),
+    "seeding ratio inverted": ("pes.seed_secondary", _seed_variant("inverted ratio")),
+    "seeding phase not projected": ("pes.seed_secondary", _seed_variant("phase not projected")),
+    "seeding keeps the last columns": ("pes.seed_columns", _last_columns),
     "Box-Muller radius without 2": ("box_muller",
                                     lambda u1, u2: tuple(z / np.sqrt(2) for z in ORIG_BOX_MULLER(u1, u2))),
 }
@@ -197,6 +240,8 @@ def test_planted_mistake_fails_a_pin(monkeypatch, mutant):
         monkeypatch.setattr(afqmc.System, "__init__", fn)
     elif target == "box_muller":
         monkeypatch.setattr(philox, "box_muller", fn)
+    elif target.startswith("pes."):
+        monkeypatch.setattr(pes, target[4:], fn)
     else:
         monkeypatch.setattr(afqmc, target, fn)
     assert first_failing_pin() is not None, f"no pin catches: {mutant}"
