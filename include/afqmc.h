@@ -136,8 +136,9 @@ afqmc_status afqmc_set_walkers(afqmc_handle h, const double* phi, const double* 
                                cudaStream_t stream);
 
 /*
- * afqmc_set_step -- set the step counter t, the time index of the counter-based field
- * stream x_{t,k,g} that the next propagation step draws from.  With afqmc_get_state and
+ * afqmc_set_step -- checkpoint/resume, no counterpart in the paper.  Sets the step counter
+ * t, the time index of the counter-based field stream x_{t,k,g} that the next propagation
+ * step draws from.  With afqmc_get_state and
  * afqmc_set_walkers this resumes a run from a checkpoint: the state between steps is
  * (Phi, w, t) for a given seed and walker offset, so a handle restored at a step right after
  * an orthonormalisation continues along the same fields as the run that wrote it.  FP64
