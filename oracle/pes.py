@@ -12,7 +12,7 @@ difference is measured.
 Readings (the paper names the steps, not their details):
 * Population control is the comb. Within each repeat, the n walkers of total weight W are
   replaced by the n walkers found at the points (j + u) W / n, j = 0 .. n-1, of the running
-  sum of the weights, with one uniform u per repeat. Every copy carries weight W / n. A dead
+  sum of the weights (summed left to right, W its last value), with one uniform u per repeat. Every copy carries weight W / n. A dead
   walker (w = 0) is never chosen. The paper says only that walkers of large weight are
   replicated and walkers of small weight removed.
 * "Phases projected" is the phaseless projection of the ratio R: w_B = w_A |R| max(0, cos arg R).
@@ -33,10 +33,10 @@ def comb_select(w, n_out, u):
     w = np.asarray(w, dtype=np.float64)
     if np.any(w < 0):
         raise ValueError("comb weights must be >= 0")
-    W = float(w.sum())
+    cum = np.cumsum(w)                 # left to right; W is its last value, so the total and
+    W = float(cum[-1]) if w.size else 0.0   # the running sums share one rounding order
     if not W > 0:
         raise ValueError("no weight to comb")
-    cum = np.cumsum(w)
     points = (np.arange(n_out) + float(u)) * (W / n_out)
     # first walker whose running sum exceeds the point: zero weights are stepped over
     idx = np.searchsorted(cum, points, side="right")
