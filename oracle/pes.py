@@ -12,9 +12,9 @@ difference is measured.
 Readings (the paper names the steps, not their details):
 * Population control is the comb. Within each repeat, the n walkers of total weight W are
   replaced by the n walkers found at the points (j + u) W / n, j = 0 .. n-1, of the running
-  sum of the weights (summed left to right, W its last value), with one uniform u per repeat. Every copy carries weight W / n. A dead
-  walker (w = 0) is never chosen. The paper says only that walkers of large weight are
-  replicated and walkers of small weight removed.
+  sum of the weights (summed left to right, W its last value), with one uniform u per
+  repeat. Every copy carries weight W / n. A dead walker (w = 0) is never chosen. The paper
+  says only that walkers of large weight are replicated and walkers of small weight removed.
 * "Phases projected" is the phaseless projection of the ratio R: w_B = w_A |R| max(0, cos arg R).
 * When B has fewer electrons of a spin (an ion seeded from the neutral), its walker keeps the
   first N_s^B columns of that spin block. These are the propagated images of the trial's
