@@ -149,6 +149,33 @@ afqmc_status afqmc_set_walkers(afqmc_handle h, const double* phi, const double* 
 afqmc_status afqmc_set_step(afqmc_handle h, uint64_t step, cudaStream_t stream);
 
 /*
+ * afqmc_population_control -- population control of the preliminary equilibration scheme
+ * (Sec. II.C), applied to the primary system while it equilibrates alone.  It is the comb:
+ * within each repeat r, the n walkers' weights are summed left to right (a dead walker counts
+ * 0; W is the last running sum), and walker j of the repeat becomes a copy of the first walker
+ * whose running sum exceeds (j + u[r]) W / n.  Every copy has weight W / n and is alive; the
+ * copies' Theta and log O are recomputed from Phi.
+ *   u [R] uniforms in [0, 1), host or device, drawn by the caller.
+ * Phaseless handles only (ARG otherwise).  Synchronises the stream.  Errors: ARG, STATE
+ * (tangent mode), NUMERIC (a repeat with no live walker; the walkers are left unchanged), CUDA.
+ */
+afqmc_status afqmc_population_control(afqmc_handle h, const double* u, cudaStream_t stream);
+
+/*
+ * afqmc_seed_secondary -- second stage of the preliminary equilibration scheme (Sec. II.C):
+ * the secondary system B starts from the equilibrated walkers of the primary A.  Walker k of
+ * B takes the first N_up^B columns of walker k's spin-up block and the first N_dn^B columns
+ * of its spin-down block (an ion seeded from the neutral loses the last occupied trial
+ * orbital of a spin).  Its weight is w_A |R| max(0, cos arg R), R = <psi_T^B|phi_B> /
+ * <psi_T^A|phi_A>: the ratio rescales the importance sampling to B's trial, with the phase
+ * projected as in the phaseless step.  B's step counter is set to A's, so
+ * afqmc_pair_delta_E(A, B, ...) continues both on the shared fields.
+ * Requirements: same M, walkers and repeats, N_s^B <= N_s^A, phaseless handles.
+ * Asynchronous on the stream.  Errors: ARG, STATE (tangent mode), CUDA.
+ */
+afqmc_status afqmc_seed_secondary(afqmc_handle B, afqmc_handle A, cudaStream_t stream);
+
+/*
  * afqmc_get_state -- copy the population out.  Any output may be NULL.
  *   phi  [2][Nw][M][N]  walker determinants
  *   logO [2][Nw]        log <psi_T|phi_k> (branch of the imaginary part unspecified)

@@ -42,6 +42,8 @@ SIGNATURES = {
     "afqmc_set_walkers": (ctypes.c_int, [VP, VP, VP, VP]),
     "afqmc_get_state": (ctypes.c_int, [VP, VP, VP, VP, VP, VP]),
     "afqmc_set_step": (ctypes.c_int, [VP, ctypes.c_uint64, VP]),
+    "afqmc_population_control": (ctypes.c_int, [VP, VP, VP]),
+    "afqmc_seed_secondary": (ctypes.c_int, [VP, VP, VP]),
     "afqmc_get_info": (ctypes.c_int, [VP, ctypes.POINTER(AfqmcInfo), VP]),
     "afqmc_propagate": (ctypes.c_int, [VP, ctypes.c_int, VP, VP]),
     "afqmc_orthonormalise": (ctypes.c_int, [VP, VP]),

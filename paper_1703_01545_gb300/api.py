@@ -85,6 +85,16 @@ def afqmc_set_step(h, step, stream=None):
     _check(_lib.load().afqmc_set_step(h, int(step), _stream(stream)), h, "afqmc_set_step")
 
 
+def afqmc_population_control(h, u, stream=None):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    _check(_lib.load().afqmc_population_control(h, _ptr(u), _stream(stream)), h,
+           "afqmc_population_control")
+
+
+def afqmc_seed_secondary(B, A, stream=None):
+    _check(_lib.load().afqmc_seed_secondary(B, A, _stream(stream)), B, "afqmc_seed_secondary")
+
+
 def afqmc_get_state(h, phi=None, logO=None, w=None, alive=None, stream=None):
     _check(_lib.load().afqmc_get_state(h, _ptr(phi), _ptr(logO), _ptr(w), _ptr(alive),
                                        _stream(stream)), h, "afqmc_get_state")
@@ -264,6 +274,18 @@ class System:
                                              int(energy_every), int(checkpoint), _ptr(e), _ptr(g),
                                              _stream(None)), self.h, "afqmc_adjoint_run")
         return float(e[0]), g
+
+    def population_control(self, u):
+        """Comb each repeat's walkers (Sec. II.C); u [n_repeats] uniforms in [0, 1)."""
+        u = np.asarray(u, dtype=np.float64)
+        if u.shape != (self.n_repeats,):
+            raise ValueError(f"need one uniform per repeat ({self.n_repeats})")
+        afqmc_population_control(self.h, u)
+
+    def seed_from(self, primary):
+        """Start this (secondary) system from the walkers of an equilibrated primary system
+        (Sec. II.C), weights rescaled to this system's trial; the step counter follows."""
+        afqmc_seed_secondary(self.h, primary.h)
 
     def checkpoint(self):
         """Resumable state (walkers, weights, step counter and the run's identity); best

@@ -593,6 +593,50 @@ afqmc_status afqmc_set_step(afqmc_handle h, uint64_t step, cudaStream_t s) {
   return AFQMC_OK;
 }
 
+afqmc_status afqmc_population_control(afqmc_handle h, const double* u, cudaStream_t s) {
+  if (!h) return AFQMC_ERR_ARG;
+  if (!u) return set_err(h, AFQMC_ERR_ARG, "u is NULL");
+  if (h->opt.mode != AFQMC_PHASELESS)
+    return set_err(h, AFQMC_ERR_ARG, "population control needs real (phaseless) weights");
+  if (h->tangent_on) return set_err(h, AFQMC_ERR_STATE, "tangent mode is on");
+  const int R = h->R;
+  // between steps phi2, aux and esum are free scratch: the running sums, the comb's picks and
+  // (u, W / n) per repeat
+  double* u_dev = h->esum;
+  double* share = h->esum + R;
+  int* src = reinterpret_cast<int*>(h->aux);
+  AFQ_CK(cudaMemcpyAsync(u_dev, u, sizeof(double) * R, cudaMemcpyDefault, s));
+  AFQ_CK(afq::launch_comb(*h, u_dev, h->phi2, src, share, s));
+  std::vector<double> q(R);
+  AFQ_CK(cudaMemcpyAsync(q.data(), share, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+  AFQ_CK(cudaStreamSynchronize(s));
+  for (double v : q)
+    if (!(v > 0.0) || !std::isfinite(v))
+      return set_err(h, AFQMC_ERR_NUMERIC, "a repeat has no live walker to comb");
+  AFQ_CK(afq::launch_apply_comb(*h, src, share, h->theta, s));
+  return overlap_launch(h, nullptr, afq::OV_REFRESH, s);
+}
+
+afqmc_status afqmc_seed_secondary(afqmc_handle B, afqmc_handle A, cudaStream_t s) {
+  if (!A || !B || A == B) return AFQMC_ERR_ARG;
+  if (B->M != A->M || B->Nw != A->Nw || B->R != A->R || B->n_up > A->n_up || B->n_dn > A->n_dn)
+    return set_err(B, AFQMC_ERR_ARG,
+                   "the secondary system needs the primary's basis size, walkers and repeats, "
+                   "and no more electrons of either spin");
+  if (A->opt.mode != AFQMC_PHASELESS || B->opt.mode != AFQMC_PHASELESS)
+    return set_err(B, AFQMC_ERR_ARG, "seeding projects phases: phaseless handles only");
+  if (A->tangent_on || B->tangent_on) return set_err(B, AFQMC_ERR_STATE, "tangent mode is on");
+  afqmc_ctx* h = B;   // the error helpers below report on B
+  AFQ_CK(afq::launch_seed_columns(*A, *B, s));
+  AFQ_CK(afq::launch_init_weights(B->w, B->alive, nullptr, B->Nw, s));
+  afqmc_status rs = overlap_launch(B, nullptr, afq::OV_REFRESH, s);
+  if (rs != AFQMC_OK) return rs;
+  AFQ_CK(afq::launch_seed_weights(*A, *B, s));
+  AFQ_CK(afq::set_step(*B, (unsigned long long)A->step, s));
+  B->step = A->step;
+  return AFQMC_OK;
+}
+
 afqmc_status afqmc_get_state(afqmc_handle h, double* phi, double* logO, double* w, int* alive,
                              cudaStream_t s) {
   if (!h) return AFQMC_ERR_ARG;

@@ -246,6 +246,15 @@ cudaError_t place_block(double* Z, int ldz, int r0, int c0, const double* src, i
 cudaError_t take_block(const double* Z, int ldz, int r0, int c0, double* dst, int M, double alpha,
                        cudaStream_t s);
 cudaError_t set_step(const Ctx& c, unsigned long long v, cudaStream_t s);
+// preliminary equilibration scheme (pes.cu): comb per repeat into src / share (cum: Nw
+// doubles of scratch), then gather the walkers through `scratch` ([2][Nw][N][M]) and set the
+// combed weights; seeding of B's walkers and weights from A's
+cudaError_t launch_comb(const Ctx& c, const double* u_dev, double* cum, int* src, double* share,
+                        cudaStream_t s);
+cudaError_t launch_apply_comb(const Ctx& c, const int* src, const double* share, double* scratch,
+                              cudaStream_t s);
+cudaError_t launch_seed_columns(const Ctx& A, const Ctx& B, cudaStream_t s);
+cudaError_t launch_seed_weights(const Ctx& A, const Ctx& B, cudaStream_t s);
 // out = L_exp(-dt K/2, scale * dir), the exponential's Frechet derivative (api.cu)
 afqmc_status frechet_expm(Ctx* h, const double* dir, double scale, double* out, cudaStream_t s);
 inline int pad64(int k) { return (k + 63) / 64 * 64; }

@@ -108,6 +108,8 @@ def test_setup_rejects_bad_arguments_without_a_device(lib):
     assert lib.afqmc_pair_delta_E(None, None, 5, 5, 5, 0.0, None, None, None, None, None) == 1
     assert lib.afqmc_pair_graph_kernels(None, None) == 1
     assert lib.afqmc_set_step(None, 5, None) == 1
+    assert lib.afqmc_population_control(None, None, None) == 1
+    assert lib.afqmc_seed_secondary(None, None, None) == 1
 
 
 @pytest.mark.parametrize("R,tau_eq", [(11, 0.3), (4, 0.0), (1, 0.2), (5, 10.0)])
