@@ -13,13 +13,15 @@ import pytest
 import test_oracle_pes as PES
 import test_oracle_pins as P
 import test_oracle_rng as RNG
-from oracle import afqmc, pes, philox
+import test_oracle_stats as ST
+from oracle import afqmc, pes, philox, stats
 
 ORIG = {n: getattr(afqmc, n) for n in ("force_bias", "green", "local_energy", "taylor_apply",
                                        "step_determinant", "orthonormalise", "propagate",
                                        "overlap", "modified_gram_schmidt")}
 ORIG_INIT = afqmc.System.__init__
 ORIG_PES = {n: getattr(pes, n) for n in ("comb_select", "seed_secondary", "seed_columns")}
+ORIG_STATS = {n: getattr(stats, n) for n in ("per_tau", "cumulative")}
 ORIG_BOX_MULLER = philox.box_muller
 
 PINS = [
@@ -47,6 +49,8 @@ PINS = [
     ("seeding keeps the state", lambda: PES.test_seeding_keeps_the_represented_state(2)),
     ("seeding an ion", lambda: PES.test_seeding_keeps_the_represented_state(1)),
     ("seeding phase projection", PES.test_seeding_projects_the_phase_of_the_ratio),
+    ("repeat mean and error", ST.test_per_tau_mean_and_standard_error),
+    ("cumulative averages, earliest minimum", ST.test_cumulative_and_earliest_minimum),
 ]
 
 
@@ -183,6 +187,22 @@ def _last_columns(sA, sB):
             list(range(sA.N - sB.n_dn, sA.N)))
 
 
+def _per_tau_ddof0(dE):
+    dE = np.asarray(dE, dtype=np.float64)
+    return dE.mean(axis=1), dE.std(axis=1, ddof=0) / np.sqrt(dE.shape[1])
+
+
+def _cumulative_strict(dE, taus, tau_eq):
+    return ORIG_STATS["cumulative"](dE, taus, np.nextafter(tau_eq, np.inf))
+
+
+def _estimate_latest_minimum(dE, taus, tau_eq):
+    t, C = stats.cumulative(dE, taus, tau_eq)
+    mean, se = stats.per_tau(C)
+    i = len(se) - 1 - int(np.nanargmin(se[::-1]))
+    return float(mean[i]), float(se[i]), float(t[i])
+
+
 def _ortho_stale_logO(sys, wk):
     saved = wk.logO.copy()
     ORIG["orthonormalise"](sys, wk)
@@ -215,6 +235,9 @@ MUTANTS = {
     "seeding ratio inverted": ("pes.seed_secondary", _seed_variant("inverted ratio")),
     "seeding phase not projected": ("pes.seed_secondary", _seed_variant("phase not projected")),
     "seeding keeps the last columns": ("pes.seed_columns", _last_columns),
+    "standard error with ddof 0": ("stats.per_tau", _per_tau_ddof0),
+    "equilibration cut tau > tau_eq": ("stats.cumulative", _cumulative_strict),
+    "latest instead of earliest minimum": ("stats.delta_e_estimate", _estimate_latest_minimum),
     "Box-Muller radius without 2": ("box_muller",
                                     lambda u1, u2: tuple(z / np.sqrt(2) for z in ORIG_BOX_MULLER(u1, u2))),
 }
@@ -242,6 +265,8 @@ def test_planted_mistake_fails_a_pin(monkeypatch, mutant):
         monkeypatch.setattr(philox, "box_muller", fn)
     elif target.startswith("pes."):
         monkeypatch.setattr(pes, target[4:], fn)
+    elif target.startswith("stats."):
+        monkeypatch.setattr(stats, target[6:], fn)
     else:
         monkeypatch.setattr(afqmc, target, fn)
     assert first_failing_pin() is not None, f"no pin catches: {mutant}"
