@@ -10,7 +10,7 @@ walkers by ~1e-5 Ha; the FP32 kernel is ~10x closer.  Walkers are the trial plus
 noise, orthonormalised per spin as the propagation keeps them.  Shapes cover every orbital
 padding (8, 16, 32 rows per Cholesky vector), one and two 64-wide k slices (M = 64, 96),
 spin-unbalanced blocks and walker counts that leave a ragged last tile.  The measured errors
-are written to gpurun_out/ when it exists.
+are written as JSON to the directory named by AFQMC_REPORT_DIR, when set.
 """
 import json
 import os
@@ -21,7 +21,7 @@ import pytest
 from gpu_util import need_gpu, system_data
 
 pytestmark = pytest.mark.gpu
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+OUT = os.environ.get("AFQMC_REPORT_DIR", "")
 REPORT = {}
 
 
@@ -68,7 +68,7 @@ def test_tensor_core_energy_matches_fp64(cfg, which, coupling, nw):
     REPORT[f"{cfg}{which}"] = dict(tc_max_Ha=float(d_tc.max()), tc_mean_Ha=float(d_tc.mean()),
                                    tc_bias_Ha=float(np.mean(etc.real - e64.real)),
                                    f32_max_Ha=float(d_32.max()), f32_mean_Ha=float(d_32.mean()))
-    if os.path.isdir(OUT):
+    if OUT and os.path.isdir(OUT):
         with open(os.path.join(OUT, "energy_tc_errors.json"), "w") as f:
             json.dump(REPORT, f, indent=1)
     assert np.array_equal(etc, etc2)                     # fixed-order sums: reproducible

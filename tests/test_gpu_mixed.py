@@ -4,7 +4,8 @@ Both paths take the same fields, so their difference is deterministic.  Criteria
 per-walker weights and local energies within the accumulated error of the split
 arithmetic (the tensor-core products carry ~2^-16 relative error, propagated through
 50 steps), and, the method's target, the correlated-pair energy difference within
-0.1 mHa of the FP64 path.  The measured errors are written to gpurun_out/ when it exists.
+0.1 mHa of the FP64 path.  The measured errors are written as JSON to the directory named
+by AFQMC_REPORT_DIR, when set.
 """
 import json
 import os
@@ -17,12 +18,12 @@ from oracle import afqmc as orc
 from synthetic import CONFIGS, explicit_fields
 
 pytestmark = pytest.mark.gpu
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+OUT = os.environ.get("AFQMC_REPORT_DIR", "")
 REPORT = {}
 
 
 def dump():
-    if os.path.isdir(OUT):
+    if OUT and os.path.isdir(OUT):
         with open(os.path.join(OUT, "mixed_errors.json"), "w") as f:
             json.dump(REPORT, f, indent=1)
 
