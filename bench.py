@@ -166,6 +166,21 @@ def time_oracle_sample(wl, coupling, n_walkers, blocks=1):
     return time.perf_counter() - t0
 
 
+def host_description():
+    """The host the oracle baseline ran on: machine, logical CPUs, and the CPU model when the
+    kernel reports one."""
+    import platform
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"machine": platform.machine(), "nproc": os.cpu_count(), "cpu_model": model}
+
+
 def blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -236,7 +251,8 @@ def run_reference(args, wl, rank, world):
                    "sample": f"{n_sample} of {wl['n_walkers']} pair indices per step"},
         "cpu_baseline": {"value": value, "unit": "walker-steps/s", "cores": cores, "kind": "oracle",
                          "sample": f"{n_sample} pair indices x {STEPS_PER_BLOCK} steps + MGS + "
-                                   "energy, both systems, per step"},
+                                   "energy, both systems, per step",
+                         "host": host_description()},
         "e2e": {"value": value, "unit": "walker-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -559,7 +575,8 @@ def run_ours(args, wl, rank, world, local_rank):
         ts = time_oracle_sample(wl, args.coupling, n_s)
         cpu = {"value": n_s * STEPS_PER_BLOCK / ts, "unit": "walker-steps/s", "cores": blas_threads(),
                "kind": "oracle",
-               "sample": f"{n_s} pair indices x {STEPS_PER_BLOCK} steps + MGS + energy, both systems"}
+               "sample": f"{n_s} pair indices x {STEPS_PER_BLOCK} steps + MGS + energy, both systems",
+               "host": host_description()}
     # kernel nodes of the captured measurement block (both systems), replayed once per block
     per_block = main["graph_kernels"]
     if rank == 0:

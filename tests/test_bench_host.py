@@ -34,3 +34,8 @@ def test_kernel_and_device_helper_edits_change_it():
     for old, new in (("if (i < n)", "if (i <= n)"), ("2.0f * x", "3.0f * x")):
         edited = SRC.replace(old, new)
         assert edited != SRC and bench.device_code_sha256(edited) != h
+
+
+def test_host_description_names_the_machine():
+    h = bench.host_description()
+    assert h["machine"] and h["nproc"] >= 1 and set(h) == {"machine", "nproc", "cpu_model"}
