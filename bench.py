@@ -54,6 +54,16 @@ def _measured_bf16_peak():
 
 
 BF16_PEAK_TFLOPS = _measured_bf16_peak()
+
+
+def _measured_hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0   # recipe fallback
+
+
+HBM_PEAK_GBS = _measured_hbm_peak()
 # FP32 SIMT peak derived from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -229,6 +239,35 @@ def traffic_for(kernel_file, name):
         return ent if ent.get("source_sha256") == hashlib.sha256(src.encode()).hexdigest() else None
     except Exception:
         return None
+
+
+def step_hbm_report(precision, workload, propagation_variant, ms_per_block):
+    """DRAM rate of one measurement block of the split-precision step at the M=64 workload:
+    the recorded ncu DRAM bytes of each kernel captured there (system A's capture stands for
+    both systems), times its launches per block, over the block's CUDA-event time.  Kernels
+    without a current capture count zero, so this is a lower bound on the step's traffic.
+    None for other workloads and precisions."""
+    if precision != "bf16x3" or workload != "C2" or not ms_per_block > 0:
+        return None
+    steps = 2 * STEPS_PER_BLOCK            # propagation steps of both systems in one block
+    items = [("walker_fast.cu", "overlap_fast_C2", steps), ("gemm_tc.cu", "vhs_tc_C2", steps),
+             ("energy_tc.cu", "energy_tc_C2", 2), ("walker_fast.cu", "mgs_reg_C2", 2)]
+    if propagation_variant == 3:
+        items.insert(0, ("propagate_tc.cu", "propagate_tc_C2", steps))
+    counted, total = {}, 0.0
+    for kernel_file, name, launches in items:
+        t = traffic_for(kernel_file, name)
+        if t:
+            counted[t["kernel"]] = launches
+            total += launches * float(t["dram_bytes_per_launch"])
+    if not counted:
+        return None
+    gbs = total / (ms_per_block / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+            "frac": gbs / HBM_PEAK_GBS, "dram_bytes_per_block": total,
+            "launches_per_block": counted,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+            "note": "recorded ncu DRAM bytes of the captured kernels only (a lower bound)"}
 
 
 def run_reference(args, wl, rank, world):
@@ -595,6 +634,8 @@ def run_ours(args, wl, rank, world, local_rank):
             "gpu_launches": per_block * K, "alive_walkers": main["alive"],
             "sigma_sqrt_t": comp, "correlated_vs_independent": corr, "other_coupling": other,
             "replicas_dE": replicas,
+            "step_hbm": step_hbm_report(args.precision, args.workload,
+                                        roofline.get("variant"), ms / K),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -39,3 +39,18 @@ def test_kernel_and_device_helper_edits_change_it():
 def test_host_description_names_the_machine():
     h = bench.host_description()
     assert h["machine"] and h["nproc"] >= 1 and set(h) == {"machine", "nproc", "cpu_model"}
+
+
+def test_step_hbm_report_sums_the_current_captures():
+    r = bench.step_hbm_report("bf16x3", "C2", 3, 2.74)
+    assert r is not None and r["unit"] == "GB/s" and 0 < r["frac"] < 1
+    per_block = sum(n * bench.traffic_for(f, name)["dram_bytes_per_launch"]
+                    for f, name, n in (("propagate_tc.cu", "propagate_tc_C2", 10),
+                                       ("walker_fast.cu", "overlap_fast_C2", 10),
+                                       ("gemm_tc.cu", "vhs_tc_C2", 10),
+                                       ("energy_tc.cu", "energy_tc_C2", 2))
+                    if bench.traffic_for(f, name))
+    assert r["dram_bytes_per_block"] >= per_block > 0
+    assert abs(r["achieved"] - r["dram_bytes_per_block"] / 2.74e-3 / 1e9) < 1e-9 * r["achieved"]
+    assert bench.step_hbm_report("fp64", "C2", None, 2.74) is None
+    assert bench.step_hbm_report("bf16x3", "C3", 3, 2.74) is None
