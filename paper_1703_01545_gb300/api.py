@@ -26,18 +26,25 @@ def _torch():
         return None
 
 
-def _ptr(a):
-    """Raw pointer of a C-contiguous float64/int32 numpy array or torch tensor (or None)."""
+def _ptr(a, kind="float64"):
+    """Raw pointer of a C-contiguous numpy array or torch tensor whose elements are what the C
+    side reads (``kind``: "float64", or "int32" for the alive flags), or None.  Any other
+    element type is refused rather than reinterpreted."""
     if a is None:
         return None
     t = _torch()
     if t is not None and isinstance(a, t.Tensor):
         if not a.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        want = {"float64": t.float64, "int32": t.int32}[kind]
+        if a.dtype != want:
+            raise TypeError(f"tensor must be {kind}, not {a.dtype}")
         return ctypes.c_void_p(a.data_ptr())
     if isinstance(a, np.ndarray):
         if not a.flags["C_CONTIGUOUS"]:
             raise ValueError("array must be C-contiguous")
+        if a.dtype != np.dtype(kind):
+            raise TypeError(f"array must be {kind}, not {a.dtype}")
         return ctypes.c_void_p(a.ctypes.data)
     raise TypeError(f"unsupported buffer type {type(a)}")
 
@@ -96,7 +103,7 @@ def afqmc_seed_secondary(B, A, stream=None):
 
 
 def afqmc_get_state(h, phi=None, logO=None, w=None, alive=None, stream=None):
-    _check(_lib.load().afqmc_get_state(h, _ptr(phi), _ptr(logO), _ptr(w), _ptr(alive),
+    _check(_lib.load().afqmc_get_state(h, _ptr(phi), _ptr(logO), _ptr(w), _ptr(alive, "int32"),
                                        _stream(stream)), h, "afqmc_get_state")
 
 

@@ -57,3 +57,20 @@ def test_make_checks_shapes_and_step():
         checkpoint.make(s, phi, w[:3], 0)
     with pytest.raises(ValueError):
         checkpoint.make(s, phi, w, -1)
+
+
+def test_buffers_of_the_wrong_element_type_are_refused():
+    """The binding hands raw pointers to C, which reads float64 (int32 for the alive flags):
+    any other element type is refused instead of being reinterpreted."""
+    import torch
+    from paper_1703_01545_gb300.api import _ptr
+    assert _ptr(None) is None
+    assert _ptr(np.zeros(3)).value and _ptr(np.zeros(3, np.int32), "int32").value
+    assert _ptr(torch.zeros(3, dtype=torch.float64)).value
+    for bad in (np.zeros(3, np.float32), np.zeros(3, np.int64), torch.zeros(3)):
+        with pytest.raises(TypeError):
+            _ptr(bad)
+    with pytest.raises(TypeError):
+        _ptr(np.zeros(3), "int32")
+    with pytest.raises(ValueError):
+        _ptr(np.zeros((3, 3))[:, 0])
