@@ -134,3 +134,23 @@ def test_host_reblocking_matches_oracle(lib):
     for n in (15, 16, 1000, 4097):
         x = np.cumsum(rng.standard_normal(n)) * 0.01
         assert abs(afqmc_reblock_error(x) - stats.reblock(x)) <= 1e-14 * max(1e-300, stats.reblock(x))
+
+
+def test_host_statistics_edge_cases(lib):
+    """Argument errors; no measurement after tau_eq (NaN estimate); one repeat (NaN error,
+    the last cumulative mean); reblocking of a series too short for one 16-block level."""
+    from paper_1703_01545_gb300 import afqmc_delta_E_stats, afqmc_reblock_error
+    d = np.ones(4)
+    est = np.empty(3)
+    assert lib.afqmc_delta_E_stats(None, d.ctypes.data, 2, 2, 0.0, None, None, None) == 1
+    assert lib.afqmc_delta_E_stats(d.ctypes.data, d.ctypes.data, 2, 0, 0.0, None, None, None) == 1
+    assert lib.afqmc_delta_E_stats(d.ctypes.data, d.ctypes.data, -1, 2, 0.0, None, None, None) == 1
+    assert lib.afqmc_delta_E_stats(d.ctypes.data, d.ctypes.data, 0, 2, 0.0, None, None,
+                                   est.ctypes.data) == 0 and np.all(np.isnan(est))
+    dE = np.array([[1.0, 2.0], [3.0, 5.0]])
+    _, _, e = afqmc_delta_E_stats(dE, np.array([0.1, 0.2]), 0.5)       # nothing after tau_eq
+    assert all(np.isnan(e))
+    _, se, e = afqmc_delta_E_stats(np.array([[1.0], [3.0], [2.0]]), np.array([0.1, 0.2, 0.3]), 0.0)
+    assert np.all(np.isnan(se)) and e[0] == 2.0 and np.isnan(e[1]) and e[2] == 0.3
+    assert afqmc_reblock_error(np.arange(15.0)) == 0.0
+    assert np.isnan(lib.afqmc_reblock_error(None, 5))
