@@ -35,7 +35,8 @@ typedef enum {
   AFQMC_OK = 0,
   AFQMC_ERR_ARG = 1,      /* invalid argument (sizes, null pointers, mismatched pair)       */
   AFQMC_ERR_CUDA = 2,     /* a CUDA runtime call or kernel launch failed                     */
-  AFQMC_ERR_NUMERIC = 3,  /* singular trial overlap at setup, or every walker is dead       */
+  AFQMC_ERR_NUMERIC = 3,  /* singular trial overlap at setup, every walker dead, or a repeat
+                             with no live walker to comb                                    */
   AFQMC_ERR_STATE = 4,    /* call not valid in the handle's current state                    */
   AFQMC_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up                              */
   AFQMC_ERR_NOMEM = 6     /* device allocation failed                                        */
