@@ -247,11 +247,13 @@ def repeat_groups(n_walkers: int, n_repeats: int):
 
 
 def mixed_energy(sys: System, w, eloc, groups, n_repeats):
-    """Per-repeat mixed estimate sum w E_L / sum w (Eq. 7; Re E_L for phaseless, Eq. 10)."""
+    """Per-repeat mixed estimate sum w E_L / sum w (Eq. 7; Re E_L for phaseless, Eq. 10).
+    The sums run over the walkers with w != 0: a dead walker contributes nothing, even when its
+    local energy is not finite (a walker killed for a non-finite overlap)."""
     E = np.empty(n_repeats)
     W = np.empty(n_repeats)
     for r in range(n_repeats):
-        m = groups == r
+        m = (groups == r) & (w != 0)
         if sys.mode == PHASELESS:
             num = np.sum(w[m].real * eloc[m].real)
             den = np.sum(w[m].real)

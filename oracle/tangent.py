@@ -186,8 +186,11 @@ def local_energy_tangent(ts: TangentSystem, phi, dphi):
 
 
 def mixed_energy_tangent(w, dlogw, eloc, deloc):
-    """(E, dE) of sum w Re E_L / sum w (phaseless)."""
+    """(E, dE) of sum w Re E_L / sum w (phaseless), over the walkers with w != 0 (a dead walker
+    contributes nothing, even when its local energy is not finite)."""
     w = np.asarray(w).real
+    live = w != 0
+    w, dlogw, eloc, deloc = w[live], np.asarray(dlogw)[live], eloc[live], deloc[live]
     dw = w * dlogw
     W = np.sum(w)
     E = np.sum(w * eloc.real) / W

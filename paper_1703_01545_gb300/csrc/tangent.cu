@@ -594,7 +594,9 @@ __global__ void __launch_bounds__(256) k_mixed_sum_tan(const double* __restrict_
   const int64_t k0 = ((int64_t)r * Nw + R - 1) / R, k1 = ((int64_t)(r + 1) * Nw + R - 1) / R;
   double acc[4] = {0, 0, 0, 0};
   for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    const double wk = w[k], dw = wk * dlogw[k];
+    const double wk = w[k];
+    if (wk == 0.0) continue;   // dead: contributes nothing (its E_L need not be finite)
+    const double dw = wk * dlogw[k];
     acc[0] += wk * eloc[k];
     acc[1] += wk;
     acc[2] += dw * eloc[k] + wk * deloc[k];

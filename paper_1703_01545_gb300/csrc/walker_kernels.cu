@@ -534,7 +534,9 @@ __global__ void __launch_bounds__(kThreads) k_energy(const double* __restrict__ 
 }
 
 // Per-repeat sums for the mixed estimate (Eq. 6): sum_k w_k E_L,k and sum_k w_k over the
-// walkers k with floor(k R / Nw) == r.  Phaseless: real weights and Re E_L (Eq. 10).
+// walkers k with floor(k R / Nw) == r.  Phaseless: real weights and Re E_L (Eq. 10).  A dead
+// walker (w = 0) adds nothing; it is skipped rather than multiplied by 0, so that the
+// non-finite local energy of a walker killed for a non-finite overlap cannot reach the sum.
 __global__ void __launch_bounds__(256) k_mixed_sum(const double* __restrict__ w, const double* __restrict__ eloc,
                                                    double* out, const int* slot, int slot_stride,
                                                    int Nw, int R, int free_proj) {
@@ -544,6 +546,7 @@ __global__ void __launch_bounds__(256) k_mixed_sum(const double* __restrict__ w,
   double acc[4] = {0, 0, 0, 0};
   for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const double wr = w[k], wi = free_proj ? w[Nw + k] : 0.0;
+    if (wr == 0.0 && wi == 0.0) continue;
     const double er = eloc[k], ei = free_proj ? eloc[Nw + k] : 0.0;
     acc[0] += wr * er - wi * ei;
     acc[1] += wr * ei + wi * er;

@@ -99,3 +99,16 @@ def test_seed_B_draws_independent_fields_for_B_only():
     same = afqmc.run_pair(sA, sB, nw, steps, seed=7, n_repeats=R)
     assert np.array_equal(same["E"][0], ind["E"][0])
     assert not np.array_equal(same["E"][1], ind["E"][1])
+
+
+def test_dead_walker_with_non_finite_energy_does_not_reach_the_estimate():
+    """A walker killed for a non-finite overlap keeps a non-finite determinant; with w = 0 it
+    must add nothing to the mixed estimate (Sec. II.B: dead walkers no longer contribute)."""
+    s, _ = c1("A", 0.01)
+    w = np.array([0.7, 0.0, 1.3, 0.9], dtype=complex)
+    eloc = np.array([-8.1, np.nan, -8.3, -8.2], dtype=complex)
+    groups = np.zeros(4, int)
+    E, W = afqmc.mixed_energy(s, w, eloc, groups, 1)
+    live = w != 0
+    assert np.isfinite(E[0]) and W[0] == w.real.sum()
+    assert abs(E[0] - np.sum(w[live].real * eloc[live].real) / W[0]) < 1e-15
