@@ -762,6 +762,7 @@ __global__ void __launch_bounds__(256) k_meas_finish(const double* __restrict__ 
   __shared__ double red[4 * 8 + 4];
   double v[2] = {0.0, 0.0};
   for (int k = threadIdx.x; k < Nw; k += blockDim.x) {
+    if (ebar[k] == 0.0) continue;   // dead walker: its E_L need not be finite
     v[0] += ebar[k] * eloc[k];
     v[1] += ebar[k];
   }
