@@ -33,6 +33,9 @@ sys.path.insert(0, ROOT)
 
 STEPS_PER_BLOCK = 5
 WORKLOADS = {
+    "C1": dict(cfg="C1", n_walkers=128, dt=0.01, repeats=11,
+               desc="synthetic pair M=8, Nchol=24, neutral 2/2 vs ion 2/1, 128 walkers per "
+                    "system, dt=0.01, energy+MGS every 5 steps, 11 repeats"),
     "C2": dict(cfg="C2", n_walkers=2048, dt=0.005, repeats=11,
                desc="synthetic pair M=64, Nchol=320, neutral 8/8 vs ion 8/7, 2048 walkers per "
                     "system, dt=0.005, energy+MGS every 5 steps, 11 repeats"),
