@@ -1,10 +1,11 @@
 // Preliminary equilibration scheme (Sec. II.C): population control of the primary system by
 // the comb, and the seeding of the secondary system's walkers from the primary's.
 //
-// Comb (the reading of the paper's "replicated / stochastically purged" walkers): within a
-// repeat, the running sum of the n weights (left to right, dead walkers counting 0; W its last
-// value) is cut at the points (j + u_r) W / n, j = 0 .. n-1, and walker j of the repeat becomes
-// a copy of the first walker whose running sum exceeds point j; every copy carries W / n.
+// Comb population control, in which heavy walkers are copied and light ones dropped
+// (Sec. II.C): within a repeat, the running sum of the n weights (left to right, dead walkers
+// counting 0; W its last value) is cut at the points (j + u_r) W / n, j = 0 .. n-1, and walker
+// j of the repeat becomes a copy of the first walker whose running sum exceeds point j; every
+// copy carries W / n.
 // Seeding: walker k of B takes the first N_s^B columns of each spin block of walker k of A,
 // and the weight w_A |R| max(0, cos arg R), R = <psi_T^B|phi_B> / <psi_T^A|phi_A>.
 #include <cmath>

@@ -2,10 +2,6 @@
 the comb of the primary system per repeat (the same walker indices: an index mismatch shows
 as an O(1) difference), the seeding of an ion from the neutral, and the correlated run that
 follows.
-
-Skipped until the PES kernels have had a first, checked run on a GB300: they were written and
-checked on the CPU only (a transliteration of the comb kernel matches the oracle's picks bit
-for bit), and an unrun kernel does not go into a GPU run unattended.
 """
 import numpy as np
 import pytest
@@ -16,8 +12,7 @@ from oracle import pes
 from oracle.philox import gaussian_fields
 from synthetic import CONFIGS
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="PES kernels not yet run on a GB300")]
+pytestmark = pytest.mark.gpu
 TOL = 1e-9
 
 
