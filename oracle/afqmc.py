@@ -35,6 +35,21 @@ Gram-Schmidt Q factor (Sec. II.D) and log O recomputed.
 Energy (Eqs. 6-7, 10): E_L = sum_s tr(h1 G_s)
       + 1/2 sum_g [ rhobar_g^2 - sum_s tr(L_g G_s L_g G_s) ],
   E = sum_k w_k Re E_L,k / sum_k w_k  (phaseless);  Re(sum w E_L / sum w) (free).
+
+Multi-determinant trial (Sec. II.D; the truncated CASSCF expansions of Sec. III):
+psi_T = sum_d c_d D_d with real M x N determinants D_d.  Every mixed quantity of the
+walker is a sum over the determinants, weighted by their share of the overlap:
+  O_d = <D_d|phi>,  <psi_T|phi> = sum_d c_d O_d,  w_d = c_d O_d / <psi_T|phi>
+  G = sum_d w_d G_d            (G_d: the Green's function above with trial D_d)
+  E_L = sum_d w_d E_L,d        (<D_d|H|phi> = O_d E_L,d; E_L,d with trial D_d)
+and the force bias takes rhobar from this G.  G_d and E_L,d need O_d != 0; a walker
+orthogonal to a determinant of the expansion (as a walker sitting on one determinant of an
+orthonormal expansion is to all the others) would need cofactor formulas instead, so the
+walkers start from a determinant outside the expansion (the paper starts them from ROHF
+determinants while the trial is built on CASSCF orbitals), and a determinant with O_d = 0
+contributes nothing.  The mean-field background <rho_g>_T, the one-body operator K and
+the energy shift E_T are those of the first determinant D_0 (any constant background is
+exact under the force-bias reweighting, and E_T cancels in every mixed estimate).
 """
 import numpy as np
 
@@ -48,7 +63,12 @@ class System:
     """Static data of one system: h1, L, trial, and the derived K, e^{-dt K/2}, C, E_T."""
 
     def __init__(self, h1, L, trial, n_up, n_dn, dt, fb_cap=1.0, mode=PHASELESS,
-                 taylor_order=6):
+                 taylor_order=6, dets=None, coeffs=None, start=None):
+        """``dets`` [Nd, M, N] and ``coeffs`` [Nd] give a multi-determinant trial (``trial``
+        is then ignored: the first determinant takes its role for <rho>_T, K and E_T) and
+        ``start`` the walkers' initial determinant (default: the trial)."""
+        if dets is not None:
+            trial = np.asarray(dets, dtype=np.float64)[0]
         self.h1 = np.asarray(h1, dtype=np.float64)
         self.L = np.asarray(L, dtype=np.float64)
         self.trial = np.asarray(trial, dtype=np.float64)
@@ -74,7 +94,14 @@ class System:
         lam, U = np.linalg.eigh(self.K)
         self.expK = (U * np.exp(-0.5 * self.dt * lam)) @ U.T
         # trial energy E_T = E_L(psi_T): the energy shift of exp(dt (E_T - H))
+        self.dets = None
         self.E_T = float(local_energy(self, self.trial[None].astype(np.complex128))[0].real)
+        self.start = self.trial if start is None else np.asarray(start, dtype=np.float64)
+        if dets is not None:
+            self.dets = np.asarray(dets, dtype=np.float64)
+            self.coeffs = np.asarray(coeffs, dtype=np.float64)
+            if self.dets.shape[1:] != (self.M, self.N) or self.coeffs.shape != self.dets.shape[:1]:
+                raise ValueError("dets [Nd, M, N] and coeffs [Nd] expected")
 
 
 class Walkers:
@@ -82,7 +109,7 @@ class Walkers:
 
     def __init__(self, sys: System, n_walkers: int, phi=None, w=None):
         if phi is None:
-            phi = np.broadcast_to(sys.trial, (n_walkers, sys.M, sys.N))
+            phi = np.broadcast_to(sys.start, (n_walkers, sys.M, sys.N))
         self.phi = np.array(phi, dtype=np.complex128)
         self.w = np.ones(n_walkers, dtype=np.complex128) if w is None else np.array(w, np.complex128)
         self.logO = overlap(sys, self.phi)
@@ -94,29 +121,63 @@ class Walkers:
         return c
 
 
-def overlap(sys: System, phi):
-    """log <psi_T|phi> = sum_s log det(Psi_s^T Phi_s)  (Cauchy-Binet)."""
+def det_overlap(sys: System, trial, phi):
+    """log <D|phi> = sum_s log det(D_s^T Phi_s) for one determinant D = trial  (Cauchy-Binet)."""
     logO = np.zeros(phi.shape[0], dtype=np.complex128)
     for a, b in sys.spins:
         if b == a:
             continue
-        O = np.einsum("ia,wib->wab", sys.trial[:, a:b], phi[:, :, a:b])
+        O = np.einsum("ia,wib->wab", trial[:, a:b], phi[:, :, a:b])
         sign, lad = np.linalg.slogdet(O)
-        logO += lad + np.log(sign)
+        logO += lad + np.log(sign.astype(np.complex128))
     return logO
 
 
-def green(sys: System, phi):
-    """Mixed Green's functions G_s [Nw, M, M], G_s[i,j] = <c+_i c_j>_mixed, for s = up, down."""
+def det_green(sys: System, trial, phi):
+    """Green's functions G_s [Nw, M, M] of the walkers with one determinant D = trial,
+    G_s[i,j] = <D| c+_i c_j |phi> / <D|phi>, for s = up, down."""
     out = []
     for a, b in sys.spins:
         if b == a:
             out.append(np.zeros((phi.shape[0], sys.M, sys.M), dtype=np.complex128))
             continue
-        Psi = sys.trial[:, a:b]
+        Psi = trial[:, a:b]
         O = np.einsum("ia,wib->wab", Psi, phi[:, :, a:b])
         Theta = phi[:, :, a:b] @ np.linalg.inv(O)
         out.append(np.swapaxes(Theta @ Psi.T, 1, 2))
+    return out
+
+
+def det_shares(sys: System, phi):
+    """Multi-determinant trial: (log <psi_T|phi> [Nw], w [Nd, Nw]) with w_d = c_d O_d /
+    <psi_T|phi>; the sum is taken relative to the largest |O_d| of each walker."""
+    logO = np.array([det_overlap(sys, D, phi) for D in sys.dets])          # [Nd, Nw]
+    top = np.max(logO.real, axis=0)
+    t = sys.coeffs[:, None] * np.exp(logO - top[None, :])
+    total = np.sum(t, axis=0)
+    return top + np.log(total), t / total[None, :]
+
+
+def overlap(sys: System, phi):
+    """log <psi_T|phi>: one determinant, or sum_d c_d <D_d|phi> for a multi-determinant trial."""
+    if sys.dets is None:
+        return det_overlap(sys, sys.trial, phi)
+    return det_shares(sys, phi)[0]
+
+
+def green(sys: System, phi):
+    """Mixed Green's functions G_s [Nw, M, M], G_s[i,j] = <psi_T|c+_i c_j|phi>/<psi_T|phi>,
+    for s = up, down; for a multi-determinant trial sum_d w_d G_d (O_d = 0: no contribution)."""
+    if sys.dets is None:
+        return det_green(sys, sys.trial, phi)
+    _, w = det_shares(sys, phi)
+    out = [np.zeros((phi.shape[0], sys.M, sys.M), dtype=np.complex128) for _ in sys.spins]
+    for D, wd in zip(sys.dets, w):
+        use = wd != 0
+        if not np.any(use):
+            continue
+        for si, Gs in enumerate(det_green(sys, D, phi[use])):
+            out[si][use] += wd[use, None, None] * Gs
     return out
 
 
@@ -223,21 +284,37 @@ def orthonormalise(sys: System, wk: Walkers):
     wk.logO[idx] = overlap(sys, phi)
 
 
+def energy_from_green(sys: System, G):
+    """E_L of walkers with single-determinant Green's functions G (Eq. 7 with Wick's theorem):
+    sum_s tr(h1 G_s) + 1/2 sum_g [ (sum_s tr L_g G_s)^2 - sum_s tr(L_g G_s L_g G_s) ]."""
+    e1 = sum(np.einsum("ij,wji->w", sys.h1, Gs) for Gs in G)
+    rb = rhobar(sys, G)
+    exch = 0.0
+    for Gs in G:
+        LG = sys.L[None, :, :, :] @ Gs[:, None, :, :]          # [w, g, M, M] = L_g G_s
+        exch = exch + np.einsum("wgik,wgki->wg", LG, LG)
+    return e1 + 0.5 * np.sum(rb * rb - exch, axis=1)
+
+
 def local_energy(sys: System, phi, chunk: int = 0):
-    """E_L [Nw] complex, from the mixed Green's functions (Eq. 7 with Wick's theorem)."""
+    """E_L [Nw] complex (Eq. 7 with Wick's theorem); for a multi-determinant trial
+    sum_d w_d E_L,d, the two-body part taken per determinant (it is not linear in G)."""
     nw = phi.shape[0]
     if chunk <= 0:
         chunk = max(1, int(4e6 // max(1, sys.X * sys.M * sys.M)))
     out = np.empty(nw, dtype=np.complex128)
     for s0 in range(0, nw, chunk):
-        G = green(sys, phi[s0:s0 + chunk])
-        e1 = sum(np.einsum("ij,wji->w", sys.h1, Gs) for Gs in G)
-        rb = rhobar(sys, G)
-        exch = 0.0
-        for Gs in G:
-            LG = sys.L[None, :, :, :] @ Gs[:, None, :, :]          # [w, g, M, M] = L_g G_s
-            exch = exch + np.einsum("wgik,wgki->wg", LG, LG)
-        out[s0:s0 + chunk] = e1 + 0.5 * np.sum(rb * rb - exch, axis=1)
+        p = phi[s0:s0 + chunk]
+        if sys.dets is None:
+            out[s0:s0 + chunk] = energy_from_green(sys, det_green(sys, sys.trial, p))
+            continue
+        _, w = det_shares(sys, p)
+        acc = np.zeros(p.shape[0], dtype=np.complex128)
+        for D, wd in zip(sys.dets, w):
+            use = wd != 0
+            if np.any(use):
+                acc[use] += wd[use] * energy_from_green(sys, det_green(sys, D, p[use]))
+        out[s0:s0 + chunk] = acc
     return out
 
 
