@@ -35,10 +35,10 @@ def build_system(M, X, n_up, n_dn, seed=1703, coupling=1.0):
     """Return dict(h1, L, trial, n_up, n_dn, M, X) for one system (cached).
 
     ``coupling``: 1.0 is the recipe as stated; the string "moderate" selects
-    ``moderate_coupling(X)`` (long-lived walkers for long-run statistics).
+    ``moderate_coupling(M, X)`` (long-lived walkers for long-run statistics).
     """
     if coupling == "moderate":
-        coupling = moderate_coupling(X)
+        coupling = moderate_coupling(M, X)
     key = (M, X, n_up, n_dn, seed, float(coupling))
     if key not in _cache:
         h1, L = make_hamiltonian(M, X, seed, coupling=coupling)
