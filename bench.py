@@ -1,8 +1,8 @@
 #!/usr/bin/env python3
 """Benchmark of the correlated-pair walker propagation (one JSON line on rank 0).
 
-Workload (default): the M=64 synthetic pair -- Nchol=320, neutral 8/8 vs ion 8/7,
-2048 walkers per system, dt=0.005, 11 repeats, shared Philox field stream.  One
+Workload (default): the M=128 synthetic pair -- Nchol=768, neutral 16/16 vs ion 16/15,
+4096 walkers per system, dt=0.005, 11 repeats, shared Philox field stream.  One
 benchmark step = one measurement block of the method for BOTH systems: 5
 propagation steps (force bias, fields, V_HS, split propagator with Taylor
 exponential, overlap/ratio/phaseless weight), one modified Gram-Schmidt pass and
@@ -46,7 +46,7 @@ WORKLOADS = {
                desc="uneven synthetic pair A: M=200, Nchol=1000, 9/9; B: M=190, Nchol=950, 8/8 "
                     "(own Hamiltonian), 2048 walkers per system, dt=0.005, 11 repeats"),
 }
-FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (no tcgen05 FP64 kind; DFMA/DMMA pipe)
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 nominal FP64 (no tcgen05 FP64 kind; DFMA/DMMA pipe)
 
 
 def _measured_bf16_peak():
@@ -71,13 +71,26 @@ HBM_PEAK_GBS = _measured_hbm_peak()
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+# oracle pair indices timed for cpu_baseline (about 10-30 s of host work per workload)
+CPU_SAMPLE = {"C1": 128, "C2": 96, "C3": 16, "C4": 8}
+# pair indices per step of the reference arm (the oracle)
+REF_SAMPLE = {"C1": 128, "C2": 16, "C3": 4, "C4": 2}
+
+
+def working_set_gb(wl, d):
+    """Bytes one propagation step of both systems streams at least: the FP64 walkers (read and
+    written) and the V_HS matrices (FP32, written and read)."""
+    M, N, nw = d["M"], d["n_up"] + d["n_dn"], wl["n_walkers"]
+    return 2 * nw * (2 * 2 * M * N * 8 + 2 * 2 * M * M * 4) / 1e9
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="C3", choices=sorted(WORKLOADS))
     ap.add_argument("--coupling", default="moderate", choices=["literal", "moderate"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp64", "bf16x3"])
     ap.add_argument("--mode", default="phaseless", choices=["phaseless", "free"],
@@ -96,6 +109,9 @@ def parse():
                          "benchmark line)")
     ap.add_argument("--walkers", type=int, default=None, help="override walkers per system")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--compare-steps", type=int, default=None,
+                    help="blocks of the FP64-against-split comparison (default: --steps at M <= 64, "
+                         "else at most 10)")
     return ap.parse_args()
 
 
@@ -191,6 +207,15 @@ def host_description():
                 break
     except OSError:
         pass
+    if model is None:   # aarch64 kernels report no model name in /proc/cpuinfo
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
     return {"machine": platform.machine(), "nproc": os.cpu_count(), "cpu_model": model}
 
 
@@ -273,10 +298,153 @@ def step_hbm_report(precision, workload, propagation_variant, ms_per_block):
             "note": "recorded ncu DRAM bytes of the captured kernels only (a lower bound)"}
 
 
+def measure_fp64_peak():
+    """Measured FP64 rate of this GPU: the best of three cuBLAS DGEMMs (4096^3, through torch),
+    in TFLOP/s; the nominal rate if the measurement fails."""
+    import torch
+    try:
+        n = 4096
+        a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        torch.matmul(a, b)
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del a, b
+        return 2.0 * n ** 3 / (best / 1e3) / 1e12, "measured: cuBLAS DGEMM 4096^3, best of 3 (burst)"
+    except Exception:
+        return FP64_NOMINAL_TFLOPS, "GB300 nominal FP64 (measurement failed)"
+
+
+def measure_kernels(afq, A, dA, nw, precision, workload, stream):
+    """Each kernel of one propagation step (and of the measurement's Gram-Schmidt and local
+    energy) timed alone with CUDA events, with its algorithmic work from the method's flop
+    counts per walker (real flops; complex x real MAC = 4, complex x complex = 8):
+      force bias 4 X N M;  V_HS 4 P X, P = M (M + 1) / 2 (packed symmetric L; the full count
+      4 M^2 X beside it);  propagator (8 order + 8) M^2 N (Taylor terms and the two one-body
+      half steps);  overlap (split path: its FP64 part, the LU, 8/3 sum N_s^3; the overlap sums
+      run as FP32 pairs and are reported beside it);  Gram-Schmidt 8 M sum N_s^2;  local energy
+      4 X M sum N_s^2 + 8 X sum N_s^2.
+    Tensor-core kernels also give the split-BF16 MMA work they issue (3 products per product,
+    padded tiles) as mma_flops.  Launches per block: 5 propagation steps, one Gram-Schmidt and
+    one energy, for one system (system A)."""
+    M, X, nu, nd = dA["M"], dA["X"], dA["n_up"], dA["n_dn"]
+    N, N2, N3 = nu + nd, nu * nu + nd * nd, nu ** 3 + nd ** 3
+    P = M * (M + 1) // 2
+    order = 6
+    f64_peak, f64_src = measure_fp64_peak()
+    bf16 = ("MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)", BF16_PEAK_TFLOPS)
+    f32 = ("derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 x 2.07 GHz", FP32_PEAK_TFLOPS)
+    f64 = (f64_src, f64_peak)
+    split = precision != "fp64"
+    pv = A.info().tuned_taylor_smem if split else -1
+    pad = lambda x, m: (x + m - 1) // m * m
+    nb2 = 2 * pad(N, 8)
+
+    def entry(which, launches, flops, bound, peak, name, mma=None, traffic=None, **extra):
+        ms = afq.afqmc_time_kernel(A.h, which, 5, stream.cuda_stream)
+        ach = flops / (ms / 1e3) / 1e12
+        e = {"bound": bound, "achieved": ach, "peak": peak[1], "unit": "TFLOP/s",
+             "frac": ach / peak[1], "traffic": traffic, "kernel": name,
+             "algorithmic_flops_per_launch": flops, "ms_per_launch": ms,
+             "launches_per_block": launches, "ms_per_block": ms * launches,
+             "peak_source": peak[0]}
+        if mma is not None:
+            e["mma_flops_per_launch"] = mma
+            e["mma_tflops"] = mma / (ms / 1e3) / 1e12
+            e["mma_frac"] = e["mma_tflops"] / peak[1]
+        e.update(extra)
+        return e
+
+    def tr(kfile, key):
+        t = traffic_for(kfile, f"{key}_{workload}")
+        return t["dram_bytes_per_launch"] if t else None
+
+    out = {}
+    fb = 4.0 * X * N * M * nw
+    vhs = 4.0 * P * X * nw
+    vhs_full = 4.0 * M * M * X * nw
+    prop = (8.0 * order + 8.0) * M * M * N * nw
+    mgs = 8.0 * M * N2 * nw
+    en = (4.0 * X * M * N2 + 8.0 * X * N2) * nw
+    if split:
+        out["force_bias"] = entry(afq.K_FORCE_BIAS, STEPS_PER_BLOCK, fb, "tensor", bf16,
+                                  "k_gemm_bf16x3_tc (force bias, split-BF16 tcgen05)",
+                                  mma=3 * 2.0 * pad(X, 128) * pad(N * M, 64) * 2 * nw,
+                                  traffic=tr("gemm_tc.cu", "force_bias_tc"))
+        out["vhs"] = entry(afq.K_VHS, STEPS_PER_BLOCK, vhs, "tensor", bf16,
+                           "k_gemm_bf16x3_tc_persist (V_HS, split-BF16 tcgen05, full M^2 rows)",
+                           mma=3 * 2.0 * pad(M * M, 128) * pad(X, 64) * 2 * nw,
+                           traffic=tr("gemm_tc.cu", "vhs_tc"),
+                           full_count_flops_per_launch=vhs_full)
+        out["vhs"]["frac_full_count"] = out["vhs"]["frac"] * vhs_full / vhs
+        if pv == 3:
+            out["propagator"] = entry(
+                afq.K_TAYLOR, STEPS_PER_BLOCK, prop, "tensor", bf16,
+                "k_propagate_tc (split-BF16 tcgen05 one-body + Taylor rounds, M <= 64)",
+                mma=nw * (order + 2) * 3.0 * 2.0 * 128 * nb2 * 64,
+                traffic=tr("propagate_tc.cu", "propagate_tc"), variant=pv)
+        elif pv == 4:
+            # per 128-row tile of orbitals and 16-wide K step holding orbitals: 3 products per
+            # one-body round, 6 per Taylor round (A_re and A_im), each 2 x 128 x 2 Np x 16 flops
+            mt = (M + 127) // 128
+            ks = sum(min(4, (M - 64 * kb + 15) // 16) for kb in range((M + 63) // 64))
+            mma4 = nw * mt * ks * (2 * 3 + order * 6) * 2.0 * 128 * nb2 * 16
+            out["propagator"] = entry(
+                afq.K_TAYLOR, STEPS_PER_BLOCK, prop, "tensor", bf16,
+                "k_propagate_tcl (split-BF16 tcgen05 one-body + Taylor rounds, V_HS streamed by TMA)",
+                mma=mma4, traffic=tr("propagate_tcl.cu", "propagate_tcl"), variant=pv)
+        else:
+            name = {2: "k_propagate_f32 (fused one-body half steps + Taylor exponential, FP32)"}.get(
+                pv, "k_gemm_tn_f32 + k_taylor_f32 + k_gemm_tn_f32 (FP32)")
+            out["propagator"] = entry(afq.K_TAYLOR, STEPS_PER_BLOCK, prop, "alu", f32, name,
+                                      traffic=tr("propagate_f32.cu", "propagate_f32") if pv == 2 else None,
+                                      variant=pv)
+        lu = 8.0 / 3.0 * N3 * nw
+        out["overlap"] = entry(afq.K_OVERLAP_UPDATE, STEPS_PER_BLOCK, lu, "alu", f64,
+                               "k_overlap_fast (update form: overlap sums as FP32 pairs, FP64 LU and "
+                               "log det, FP32 Theta)",
+                               traffic=tr("walker_fast.cu", "overlap_fast"),
+                               fp32_pair_flops_per_launch=4.0 * M * N2 * nw,
+                               fp32_theta_flops_per_launch=8.0 * M * N2 * nw,
+                               flops_note="only the FP64 LU counts against the FP64 peak")
+        out["mgs"] = entry(afq.K_MGS, 1, mgs, "alu", f64, "k_mgs_reg / k_mgs_warp (FP64 Gram-Schmidt)",
+                           traffic=tr("walker_fast.cu", "mgs_reg"))
+        p2 = 4
+        while p2 < max(nu, nd):
+            p2 *= 2
+        NPp = 2 * p2
+        out["energy"] = entry(afq.K_EXCHANGE, 1, en, "tensor", bf16,
+                              "k_energy_B + k_energy_tc (split-BF16 tcgen05 local energy)",
+                              mma=3.0 * 2.0 * (X * NPp) * (2 * NPp * nw) * pad(M, 64),
+                              traffic=tr("energy_tc.cu", "energy_tc"))
+    else:
+        out["force_bias"] = entry(afq.K_FORCE_BIAS, STEPS_PER_BLOCK, fb, "alu", f64,
+                                  "k_gemm_f64_force_bias (FP64)")
+        out["vhs"] = entry(afq.K_VHS, STEPS_PER_BLOCK, vhs, "alu", f64,
+                           "k_gemm_f64_vhs (V_HS, packed symmetric L, FP64)",
+                           traffic=tr("gemm_f64.cu", "vhs_gemm"))
+        out["propagator"] = entry(afq.K_TAYLOR, STEPS_PER_BLOCK, 8.0 * order * M * M * N * nw, "alu",
+                                  f64, "k_taylor (Taylor exponential, FP64; the one-body half steps "
+                                  "run as separate FP64 GEMMs)", traffic=tr("walker_kernels.cu", "taylor_f64"))
+        out["overlap"] = entry(afq.K_OVERLAP, STEPS_PER_BLOCK,
+                               (12.0 * M * N2 + 8.0 * N3) * nw, "alu", f64,
+                               "k_overlap (FP64 overlap, Gauss-Jordan inverse, Theta; refresh form)")
+        out["mgs"] = entry(afq.K_MGS, 1, mgs, "alu", f64, "k_mgs + overlap refresh (FP64)")
+        out["energy"] = entry(afq.K_EXCHANGE, 1, en, "alu", f64, "k_energy (FP64 local energy)")
+    return out
+
+
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return
-    n_sample = 16
+    n_sample = REF_SAMPLE[wl["cfg"]]
     for _ in range(args.warmup):
         time_oracle_sample(wl, args.coupling, n_sample)
     tot = 0.0
@@ -394,8 +562,10 @@ def run_ours(args, wl, rank, world, local_rank):
                           autotune_cache=args.autotune_cache, independent_fields=independent,
                           mode=afq.FREE if args.mode == "free" else afq.PHASELESS)
 
-    def timed(prec, coupling, clocks=None, independent=False):
-        """Pair run; independent=True gives B its own field key (uncorrelated sampling)."""
+    def timed(prec, coupling, clocks=None, independent=False, blocks=None):
+        """Pair run of `blocks` (default K) timed measurement blocks after W warm-up blocks;
+        independent=True gives B its own field key (uncorrelated sampling)."""
+        n_steps_run = (K if blocks is None else blocks) * STEPS_PER_BLOCK
         dA, dB = systems(wl, coupling)
         A = make(dA, prec, 1, independent)
         B = make(dB, prec, 2 if independent else 1, independent)
@@ -410,8 +580,8 @@ def run_ours(args, wl, rank, world, local_rank):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        res = afq.pair_delta_E(A, B, n_steps, STEPS_PER_BLOCK, STEPS_PER_BLOCK, tau_eq=tau_eq,
-                               raise_on_dead=False)
+        res = afq.pair_delta_E(A, B, n_steps_run, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
+                               tau_eq=0.25 * n_steps_run * dt, raise_on_dead=False)
         e1.record(stream)
         torch.cuda.synchronize()
         ck = clocks.stop() if clocks else None
@@ -422,7 +592,7 @@ def run_ours(args, wl, rank, world, local_rank):
             ms = float(t.item())
         alive = [A.info().n_alive, B.info().n_alive]
         return dict(ms=ms, res=res, alive=alive, clocks=ck, A=A, B=B, dA=dA,
-                    graph_kernels=afq.pair_graph_kernels(A))
+                    graph_kernels=afq.pair_graph_kernels(A), steps=n_steps_run)
 
     main = timed(args.precision, args.coupling, ClockSampler(torch.cuda.current_device()))
     ms = main["ms"]
@@ -436,137 +606,40 @@ def run_ours(args, wl, rank, world, local_rank):
                     "repeats": int(E_all.shape[2])}
     value = world * nw * n_steps / (ms / 1e3)
 
-    # kernels timed alone on this stream with CUDA events: the path's time-dominant kernel
-    # (by its share of the step in the ncu launch list) and the dominant contraction, V_HS
+    # every kernel of the step timed alone on this stream with CUDA events; the one with the
+    # largest time per measurement block is the dominant kernel reported as `roofline`
     A, dA = main["A"], main["dA"]
-    M, X, nu, nd = dA["M"], dA["X"], dA["n_up"], dA["n_dn"]
-    N, N2 = nu + nd, nu * nu + nd * nd
-    P = M * (M + 1) // 2
-    vhs_ms = afq.afqmc_time_kernel(A.h, afq.K_VHS, 5, stream.cuda_stream)
-    if args.precision == "fp64":
-        vflops = 2.0 * P * X * (2 * nw)
-        tr = traffic_for("gemm_f64.cu", "vhs_gemm_C2")
-        contraction = {"bound": "alu", "achieved": vflops / (vhs_ms / 1e3) / 1e12,
-                       "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                       "kernel": "k_gemm_f64_vhs (V_HS, packed symmetric L, FP64)",
-                       "algorithmic_flops_per_launch": vflops, "ms_per_launch": vhs_ms,
-                       "traffic": tr["dram_bytes_per_launch"] if tr else None}
-        # time-dominant kernel of the FP64 step: the Taylor exponential
-        t_ms = afq.afqmc_time_kernel(A.h, afq.K_TAYLOR, 5, stream.cuda_stream)
-        tflops = 6 * 8.0 * M * M * N * nw
-        ach = tflops / (t_ms / 1e3) / 1e12
-        trt = traffic_for("walker_kernels.cu", "taylor_f64_C2")
-        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS,
-                    "traffic": trt["dram_bytes_per_launch"] if trt else None,
-                    "kernel": "k_taylor (Taylor exponential, FP64; largest share of the FP64 step)",
-                    "algorithmic_flops_per_launch": tflops, "ms_per_launch": t_ms,
-                    "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe table); cuBLAS DGEMM measured 1.10"}
-    else:
-        useful = 2.0 * M * M * X * (2 * nw)
-        vflops = 3.0 * useful     # hi*hi + hi*lo + lo*hi BF16 products
-        tr = traffic_for("gemm_tc.cu", "vhs_tc_C2")
-        contraction = {"bound": "tensor", "achieved": vflops / (vhs_ms / 1e3) / 1e12,
-                       "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
-                       "kernel": "k_gemm_bf16x3_tc (V_HS, split-BF16 tcgen05, full M^2 rows)",
-                       "algorithmic_flops_per_launch": vflops, "useful_flops_per_launch": useful,
-                       "ms_per_launch": vhs_ms,
-                       "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                       "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, kernel timed alone)"}
-        # time-dominant kernel of the split-precision step: the propagator
-        # e^{-dt K/2} e^A e^{-dt K/2} (largest share in the launch list) in the variant the
-        # autotuner chose; its algorithmic work is `order` complex products A T plus two
-        # real-by-complex one-body products per walker
-        order = 6
-        pv = A.info().tuned_taylor_smem
-        p_ms = afq.afqmc_time_kernel(A.h, afq.K_TAYLOR, 5, stream.cuda_stream)
-        pflops = (8.0 * order + 8.0) * M * M * N * nw
-        if pv == 3:
-            # tensor cores: per walker (order + 2) rounds of 3 split-BF16 MMAs, M = 128 rows
-            # ([A_re; A_im] or E - I over 64 padded orbitals), N = 2 pad8(N), K = 64
-            nb = 2 * ((N + 7) // 8 * 8)
-            mflops = nw * (order + 2) * 3.0 * 2.0 * 128 * nb * 64
-            roofline = {"bound": "tensor", "achieved": mflops / (p_ms / 1e3) / 1e12,
-                        "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": mflops / (p_ms / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
-                        "kernel": "k_propagate_tc (split-BF16 tcgen05 one-body + Taylor rounds; "
-                                  "largest share of the split-precision step)",
-                        "algorithmic_flops_per_launch": mflops, "useful_flops_per_launch": pflops,
-                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, kernel timed alone)"}
-            trp = traffic_for("propagate_tc.cu", "propagate_tc_C2")
-        else:
-            name = {2: "k_propagate_f32 (fused one-body half steps + Taylor exponential, FP32"}.get(
-                pv, "k_gemm_tn_f32 + k_taylor_f32 + k_gemm_tn_f32 (FP32")
-            ach = pflops / (p_ms / 1e3) / 1e12
-            roofline = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": ach / FP32_PEAK_TFLOPS,
-                        "kernel": name + "; largest share of the split-precision step)",
-                        "algorithmic_flops_per_launch": pflops,
-                        "peak_source": "derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
-            trp = traffic_for("propagate_f32.cu", "propagate_f32_C2") if pv == 2 else None
-        roofline["ms_per_launch"] = p_ms
-        roofline["traffic"] = trp["dram_bytes_per_launch"] if trp else None
-        roofline["variant"] = pv
-        # the overlap / LU / log det / Theta kernel in the form every step runs (Psi^T Phi as
-        # FP32 pairs from the FP32 walkers, FP64 LU, FP32 triangular solves for Theta); its
-        # algorithmic work counted as FP64: the overlap contraction and the LU
-        o_ms = afq.afqmc_time_kernel(A.h, afq.K_OVERLAP_UPDATE, 5, stream.cuda_stream)
-        oflops = (4.0 * M * N2 + 8.0 / 3.0 * (nu ** 3 + nd ** 3)) * nw
-        tro = traffic_for("walker_fast.cu", "overlap_fast_C2")
-        overlap = {
-            "bound": "alu", "achieved": oflops / (o_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": oflops / (o_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-            "traffic": tro["dram_bytes_per_launch"] if tro else None,
-            "kernel": "k_overlap_fast (overlap as FP32 pairs, FP64 LU and log det, FP32 Theta; update form)",
-            "algorithmic_flops_per_launch": oflops, "ms_per_launch": o_ms,
-            "flops_note": "Psi^T Phi (4 M sum N_s^2) and LU (8/3 sum N_s^3) counted as FP64 work",
-            "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe table)"}
-        # the time-dominant kernel of the step: per measurement block both kernels run once per
-        # step; the larger is reported as `roofline`, the other beside it
-        if o_ms > p_ms:
-            roofline["kernel"] = roofline["kernel"].replace("; largest share of the split-precision step", "")
-            overlap["kernel"] += "; largest share of the split-precision step"
-            overlap["propagator"] = roofline
-            roofline = overlap
-        else:
-            roofline["overlap_fp64"] = overlap
-        # the tensor-core local energy: split-BF16 GEMM of Psi^T L_g Theta over (g, w) with the
-        # exchange reduction in the epilogue; MMA work counts the orbital padding to P2 per spin
-        e_ms = afq.afqmc_time_kernel(A.h, afq.K_EXCHANGE, 5, stream.cuda_stream)
-        p2 = 4
-        while p2 < max(nu, nd):
-            p2 *= 2
-        NPp, Kp = 2 * p2, (M + 63) // 64 * 64
-        eflops = 3.0 * 2.0 * (X * NPp) * (2 * NPp * nw) * Kp
-        useful_e = 2.0 * X * (nu * nu + nd * nd) * M * 2 * nw
-        tre = traffic_for("energy_tc.cu", "energy_tc_C2")
-        roofline["energy_tc"] = {
-            "bound": "tensor", "achieved": eflops / (e_ms / 1e3) / 1e12, "peak": BF16_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": eflops / (e_ms / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
-            "traffic": tre["dram_bytes_per_launch"] if tre else None,
-            "kernel": "k_energy_B + k_energy_tc + k_energy_tc_reduce (split-BF16 tcgen05 local energy)",
-            "algorithmic_flops_per_launch": eflops, "useful_flops_per_launch": useful_e,
-            "ms_per_launch": e_ms,
-            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, kernel timed alone)"}
-    contraction["frac"] = contraction["achieved"] / contraction["peak"]
-    roofline["contraction_vhs"] = contraction
+    kernels = measure_kernels(afq, A, dA, nw, args.precision, args.workload, stream)
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_block"])
+    roofline = dict(kernels[dom])
+    roofline["kernel_key"] = dom
     main["A"].close()
     main["B"].close()
 
-    # the FP64 path on the same fields: throughput and sigma_dE * sqrt(GPU seconds)
+    # the FP64 path on the same fields: throughput and sigma_dE * sqrt(GPU seconds), both paths
+    # over the same number of blocks (fewer than K where the FP64 path is slow: M >= 128)
     other_prec = "fp64" if args.precision != "fp64" else None
+    cmp_blocks = args.compare_steps or (K if wl["cfg"] in ("C1", "C2") else min(K, 10))
     comp = {}
-    runs = {args.precision: main}
+    runs = {}
     if other_prec and world == 1:
-        o = timed(other_prec, args.coupling)
+        runs[args.precision] = main
+        if cmp_blocks != K:
+            r_ = timed(args.precision, args.coupling, blocks=cmp_blocks)
+            r_["A"].close()
+            r_["B"].close()
+            runs[args.precision] = r_
+        o = timed(other_prec, args.coupling, blocks=cmp_blocks)
         o["A"].close()
         o["B"].close()
         runs[other_prec] = o
     for p_, r_ in runs.items():
         sig = r_["res"]["dE_sigma"]
-        comp[p_] = {"walker_steps_per_s": world * nw * n_steps / (r_["ms"] / 1e3),
-                    "gpu_s": r_["ms"] / 1e3, "dE_mean_Ha": r_["res"]["dE_mean"],
-                    "dE_sigma_Ha": sig, "sigma_sqrt_gpu_s": sig * (r_["ms"] / 1e3) ** 0.5}
+        comp[p_] = {"walker_steps_per_s": world * nw * r_["steps"] / (r_["ms"] / 1e3),
+                    "gpu_s": r_["ms"] / 1e3, "propagation_steps": r_["steps"],
+                    "dE_mean_Ha": r_["res"]["dE_mean"], "dE_sigma_Ha": sig,
+                    "sigma_sqrt_gpu_s": sig * (r_["ms"] / 1e3) ** 0.5,
+                    "alive_walkers": r_["alive"]}
     if "fp64" in comp and "bf16x3" in comp:
         comp["gpu_time_ratio_at_equal_sigma"] = (comp["fp64"]["sigma_sqrt_gpu_s"] /
                                                  comp["bf16x3"]["sigma_sqrt_gpu_s"]) ** 2
@@ -586,7 +659,8 @@ def run_ours(args, wl, rank, world, local_rank):
     d2h = 8 * res2["E"].size
     e2e = {"value": world * nw * n_steps / e2e_s, "unit": "walker-steps/s",
            "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
-           "note": "setup of both systems from host arrays + pair run + energy series to host"}
+           "note": "setup of both systems from host arrays (H2D copies, setup kernels and the "
+                   "kernel-variant autotuning inside) + the same pair run + energy series to host"}
 
     # correlated against independent fields at the same workload and precision (Sec. III):
     # GPU time to reach a given sigma_dE scales as sigma^2 * t
@@ -603,17 +677,9 @@ def run_ours(args, wl, rank, world, local_rank):
                 if sc > 0 else None,
                 "repeats": R, "note": "independent: system B keyed by its own seed"}
 
-    other = None
-    if world == 1:
-        oc = "literal" if args.coupling == "moderate" else "moderate"
-        r3 = timed(args.precision, oc)
-        other = {"coupling": oc, "value": nw * n_steps / (r3["ms"] / 1e3), "alive_walkers": r3["alive"]}
-        r3["A"].close()
-        r3["B"].close()
-
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_s = 96
+        n_s = CPU_SAMPLE[wl["cfg"]]
         ts = time_oracle_sample(wl, args.coupling, n_s)
         cpu = {"value": n_s * STEPS_PER_BLOCK / ts, "unit": "walker-steps/s", "cores": blas_threads(),
                "kind": "oracle",
@@ -631,14 +697,16 @@ def run_ours(args, wl, rank, world, local_rank):
             "config": {"workload": wl["desc"], "coupling": args.coupling, "precision": args.precision,
                        "mode": args.mode,
                        "step": "one measurement block (5 propagation steps + MGS + energy) of both systems",
-                       "l2": "inputs larger than L2 (per-step working set ~0.5 GB)",
+                       "l2": f"inputs larger than L2 (walkers and V_HS alone: "
+                             f"{working_set_gb(wl, dA):.2f} GB per step against 0.13 GB of L2)",
+                       "fp64_comparison_blocks": cmp_blocks,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clocks"],
             "gpu_launches": per_block * K, "alive_walkers": main["alive"],
-            "sigma_sqrt_t": comp, "correlated_vs_independent": corr, "other_coupling": other,
+            "sigma_sqrt_t": comp, "correlated_vs_independent": corr, "kernels": kernels,
             "replicas_dE": replicas,
             "step_hbm": step_hbm_report(args.precision, args.workload,
-                                        roofline.get("variant"), ms / K),
+                                        kernels["propagator"].get("variant"), ms / K),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

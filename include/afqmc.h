@@ -123,6 +123,33 @@ afqmc_status afqmc_setup(afqmc_handle* out, const double* h1, const double* L,
                          const double* trial, int M, int X, int n_up, int n_dn,
                          const afqmc_options* opt, cudaStream_t stream);
 
+/*
+ * afqmc_setup_multidet -- Sec. II.D and the truncated CASSCF trials of Sec. III: a system
+ * whose trial is a multi-determinant expansion psi_T = sum_d c_d D_d.  The walkers are
+ * propagated exactly as with one determinant; every mixed quantity is a sum over the
+ * determinants weighted by their shares w_d = c_d O_d / <psi_T|phi>, O_d = <D_d|phi>:
+ *   <psi_T|phi> = sum_d c_d O_d (importance function, overlap ratio and phase),
+ *   force bias from G = sum_d w_d G_d (Eq. 9), local energy E_L = sum_d w_d E_L,d (Eq. 7).
+ * <rho_g>_T, K, C and E_T are those of the first determinant D_0 (a constant background is
+ * exact under the force-bias reweighting; E_T cancels in every mixed estimate).
+ *   dets   [n_det][M][N], each [D_up | D_dn] real with orthonormal columns per spin; host
+ *          or device memory, copied.
+ *   coeffs [n_det] real CI coefficients (host or device), finite, not all zero.
+ *   start  [M][N] initial determinant of every walker (host or device), or NULL for D_0.
+ *          A determinant with O_d = 0 contributes nothing (its Green's function would need
+ *          cofactor formulas), so start should overlap every D_d: a walker sitting on one
+ *          determinant of an orthonormal expansion is orthogonal to all the others.
+ *   1 <= n_det <= 4096; the other arguments as afqmc_setup.  FP64 only (ARG for
+ *   AFQMC_BF16X3); afqmc_set_tangent and afqmc_adjoint_run refuse these handles (ARG).
+ * Memory grows with n_det: Theta_d and the force bias of every determinant, n_det *
+ * 2 Nw (N M + X) doubles.  Synchronises the stream.  Errors: ARG, NUMERIC (a walker's
+ * start has zero overlap with psi_T), NOMEM, CUDA.  *out is NULL on failure.
+ */
+afqmc_status afqmc_setup_multidet(afqmc_handle* out, const double* h1, const double* L,
+                                  const double* dets, const double* coeffs, int n_det,
+                                  const double* start, int M, int X, int n_up, int n_dn,
+                                  const afqmc_options* opt, cudaStream_t stream);
+
 /* Release every device buffer of h.  h may be NULL. */
 afqmc_status afqmc_destroy(afqmc_handle h);
 
@@ -337,12 +364,15 @@ afqmc_status afqmc_delta_E_stats(const double* dE, const double* taus, int n_mea
  * Theta kernel in its refresh form, which recomputes the same values from the current
  * walkers), AFQMC_K_OVERLAP_UPDATE (AFQMC_BF16X3 only, ERR_ARG otherwise: the same kernel in
  * the form each propagation step runs, FP32-pair overlap sums from the FP32 walkers, without
- * the weight update; one refresh afterwards restores Theta and log O).  None of them changes
- * the walkers or the weights.
+ * the weight update; one refresh afterwards restores Theta and log O), AFQMC_K_MGS (the
+ * modified Gram-Schmidt pass in the form afqmc_orthonormalise runs it, with its overlap
+ * update or refresh).  None of them changes the weights; none but AFQMC_K_MGS changes the
+ * walkers, and AFQMC_K_MGS, applied to walkers that are already orthonormal (as after
+ * afqmc_orthonormalise), changes them and log O only by rounding.
  * Synchronises the stream.  Errors: ARG, CUDA.
  */
 enum { AFQMC_K_VHS = 0, AFQMC_K_FORCE_BIAS = 1, AFQMC_K_TAYLOR = 2, AFQMC_K_EXCHANGE = 3,
-       AFQMC_K_OVERLAP = 4, AFQMC_K_OVERLAP_UPDATE = 5 };
+       AFQMC_K_OVERLAP = 4, AFQMC_K_OVERLAP_UPDATE = 5, AFQMC_K_MGS = 6 };
 afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms,
                                cudaStream_t stream);
 
@@ -374,6 +404,9 @@ afqmc_status afqmc_select_kernel(afqmc_handle h, int which, int variant);
  *   e_local [2][Nw] (real parts, then imaginary parts).
  * Problems whose fixed part (X*N*M + 2*N*M doubles plus one walker) exceeds the
  * array are rejected with ERR_ARG before anything is launched.
+ * A walker whose overlap with the trial is singular (or not finite) has no local
+ * energy: both of its e_local entries are set to NaN while the call still returns OK;
+ * the other walkers are unaffected.
  * The first call on a device looks up the array's device address (once per device,
  * with that device current); make that first call before any stream capture.
  * Asynchronous on `stream`.  Every call shares the one array, so calls whose work

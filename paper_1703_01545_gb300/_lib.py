@@ -38,6 +38,9 @@ SIGNATURES = {
     "afqmc_last_error": (ctypes.c_char_p, [VP]),
     "afqmc_setup": (ctypes.c_int, [ctypes.POINTER(VP), VP, VP, VP, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, ctypes.POINTER(AfqmcOptions), VP]),
+    "afqmc_setup_multidet": (ctypes.c_int, [ctypes.POINTER(VP), VP, VP, VP, VP, ctypes.c_int, VP,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(AfqmcOptions), VP]),
     "afqmc_destroy": (ctypes.c_int, [VP]),
     "afqmc_set_walkers": (ctypes.c_int, [VP, VP, VP, VP]),
     "afqmc_get_state": (ctypes.c_int, [VP, VP, VP, VP, VP, VP]),

@@ -79,6 +79,15 @@ def afqmc_setup(h1, L, trial, M, X, n_up, n_dn, opt, stream=None):
     return h
 
 
+def afqmc_setup_multidet(h1, L, dets, coeffs, start, M, X, n_up, n_dn, opt, stream=None):
+    h = ctypes.c_void_p()
+    code = _lib.load().afqmc_setup_multidet(ctypes.byref(h), _ptr(h1), _ptr(L), _ptr(dets),
+                                            _ptr(coeffs), len(coeffs), _ptr(start), M, X, n_up,
+                                            n_dn, ctypes.byref(opt), _stream(stream))
+    _check(code, None, "afqmc_setup_multidet")
+    return h
+
+
 def afqmc_destroy(h):
     _check(_lib.load().afqmc_destroy(h), None, "afqmc_destroy")
 
@@ -160,7 +169,7 @@ def afqmc_delta_E_stats(dE, taus, tau_eq):
     return mt, st, tuple(est)
 
 
-K_VHS, K_FORCE_BIAS, K_TAYLOR, K_EXCHANGE, K_OVERLAP, K_OVERLAP_UPDATE = 0, 1, 2, 3, 4, 5
+K_VHS, K_FORCE_BIAS, K_TAYLOR, K_EXCHANGE, K_OVERLAP, K_OVERLAP_UPDATE, K_MGS = 0, 1, 2, 3, 4, 5, 6
 
 
 def afqmc_time_kernel(h, which, reps, stream=None):
@@ -181,9 +190,18 @@ class System:
     def __init__(self, h1, L, trial, n_up, n_dn, dt=0.01, n_walkers=128, taylor_order=6,
                  mode=PHASELESS, n_repeats=1, seed=1, fb_cap=1.0, walker_offset=0,
                  precision=FP64, autotune=True, autotune_cache=None, independent_fields=False,
-                 stream=None):
+                 stream=None, dets=None, coeffs=None, start=None):
+        """``dets`` [Nd, M, N] and ``coeffs`` [Nd] (with ``trial`` None) give a
+        multi-determinant trial (afqmc_setup_multidet, FP64), ``start`` the walkers' first
+        determinant [M, N]."""
         h1 = np.ascontiguousarray(h1, dtype=np.float64)
         L = np.ascontiguousarray(L, dtype=np.float64)
+        if dets is not None:
+            dets = np.ascontiguousarray(dets, dtype=np.float64)
+            coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+            if start is not None:
+                start = np.ascontiguousarray(start, dtype=np.float64)
+            trial = dets[0]
         trial = np.ascontiguousarray(trial, dtype=np.float64)
         self.M, self.X = h1.shape[0], L.shape[0]
         self.n_up, self.n_dn, self.N = int(n_up), int(n_dn), int(n_up) + int(n_dn)
@@ -196,7 +214,12 @@ class System:
         o.autotune_cache = autotune_cache.encode() if autotune_cache else None
         o.independent_fields = 1 if independent_fields else 0
         self.opt = o
-        self.h = afqmc_setup(h1, L, trial, self.M, self.X, self.n_up, self.n_dn, o, stream)
+        self.n_det = 0 if dets is None else len(coeffs)
+        if dets is None:
+            self.h = afqmc_setup(h1, L, trial, self.M, self.X, self.n_up, self.n_dn, o, stream)
+        else:
+            self.h = afqmc_setup_multidet(h1, L, dets, coeffs, start, self.M, self.X, self.n_up,
+                                          self.n_dn, o, stream)
 
     def close(self):
         if self.h is not None:

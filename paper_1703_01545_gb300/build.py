@@ -18,7 +18,7 @@ SOURCES = ["gemm_f64.cu", "walker_kernels.cu", "setup_kernels.cu", "api.cu", "pa
            "noalloc.cu", "gemm_tc.cu", "mixed_kernels.cu", "walker_fast.cu", "autotune.cu",
            "tangent.cu", "adjoint_kernels.cu", "adjoint.cu",
            "energy_tc.cu", "propagate_f32.cu",
-           "propagate_tc.cu", "pes.cu"]
+           "propagate_tc.cu", "propagate_tcl.cu", "pes.cu", "multidet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

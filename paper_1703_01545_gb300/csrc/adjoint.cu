@@ -264,6 +264,7 @@ extern "C" afqmc_status afqmc_adjoint_run(afqmc_handle h, int n_steps, const dou
   if (h->opt.precision != AFQMC_FP64 || h->opt.mode != AFQMC_PHASELESS)
     return fail(h, AFQMC_ERR_ARG, "the adjoint needs the FP64 phaseless path");
   if (h->R != 1) return fail(h, AFQMC_ERR_ARG, "the adjoint needs n_repeats == 1");
+  if (h->n_det > 0) return fail(h, AFQMC_ERR_ARG, "the adjoint needs a single-determinant trial");
   if (n_steps < 1) return fail(h, AFQMC_ERR_ARG, "n_steps must be >= 1");
   if (energy_every < 1 || energy_every > n_steps)
     return fail(h, AFQMC_ERR_ARG, "energy_every must be in [1, n_steps]");

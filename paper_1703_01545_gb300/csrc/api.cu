@@ -72,6 +72,10 @@ void free_ctx(Ctx* h) {
     }
   if (h->ovdet) cudaFree(h->ovdet);
   if (h->emI_pk) cudaFree(h->emI_pk);
+  for (__nv_bfloat16* b : {h->tcl_ahi, h->tcl_alo, h->tcl_ehi, h->tcl_elo})
+    if (b) cudaFree(b);
+  delete[] h->tcl_maps;
+  h->tcl_maps = nullptr;
   for (double* b : {h->Bneg, h->dexpK, h->htilP, h->dphi, h->dphi2, h->dtheta, h->drhobar, h->dU,
                     h->dAvhs, h->dlogO, h->dlogw, h->daux, h->deloc, h->desum})
     if (b) cudaFree(b);
@@ -79,6 +83,9 @@ void free_ctx(Ctx* h) {
                    h->rhobar32, h->rho_mf32})
     if (b) cudaFree(b);
   if (h->d_tc_err) cudaFree(h->d_tc_err);
+  for (double* b : {h->md_coef, h->md_psi, h->md_Ltil, h->md_htil, h->md_logO, h->md_theta,
+                    h->md_share, h->md_rhobar, h->md_eloc})
+    if (b) cudaFree(b);
   if (h->etc) {
     for (afq::TcOperand* op : {h->etc->A, h->etc->B})
       if (op) {
@@ -121,6 +128,7 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   AFQ_CK(afq::prepare_fast_walker_kernels(*h));
   AFQ_CK(afq::prepare_propagate_f32());
   AFQ_CK(afq::prepare_propagate_tc());
+  AFQ_CK(afq::prepare_propagate_tcl());
   if ((st = make_operand(h, &h->tc_L, (int)MM, X, s)) != AFQMC_OK) return st;
   if ((st = make_operand(h, &h->tc_Ltil, X, (int)NM, s)) != AFQMC_OK) return st;
   if ((st = make_operand(h, &h->tc_U, 2 * Nw, X, s)) != AFQMC_OK) return st;
@@ -158,6 +166,21 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   if (e == cudaSuccess && afq::propagate_tc_ok(*h)) {
     if (dalloc(h, &h->emI_pk, 64 * 64) != AFQMC_OK) return AFQMC_ERR_NOMEM;
     e = afq::pack_propagate_tc(*h, h->emI_pk, s);
+  }
+  if (e == cudaSuccess && afq::propagate_tcl_ok(*h)) {
+    // V_HS in split form for the large-M tensor-core propagator (zero until the first step)
+    const size_t na = 2 * (size_t)Nw * M * afq::propagate_tcl_mp(M), ne = (size_t)M * afq::propagate_tcl_mp(M);
+    if (dalloc(h, &h->tcl_ahi, na) != AFQMC_OK || dalloc(h, &h->tcl_alo, na) != AFQMC_OK ||
+        dalloc(h, &h->tcl_ehi, ne) != AFQMC_OK || dalloc(h, &h->tcl_elo, ne) != AFQMC_OK) {
+      if (own) {
+        cudaStreamSynchronize(s);
+        cudaFree(tmp);
+      }
+      return AFQMC_ERR_NOMEM;
+    }
+    e = cudaMemsetAsync(h->tcl_ahi, 0, na * 2, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->tcl_alo, 0, na * 2, s);
+    if (e == cudaSuccess) e = afq::setup_propagate_tcl(*h, s);
   }
   // Theta of the current walkers in FP32 and as the split force-bias operand
   if (e == cudaSuccess && overlap_launch(h, nullptr, afq::OV_REFRESH, s) != AFQMC_OK)
@@ -201,19 +224,18 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
 
 // One split-precision step: tensor-core contractions, FP32 propagator, FP64 overlaps.
 afqmc_status step_launch_mixed(Ctx* h, const double* fields_t, cudaStream_t s) {
-  const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
-  const int64_t MM = (int64_t)M * M;
+  const int X = h->X, Nw = h->Nw;
   if (h->opt.mode == AFQMC_PHASELESS) {
     // the Theta operand was written by the last overlap kernel
     AFQ_CK(afq::gemm_bf16x3(*h->tc_Ltil, *h->tc_Theta, X, 2 * Nw, 1.0f, h->rhobar32, X,
                             h->d_tc_err, s));
   }
   AFQ_CK(afq::launch_fields_mixed(*h, fields_t, s));
-  AFQ_CK(afq::gemm_bf16x3(*h->tc_L, *h->tc_U, (int)MM, 2 * Nw, 1.0f, h->Avhs32, MM, h->d_tc_err, s));
-  // Phi' = e^{-dt K/2} e^A e^{-dt K/2} Phi into theta (FP64; the tensor-core propagator writes
-  // the live walkers in place) and, variants 2 and 3, into phi32 (FP32)
   const int pv = afq::propagation_variant(*h);
-  double* pout = pv == 3 ? h->phi : h->theta;
+  AFQ_CK(afq::vhs_launch(*h, pv, s));
+  // Phi' = e^{-dt K/2} e^A e^{-dt K/2} Phi into theta (FP64; the tensor-core propagators write
+  // the live walkers in place) and, variants 2 to 4, into phi32 (FP32)
+  double* pout = pv >= 3 ? h->phi : h->theta;
   AFQ_CK(afq::launch_propagation(*h, pv, pout, h->phi32, s));
   afqmc_status os = overlap_launch(h, pout, afq::OV_UPDATE, s, pv >= 2 ? h->phi32 : nullptr);
   if (os != AFQMC_OK) return os;
@@ -228,6 +250,8 @@ afqmc_status energy_launch(Ctx* h, cudaStream_t s) {
     } else {
       AFQ_CK(afq::launch_energy_tiled(*h, h->theta32, h->LtT, s));
     }
+  } else if (h->n_det > 0) {
+    AFQ_CK(afq::md_energy(*h, s));
   } else {
     AFQ_CK(afq::launch_energy(*h, s));
   }
@@ -284,9 +308,14 @@ afqmc_status step_launch(Ctx* h, const double* fields_t, cudaStream_t s) {
   const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
   const int64_t NM = (int64_t)N * M;
   if (h->opt.mode == AFQMC_PHASELESS) {
-    // rhobar[(p,w)][g] = sum_(n,i) Ltil[g][(n,i)] Theta[(p,w)][(n,i)]       (Eq. 9)
-    AFQ_CK(afq::gemm_tn_f64(X, 2 * Nw, (int)NM, 1.0, h->Ltil, NM, 0, h->theta, NM, 0, 0.0,
-                            h->rhobar, X, 0, 1, s, afq::GEMM_FORCE_BIAS));
+    // rhobar[(p,w)][g] = sum_(n,i) Ltil[g][(n,i)] Theta[(p,w)][(n,i)]       (Eq. 9); a
+    // multi-determinant trial sums the determinants' contractions with their shares
+    if (h->n_det > 0) {
+      AFQ_CK(afq::md_force_bias(*h, s));
+    } else {
+      AFQ_CK(afq::gemm_tn_f64(X, 2 * Nw, (int)NM, 1.0, h->Ltil, NM, 0, h->theta, NM, 0, 0.0,
+                              h->rhobar, X, 0, 1, s, afq::GEMM_FORCE_BIAS));
+    }
   }
   AFQ_CK(afq::launch_fields(*h, fields_t, s));
   // packed A[(p,w)][ij] = sum_g Lt[ij][g] U[(p,w)][g]                         (Eq. 11)
@@ -299,7 +328,8 @@ afqmc_status step_launch(Ctx* h, const double* fields_t, cudaStream_t s) {
   AFQ_CK(afq::gemm_tn_f64(M, 2 * Nw * N, M, 1.0, h->expK, M, 0, h->phi2, M, 0, 0.0, h->theta,
                           M, 0, 1, s, afq::GEMM_ONEBODY));
   // new overlaps, Theta, ratio, phase, weight; live walkers take the new determinant
-  AFQ_CK(afq::launch_overlap(*h, h->theta, afq::OV_UPDATE, s));
+  afqmc_status os = overlap_launch(h, h->theta, afq::OV_UPDATE, s);
+  if (os != AFQMC_OK) return os;
   AFQ_CK(afq::launch_step_advance(*h, s));
   return AFQMC_OK;
 }
@@ -307,6 +337,10 @@ afqmc_status step_launch(Ctx* h, const double* fields_t, cudaStream_t s) {
 // Overlap / Theta / weight kernel: the warp-synchronous variant in split-precision mode.
 afqmc_status overlap_launch(Ctx* h, const double* src, int mode, cudaStream_t s,
                             const float* src32) {
+  if (h->n_det > 0) {
+    AFQ_CK(afq::md_overlap(*h, src, mode, s));
+    return AFQMC_OK;
+  }
   if (h->theta32 && h->tc_Theta && afq::fast_walker_kernels_ok(*h)) {
     AFQ_CK(afq::launch_overlap_fast(*h, src, mode, s, src32));
   } else {
@@ -559,6 +593,85 @@ afqmc_status afqmc_setup(afqmc_handle* out, const double* h1_in, const double* L
   return AFQMC_OK;
 }
 
+afqmc_status afqmc_setup_multidet(afqmc_handle* out, const double* h1, const double* L,
+                                  const double* dets, const double* coeffs, int n_det,
+                                  const double* start, int M, int X, int n_up, int n_dn,
+                                  const afqmc_options* opt, cudaStream_t s) {
+  if (!out) return AFQMC_ERR_ARG;
+  *out = nullptr;
+  if (!dets || !coeffs || !opt || n_det < 1 || n_det > 4096) return AFQMC_ERR_ARG;
+  if (opt->precision != AFQMC_FP64) return AFQMC_ERR_ARG;
+  std::vector<double> c(n_det);
+  if (cudaMemcpy(c.data(), coeffs, sizeof(double) * n_det, cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return AFQMC_ERR_ARG;
+  }
+  bool any = false;
+  for (double v : c) {
+    if (!std::isfinite(v)) return AFQMC_ERR_ARG;
+    any = any || v != 0.0;
+  }
+  if (!any) return AFQMC_ERR_ARG;
+  // the first determinant plays the single-determinant trial's part: <rho_g>_T, K, E_T
+  afqmc_handle h = nullptr;
+  afqmc_status st = afqmc_setup(&h, h1, L, dets, M, X, n_up, n_dn, opt, s);
+  if (st != AFQMC_OK) return st;
+  const int N = h->N, Nw = h->Nw;
+  const int64_t NM = (int64_t)N * M;
+  auto fail_with = [&](afqmc_status code) {
+    afqmc_destroy(h);
+    return code;
+  };
+  double* tmp = nullptr;
+  if (dalloc(h, &h->md_coef, n_det) != AFQMC_OK || dalloc(h, &h->md_psi, n_det * NM) != AFQMC_OK ||
+      dalloc(h, &h->md_Ltil, (size_t)n_det * X * NM) != AFQMC_OK ||
+      dalloc(h, &h->md_htil, n_det * NM) != AFQMC_OK ||
+      dalloc(h, &h->md_logO, (size_t)n_det * 2 * Nw) != AFQMC_OK ||
+      dalloc(h, &h->md_theta, (size_t)n_det * 2 * Nw * NM) != AFQMC_OK ||
+      dalloc(h, &h->md_share, (size_t)n_det * 2 * Nw) != AFQMC_OK ||
+      dalloc(h, &h->md_rhobar, (size_t)n_det * 2 * Nw * X) != AFQMC_OK ||
+      dalloc(h, &h->md_eloc, (size_t)n_det * 2 * Nw) != AFQMC_OK ||
+      dalloc(h, &tmp, (size_t)(n_det + 1) * NM) != AFQMC_OK)
+    return fail_with(AFQMC_ERR_NOMEM);
+  cudaError_t e = cudaMemcpyAsync(h->md_coef, c.data(), sizeof(double) * n_det,
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tmp, dets, sizeof(double) * n_det * NM, cudaMemcpyDefault, s);
+  for (int d = 0; d < n_det && e == cudaSuccess; ++d) {
+    double* pd = h->md_psi + d * NM;
+    e = afq::launch_transpose(tmp + d * NM, pd, M, N, s);          // [M][N] -> [N][M]
+    if (e == cudaSuccess)
+      e = afq::gemm_tn_f64(M, N, M, 1.0, h->L, M, (int64_t)M * M, pd, M, 0, 0.0,
+                           h->md_Ltil + (int64_t)d * X * NM, M, NM, X, s);
+    if (e == cudaSuccess)
+      e = afq::gemm_tn_f64(M, N, M, 1.0, h->h1, M, 0, pd, M, 0, 0.0, h->md_htil + d * NM, M, 0,
+                           1, s);
+  }
+  if (e == cudaSuccess && start) {
+    double* st_t = tmp + n_det * NM;
+    e = cudaMemcpyAsync(tmp, start, sizeof(double) * NM, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = afq::launch_transpose(tmp, st_t, M, N, s);
+    if (e == cudaSuccess) e = afq::launch_broadcast_walkers(st_t, h->phi, Nw, (int)NM, s);
+  }
+  if (e == cudaSuccess) e = afq::launch_init_weights(h->w, h->alive, nullptr, Nw, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flags, 0, sizeof(int) * 4, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  if (e != cudaSuccess) {
+    cuda_fail(h, "afqmc_setup_multidet", e);
+    return fail_with(AFQMC_ERR_CUDA);
+  }
+  h->n_det = n_det;
+  if ((st = overlap_launch(h, nullptr, afq::OV_REFRESH, s)) != AFQMC_OK) return fail_with(st);
+  int flags = 0;
+  e = cudaMemcpyAsync(&flags, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_with(AFQMC_ERR_CUDA);
+  if (flags != 0) return fail_with(AFQMC_ERR_NUMERIC);
+  *out = h;
+  return AFQMC_OK;
+}
+
 afqmc_status afqmc_destroy(afqmc_handle h) {
   if (!h) return AFQMC_OK;
   free_ctx(h);
@@ -730,7 +843,11 @@ afqmc_status afqmc_energy(afqmc_handle h, double* e_local, double* e_mixed, doub
 }
 
 afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, cudaStream_t s) {
-  if (!h || !ms || reps < 1 || which < 0 || which > 5) return AFQMC_ERR_ARG;
+  if (!h || !ms || reps < 1 || which < 0 || which > 6) return AFQMC_ERR_ARG;
+  if (which == AFQMC_K_MGS && h->tangent_on) {
+    h->err = "AFQMC_K_MGS is not timed in tangent mode";
+    return AFQMC_ERR_STATE;
+  }
   const bool fast_ov = h->theta32 && h->tc_Theta && h->phi32 && afq::fast_walker_kernels_ok(*h);
   if (which == AFQMC_K_OVERLAP_UPDATE && !fast_ov) {
     h->err = "AFQMC_K_OVERLAP_UPDATE times the split-precision overlap kernel only";
@@ -743,13 +860,12 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
   AFQ_CK(cudaEventCreate(&e1));
   auto one = [&]() -> cudaError_t {
     switch (which) {
-      case AFQMC_K_VHS:
-        if (h->tc_L)
-          return afq::gemm_bf16x3(*h->tc_L, *h->tc_U, M * M, 2 * Nw, 1.0f, h->Avhs32,
-                                  (int64_t)M * M, h->d_tc_err, s);
+      case AFQMC_K_VHS:   // split precision: in the form the propagation variant reads
+        if (h->tc_L) return afq::vhs_launch(*h, afq::propagation_variant(*h), s);
         return afq::gemm_tn_f64((int)h->P, 2 * Nw, X, 1.0, h->Lt, X, 0, h->U, X, 0, 0.0, h->Avhs,
                                 h->P, 0, 1, s, afq::GEMM_VHS);
       case AFQMC_K_FORCE_BIAS:
+        if (h->n_det > 0) return afq::md_force_bias(*h, s);
         if (h->tc_Ltil)
           return afq::gemm_bf16x3(*h->tc_Ltil, *h->tc_Theta, X, 2 * Nw, 1.0f, h->rhobar32, X,
                                   h->d_tc_err, s);
@@ -758,13 +874,19 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms, 
       case AFQMC_K_OVERLAP_UPDATE:   // Phi <- Phi (unchanged), Theta from the FP32 walkers
         return afq::launch_overlap_fast(*h, h->phi, afq::OV_UPDATE, s, h->phi32, false);
       case AFQMC_K_OVERLAP:
+        if (h->n_det > 0) return afq::md_overlap(*h, nullptr, afq::OV_REFRESH, s);
         if (h->theta32 && h->tc_Theta && afq::fast_walker_kernels_ok(*h))
           return afq::launch_overlap_fast(*h, nullptr, afq::OV_REFRESH, s);
         return afq::launch_overlap(*h, nullptr, afq::OV_REFRESH, s);
+      case AFQMC_K_MGS: {
+        const afqmc_status st = ortho_launch(h, s);
+        return st == AFQMC_OK ? cudaSuccess : cudaErrorUnknown;
+      }
       case AFQMC_K_TAYLOR:   // split precision: the fused propagator times its two one-body products too
         if (h->phi32) return afq::launch_propagation(*h, afq::propagation_variant(*h), h->theta, nullptr, s);
         return afq::launch_taylor(*h, h->phi2, s);
       default:
+        if (h->n_det > 0) return afq::md_energy(*h, s);
         if (h->etc && h->tune_energy_wb <= 0) return afq::launch_energy_tc(*h, s);
         if (h->LtT) return afq::launch_energy_tiled(*h, h->theta32, h->LtT, s);
         return afq::launch_energy(*h, s);
@@ -879,6 +1001,7 @@ afqmc_status afqmc_set_tangent(afqmc_handle h, const double* P, cudaStream_t s) 
   }
   if (h->opt.precision != AFQMC_FP64 || h->opt.mode != AFQMC_PHASELESS)
     return set_err(h, AFQMC_ERR_ARG, "tangent mode needs the FP64 phaseless path");
+  if (h->n_det > 0) return set_err(h, AFQMC_ERR_ARG, "tangent mode needs a single-determinant trial");
   if (!afq::tangent_fits(*h)) return set_err(h, AFQMC_ERR_ARG, "tangent kernels exceed shared memory");
   const int M = h->M, X = h->X, N = h->N, Nw = h->Nw;
   const int64_t NM = (int64_t)N * M;
@@ -979,7 +1102,7 @@ afqmc_status afqmc_select_kernel(afqmc_handle h, int which, int variant) {
     return AFQMC_OK;
   }
   if (which == AFQMC_K_TAYLOR) {
-    if (variant < 0 || variant > 3 || !afq::taylor_variant_ok(*h, variant))
+    if (variant < 0 || variant > 4 || !afq::taylor_variant_ok(*h, variant))
       return set_err(h, AFQMC_ERR_ARG, "Taylor variant unsupported for this shape");
     h->tune_taylor_smem = variant;
     return AFQMC_OK;

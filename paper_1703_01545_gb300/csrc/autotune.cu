@@ -82,7 +82,7 @@ float time_variant(F launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
 cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto cache = load(cache_path);
-  const std::string ke = key_of(c, "energy_v2"), kt = key_of(c, "propagate_v2");
+  const std::string ke = key_of(c, "energy_v2"), kt = key_of(c, "propagate_v3");
   bool dirty = false;
   cudaEvent_t e0, e1;
   cudaError_t err = cudaEventCreate(&e0);
@@ -112,10 +112,10 @@ cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s) {
     c.tune_taylor_smem = cache[kt];
   } else {
     float best = 1e30f;
-    // the whole one-body + Taylor propagation: tensor-core (3) or fused FP32 kernel (2), or
+    // the whole one-body + Taylor propagation: tensor-core (3, 4) or fused FP32 kernel (2), or
     // GEMM, Taylor (1, 0), GEMM;
     // every variant writes only scratch (phi32, the FP64 theta buffer)
-    for (int v : {3, 2, 1, 0}) {
+    for (int v : {3, 4, 2, 1, 0}) {
       if (!taylor_variant_ok(c, v)) continue;
       const float t = time_variant([&]() { return launch_propagation(c, v, c.theta, c.phi32, s); },
                                    s, e0, e1);

@@ -45,12 +45,30 @@ struct TcLayout {
   static constexpr int SMEM_BYTES = BAR_OFFSET + 256 + 1024;  // barriers + TMEM slot + alignment
 };
 
+// Split output of 32 accumulator columns of output row m = i M + j: hi = bf16(x), lo =
+// bf16(x - hi) at n * ld + i * Mp + j for columns n = n0 .. n0 + 31 below Nd.
+__device__ __forceinline__ void store_split(const SplitOut& so, int m, int n0, int Nd, float alpha,
+                                            const uint32_t (&v)[32]) {
+  const int i = m / so.M, j = m - i * so.M;
+  const int64_t off = (int64_t)i * so.Mp + j;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    const int n = n0 + q;
+    if (n < Nd) {
+      const float x = alpha * __uint_as_float(v[q]);
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      so.hi[(int64_t)n * so.ld + off] = h;
+      so.lo[(int64_t)n * so.ld + off] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+  }
+}
+
 template <int BN, int STAGES, class TC>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_bf16x3_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                      int Md, int Nd, int nkb, float alpha, TC* __restrict__ C, int64_t ldc,
-                     int* err, uint64_t wait_ns, int skip_producer) {
+                     SplitOut so, int* err, uint64_t wait_ns, int skip_producer) {
   using Lay = TcLayout<BN, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -134,10 +152,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
       if (m < Md) {
+        if (so.hi) {
+          store_split(so, m, n0 + c0, Nd, alpha, v);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = n0 + c0 + j;
-          if (n < Nd) C[(int64_t)n * ldc + m] = (TC)(alpha * __uint_as_float(v[j]));
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + c0 + j;
+            if (n < Nd) C[(int64_t)n * ldc + m] = (TC)(alpha * __uint_as_float(v[j]));
+          }
         }
       }
     }
@@ -171,7 +193,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
     k_gemm_bf16x3_tc_persist(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                              const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                              int Md, int Nd, int nkb, float alpha, float* __restrict__ C, int64_t ldc,
-                             int* err, uint64_t wait_ns) {
+                             SplitOut so, int* err, uint64_t wait_ns) {
   using Lay = PLayoutG;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -279,10 +301,14 @@ __global__ void __launch_bounds__(PTHREADS, 1)
         uint32_t v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * PBN + c0), v);
         if (m < Md) {
+          if (so.hi) {
+            store_split(so, m, n0 + c0, Nd, alpha, v);
+          } else {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c0 + j;
-            if (n < Nd) C[(int64_t)n * ldc + m] = alpha * __uint_as_float(v[j]);
+            for (int j = 0; j < 32; ++j) {
+              const int n = n0 + c0 + j;
+              if (n < Nd) C[(int64_t)n * ldc + m] = alpha * __uint_as_float(v[j]);
+            }
           }
         }
       }
@@ -334,12 +360,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 template <int BN, int STAGES, class TC>
 cudaError_t launch_tc(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha, TC* C,
                       int64_t ldc, int* err, cudaStream_t s, uint64_t wait_ns = kWaitLimitNs,
-                      int skip_producer = 0) {
+                      int skip_producer = 0, SplitOut so = SplitOut()) {
   using Lay = TcLayout<BN, STAGES>;
   dim3 grid((Md + BM - 1) / BM, (Nd + BN - 1) / BN);
   if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
   k_gemm_bf16x3_tc<BN, STAGES, TC><<<grid, NTHREADS, Lay::SMEM_BYTES, s>>>(
-      A.map_hi, A.map_lo, B.map_hi, B.map_lo, Md, Nd, A.Kp / BK, alpha, C, ldc, err, wait_ns,
+      A.map_hi, A.map_lo, B.map_hi, B.map_lo, Md, Nd, A.Kp / BK, alpha, C, ldc, so, err, wait_ns,
       skip_producer);
   return cudaGetLastError();
 }
@@ -384,8 +410,9 @@ cudaError_t split_bf16(const double* in, int64_t ld_in, int rows, int K, int Kp,
 int tc_bn() { return 128; }
 int tc_pad_rows(int rows) { return (rows + 127) / 128 * 128; }
 
-cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,
-                        float* C, int64_t ldc, int* err, cudaStream_t s) {
+namespace {
+cudaError_t gemm_f32_or_split(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,
+                              float* C, int64_t ldc, const SplitOut& so, int* err, cudaStream_t s) {
   if (A.Kp != B.Kp || Md > A.rows || Nd > B.rows) return cudaErrorInvalidValue;
   if (Md <= 0 || Nd <= 0) return cudaSuccess;
   // at least two 128 x 256 tiles per SM: the persistent kernel, whose epilogue overlaps the
@@ -395,10 +422,25 @@ cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, 
   if (tiles >= 2 * 152 && B.rows % PBN == 0) {
     const int grid = (int)std::min<int64_t>(tiles, 152);
     k_gemm_bf16x3_tc_persist<<<grid, PTHREADS, PLayoutG::SMEM_BYTES, s>>>(
-        A.map_hi, A.map_lo, B.map_hi, B.map_lo, Md, Nd, A.Kp / BK, alpha, C, ldc, err, kWaitLimitNs);
+        A.map_hi, A.map_lo, B.map_hi, B.map_lo, Md, Nd, A.Kp / BK, alpha, C, ldc, so, err,
+        kWaitLimitNs);
     return cudaGetLastError();
   }
-  return launch_tc<128, 3, float>(A, B, Md, Nd, alpha, C, ldc, err, s);
+  return launch_tc<128, 3, float>(A, B, Md, Nd, alpha, C, ldc, err, s, kWaitLimitNs, 0, so);
+}
+}  // namespace
+
+cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,
+                        float* C, int64_t ldc, int* err, cudaStream_t s) {
+  return gemm_f32_or_split(A, B, Md, Nd, alpha, C, ldc, SplitOut(), err, s);
+}
+
+cudaError_t gemm_bf16x3_split_out(const TcOperand& A, const TcOperand& B, int Md, int Nd,
+                                  float alpha, const SplitOut& so, int* err, cudaStream_t s) {
+  if (!so.hi || !so.lo || so.M < 1 || so.Mp < so.M || (int64_t)so.M * so.M != Md ||
+      so.ld < (int64_t)so.M * so.Mp)
+    return cudaErrorInvalidValue;
+  return gemm_f32_or_split(A, B, Md, Nd, alpha, nullptr, 0, so, err, s);
 }
 
 cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,

@@ -92,6 +92,11 @@ struct Ctx {
   float *psi32h = nullptr, *psi32l = nullptr;   // [N][M]  psi = psi32h + psi32l (FP32 pair)
   double* ovdet = nullptr;    // [Nw][8]  per-walker determinant factors between the overlap kernels
   uint32_t* emI_pk = nullptr; // [64][64] e^{-dt K/2} - I as split-bf16 words (tensor-core propagator)
+  // large-M tensor-core propagator (propagate_tcl.cu): V_HS as split bf16 [2][Nw][M][Mp] (written
+  // by the V_HS contraction when that propagator runs), e^{-dt K/2} - I as split bf16 [M][Mp],
+  // and their four tensor maps (A hi, A lo, E hi, E lo)
+  __nv_bfloat16 *tcl_ahi = nullptr, *tcl_alo = nullptr, *tcl_ehi = nullptr, *tcl_elo = nullptr;
+  CUtensorMap* tcl_maps = nullptr;
   float* rhobar32 = nullptr;  // [2][Nw][X]  force bias of the split-precision step (FP32 GEMM output)
   float* rho_mf32 = nullptr;  // [X]         <rho_g>_T in FP32
   int* d_tc_err = nullptr;    // set by a tensor-core kernel whose bounded wait expired
@@ -109,6 +114,17 @@ struct Ctx {
   double *drhobar = nullptr, *dU = nullptr;                      // [2][Nw][X]
   double* dAvhs = nullptr;    // [2][Nw][P]
   double *dlogO = nullptr, *dlogw = nullptr, *daux = nullptr, *deloc = nullptr, *desum = nullptr;
+  // multi-determinant trial psi_T = sum_d c_d D_d (multidet.cu; FP64); n_det = 0: one determinant
+  int n_det = 0;
+  double* md_coef = nullptr;   // [Nd]        c_d
+  double* md_psi = nullptr;    // [Nd][N][M]  columns of D_d
+  double* md_Ltil = nullptr;   // [Nd][X][N][M] rows of D_d,s^T L_g
+  double* md_htil = nullptr;   // [Nd][N][M]  rows of D_d,s^T h1
+  double* md_logO = nullptr;   // [Nd][2][Nw] log O_d (-inf: O_d = 0)
+  double* md_theta = nullptr;  // [Nd][2][Nw][N][M] Theta_d
+  double* md_share = nullptr;  // [Nd][2][Nw] w_d = c_d O_d / <psi_T|phi>
+  double* md_rhobar = nullptr; // [Nd][2][Nw][X] force bias of each determinant
+  double* md_eloc = nullptr;   // [Nd][2][Nw] local energy of each determinant
   // pair-run graph cache (owned; see pair.cu)
   void* pair_cache = nullptr;
   uint64_t uid = 0;           // unique per handle, so a cached graph never outlives its partner
@@ -144,6 +160,18 @@ cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, 
                         float* C, int64_t ldc, int* err, cudaStream_t s);
 cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, float alpha,
                         double* C, int64_t ldc, int* err, cudaStream_t s);
+// Split-BF16 output of the product C[n][m] with Md = M^2 rows m = i M + j: hi = bf16(C) and
+// lo = bf16(C - hi) stored at n * ld + i * Mp + j (Mp >= M elements per orbital row, so that the
+// rows of every matrix meet the 16-byte stride rule of a TMA descriptor); the padding entries
+// j >= M are not written.
+struct SplitOut {
+  __nv_bfloat16* hi = nullptr;
+  __nv_bfloat16* lo = nullptr;
+  int M = 0, Mp = 0;
+  int64_t ld = 0;
+};
+cudaError_t gemm_bf16x3_split_out(const TcOperand& A, const TcOperand& B, int Md, int Nd,
+                                  float alpha, const SplitOut& so, int* err, cudaStream_t s);
 cudaError_t prepare_tc_kernels();
 cudaError_t gemm_bf16x3_wait_selftest(const TcOperand& A, const TcOperand& B, int Md, int Nd,
                                       float* C, int64_t ldc, int* err, uint64_t wait_ns,
@@ -177,11 +205,22 @@ bool propagate_tc_ok(const Ctx& c);
 cudaError_t prepare_propagate_tc();
 cudaError_t pack_propagate_tc(const Ctx& c, uint32_t* emI_pk, cudaStream_t s);
 cudaError_t launch_propagate_tc(const Ctx& c, double* out, float* out32, cudaStream_t s);
-// Propagation variants of the split-precision step: 3 tensor-core kernel, 2 fused FP32 kernel,
-// 1 / 0 two FP32 GEMMs around a Taylor kernel with A in shared memory / through L1.  The
-// effective variant is the tuned one, else the first the shape supports in that order.
+// large-M tensor-core propagator (propagate_tcl.cu), M <= 256 and N <= 32: reads V_HS in the
+// split form c.tcl_ahi / c.tcl_alo (rows of Mp = propagate_tcl_mp(M) elements)
+bool propagate_tcl_ok(const Ctx& c);
+int propagate_tcl_mp(int M);
+cudaError_t prepare_propagate_tcl();
+cudaError_t setup_propagate_tcl(Ctx& c, cudaStream_t s);
+cudaError_t launch_propagate_tcl(const Ctx& c, double* out, float* out32, cudaStream_t s);
+// Propagation variants of the split-precision step: 4 large-M tensor-core kernel, 3 tensor-core
+// kernel (M <= 64, N <= 16), 2 fused FP32 kernel, 1 / 0 two FP32 GEMMs around a Taylor kernel
+// with A in shared memory / through L1.  The effective variant is the tuned one, else the
+// first the shape supports in the order 3, 4, 2, 1, 0.  Variant 4 reads V_HS in its split form,
+// the others in FP32 (c.Avhs32): vhs_launch writes the form the variant reads.
 int propagation_variant(const Ctx& c);
-// Phi' of every walker from c.phi and c.Avhs32 into out (FP64); variants 2 and 3 also write
+// V_HS of every walker from the split coefficients c.tc_U, in the form variant `pv` reads
+cudaError_t vhs_launch(const Ctx& c, int pv, cudaStream_t s);
+// Phi' of every walker from c.phi and V_HS into out (FP64); variants 2, 3 and 4 also write
 // the FP32 copy out32 (may be null), variants 0 and 1 use c.phi32 as scratch
 cudaError_t launch_propagation(const Ctx& c, int variant, double* out, float* out32, cudaStream_t s);
 // tensor-core local energy (energy_tc.cu)
@@ -259,10 +298,19 @@ cudaError_t launch_seed_weights(const Ctx& A, const Ctx& B, cudaStream_t s);
 afqmc_status frechet_expm(Ctx* h, const double* dir, double scale, double* out, cudaStream_t s);
 inline int pad64(int k) { return (k + 63) / 64 * 64; }
 
-enum OverlapMode { OV_REFRESH = 0, OV_UPDATE = 1 };
+// OV_DET: overlap, log det and Theta of every determinant of a multi-determinant trial from
+// src (or the current walkers when src is null), with no weight update and no walker killed
+enum OverlapMode { OV_REFRESH = 0, OV_UPDATE = 1, OV_DET = 2 };
 cudaError_t prepare_kernels(const Ctx& c);
 cudaError_t launch_overlap(const Ctx& c, const double* src, int mode, cudaStream_t s,
                            int n_walkers = -1);
+// multi-determinant trial (multidet.cu, FP64): log O_d and Theta_d of every determinant
+// (walker_kernels.cu), the overlap update or refresh with the shares w_d, the force bias and
+// the local energy as share-weighted sums over the determinants
+cudaError_t launch_overlap_dets(const Ctx& c, const double* src, cudaStream_t s);
+cudaError_t md_overlap(const Ctx& c, const double* src, int mode, cudaStream_t s);
+cudaError_t md_force_bias(const Ctx& c, cudaStream_t s);
+cudaError_t md_energy(const Ctx& c, cudaStream_t s);
 cudaError_t launch_fields(const Ctx& c, const double* fields, cudaStream_t s);
 cudaError_t launch_taylor(const Ctx& c, double* phi_io, cudaStream_t s);
 cudaError_t launch_mgs(const Ctx& c, cudaStream_t s);

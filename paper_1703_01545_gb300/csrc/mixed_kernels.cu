@@ -704,16 +704,32 @@ cudaError_t launch_energy_tiled(const Ctx& c, const float* theta32, const float*
 
 bool energy_variant_ok(const Ctx& c, int wb) { return energy_wb_ok(c, wb); }
 bool taylor_variant_ok(const Ctx& c, int v) {
-  return v == 3 ? propagate_tc_ok(c) : v == 2 ? propagate_f32_ok(c) : v == 1 ? taylor_smem_ok(c) : v == 0;
+  return v == 4 ? (propagate_tcl_ok(c) && c.tcl_maps != nullptr)
+       : v == 3 ? propagate_tc_ok(c) : v == 2 ? propagate_f32_ok(c) : v == 1 ? taylor_smem_ok(c) : v == 0;
 }
 
 int propagation_variant(const Ctx& c) {
   if (c.tune_taylor_smem >= 0 && taylor_variant_ok(c, c.tune_taylor_smem)) return c.tune_taylor_smem;
-  for (int v : {3, 2, 1}) if (taylor_variant_ok(c, v)) return v;
+  for (int v : {3, 4, 2, 1}) if (taylor_variant_ok(c, v)) return v;
   return 0;
 }
 
+cudaError_t vhs_launch(const Ctx& c, int pv, cudaStream_t s) {
+  const int64_t MM = (int64_t)c.M * c.M;
+  if (pv == 4) {
+    SplitOut so;
+    so.hi = c.tcl_ahi;
+    so.lo = c.tcl_alo;
+    so.M = c.M;
+    so.Mp = propagate_tcl_mp(c.M);
+    so.ld = (int64_t)c.M * so.Mp;
+    return gemm_bf16x3_split_out(*c.tc_L, *c.tc_U, (int)MM, 2 * c.Nw, 1.0f, so, c.d_tc_err, s);
+  }
+  return gemm_bf16x3(*c.tc_L, *c.tc_U, (int)MM, 2 * c.Nw, 1.0f, c.Avhs32, MM, c.d_tc_err, s);
+}
+
 cudaError_t launch_propagation(const Ctx& c, int variant, double* out, float* out32, cudaStream_t s) {
+  if (variant == 4) return launch_propagate_tcl(c, out, out32, s);
   if (variant == 3) return launch_propagate_tc(c, out, out32, s);
   if (variant == 2) return launch_propagate_f32(c, out, out32, s);
   const int M = c.M, cols = 2 * c.Nw * c.N;

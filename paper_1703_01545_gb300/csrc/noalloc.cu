@@ -41,13 +41,17 @@ cudaError_t scratch_for_current_device(void** out) {
   return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// Device memory of device `dev` (managed memory is reachable from every device).  A buffer
+// on another GPU is refused: the kernels would read it over the peer link, or fault without
+// peer access.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // caller layout phi[2][Nw][M][N] (walkers w0..w0+c) -> internal [2][c][N][M]
@@ -63,13 +67,15 @@ __global__ void k_chunk_to_internal(const double* __restrict__ phi, double* __re
   }
 }
 
-// internal eloc[2][c] -> caller e_local[2][Nw] at walkers w0..w0+c
-__global__ void k_chunk_energy_out(const double* __restrict__ el, double* __restrict__ out,
-                                   int Nw, int w0, int c) {
+// internal eloc[2][c] -> caller e_local[2][Nw] at walkers w0..w0+c; a walker the overlap
+// refresh killed (singular or non-finite overlap: it has no Green's function) gets NaN
+__global__ void k_chunk_energy_out(const double* __restrict__ el, const int* __restrict__ alive,
+                                   double* __restrict__ out, int Nw, int w0, int c) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= c) return;
-  out[w0 + k] = el[k];
-  out[(int64_t)Nw + w0 + k] = el[c + k];
+  const bool ok = alive[k] != 0;
+  out[w0 + k] = ok ? el[k] : NAN;
+  out[(int64_t)Nw + w0 + k] = ok ? el[c + k] : NAN;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -86,17 +92,20 @@ extern "C" afqmc_status afqmc_local_energy_static(const double* h1, const double
   if (M < 1 || X < 1 || n_up < 0 || n_dn < 0 || N < 1 || n_up > M || n_dn > M || n_up > 32 ||
       n_dn > 32 || (int64_t)N * M > 4096 || n_walkers < 1)
     return AFQMC_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return AFQMC_ERR_CUDA;
   for (const void* p : {(const void*)h1, (const void*)L, (const void*)trial, (const void*)phi,
                         (const void*)e_local})
-    if (!on_device(p)) return AFQMC_ERR_ARG;
+    if (!on_device(p, dev)) return AFQMC_ERR_ARG;
   // fixed part: psi [N][M], Ltil [X][N][M], htil [N][M], flags
   const size_t NM = (size_t)N * M;
   const size_t fixed = align256(NM * 8) + align256((size_t)X * NM * 8) + align256(NM * 8) + 256;
-  // per walker: phi, theta [2][N][M]; logO, w, eloc [2]; aux [4]; alive
-  const size_t per_w = 4 * NM * 8 + 10 * 8 + 4;
-  if (fixed + per_w + 6 * 256 > kStaticScratchBytes) return AFQMC_ERR_ARG;
+  // per walker: phi, theta [2][N][M]; logO, w, eloc [2]; aux [4]; alive.  The seven
+  // per-walker buffers are each rounded up to 256 bytes, so 7 * 256 bytes of slack suffice.
+  const size_t per_w = 4 * NM * 8 + 10 * 8 + 4, slack = 7 * 256;
+  if (fixed + per_w + slack > kStaticScratchBytes) return AFQMC_ERR_ARG;
   const int chunk = (int)std::min<size_t>((size_t)n_walkers,
-                                          (kStaticScratchBytes - fixed - 6 * 256) / per_w);
+                                          (kStaticScratchBytes - fixed - slack) / per_w);
   void* base = nullptr;
   if (scratch_for_current_device(&base) != cudaSuccess) return AFQMC_ERR_CUDA;
   unsigned char* p = static_cast<unsigned char*>(base);
@@ -141,7 +150,8 @@ extern "C" afqmc_status afqmc_local_energy_static(const double* h1, const double
     if (e == cudaSuccess) e = afq::launch_overlap(c, nullptr, afq::OV_REFRESH, s);
     if (e == cudaSuccess) e = afq::launch_energy(c, s);
     if (e == cudaSuccess) {
-      k_chunk_energy_out<<<(cw + 255) / 256, 256, 0, s>>>(c.eloc, e_local, n_walkers, w0, cw);
+      k_chunk_energy_out<<<(cw + 255) / 256, 256, 0, s>>>(c.eloc, c.alive, e_local, n_walkers,
+                                                           w0, cw);
       e = cudaGetLastError();
     }
   }

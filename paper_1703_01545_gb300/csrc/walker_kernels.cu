@@ -40,6 +40,9 @@ struct OverlapArgs {
   int* flags;
   int M, N, n_up, Nw, mode, free_proj;
   double log_shift;    // -dt (C - E_T)
+  // mode OV_DET (determinants of a multi-determinant trial, grid row blockIdx.y = d): psi,
+  // theta and logO of determinant d start d * det_* elements on; 0 for a single determinant
+  int64_t det_psi, det_theta, det_logO;
 };
 
 // MIXED: Theta = Phi O^{-1} is formed in FP32 (O, its inverse and log det stay FP64) and
@@ -56,8 +59,12 @@ __global__ void __launch_bounds__(kThreads) k_overlap(OverlapArgs a) {
   __shared__ int s_piv, s_bad;
 
   const bool live = a.alive[wk] != 0;
+  // OV_DET: overlap, log det and Theta of determinant blockIdx.y only (no weight update)
+  const double* psi_d = a.psi + blockIdx.y * a.det_psi;
+  double* theta_d = a.theta + blockIdx.y * a.det_theta;
+  double* logO_d = a.logO + blockIdx.y * a.det_logO;
   const bool upd = (a.mode == OV_UPDATE) && live;
-  const double* src = upd ? a.src : a.phi;
+  const double* src = (upd || (a.mode == OV_DET && a.src)) ? a.src : a.phi;
   const int64_t plane = (int64_t)a.Nw * N * M;
   const int64_t wbase = (int64_t)wk * N * M;
   if (tid == 0) { s_ld[0] = 0.0; s_ld[1] = 0.0; s_bad = 0; }
@@ -78,7 +85,7 @@ __global__ void __launch_bounds__(kThreads) k_overlap(OverlapArgs a) {
       const int r = e / w2, c = e % w2;
       double re = 0, im = 0;
       if (c < ns) {
-        const double* pr = a.psi + (int64_t)(n0 + r) * M;
+        const double* pr = psi_d + (int64_t)(n0 + r) * M;
         const double* fr = ph + c * M;
         const double* fi = ph + nmax * M + c * M;
         for (int i = 0; i < M; ++i) {
@@ -180,8 +187,8 @@ __global__ void __launch_bounds__(kThreads) k_overlap(OverlapArgs a) {
             re = fma(xr, orr, fma(-xi, oi, re));
             im = fma(xr, oi, fma(xi, orr, im));
           }
-        a.theta[gi] = re;
-        a.theta[plane + gi] = im;
+        theta_d[gi] = re;
+        theta_d[plane + gi] = im;
       }
       if (upd) {
         a.phi[gi] = ph[b * M + i];
@@ -194,6 +201,11 @@ __global__ void __launch_bounds__(kThreads) k_overlap(OverlapArgs a) {
   const bool bad = s_bad != 0;
   const double ld_re = s_ld[0], ld_im = s_ld[1];
   if (bad || !isfinite(ld_re) || !isfinite(ld_im)) {
+    if (a.mode == OV_DET) {            // this determinant contributes nothing to the trial
+      logO_d[wk] = -INFINITY;
+      logO_d[a.Nw + wk] = 0.0;
+      return;
+    }
     atomicAdd(a.flags, 1);
     if (upd || a.mode == OV_REFRESH) {
       a.w[wk] = 0.0;
@@ -203,8 +215,8 @@ __global__ void __launch_bounds__(kThreads) k_overlap(OverlapArgs a) {
     return;
   }
   if (!upd) {
-    a.logO[wk] = ld_re;
-    a.logO[a.Nw + wk] = ld_im;
+    logO_d[wk] = ld_re;
+    logO_d[a.Nw + wk] = ld_im;
     return;
   }
   const double* x = a.aux + 4 * (int64_t)wk;
@@ -619,12 +631,24 @@ cudaError_t launch_overlap(const Ctx& c, const double* src, int mode, cudaStream
   a.M = c.M; a.N = c.N; a.n_up = c.n_up; a.Nw = c.Nw; a.mode = mode;
   a.free_proj = c.opt.mode == AFQMC_FREE;
   a.log_shift = -c.opt.dt * (c.c_mf - c.e_trial);
-  const int nmax = c.n_up > c.N - c.n_up ? c.n_up : c.N - c.n_up;
+  a.det_psi = a.det_theta = a.det_logO = 0;
   const size_t smem = smem_overlap(c);
-  (void)nmax;
   const int grid = n_walkers > 0 ? n_walkers : c.Nw;
   if (c.theta32 && c.tc_Theta) k_overlap<true><<<grid, kThreads, smem, s>>>(a);
   else k_overlap<false><<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_overlap_dets(const Ctx& c, const double* src, cudaStream_t s) {
+  if (c.n_det < 1 || c.n_det > 65535) return cudaErrorInvalidValue;
+  OverlapArgs a = {};
+  a.src = src; a.phi = c.phi; a.alive = c.alive; a.aux = c.aux; a.flags = c.d_flags;
+  a.psi = c.md_psi; a.theta = c.md_theta; a.logO = c.md_logO; a.w = c.w;
+  a.M = c.M; a.N = c.N; a.n_up = c.n_up; a.Nw = c.Nw; a.mode = OV_DET;
+  a.det_psi = (int64_t)c.N * c.M;
+  a.det_theta = 2 * (int64_t)c.Nw * c.N * c.M;
+  a.det_logO = 2 * (int64_t)c.Nw;
+  k_overlap<false><<<dim3(c.Nw, c.n_det), kThreads, smem_overlap(c), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -104,6 +104,8 @@ def test_setup_rejects_bad_arguments_without_a_device(lib):
     bad.independent_fields = 2
     assert call(opt=bad) == 1
     assert lib.afqmc_setup(None, None, None, None, 1, 1, 1, 0, None, None) == 1
+    assert lib.afqmc_setup_multidet(None, None, None, None, None, 1, None, 1, 1, 1, 0, None,
+                                    None) == 1
     assert lib.afqmc_destroy(None) == 0
     assert lib.afqmc_pair_delta_E(None, None, 5, 5, 5, 0.0, None, None, None, None, None) == 1
     assert lib.afqmc_pair_graph_kernels(None, None) == 1

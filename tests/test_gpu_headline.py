@@ -1,0 +1,129 @@
+"""The M=128 correlated pair at full size (Nchol=768, neutral 16/16 against ion 16/15, 4096
+walkers per system, dt=0.005, 11 repeats): both precisions against the FP64 oracle.
+
+The oracle follows sampled pair indices k exactly through 50 steps (Gram-Schmidt every 5 steps,
+the shared Philox field stream of Sec. II.B), so every walker it follows is compared element by
+element with the same walker on the GPU.
+
+* FP64 path: 1e-9 relative on weights, local energies and determinants (the parity bar).
+* Split-precision path, with each kernel variant forced in turn: within the split arithmetic's
+  accumulated error.  A tensor-core product carries ~2^-16 relative error (split BF16, FP32
+  accumulation) and Theta is FP32; over 50 steps the measured per-walker errors at the M=64
+  shapes are ~1e-5 on E_L and ~1e-4 on w, so the bars are 1e-4 on E_L and 1e-3 on w and Phi:
+  ten times the measured error, and a hundred times tighter than an error of the size of one
+  unsplit BF16 rounding would give.
+The measured errors are written as JSON to the directory named by AFQMC_REPORT_DIR, when set.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu, system_data
+from oracle import afqmc as orc
+from synthetic import CONFIGS
+
+pytestmark = pytest.mark.gpu
+CFG = CONFIGS["C3"]
+SEED, R, STEPS = 1, 11, 50
+SAMPLE = np.array([0, 1, 977, 2048, 4094, 4095])
+OUT = os.environ.get("AFQMC_REPORT_DIR", "")
+REPORT = {}
+
+
+def dump():
+    if OUT and os.path.isdir(OUT):
+        with open(os.path.join(OUT, "headline_errors.json"), "w") as f:
+            json.dump(REPORT, f, indent=1)
+
+
+@pytest.fixture(scope="module")
+def data():
+    need_gpu()                     # skip before the oracle's reference run when there is no GPU
+    return [system_data("C3", w, "moderate") for w in ("A", "B")]
+
+
+@pytest.fixture(scope="module")
+def reference(data):
+    """The oracle's pair run on the sampled pair indices: walkers and E_L after 50 steps."""
+    osys = [orc.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], CFG["dt"])
+            for d in data]
+    ref = orc.run_pair(osys[0], osys[1], CFG["n_walkers"], STEPS, seed=SEED, energy_every=STEPS,
+                       walker_index=SAMPLE, n_repeats=R, record_walkers=True)
+    return [(ref["walkers"][i], ref["records"][i][-1]["eloc"]) for i in range(2)]
+
+
+def run_gpu(afq, data, precision, taylor=None, energy=None):
+    gpu = [afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=CFG["dt"],
+                      n_walkers=CFG["n_walkers"], seed=SEED, n_repeats=R, precision=precision)
+           for d in data]
+    for g in gpu:
+        if taylor is not None:
+            g.select_kernel(afq.K_TAYLOR, taylor)
+        if energy is not None:
+            g.select_kernel(afq.K_EXCHANGE, energy)
+    res = afq.pair_delta_E(gpu[0], gpu[1], STEPS, 5, 5, raise_on_dead=False)
+    out = []
+    for g in gpu:
+        st = g.state()
+        el, _, _ = g.energy()
+        out.append((st, el))
+        g.close()
+    return res, out
+
+
+def errors(st, el, wk, el_o):
+    """Largest relative errors over the sampled walkers alive on both sides."""
+    live = wk.alive & st["alive"][SAMPLE]
+    scale = np.abs(wk.phi).max(axis=(1, 2))
+    phi = (np.abs(st["phi"][SAMPLE] - wk.phi).max(axis=(1, 2)) / scale)[live]
+    w = (np.abs(st["w"].real[SAMPLE] - wk.w.real) / np.abs(wk.w.real))[live]
+    e = (np.abs(el[SAMPLE] - el_o) / np.abs(el_o))[live]
+    return dict(phi=float(phi.max()), w=float(w.max()), E_L=float(e.max()),
+                alive_both=int(live.sum()), alive_oracle=int(wk.alive.sum()))
+
+
+def test_full_size_pair_fp64(data, reference):
+    afq = need_gpu()
+    res, out = run_gpu(afq, data, afq.FP64)
+    assert np.all(np.isfinite(res["E"]))
+    for (st, el), (wk, el_o) in zip(out, reference):
+        assert np.array_equal(st["alive"][SAMPLE], wk.alive)
+        err = errors(st, el, wk, el_o)
+        REPORT.setdefault("fp64", []).append(err)
+        dump()
+        assert err["phi"] < 1e-9 and err["w"] < 1e-9 and err["E_L"] < 1e-9, err
+        d = np.exp(st["logO"][SAMPLE][wk.alive] - wk.logO[wk.alive]) - 1
+        assert np.abs(d).max() < 1e-9
+
+
+# propagation variants at M=128 (select_kernel K_TAYLOR): 4 tensor cores (V_HS streamed as split
+# BF16), 2 the fused FP32 kernel, 1 / 0 two FP32 GEMMs around the Taylor kernel with A in shared
+# memory / through L1; the local energy on the tensor cores (K_EXCHANGE 0) or the FP32 kernel
+# with 4 walkers per CTA
+VARIANTS = [(4, 0), (2, 0), (1, 0), (0, 4)]
+
+
+@pytest.mark.parametrize("taylor,energy", VARIANTS)
+def test_full_size_pair_split_precision(data, reference, taylor, energy):
+    afq = need_gpu()
+    res, out = run_gpu(afq, data, afq.BF16X3, taylor=taylor, energy=energy)
+    assert np.all(np.isfinite(res["E"]))
+    for i, ((st, el), (wk, el_o)) in enumerate(zip(out, reference)):
+        err = errors(st, el, wk, el_o)
+        REPORT[f"split_taylor{taylor}_energy{energy}_{'AB'[i]}"] = err
+        dump()
+        # a walker may sit on the cos cut within rounding; none of the sample should
+        assert err["alive_both"] == err["alive_oracle"], err
+        assert err["E_L"] < 1e-4 and err["w"] < 1e-3 and err["phi"] < 1e-3, err
+
+
+def test_split_precision_rejects_unsupported_variants(data):
+    afq = need_gpu()
+    d = data[0]
+    g = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=CFG["dt"], n_walkers=64,
+                   precision=afq.BF16X3)
+    with pytest.raises(afq.AfqmcError):
+        g.select_kernel(afq.K_TAYLOR, 3)     # the M <= 64 tensor-core propagator
+    g.close()

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from gpu_util import need_gpu, system_data
-from synthetic import CONFIGS, explicit_fields
+from synthetic import make_hamiltonian, scf_trial, CONFIGS, explicit_fields
 
 pytestmark = pytest.mark.gpu
 
@@ -74,17 +74,28 @@ def test_tensor_core_propagator_matches_fp32(cfg, which, coupling, nw):
 
 
 def test_tensor_core_propagator_refuses_large_shapes():
+    """Variant 3 takes M <= 64 and N <= 16, variant 4 M <= 256 and N <= 32."""
     afq = need_gpu()
     d = system_data("C5", "A", "moderate")
     s = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=0.005, n_walkers=8,
                    precision=afq.BF16X3, autotune=False)
     with pytest.raises(RuntimeError):
         s.select_kernel(afq.K_TAYLOR, 3)
+    s.select_kernel(afq.K_TAYLOR, 4)            # M = 96, 12 + 12 columns
+    assert s.info().tuned_taylor_smem == 4
     s.close()
+    h1, L = make_hamiltonian(40, 8, 5)
+    tr, _, _ = scf_trial(h1, L, 17, 17)
+    big = afq.System(h1, L, tr, 17, 17, dt=0.005, n_walkers=4, precision=afq.BF16X3,
+                     autotune=False)
+    with pytest.raises(RuntimeError):
+        big.select_kernel(afq.K_TAYLOR, 4)       # 34 occupied columns
+    big.close()
 
 
-def test_dead_walkers_keep_their_state_with_in_place_propagation():
-    """The tensor-core propagator writes live walkers in place and skips dead ones (killed by the
+@pytest.mark.parametrize("variant", [3, 4])
+def test_dead_walkers_keep_their_state_with_in_place_propagation(variant):
+    """The tensor-core propagators write live walkers in place and skip dead ones (killed by the
     cos cut, Sec. II.B): a dead walker's Phi and weight stay bit for bit as they were, and the
     mixed energy stays finite."""
     afq = need_gpu()
@@ -92,7 +103,7 @@ def test_dead_walkers_keep_their_state_with_in_place_propagation():
     nw = 64
     s = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=0.1, n_walkers=nw,
                    precision=afq.BF16X3, fb_cap=0.3, autotune=False)
-    s.select_kernel(afq.K_TAYLOR, 3)
+    s.select_kernel(afq.K_TAYLOR, variant)
     fields = explicit_fields(30, nw, d["X"], seed=41)
     s.propagate(20, fields[:20])
     s.orthonormalise()

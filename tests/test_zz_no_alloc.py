@@ -67,3 +67,46 @@ def test_static_energy_rejects_oversize_and_host_pointers():
     host = np.zeros(16)
     hp = ctypes.c_void_p(host.ctypes.data)
     assert lib.afqmc_local_energy_static(hp, p, p, p, d["M"], d["X"], 2, 2, 1, p, None) == 1
+
+
+def test_static_energy_marks_singular_walkers():
+    """A walker with a zero column has an exactly singular overlap (Eq. 6's Green's function
+    does not exist): its entries come back NaN, every other walker as before."""
+    afq = need_gpu()
+    import torch
+    from paper_1703_01545_gb300 import _lib
+    lib = _lib.load()
+    d = system_data("C1", "A")
+    nw, bad = 24, 5
+    s = afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=0.01, n_walkers=nw,
+                   seed=9)
+    s.propagate(4)
+    st = s.state()
+    want, _, _ = s.energy()
+    s.close()
+    phi = np.stack([st["phi"].real, st["phi"].imag])
+    phi[:, bad, :, 1] = 0.0                     # walker `bad`: spin-up column 1 set to zero
+    phi_dev = torch.from_numpy(np.ascontiguousarray(phi)).cuda()
+    out = torch.zeros(2 * nw, dtype=torch.float64, device="cuda")
+    assert _call(lib, d, phi_dev, nw, out, torch) == 0
+    got = out.cpu().numpy()
+    got = got[:nw] + 1j * got[nw:]
+    assert np.isnan(got[bad].real) and np.isnan(got[bad].imag)
+    keep = np.arange(nw) != bad
+    assert np.max(np.abs(got[keep] - want[keep]) / np.abs(want[keep])) < TOL
+
+
+def test_static_energy_rejects_another_devices_memory():
+    """Buffers on a GPU other than the current one are refused before any launch."""
+    need_gpu()
+    import torch
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one visible GPU")
+    from paper_1703_01545_gb300 import _lib
+    lib = _lib.load()
+    d = system_data("C1", "A")
+    here = torch.zeros(4096, dtype=torch.float64, device="cuda:0")
+    there = torch.zeros(4096, dtype=torch.float64, device="cuda:1")
+    p, q = ctypes.c_void_p(here.data_ptr()), ctypes.c_void_p(there.data_ptr())
+    with torch.cuda.device(0):
+        assert lib.afqmc_local_energy_static(p, p, p, q, d["M"], d["X"], 2, 2, 4, p, None) == 1
