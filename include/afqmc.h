@@ -88,10 +88,16 @@ typedef struct {
   int tuned_energy_walkers_per_cta; /* local-energy kernel of the split-precision step: 0 =
                                        tensor cores, 2/4/8 = FP32 kernel with that many walkers
                                        per CTA, -1 = not tuned (tensor cores where supported) */
-  int tuned_taylor_smem;            /* propagation variant of the split-precision step: 3 =
-                                       tensor cores, 2 = fused FP32 kernel, 1 / 0 = Taylor
+  int tuned_taylor_smem;            /* propagation variant of the split-precision step: 4 =
+                                       tensor cores with V_HS streamed (M <= 256), 3 = tensor
+                                       cores (M <= 64), 2 = fused FP32 kernel, 1 / 0 = Taylor
                                        kernel with A in shared memory / through L1, -1 = not
                                        tuned */
+  int tuned_orthonormalise;         /* orthonormalisation of the split-precision step: 1 =
+                                       Cholesky QR, 0 = modified Gram-Schmidt kernels, -1 = not
+                                       tuned (Gram-Schmidt)                                  */
+  int n_det;                        /* determinants of a multi-determinant trial; 0 for a
+                                       single-determinant trial                             */
 } afqmc_info;
 
 /* Fill *o with dt = 0.01, n_walkers = 128, taylor_order = 6, FP64, phaseless,
@@ -381,10 +387,15 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms,
  * the variant of a tunable kernel of the split-precision step, overriding the autotuner.
  *   which AFQMC_K_EXCHANGE: variant 0 = tensor-core local energy, 2 / 4 / 8 = FP32 kernel
  *                           with that many walkers per CTA;
- *   which AFQMC_K_TAYLOR:   the propagation e^{-dt K/2} e^A e^{-dt K/2}: variant 3 = split-BF16
- *                           tensor-core kernel (M <= 64, N <= 16), 2 = one fused FP32 kernel
- *                           per walker, 0 / 1 = two FP32 GEMMs around a Taylor kernel reading A
- *                           through L1 (0) or from shared memory (1).
+ *   which AFQMC_K_TAYLOR:   the propagation e^{-dt K/2} e^A e^{-dt K/2}: variant 4 = split-BF16
+ *                           tensor-core kernel over V_HS streamed as split BF16 by TMA
+ *                           (M <= 256, N <= 32), 3 = split-BF16 tensor-core kernel (M <= 64,
+ *                           N <= 16), 2 = one fused FP32 kernel per walker, 0 / 1 = two FP32
+ *                           GEMMs around a Taylor kernel reading A through L1 (0) or from
+ *                           shared memory (1);
+ *   which AFQMC_K_MGS:      the orthonormalisation: 1 = Cholesky QR (Gram matrix in FP32
+ *                           pairs, R and log det R in FP64, Q in FP32), 0 = modified
+ *                           Gram-Schmidt in FP64.
  * The choice shows in afqmc_get_info.  Errors: ARG (FP64 handle, unknown kernel, or a
  * variant this shape does not support).
  */

@@ -24,7 +24,8 @@ class AfqmcInfo(ctypes.Structure):
                 ("n_dn", ctypes.c_int), ("n_walkers", ctypes.c_int), ("n_repeats", ctypes.c_int),
                 ("step", ctypes.c_uint64), ("e_trial", ctypes.c_double),
                 ("c_mf", ctypes.c_double), ("n_alive", ctypes.c_int),
-                ("tuned_energy_walkers_per_cta", ctypes.c_int), ("tuned_taylor_smem", ctypes.c_int)]
+                ("tuned_energy_walkers_per_cta", ctypes.c_int), ("tuned_taylor_smem", ctypes.c_int),
+                ("tuned_orthonormalise", ctypes.c_int), ("n_det", ctypes.c_int)]
 
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "numerical failure",

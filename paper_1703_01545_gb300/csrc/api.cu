@@ -772,6 +772,8 @@ afqmc_status afqmc_get_info(afqmc_handle h, afqmc_info* info, cudaStream_t s) {
   info->e_trial = h->e_trial; info->c_mf = h->c_mf;
   info->tuned_energy_walkers_per_cta = h->tune_energy_wb;
   info->tuned_taylor_smem = h->tune_taylor_smem;
+  info->tuned_orthonormalise = h->tune_mgs;
+  info->n_det = h->n_det;
   std::vector<int> al(h->Nw);
   AFQ_CK(cudaMemcpyAsync(al.data(), h->alive, sizeof(int) * h->Nw, cudaMemcpyDeviceToHost, s));
   AFQ_CK(cudaStreamSynchronize(s));
@@ -1099,6 +1101,12 @@ afqmc_status afqmc_select_kernel(afqmc_handle h, int which, int variant) {
                                        afq::energy_variant_ok(*h, variant);
     if (!ok) return set_err(h, AFQMC_ERR_ARG, "local-energy variant unsupported for this shape");
     h->tune_energy_wb = variant;
+    return AFQMC_OK;
+  }
+  if (which == AFQMC_K_MGS) {
+    if (variant != 0 && !(variant == 1 && afq::mgs_chol_ok(*h)))
+      return set_err(h, AFQMC_ERR_ARG, "orthonormalisation variant unsupported for this shape");
+    h->tune_mgs = variant;
     return AFQMC_OK;
   }
   if (which == AFQMC_K_TAYLOR) {

@@ -82,7 +82,8 @@ float time_variant(F launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
 cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto cache = load(cache_path);
-  const std::string ke = key_of(c, "energy_v2"), kt = key_of(c, "propagate_v3");
+  const std::string ke = key_of(c, "energy_v2"), kt = key_of(c, "propagate_v3"),
+                    km = key_of(c, "orthonormalise_v1");
   bool dirty = false;
   cudaEvent_t e0, e1;
   cudaError_t err = cudaEventCreate(&e0);
@@ -122,6 +123,22 @@ cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s) {
       if (t < best) { best = t; c.tune_taylor_smem = v; }
     }
     cache[kt] = c.tune_taylor_smem;
+    dirty = true;
+  }
+  if (cache.count(km) && (cache[km] == 0 || mgs_chol_ok(c))) {
+    c.tune_mgs = cache[km];
+  } else {
+    // Cholesky QR (1) against the Gram-Schmidt kernels (0), on walkers that are orthonormal
+    // already (the trial at setup), so the timing changes them only by rounding; log O is not
+    // touched
+    float best = 1e30f;
+    for (int v : {1, 0}) {
+      if (v == 1 && !mgs_chol_ok(c)) continue;
+      c.tune_mgs = v;
+      const float t = time_variant([&]() { return launch_mgs_warp(c, s, false); }, s, e0, e1);
+      if (t < best) { best = t; cache[km] = v; }
+    }
+    c.tune_mgs = cache[km];
     dirty = true;
   }
   cudaEventDestroy(e0);

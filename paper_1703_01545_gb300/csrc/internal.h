@@ -104,6 +104,7 @@ struct Ctx {
   // autotuned variants (autotune.cpp); -1 = not tuned, use the default
   int tune_energy_wb = -1;    // local energy: 0 tensor cores, else walkers per CTA of the FP32 kernel (2, 4, 8)
   int tune_taylor_smem = -1;  // propagation: 2 fused kernel; Taylor kernel with A in shared memory (1) or L1 (0)
+  int tune_mgs = -1;          // orthonormalisation: 1 Cholesky QR, 0 modified Gram-Schmidt kernels
   // tangent mode (tangent.cu): derivative along h1 -> h1 + lambda P, FP64 path only
   bool tangent_on = false;
   double* Bneg = nullptr;     // [M][M]  -dt K / 2 (kept from setup)
@@ -240,6 +241,7 @@ cudaError_t launch_overlap_fast(const Ctx& c, const double* src, int mode, cudaS
                                 const float* src32 = nullptr, bool with_weights = true);
 // update_logO: subtract log det R (the column norms) from log O instead of recomputing it
 cudaError_t launch_mgs_warp(const Ctx& c, cudaStream_t s, bool update_logO = false);
+bool mgs_chol_ok(const Ctx& c);
 cudaError_t launch_fields_mixed(const Ctx& c, const double* fields, cudaStream_t s);
 // tangent mode (tangent.cu)
 bool tangent_fits(const Ctx& c);

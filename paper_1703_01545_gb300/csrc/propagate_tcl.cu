@@ -45,8 +45,7 @@ using namespace tc;
 
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kTile = 128 * 64 * 2;       // one 128-row x 64-K bf16 tile, 128-byte swizzle
-constexpr int kThreads = 192;
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 12;
 
 __device__ __forceinline__ uint32_t sw128_off(int r, int k) {
   return (uint32_t)(r * 128 + ((((k >> 3) ^ r) & 7) << 4) + ((k & 7) << 1));
@@ -74,11 +73,25 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
       : "memory");
 }
 
+// L2 prefetch hint over the 16-byte-aligned interior of [p, p + bytes) (the bulk prefetch needs a
+// 16-byte-aligned address and size)
+__device__ __forceinline__ void prefetch_l2(const void* p, uint64_t bytes) {
+  const uint64_t a = reinterpret_cast<uint64_t>(p);
+  const uint64_t lo = (a + 15) & ~uint64_t(15), hi = (a + bytes) & ~uint64_t(15);
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo))
+                 : "memory");
+}
+
 // Static shape of one launch (host-computed).
 struct TclShape {
+  const __nv_bfloat16 *ahi, *alo;   // V_HS split planes [2][Nw][M][Mp] (L2 prefetch of the next walker)
+  int Mp;                // elements per orbital row of the split planes
   int M, N, Np, n2;      // orbitals, occupied columns, N rounded up to 8, MMA N = 2 Np
   int MT, KB;            // 128-row tiles of orbitals, 64-wide K blocks
   int nst;               // ring stages
+  int resident;          // 1: A of a walker held in shared memory for all its Taylor rounds
+  int ares_off;          // resident A region: 4 KB tiles (A_re hi, lo, A_im hi, lo per K block)
   int bkb;               // bytes of one K block of the term operand (3 Np rows x 128 bytes)
   int dcol;              // TMEM column stride between tiles (D and S regions)
   uint32_t tcols;        // TMEM columns allocated
@@ -90,7 +103,8 @@ struct TclShape {
 // Tiles of a round, in order: for each row tile t and K block kb: E hi, E lo (one-body) or
 // A_re hi, A_re lo, A_im hi, A_im lo (Taylor).
 
-__global__ void __launch_bounds__(kThreads, 1)
+template <int EPI>
+__global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
     k_propagate_tcl(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
                     const __grid_constant__ CUtensorMap tmEhi, const __grid_constant__ CUtensorMap tmElo,
                     const TclShape sh, const double* phi_in, double* phi_out,
@@ -103,7 +117,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kMaxStages);
   const uint32_t dfull = smem_u32(bars + 2 * kMaxStages), bready = smem_u32(bars + 2 * kMaxStages + 1);
   const uint32_t done = smem_u32(bars + 2 * kMaxStages + 2);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kMaxStages + 3);
+  const uint32_t afull = smem_u32(bars + 2 * kMaxStages + 3), aempty = smem_u32(bars + 2 * kMaxStages + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kMaxStages + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rounds = sh.order + 2;
@@ -115,13 +130,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(empty0 + 8 * q, 1);
     }
     mbar_init(dfull, 1);
-    mbar_init(bready, 128);
+    mbar_init(bready, 32 * EPI);
     mbar_init(done, 1);
+    mbar_init(afull, 1);
+    mbar_init(aempty, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // the term operand starts at zero: padded rows and K beyond M stay zero throughout
-  for (int e = threadIdx.x; e < 2 * sh.KB * sh.bkb / 16; e += kThreads)
+  for (int e = threadIdx.x; e < 2 * sh.KB * sh.bkb / 16; e += blockDim.x)
     reinterpret_cast<uint4*>(smem + sh.bhi_off)[e] = make_uint4(0u, 0u, 0u, 0u);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
   if (warp == 1) {
@@ -140,12 +157,42 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---- TMA producer: the same walker and tile order the MMA issuer consumes ----
-      int g = 0;
+      int g = 0, aw = 0;
       bool ok = true;
+      const uint64_t abytes = (uint64_t)sh.M * sh.Mp * 2;   // one plane of A, hi or lo
+      const uint64_t pbytes = (uint64_t)NM * 8;             // one plane of Phi
       for (int w = blockIdx.x; w < sh.Nw && ok; w += gridDim.x) {
         if (alive && !alive[w]) continue;
+        // the next walker's A planes and Phi towards L2 while this one is propagated
+        const int wn = w + gridDim.x;
+        if (wn < sh.Nw) {
+          for (int z = 0; z < 2; ++z) {
+            const int64_t ao = ((int64_t)z * sh.Nw + wn) * sh.M * sh.Mp;
+            prefetch_l2(sh.ahi + ao, abytes);
+            prefetch_l2(sh.alo + ao, abytes);
+            prefetch_l2(phi_in + z * plane + (int64_t)wn * NM, pbytes);
+          }
+        }
         for (int q = 0; q < rounds && ok; ++q) {
           const bool taylor = q >= 1 && q <= sh.order;
+          if (sh.resident && taylor) {
+            if (q == 1) {
+              // this walker's A into the resident region once the previous walker's last
+              // Taylor round has read it (aempty), all tiles on one barrier
+              if (aw > 0 && !mbar_wait(aempty, (aw - 1) & 1, err, wait_ns)) {
+                fail();
+                ok = false;
+                break;
+              }
+              mbar_expect_tx(afull, 4 * sh.KB * kTile);
+              for (int kb = 0; kb < sh.KB; ++kb)
+                for (int u = 0; u < 4; ++u)
+                  tma_load_3d(smem_u32(smem + sh.ares_off + (kb * 4 + u) * kTile),
+                              (u & 1) ? &tmAlo : &tmAhi, afull, kb * 64, 0, (u >> 1) * sh.Nw + w);
+              ++aw;
+            }
+            continue;
+          }
           for (int t = 0; t < sh.MT && ok; ++t)
             for (int kb = 0; kb < sh.KB && ok; ++kb)
               for (int u = 0; u < (taylor ? 4 : 2); ++u, ++g) {
@@ -172,13 +219,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       // every issued tile must have landed before the CTA may exit
       for (int q = (g > sh.nst ? g - sh.nst : 0); q < g; ++q)
         mbar_wait(full0 + 8 * (q % sh.nst), (q / sh.nst) & 1, err, wait_ns);
+      if (aw > 0) mbar_wait(afull, (aw - 1) & 1, err, wait_ns);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer ----
       const uint32_t idesc = idesc_n(sh.n2);
       const uint32_t bhi = smem_u32(smem + sh.bhi_off), blo = smem_u32(smem + sh.blo_off);
-      int g = 0, rq = 0;
+      int g = 0, rq = 0, aw = 0;
       bool ok = true;
       for (int w = blockIdx.x; w < sh.Nw && ok; w += gridDim.x) {
         if (alive && !alive[w]) continue;
@@ -186,6 +234,33 @@ __global__ void __launch_bounds__(kThreads, 1)
           const bool taylor = q >= 1 && q <= sh.order;
           if (*abort_flag || !mbar_wait(bready, rq & 1, err, wait_ns)) { fail(); ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (sh.resident && taylor) {
+            // A resident in shared memory: one tile row (MT = 1), the K blocks' four tiles
+            if (q == 1) {
+              if (!mbar_wait(afull, aw & 1, err, wait_ns)) { fail(); ok = false; break; }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              ++aw;
+            }
+            bool first = true;
+            for (int kb = 0; kb < sh.KB; ++kb) {
+              const int nks = min(4, (sh.M - 64 * kb + 15) / 16);
+              for (int u = 0; u < 4; ++u) {
+                const uint64_t a = sw128_desc(smem_u32(smem + sh.ares_off + (kb * 4 + u) * kTile));
+                const uint32_t roff = (uint32_t)(kb * sh.bkb + (u >= 2 ? 0 : sh.Np * 128));
+                const uint64_t bh = sw128_desc(bhi + roff), bl = sw128_desc(blo + roff);
+                const bool hi = (u & 1) == 0;
+                for (int ks = 0; ks < nks; ++ks) {
+                  const uint64_t dk = (uint64_t)(2 * ks);
+                  mma_bf16(tmem, a + dk, bh + dk, idesc, first ? 0u : 1u);
+                  first = false;
+                  if (hi) mma_bf16(tmem, a + dk, bl + dk, idesc, 1u);
+                }
+              }
+            }
+            if (q == sh.order) mma_commit(aempty);   // the region is free once these complete
+            mma_commit(dfull);
+            continue;
+          }
           for (int t = 0; t < sh.MT && ok; ++t) {
             const uint32_t d = tmem + (uint32_t)(t * sh.dcol);
             bool first = true;
@@ -220,8 +295,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_commit(done);   // arrives once every issued MMA has completed
     }
   } else {
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 ----
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31; with 8 epilogue warps two
+    // share each lane quadrant and take alternate 16-column chunks ----
     const int r = 32 * (warp & 3) + lane;
+    const int half = EPI == 8 ? (warp - 2) >> 2 : 0, cstep = EPI == 8 ? 32 : 16;
     const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
     uint8_t* bh8 = smem + sh.bhi_off;
     uint8_t* bl8 = smem + sh.blo_off;
@@ -250,16 +327,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = 0; t < sh.MT; ++t) {
         const int i = 128 * t + r;
         const bool in_b = i < 64 * sh.KB;
-        for (int c0 = 0; c0 < sh.n2; c0 += 16) {
-          uint32_t v[16];
+        for (int c0 = 16 * half; c0 < sh.n2; c0 += cstep) {
+          // the chunk's 16 loads first, all in flight together, then the operand stores
+          double xv[16];
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int c = c0 + e, b = c < sh.Np ? c : c - sh.Np;
-            float x = 0.f;
-            if (i < sh.M && b < sh.N)
-              x = (float)phi_in[(c < sh.Np ? 0 : plane) + ((int64_t)w * sh.N + b) * sh.M + i];
+            xv[e] = (i < sh.M && b < sh.N)
+                        ? phi_in[(c < sh.Np ? 0 : plane) + ((int64_t)w * sh.N + b) * sh.M + i]
+                        : 0.0;
+          }
+          uint32_t v[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float x = (float)xv[e];
             v[e] = __float_as_uint(x);
-            if (in_b) put_term(i, c, x, false);
+            if (in_b) put_term(i, c0 + e, x, false);
           }
           tmem_st16(tmem + lanes + sreg + (uint32_t)(t * sh.dcol + c0), v);
         }
@@ -277,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int t = 0; t < sh.MT; ++t) {
           const int i = 128 * t + r;
           const bool in_b = i < 64 * sh.KB;
-          for (int c0 = 0; c0 < sh.n2; c0 += 16) {
+          for (int c0 = 16 * half; c0 < sh.n2; c0 += cstep) {
             uint32_t dv[16], sv[16];
             tmem_ld16(tmem + lanes + (uint32_t)(t * sh.dcol + c0), dv);
             tmem_ld16(tmem + lanes + sreg + (uint32_t)(t * sh.dcol + c0), sv);
@@ -378,8 +461,11 @@ cudaError_t make_map(CUtensorMap* map, void* base, int M, int Mp, int64_t nz) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-TclShape shape_of(const Ctx& c, int nst) {
+TclShape shape_of(const Ctx& c, int nst, int resident) {
   TclShape s{};
+  s.ahi = c.tcl_ahi;
+  s.alo = c.tcl_alo;
+  s.Mp = propagate_tcl_mp(c.M);
   s.M = c.M;
   s.N = c.N;
   s.Np = (c.N + 7) / 8 * 8;
@@ -394,34 +480,54 @@ TclShape shape_of(const Ctx& c, int nst) {
   s.tcols = cols;
   s.order = c.opt.taylor_order;
   s.Nw = c.Nw;
+  s.resident = resident;
   s.ring_off = 0;
-  s.bhi_off = nst * kTile;
+  s.ares_off = nst * kTile;
+  s.bhi_off = s.ares_off + (resident ? 4 * s.KB * kTile : 0);
   s.blo_off = s.bhi_off + s.KB * s.bkb;
   s.bar_off = s.blo_off + s.KB * s.bkb;
-  s.smem_bytes = s.bar_off + 8 * (2 * kMaxStages + 3) + 16 + 1024;
+  s.smem_bytes = s.bar_off + 8 * (2 * kMaxStages + 5) + 16 + 1024;
   return s;
 }
 
-// the deepest ring (2..4 stages) that keeps two CTAs per SM, else 3 stages at one CTA per SM
-int stages_for(const Ctx& c) {
-  for (int nst = kMaxStages; nst >= 2; --nst)
-    if (shape_of(c, nst).smem_bytes <= 113 * 1024) return nst;
-  return 3;
+// Launch form: A resident with a 2-stage ring for e^{-dt K/2} - I and 8 epilogue warps, one CTA
+// per SM (M <= 128); else A streamed, two CTAs per SM of 4 epilogue warps when a ring of at
+// least 4 stages fits 113 KB, otherwise one CTA per SM of 8 epilogue warps with the deepest
+// ring that fits.
+TclShape plan(const Ctx& c) {
+  if (c.M <= 128) {
+    const TclShape s = shape_of(c, 2, 1);
+    if (s.smem_bytes <= 227 * 1024) return s;
+  }
+  for (int nst = 8; nst >= 4; --nst) {
+    const TclShape s = shape_of(c, nst, 0);
+    if (s.smem_bytes <= 113 * 1024) return s;
+  }
+  for (int nst = kMaxStages; nst >= 2; --nst) {
+    const TclShape s = shape_of(c, nst, 0);
+    if (s.smem_bytes <= 227 * 1024) return s;
+  }
+  return shape_of(c, 2, 0);
 }
+
+bool two_per_sm(const TclShape& s) { return !s.resident && s.smem_bytes <= 113 * 1024; }
 
 }  // namespace
 
 bool propagate_tcl_ok(const Ctx& c) {
   if (c.M < 1 || c.M > 256 || c.N < 1 || c.N > 32 || c.opt.taylor_order < 1) return false;
-  const TclShape s = shape_of(c, stages_for(c));
+  const TclShape s = plan(c);
   return s.smem_bytes <= 227 * 1024 && s.tcols <= 256;
 }
 
 int propagate_tcl_mp(int M) { return (M + 7) / 8 * 8; }
 
 cudaError_t prepare_propagate_tcl() {
-  return cudaFuncSetAttribute(k_propagate_tcl, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_propagate_tcl<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_propagate_tcl<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return e;
 }
 
 // Tensor maps of the split A planes (ahi/alo: [2][Nw][M][Mp] bf16) and of E - I (ehi/elo:
@@ -449,12 +555,17 @@ cudaError_t setup_propagate_tcl(Ctx& c, cudaStream_t s) {
 // as they are.
 cudaError_t launch_propagate_tcl(const Ctx& c, double* out, float* out32, cudaStream_t s) {
   if (!propagate_tcl_ok(c) || !c.tcl_maps) return cudaErrorInvalidValue;
-  const TclShape sh = shape_of(c, stages_for(c));
-  const int per_sm = sh.smem_bytes <= 113 * 1024 ? 2 : 1;
-  const int grid = std::min(c.Nw, 152 * per_sm);
-  k_propagate_tcl<<<grid, kThreads, sh.smem_bytes, s>>>(
-      c.tcl_maps[0], c.tcl_maps[1], c.tcl_maps[2], c.tcl_maps[3], sh, c.phi, out, out32,
-      out == c.phi ? c.alive : nullptr, c.d_tc_err, kWaitNs);
+  const TclShape sh = plan(c);
+  const int* al = out == c.phi ? c.alive : nullptr;
+  if (two_per_sm(sh)) {
+    k_propagate_tcl<4><<<std::min(c.Nw, 2 * 152), 64 + 32 * 4, sh.smem_bytes, s>>>(
+        c.tcl_maps[0], c.tcl_maps[1], c.tcl_maps[2], c.tcl_maps[3], sh, c.phi, out, out32, al,
+        c.d_tc_err, kWaitNs);
+  } else {
+    k_propagate_tcl<8><<<std::min(c.Nw, 152), 64 + 32 * 8, sh.smem_bytes, s>>>(
+        c.tcl_maps[0], c.tcl_maps[1], c.tcl_maps[2], c.tcl_maps[3], sh, c.phi, out, out32, al,
+        c.d_tc_err, kWaitNs);
+  }
   return cudaGetLastError();
 }
 

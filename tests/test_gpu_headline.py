@@ -54,7 +54,7 @@ def reference(data):
     return [(ref["walkers"][i], ref["records"][i][-1]["eloc"]) for i in range(2)]
 
 
-def run_gpu(afq, data, precision, taylor=None, energy=None):
+def run_gpu(afq, data, precision, taylor=None, energy=None, mgs=None):
     gpu = [afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=CFG["dt"],
                       n_walkers=CFG["n_walkers"], seed=SEED, n_repeats=R, precision=precision)
            for d in data]
@@ -63,6 +63,8 @@ def run_gpu(afq, data, precision, taylor=None, energy=None):
             g.select_kernel(afq.K_TAYLOR, taylor)
         if energy is not None:
             g.select_kernel(afq.K_EXCHANGE, energy)
+        if mgs is not None:
+            g.select_kernel(afq.K_MGS, mgs)
     res = afq.pair_delta_E(gpu[0], gpu[1], STEPS, 5, 5, raise_on_dead=False)
     out = []
     for g in gpu:
@@ -101,18 +103,19 @@ def test_full_size_pair_fp64(data, reference):
 # propagation variants at M=128 (select_kernel K_TAYLOR): 4 tensor cores (V_HS streamed as split
 # BF16), 2 the fused FP32 kernel, 1 / 0 two FP32 GEMMs around the Taylor kernel with A in shared
 # memory / through L1; the local energy on the tensor cores (K_EXCHANGE 0) or the FP32 kernel
-# with 4 walkers per CTA
-VARIANTS = [(4, 0), (2, 0), (1, 0), (0, 4)]
+# with 4 walkers per CTA; the orthonormalisation as Cholesky QR (K_MGS 1) or modified
+# Gram-Schmidt (0)
+VARIANTS = [(4, 0, 1), (4, 0, 0), (2, 0, 1), (1, 0, 0), (0, 4, 1)]
 
 
-@pytest.mark.parametrize("taylor,energy", VARIANTS)
-def test_full_size_pair_split_precision(data, reference, taylor, energy):
+@pytest.mark.parametrize("taylor,energy,mgs", VARIANTS)
+def test_full_size_pair_split_precision(data, reference, taylor, energy, mgs):
     afq = need_gpu()
-    res, out = run_gpu(afq, data, afq.BF16X3, taylor=taylor, energy=energy)
+    res, out = run_gpu(afq, data, afq.BF16X3, taylor=taylor, energy=energy, mgs=mgs)
     assert np.all(np.isfinite(res["E"]))
     for i, ((st, el), (wk, el_o)) in enumerate(zip(out, reference)):
         err = errors(st, el, wk, el_o)
-        REPORT[f"split_taylor{taylor}_energy{energy}_{'AB'[i]}"] = err
+        REPORT[f"split_taylor{taylor}_energy{energy}_mgs{mgs}_{'AB'[i]}"] = err
         dump()
         # a walker may sit on the cos cut within rounding; none of the sample should
         assert err["alive_both"] == err["alive_oracle"], err

@@ -36,12 +36,12 @@ def gpu_sys(afq, d, nw, dt, precision, seed=1, R=1):
 # (select_kernel) propagation: 4 tensor cores (streamed V_HS, M <= 256), 3 tensor cores (M <= 64),
 # 2 fused FP32 kernel, 1 FP32 GEMMs + Taylor kernel; local energy: 0 tensor cores, 2 / 4 / 8
 # FP32 kernel with that many walkers per CTA
-@pytest.mark.parametrize("cfg,which,coupling,nw,taylor,energy", [
-    ("C1", "A", 1.0, 128, 3, 0), ("C1", "A", 1.0, 128, 2, 4), ("C1", "B", 1.0, 128, 3, 0),
-    ("C1", "B", 1.0, 128, 4, 0), ("C2", "B", "moderate", 96, 3, 0),
-    ("C2", "B", "moderate", 96, 2, 0), ("C2", "A", "moderate", 96, 1, 8),
-    ("C2", "A", "moderate", 96, 4, 0)])
-def test_mixed_walkers_track_fp64_oracle(cfg, which, coupling, nw, taylor, energy):
+@pytest.mark.parametrize("cfg,which,coupling,nw,taylor,energy,mgs", [
+    ("C1", "A", 1.0, 128, 3, 0, 0), ("C1", "A", 1.0, 128, 2, 4, 1), ("C1", "B", 1.0, 128, 3, 0, 1),
+    ("C1", "B", 1.0, 128, 4, 0, 0), ("C2", "B", "moderate", 96, 3, 0, 0),
+    ("C2", "B", "moderate", 96, 2, 0, 1), ("C2", "A", "moderate", 96, 1, 8, 0),
+    ("C2", "A", "moderate", 96, 4, 0, 1)])
+def test_mixed_walkers_track_fp64_oracle(cfg, which, coupling, nw, taylor, energy, mgs):
     """Each kernel variant, forced, against the oracle after 50 steps on the same fields.  Bars:
     1e-4 relative on E_L, 1e-3 on w, 1e-4 Ha on the mixed energy, about ten times the errors
     measured at these shapes (E_L ~1e-5, w ~1e-4, mixed energy ~1e-5 Ha)."""
@@ -52,8 +52,10 @@ def test_mixed_walkers_track_fp64_oracle(cfg, which, coupling, nw, taylor, energ
     g = gpu_sys(afq, d, nw, dt, afq.BF16X3)
     g.select_kernel(afq.K_TAYLOR, taylor)
     g.select_kernel(afq.K_EXCHANGE, energy)
+    g.select_kernel(afq.K_MGS, mgs)
     info = g.info()
-    assert (info.tuned_taylor_smem, info.tuned_energy_walkers_per_cta) == (taylor, energy)
+    assert (info.tuned_taylor_smem, info.tuned_energy_walkers_per_cta,
+            info.tuned_orthonormalise) == (taylor, energy, mgs)
     o = orc.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt)
     wk = orc.Walkers(o, nw)
     errs = []
@@ -71,7 +73,7 @@ def test_mixed_walkers_track_fp64_oracle(cfg, which, coupling, nw, taylor, energ
     e_rel = np.max(np.abs(el[live] - el_o[live]) / np.abs(el_o[live]))
     w_rel = np.max(np.abs(st["w"].real[live] - wk.w.real[live]) / np.abs(wk.w.real[live]))
     em_o, _ = orc.mixed_energy(o, wk.w, el_o, np.zeros(nw, int), 1)
-    REPORT[f"{cfg}{which}_taylor{taylor}_energy{energy}"] = dict(
+    REPORT[f"{cfg}{which}_taylor{taylor}_energy{energy}_mgs{mgs}"] = dict(
         max_rel_E_L=float(e_rel), max_rel_w=float(w_rel), mixed_E_err_Ha=float(em[0] - em_o[0]))
     dump()
     assert e_rel < 1e-4 and w_rel < 1e-3, (e_rel, w_rel)
@@ -134,6 +136,36 @@ def test_autotuner_picks_valid_variants_and_persists(tmp_path):
                     precision=afq.FP64)
     assert s4.info().tuned_energy_walkers_per_cta == -1
     s4.close()
+
+
+@pytest.mark.parametrize("cfg,which", [("C2", "B"), ("C3", "B")])
+def test_cholesky_qr_orthonormalises_and_lowers_log_overlap(cfg, which):
+    """Cholesky QR (K_MGS 1): per spin block Q^H Q = I (Q in FP32), Q spans the walker's
+    columns (the energy, invariant under Phi -> Phi R^{-1}, is unchanged), log O lowered by
+    log det R agrees with a recomputation, and Q equals the oracle's modified Gram-Schmidt."""
+    afq = need_gpu()
+    d = system_data(cfg, which, "moderate")
+    nw = 64
+    g = gpu_sys(afq, d, nw, CONFIGS[cfg]["dt"], afq.BF16X3)
+    g.select_kernel(afq.K_MGS, 1)
+    g.propagate(5, explicit_fields(5, nw, d["X"], seed=23))
+    before = g.state()
+    _, em0, _ = g.energy()
+    g.orthonormalise()
+    after = g.state()
+    _, em1, _ = g.energy()
+    o = orc.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], CONFIGS[cfg]["dt"])
+    for a, b in o.spins:
+        Q = after["phi"][:, :, a:b]
+        gram = np.einsum("wia,wib->wab", Q.conj(), Q)
+        assert np.abs(gram - np.eye(b - a)).max() < 5e-6
+        ref = orc.modified_gram_schmidt(before["phi"][:, :, a:b])
+        assert np.abs(Q - ref).max() < 5e-6
+    assert abs(em1[0] - em0[0]) < 1e-5 * abs(em0[0])
+    live = before["alive"]
+    rec = orc.overlap(o, after["phi"])
+    assert np.abs(np.exp(after["logO"][live] - rec[live]) - 1).max() < 1e-5
+    g.close()
 
 
 def test_gram_schmidt_log_overlap_update_matches_recomputation():
