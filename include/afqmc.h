@@ -46,14 +46,18 @@ typedef enum {
  * free projection (no force bias, complex weights). */
 enum { AFQMC_PHASELESS = 0, AFQMC_FREE = 1 };
 
-/* Arithmetic of the step.  Determinants, overlaps, ratios, phases, weights and MGS are
- * float64 in every mode.
- *   AFQMC_FP64:   every contraction in float64.
- *   AFQMC_BF16X3: the Cholesky contractions (force bias, Eq. 9; V_HS, Eq. 11) on the
+/* Arithmetic of the step.  Overlap ratios, phases and weights are float64 in every mode.
+ *   AFQMC_FP64:   every contraction, the determinants and MGS in float64.
+ *   AFQMC_BF16X3: every product over the Cholesky index or the orbital basis runs on the
  *                 tensor cores with split operands x = hi + lo (two bf16), three MMAs per
- *                 product (hi*hi + hi*lo + lo*hi) accumulated in FP32; the propagator
- *                 products (one-body half steps, Taylor exponential) and the exchange
- *                 energy in FP32. */
+ *                 product (hi*hi + hi*lo + lo*hi) accumulated in FP32: the force bias
+ *                 (Eq. 9), V_HS (Eq. 11), the one-body half steps and the Taylor terms of
+ *                 the propagator for M <= 256, N <= 32 (FP32 CUDA-core kernels otherwise)
+ *                 and the two-body local energy (the FP32 kernel where the tensor-core one
+ *                 does not apply).  Walkers are kept in float64 and float32; the
+ *                 overlap-and-Theta kernel and the orthonormalisation work in FP32 pairs
+ *                 with float64 log-determinants (Cholesky QR with the Gram matrix in FP32
+ *                 pairs, or Gram-Schmidt in float64; select_kernel K_MGS). */
 enum { AFQMC_FP64 = 0, AFQMC_BF16X3 = 1 };
 
 typedef struct afqmc_ctx* afqmc_handle;

@@ -94,6 +94,7 @@ void free_ctx(Ctx* h) {
         delete op;
       }
     if (h->etc->part) cudaFree(h->etc->part);
+    if (h->etc->trs) cudaFree(h->etc->trs);
     delete h->etc;
     h->etc = nullptr;
   }
@@ -202,7 +203,9 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
       const size_t ka = (size_t)ra * h->etc->Kp, kb = (size_t)rb * h->etc->Kp;
       if (dalloc(h, &h->etc->A->hi, ka) != AFQMC_OK || dalloc(h, &h->etc->A->lo, ka) != AFQMC_OK ||
           dalloc(h, &h->etc->B->hi, kb) != AFQMC_OK || dalloc(h, &h->etc->B->lo, kb) != AFQMC_OK ||
-          dalloc(h, &h->etc->part, 2 * (size_t)h->etc->RT * h->etc->NwP) != AFQMC_OK) {
+          dalloc(h, &h->etc->part, 2 * (size_t)h->etc->RT * h->etc->NwP) != AFQMC_OK ||
+          (afq::energy_tc_spin(*h) &&
+           dalloc(h, &h->etc->trs, 2 * 2 * (size_t)Nw * X) != AFQMC_OK)) {
         if (own) {
           cudaStreamSynchronize(s);
           cudaFree(tmp);

@@ -93,6 +93,46 @@ __global__ void k_energy_B(const float* __restrict__ th, int Nw, int N, int M, i
   }
 }
 
+// Spin-blocked layout (M > 64): one GEMM per spin, so no cross-spin block is computed.  A rows
+// (s, g, a), a < P2 of spin s (zero beyond N_s), each spin's rows padded to whole row tiles
+// (RTs of them); B rows (s, w, re/im, b) padded to whole column tiles (CTs of them).
+__global__ void k_energy_A_spin(const double* __restrict__ Ltil, int X, int N, int M, int nu,
+                                int P2, int Kp, int RTs, __nv_bfloat16* __restrict__ hi,
+                                __nv_bfloat16* __restrict__ lo) {
+  const int64_t per = (int64_t)RTs * EBM, total = 2 * per * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = e / Kp;
+    const int k = (int)(e % Kp), sp = (int)(row / per);
+    const int64_t r = row % per;
+    const int g = (int)(r / P2), a = (int)(r % P2), ns = sp ? N - nu : nu;
+    const double x = (g < X && a < ns && k < M) ? Ltil[((int64_t)g * N + (sp ? nu : 0) + a) * M + k] : 0.0;
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+  }
+}
+
+__global__ void k_energy_B_spin(const float* __restrict__ th, int Nw, int N, int M, int nu, int P2,
+                                int Kp, int CTs, int nw, __nv_bfloat16* __restrict__ hi,
+                                __nv_bfloat16* __restrict__ lo) {
+  const int64_t plane = (int64_t)Nw * N * M, per = (int64_t)CTs * EBN;
+  const int64_t total = 2 * per * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = e / Kp;
+    const int k = (int)(e % Kp), sp = (int)(row / per);
+    const int64_t r = row % per;
+    const int w = (int)(r / (2 * P2)), p = (int)((r / P2) & 1), b = (int)(r % P2);
+    const int ns = sp ? N - nu : nu;
+    const float x = (w < nw && b < ns && k < M)
+                        ? th[p * plane + ((int64_t)w * N + (sp ? nu : 0) + b) * M + k] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
 // Persistent CTAs (one per SM) over the (row tile, column tile) pairs, m-fastest, 10 warps:
 //   warp 8 / lane 0  TMA producer
 //   warp 9 / lane 0  MMA issuer: per 64-wide k slice 4 x 3 tcgen05.mma (K = 16, N = 256) into
@@ -104,14 +144,18 @@ __global__ void k_energy_B(const float* __restrict__ th, int Nw, int N, int M, i
 // part[(tile_row * 2 + re/im) * NwP + w] = sum over the tile's g of E2(g, w).
 // Every mbarrier wait is bounded; on expiry *err is set, the epilogue warps stop together
 // (a shared flag read after their barrier), the CTA drains what it issued and frees its TMEM.
-template <int NP>
+// SPIN: spin-blocked layout (rows of one spin block per g, NP = P2): tiles t = (s, column
+// tile, row tile), the exchange over the whole block, and the traces tr T^s_g to trs (the
+// reduction forms the Coulomb term from both spins); otherwise both spins per g (NP = 2 P2),
+// exchange per spin block and the Coulomb term.
+template <int NP, bool SPIN>
 __global__ void __launch_bounds__(EPTHREADS, 1)
     k_energy_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                 const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                 int nkb, int RT, int CT, float* __restrict__ part, int NwP, int* err,
-                uint64_t wait_ns) {
+                uint64_t wait_ns, float2* __restrict__ trs, int X, int Nw) {
   using Lay = ELayout<NP>;
-  constexpr int CW = Lay::CW, WPT = Lay::WPT, P2 = NP / 2, WPG = CW / (2 * NP);
+  constexpr int CW = Lay::CW, WPT = Lay::WPT, P2 = SPIN ? NP : NP / 2, WPG = CW / (2 * NP);
   extern __shared__ uint8_t esm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(esm_raw) + 1023) &
                                              ~uintptr_t(1023));
@@ -123,7 +167,15 @@ __global__ void __launch_bounds__(EPTHREADS, 1)
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + 2);
   const uint32_t tfull0 = smem_u32(bars + 4), tempty0 = smem_u32(bars + 6), done = smem_u32(bars + 8);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = RT * CT;
+  const int ntiles = (SPIN ? 2 : 1) * RT * CT;
+  // tile t: spin block sp, row tile rt, column tile ct (rows and columns of the same spin)
+  auto tile_of = [&](int t, int& m0, int& n0, int& rt_all, int& ct) {
+    const int sp = t / (RT * CT), r = t % (RT * CT), rt = r % RT;
+    ct = r / RT;
+    rt_all = sp * RT + rt;
+    m0 = rt_all * EBM;
+    n0 = (sp * CT + ct) * EBN;
+  };
 
   if (threadIdx.x == 0) {
     for (int q = 0; q < 2; ++q) {
@@ -154,7 +206,8 @@ __global__ void __launch_bounds__(EPTHREADS, 1)
       int g = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int m0 = (t % RT) * EBM, n0 = (t / RT) * EBN;
+        int m0, n0, rt_all, ct;
+        tile_of(t, m0, n0, rt_all, ct);
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = g % ESTAGES, use = g / ESTAGES;
           if (g >= ESTAGES && !mbar_wait(empty0 + 8 * s, (use - 1) & 1, err, wait_ns)) { ok = false; break; }
@@ -211,9 +264,11 @@ __global__ void __launch_bounds__(EPTHREADS, 1)
     constexpr int NG = EBN / CW, NGH = NG / 2;   // column groups per tile, per half
     float* S = stg + warp * 32 * (CW + 1);
     const int quad = warp & 3, half = warp >> 2;
-    const int a = lane % NP, gl = lane / NP, s0 = a < P2 ? 0 : P2;
+    const int a = lane % NP, gl = lane / NP, s0 = (SPIN || a < P2) ? 0 : P2;
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      int m0_, n0_, rt_all, ct_t;
+      tile_of(t, m0_, n0_, rt_all, ct_t);
       const int b = i & 1;
       float* rb = red + b * (4 * WPT * 2);
       const bool ok = mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, err, wait_ns);
@@ -255,8 +310,16 @@ __global__ void __launch_bounds__(EPTHREADS, 1)
               dr += __shfl_xor_sync(0xffffffffu, dr, o);
               di += __shfl_xor_sync(0xffffffffu, di, o);
             }
-            float er = a == 0 ? 0.5f * (dr * dr - di * di - exr) : 0.f;
-            float ei = a == 0 ? 0.5f * (2.f * dr * di - exi) : 0.f;
+            // the Coulomb term (sum_s tr T^s)^2 needs both spins: in the spin-blocked layout
+            // the traces tr T^s_g go to trs and the reduction combines the spins
+            if (SPIN && a == 0) {
+              const int sp = rt_all / RT;
+              const int g = ((rt_all - sp * RT) * EBM + quad * 32 + lane) / NP;
+              const int w = ct_t * WPT + grp * WPG + wi;
+              if (g < X && w < Nw) trs[((int64_t)sp * Nw + w) * X + g] = make_float2(dr, di);
+            }
+            float er = a == 0 ? 0.5f * ((SPIN ? 0.f : dr * dr - di * di) - exr) : 0.f;
+            float ei = a == 0 ? 0.5f * ((SPIN ? 0.f : 2.f * dr * di) - exi) : 0.f;
 #pragma unroll
             for (int o = NP; o < 32; o <<= 1) {                        // over the warp's g blocks
               er += __shfl_xor_sync(0xffffffffu, er, o);
@@ -277,7 +340,7 @@ __global__ void __launch_bounds__(EPTHREADS, 1)
       asm volatile("bar.sync 1, %0;" ::"n"(32 * EWARPS) : "memory");   // the epilogue warps
       if (*s_fail) break;
       if (threadIdx.x < WPT) {
-        const int w = (t / RT) * WPT + threadIdx.x, rt = t % RT;
+        const int w = ct_t * WPT + threadIdx.x, rt = rt_all;
         float sr = 0.f, si = 0.f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -535,11 +598,15 @@ __global__ void __launch_bounds__(EBLayout<NP>::THREADS, 1)
 // eloc[w] = sum_e htil[e] Theta_w[e] (FP64) + sum over row tiles of part for the first nw of
 // the Nw walkers (one warp per walker;
 // every sum in a fixed order, so repeated evaluations agree bit for bit).
+// E_L per walker: the one-body term sum htil . Theta (FP64), the row tiles' partial two-body
+// sums in a fixed order, and (spin-blocked layout) the Coulomb term 1/2 sum_g (sum_s tr T^s_g)^2
+// from the traces trs ([2][Nw][X] complex); trs null: already in the partials.
 __global__ void __launch_bounds__(256) k_energy_tc_reduce(const float* __restrict__ part, int RT, int NwP,
                                                           const float* __restrict__ th,
                                                           const double* __restrict__ htil,
                                                           double* __restrict__ eloc, int Nw, int nw,
-                                                          int NM) {
+                                                          int NM, const float2* __restrict__ trs,
+                                                          int X) {
   const int lane = threadIdx.x & 31, w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= nw) return;
   const int64_t plane = (int64_t)Nw * NM;
@@ -549,6 +616,13 @@ __global__ void __launch_bounds__(256) k_energy_tc_reduce(const float* __restric
     r = fma(h, (double)th[(int64_t)w * NM + e], r);
     i = fma(h, (double)th[plane + (int64_t)w * NM + e], i);
   }
+  if (trs)
+    for (int g = lane; g < X; g += 32) {
+      const float2 u = trs[(int64_t)w * X + g], d = trs[((int64_t)Nw + w) * X + g];
+      const double pr = (double)u.x + (double)d.x, pi = (double)u.y + (double)d.y;
+      r += 0.5 * (pr * pr - pi * pi);
+      i += pr * pi;
+    }
   for (int t = lane; t < RT; t += 32) {
     r += (double)part[(int64_t)(2 * t) * NwP + w];
     i += (double)part[(int64_t)(2 * t + 1) * NwP + w];
@@ -564,6 +638,27 @@ __global__ void __launch_bounds__(256) k_energy_tc_reduce(const float* __restric
 }
 
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+// spin-blocked form (M > 64): NPS = P2 rows per Cholesky vector and spin
+template <int NPS>
+cudaError_t launch_spin(const Ctx& c, const EnergyTc& et, int n_walkers, cudaStream_t s) {
+  using Lay = ELayout<NPS>;
+  const int NM = c.N * c.M, nw = n_walkers > 0 ? n_walkers : c.Nw;
+  const int RTs = et.RT / 2, CTs = (c.Nw * 2 * NPS + EBN - 1) / EBN;
+  k_energy_B_spin<<<grid_for((int64_t)2 * CTs * EBN * et.Kp), 256, 0, s>>>(
+      c.theta32, c.Nw, c.N, c.M, c.n_up, NPS, et.Kp, CTs, nw, et.B->hi, et.B->lo);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(2 * RTs * CTs, 152);
+  k_energy_tc<NPS, true><<<grid, EPTHREADS, Lay::SMEM_BYTES, s>>>(
+      et.A->map_hi, et.A->map_lo, et.B->map_hi, et.B->map_lo, et.Kp / EBK, RTs, CTs, et.part,
+      et.NwP, c.d_tc_err, kEWaitNs, reinterpret_cast<float2*>(et.trs), c.X, c.Nw);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_energy_tc_reduce<<<(nw + 7) / 8, 256, 0, s>>>(et.part, et.RT, et.NwP, c.theta32, c.htil, c.eloc,
+                                                  c.Nw, nw, NM, reinterpret_cast<const float2*>(et.trs),
+                                                  c.X);
+  return cudaGetLastError();
+}
 
 template <int NP>
 cudaError_t launch_np(const Ctx& c, const EnergyTc& et, int n_walkers, cudaStream_t s) {
@@ -586,13 +681,13 @@ cudaError_t launch_np(const Ctx& c, const EnergyTc& et, int n_walkers, cudaStrea
         c.d_tc_err, kEWaitNs);
   } else {
     const int grid = std::min(et.RT * ct, 152);
-    k_energy_tc<NP><<<grid, EPTHREADS, Lay::SMEM_BYTES, s>>>(et.A->map_hi, et.A->map_lo, et.B->map_hi,
-                                                            et.B->map_lo, et.Kp / EBK, et.RT, ct, et.part,
-                                                            et.NwP, c.d_tc_err, kEWaitNs);
+    k_energy_tc<NP, false><<<grid, EPTHREADS, Lay::SMEM_BYTES, s>>>(
+        et.A->map_hi, et.A->map_lo, et.B->map_hi, et.B->map_lo, et.Kp / EBK, et.RT, ct, et.part,
+        et.NwP, c.d_tc_err, kEWaitNs, nullptr, c.X, c.Nw);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_energy_tc_reduce<<<(nw + 7) / 8, 256, 0, s>>>(et.part, nparts, et.NwP, c.theta32, c.htil, c.eloc,
-                                                 c.Nw, nw, NM);
+                                                 c.Nw, nw, NM, nullptr, 0);
   return cudaGetLastError();
 }
 
@@ -606,14 +701,23 @@ int energy_tc_np(const Ctx& c) {
 }
 
 cudaError_t prepare_energy_tc_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_energy_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_energy_tc<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        ELayout<8>::SMEM_BYTES);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_energy_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_energy_tc<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              ELayout<16>::SMEM_BYTES);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_energy_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_energy_tc<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              ELayout<32>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_energy_tc<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             ELayout<4>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_energy_tc<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             ELayout<8>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_energy_tc<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             ELayout<16>::SMEM_BYTES);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_energy_tc_bres<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              EBLayout<8>::SMEM_BYTES);
@@ -628,8 +732,21 @@ cudaError_t prepare_energy_tc_kernels() {
 
 // Operand buffers are allocated by the caller (sizes from energy_tc_sizes); this fills the
 // A operand and encodes both tensor maps.
+// M > 64 (more than one 64-wide k slice): the spin-blocked layout, rows of P2 = NP / 2 per
+// Cholesky vector and spin, RT counting the row tiles of both spins
+bool energy_tc_spin(const Ctx& c) { return pad64(c.M) > EBK; }
+
 void energy_tc_sizes(const Ctx& c, int NP, int* rows_A, int* rows_B, int* Kp, int* RT, int* NwP) {
   *Kp = pad64(c.M);
+  if (energy_tc_spin(c)) {
+    const int P2 = NP / 2;
+    const int RTs = (c.X * P2 + EBM - 1) / EBM, CTs = (c.Nw * 2 * P2 + EBN - 1) / EBN;
+    *rows_A = 2 * RTs * EBM;
+    *rows_B = 2 * CTs * EBN;
+    *RT = 2 * RTs;
+    *NwP = CTs * EBN / (2 * P2);
+    return;
+  }
   *rows_A = (c.X * NP + EBM - 1) / EBM * EBM;
   *rows_B = (c.Nw * 2 * NP + EBN - 1) / EBN * EBN;
   *RT = *rows_A / EBM;
@@ -642,8 +759,12 @@ cudaError_t energy_tc_init(const Ctx& c, EnergyTc& et, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMemsetAsync(et.B->hi, 0, sizeof(__nv_bfloat16) * (size_t)et.B->rows * et.Kp, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(et.B->lo, 0, sizeof(__nv_bfloat16) * (size_t)et.B->rows * et.Kp, s);
   if (e != cudaSuccess) return e;
-  k_energy_A<<<grid_for((int64_t)c.X * et.NP * et.Kp), 256, 0, s>>>(c.Ltil, c.X, c.N, c.M, c.n_up, et.NP,
-                                                                   et.Kp, et.A->hi, et.A->lo);
+  if (energy_tc_spin(c))
+    k_energy_A_spin<<<grid_for((int64_t)et.A->rows * et.Kp), 256, 0, s>>>(
+        c.Ltil, c.X, c.N, c.M, c.n_up, et.NP / 2, et.Kp, et.RT / 2, et.A->hi, et.A->lo);
+  else
+    k_energy_A<<<grid_for((int64_t)c.X * et.NP * et.Kp), 256, 0, s>>>(c.Ltil, c.X, c.N, c.M, c.n_up,
+                                                                     et.NP, et.Kp, et.A->hi, et.A->lo);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = tc_make_operand(*et.A, et.A->hi, et.A->lo, et.A->rows, et.Kp, EBM)) != cudaSuccess) return e;
   return tc_make_operand(*et.B, et.B->hi, et.B->lo, et.B->rows, et.Kp, EBN / 2);
@@ -651,6 +772,14 @@ cudaError_t energy_tc_init(const Ctx& c, EnergyTc& et, cudaStream_t s) {
 
 cudaError_t launch_energy_tc(const Ctx& c, cudaStream_t s, int n_walkers) {
   const EnergyTc& et = *c.etc;
+  if (energy_tc_spin(c)) {
+    switch (et.NP) {
+      case 8: return launch_spin<4>(c, et, n_walkers, s);
+      case 16: return launch_spin<8>(c, et, n_walkers, s);
+      case 32: return launch_spin<16>(c, et, n_walkers, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (et.NP) {
     case 8: return launch_np<8>(c, et, n_walkers, s);
     case 16: return launch_np<16>(c, et, n_walkers, s);

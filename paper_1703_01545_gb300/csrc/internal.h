@@ -43,6 +43,7 @@ struct EnergyTc {
   TcOperand* A = nullptr;     // rows (g, n') of Psi^T L_g, spin blocks padded to NP / 2
   TcOperand* B = nullptr;     // rows (w, re/im, n') of Theta
   float* part = nullptr;      // [RT][2][NwP] partial two-body energies per row tile
+  float* trs = nullptr;       // spin-blocked form: [2 spins][Nw][X] (re, im) traces tr T^s_g
   int NP = 0, Kp = 0, RT = 0, NwP = 0;
 };
 
@@ -228,6 +229,7 @@ cudaError_t launch_propagation(const Ctx& c, int variant, double* out, float* ou
 int energy_tc_np(const Ctx& c);   // padded orbitals per Cholesky vector (8, 16, 32) or 0
 cudaError_t prepare_energy_tc_kernels();
 void energy_tc_sizes(const Ctx& c, int NP, int* rows_A, int* rows_B, int* Kp, int* RT, int* NwP);
+bool energy_tc_spin(const Ctx& c);   // M > 64: one product per spin block
 cudaError_t energy_tc_init(const Ctx& c, EnergyTc& et, cudaStream_t s);
 cudaError_t launch_energy_tc(const Ctx& c, cudaStream_t s, int n_walkers = -1);
 // runtime autotuner (autotune.cpp): times the variants on the handle's buffers at setup

@@ -47,10 +47,6 @@ constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kTile = 128 * 64 * 2;       // one 128-row x 64-K bf16 tile, 128-byte swizzle
 constexpr int kMaxStages = 12;
 
-__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
-  return (uint32_t)(r * 128 + ((((k >> 3) ^ r) & 7) << 4) + ((k & 7) << 1));
-}
-
 __device__ __forceinline__ uint32_t idesc_n(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
@@ -73,6 +69,8 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
       : "memory");
 }
 
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // L2 prefetch hint over the 16-byte-aligned interior of [p, p + bytes) (the bulk prefetch needs a
 // 16-byte-aligned address and size)
 __device__ __forceinline__ void prefetch_l2(const void* p, uint64_t bytes) {
@@ -83,6 +81,78 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint64_t bytes) {
                  : "memory");
 }
 
+// One 16-lane x 16-column block of 32-bit TMEM cells in the mma fragment layout: thread t holds
+// lanes t/4 (v[0,1], v[4,5]) and 8 + t/4 (v[2,3], v[6,7]), columns 2 (t%4) + {0, 1} (v[0..3])
+// and 8 + 2 (t%4) + {0, 1} (v[4..7]).
+__device__ __forceinline__ void tmem_ld_frag(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                 "=r"(v[7])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st_frag(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.16x256b.x2.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(
+                   taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+
+// Transposed 8x8 stores of 16-bit pairs: register j of thread t holds row t/4, columns
+// 2 (t%4) + {0, 1} of matrix j; row k of matrix j (its column k) goes to the 16 bytes at the
+// address thread 8 j + k supplies.
+__device__ __forceinline__ void stsm_x4_t(uint32_t addr, const uint32_t (&r)[4]) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+
+__device__ __forceinline__ void stsm_x2_t(uint32_t addr, uint32_t r0, uint32_t r1) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x2.trans.shared.b16 [%0], {%1, %2};" ::"r"(addr), "r"(r0),
+               "r"(r1)
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t elect_one() {
+  uint32_t p;
+  asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.u32 %0, 1, 0, P;\n\t}"
+               : "=r"(p));
+  return p;
+}
+
+// x = hi + lo for a pair of floats (a in the low half): both halves as packed BF16 pairs
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// One product round with every A plane in tensor memory (plane u, K block kb at abase + 32 (u KB
+// + kb)): NPL = 4 for a Taylor term (A_re hi, lo, A_im hi, lo), 2 for a one-body half step (E - I
+// hi, lo).  B descriptors dbh / dbl address the term operand; A_re and E - I take rows Np..3Np
+// (offset np16), A_im rows 0..2Np.  The hi planes take two MMAs per 16-wide K step (x B hi,
+// x B lo), the lo planes one; the last K block stops after nks_last steps.
+template <int KB, int NPL>
+__device__ __forceinline__ void mma_round_tmem(uint32_t d, uint32_t abase, uint64_t dbh, uint64_t dbl,
+                                               uint32_t bkb16, uint32_t np16, uint32_t idesc,
+                                               int nks_last) {
+#pragma unroll
+  for (int kb = 0; kb < KB; ++kb)
+#pragma unroll
+    for (int u = 0; u < NPL; ++u) {
+      const uint32_t ta = abase + (uint32_t)(32 * (u * KB + kb));
+      const uint64_t roff = (uint64_t)(kb * bkb16 + (u >= 2 ? 0u : np16));
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        if (kb == KB - 1 && ks >= nks_last) break;
+        const uint64_t dk = roff + (uint64_t)(2 * ks);
+        mma_bf16_ta(d, ta + (uint32_t)(8 * ks), dbh + dk, idesc, (kb | u | ks) != 0 ? 1u : 0u);
+        if ((u & 1) == 0) mma_bf16_ta(d, ta + (uint32_t)(8 * ks), dbl + dk, idesc, 1u);
+      }
+    }
+}
+
 // Static shape of one launch (host-computed).
 struct TclShape {
   const __nv_bfloat16 *ahi, *alo;   // V_HS split planes [2][Nw][M][Mp] (L2 prefetch of the next walker)
@@ -90,8 +160,12 @@ struct TclShape {
   int M, N, Np, n2;      // orbitals, occupied columns, N rounded up to 8, MMA N = 2 Np
   int MT, KB;            // 128-row tiles of orbitals, 64-wide K blocks
   int nst;               // ring stages
-  int resident;          // 1: A of a walker held in shared memory for all its Taylor rounds
-  int ares_off;          // resident A region: 4 KB tiles (A_re hi, lo, A_im hi, lo per K block)
+  int resident;          // 1: A of a walker held in tensor memory for all its Taylor rounds,
+                         // staged through a shared-memory region the producer fills ahead
+  int ares_off;          // shared staging of A: 4 KB tiles (A_re hi, lo, A_im hi, lo per K block)
+  int acol;              // resident form: TMEM column of A (plane P, K block kb at acol + 32 (P KB + kb))
+  int eres, ecol;        // 1: e^{-dt K/2} - I also in tensor memory (hi, lo planes from ecol), loaded
+                         // once per CTA; the one-body rounds then need no ring
   int bkb;               // bytes of one K block of the term operand (3 Np rows x 128 bytes)
   int dcol;              // TMEM column stride between tiles (D and S regions)
   uint32_t tcols;        // TMEM columns allocated
@@ -117,7 +191,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kMaxStages);
   const uint32_t dfull = smem_u32(bars + 2 * kMaxStages), bready = smem_u32(bars + 2 * kMaxStages + 1);
   const uint32_t done = smem_u32(bars + 2 * kMaxStages + 2);
-  const uint32_t afull = smem_u32(bars + 2 * kMaxStages + 3), aempty = smem_u32(bars + 2 * kMaxStages + 4);
+  const uint32_t afull = smem_u32(bars + 2 * kMaxStages + 3), acopied = smem_u32(bars + 2 * kMaxStages + 4);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kMaxStages + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -133,7 +207,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
     mbar_init(bready, 32 * EPI);
     mbar_init(done, 1);
     mbar_init(afull, 1);
-    mbar_init(aempty, 1);
+    mbar_init(acopied, 32 * EPI);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -161,6 +235,15 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
       bool ok = true;
       const uint64_t abytes = (uint64_t)sh.M * sh.Mp * 2;   // one plane of A, hi or lo
       const uint64_t pbytes = (uint64_t)NM * 8;             // one plane of Phi
+      if (sh.eres) {
+        // e^{-dt K/2} - I through the staging region into tensor memory, once per CTA
+        mbar_expect_tx(afull, 2 * sh.KB * kTile);
+        for (int kb = 0; kb < sh.KB; ++kb)
+          for (int u = 0; u < 2; ++u)
+            tma_load_2d(smem_u32(smem + sh.ares_off + (kb * 4 + u) * kTile), u ? &tmElo : &tmEhi, afull,
+                        kb * 64, 0);
+        ++aw;
+      }
       for (int w = blockIdx.x; w < sh.Nw && ok; w += gridDim.x) {
         if (alive && !alive[w]) continue;
         // the next walker's A planes and Phi towards L2 while this one is propagated
@@ -175,24 +258,22 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
         }
         for (int q = 0; q < rounds && ok; ++q) {
           const bool taylor = q >= 1 && q <= sh.order;
-          if (sh.resident && taylor) {
-            if (q == 1) {
-              // this walker's A into the resident region once the previous walker's last
-              // Taylor round has read it (aempty), all tiles on one barrier
-              if (aw > 0 && !mbar_wait(aempty, (aw - 1) & 1, err, wait_ns)) {
-                fail();
-                ok = false;
-                break;
-              }
-              mbar_expect_tx(afull, 4 * sh.KB * kTile);
-              for (int kb = 0; kb < sh.KB; ++kb)
-                for (int u = 0; u < 4; ++u)
-                  tma_load_3d(smem_u32(smem + sh.ares_off + (kb * 4 + u) * kTile),
-                              (u & 1) ? &tmAlo : &tmAhi, afull, kb * 64, 0, (u >> 1) * sh.Nw + w);
-              ++aw;
+          if (sh.resident && q == 0) {
+            // this walker's A into the staging region once the epilogue has copied the previous
+            // walker's A to tensor memory (acopied), all tiles on one barrier
+            if (aw > 0 && !mbar_wait(acopied, (aw - 1) & 1, err, wait_ns)) {
+              fail();
+              ok = false;
+              break;
             }
-            continue;
+            mbar_expect_tx(afull, 4 * sh.KB * kTile);
+            for (int kb = 0; kb < sh.KB; ++kb)
+              for (int u = 0; u < 4; ++u)
+                tma_load_3d(smem_u32(smem + sh.ares_off + (kb * 4 + u) * kTile),
+                            (u & 1) ? &tmAlo : &tmAhi, afull, kb * 64, 0, (u >> 1) * sh.Nw + w);
+            ++aw;
           }
+          if (sh.resident && (taylor || sh.eres)) continue;
           for (int t = 0; t < sh.MT && ok; ++t)
             for (int kb = 0; kb < sh.KB && ok; ++kb)
               for (int u = 0; u < (taylor ? 4 : 2); ++u, ++g) {
@@ -222,131 +303,179 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
       if (aw > 0) mbar_wait(afull, (aw - 1) & 1, err, wait_ns);
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---- MMA issuer ----
-      const uint32_t idesc = idesc_n(sh.n2);
-      const uint32_t bhi = smem_u32(smem + sh.bhi_off), blo = smem_u32(smem + sh.blo_off);
-      int g = 0, rq = 0, aw = 0;
-      bool ok = true;
-      for (int w = blockIdx.x; w < sh.Nw && ok; w += gridDim.x) {
-        if (alive && !alive[w]) continue;
-        for (int q = 0; q < rounds && ok; ++q, ++rq) {
-          const bool taylor = q >= 1 && q <= sh.order;
-          if (*abort_flag || !mbar_wait(bready, rq & 1, err, wait_ns)) { fail(); ok = false; break; }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          if (sh.resident && taylor) {
-            // A resident in shared memory: one tile row (MT = 1), the K blocks' four tiles
-            if (q == 1) {
-              if (!mbar_wait(afull, aw & 1, err, wait_ns)) { fail(); ok = false; break; }
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              ++aw;
+    // ---- MMA issuer: the whole warp follows the loop, so every operand address is warp-uniform,
+    // and one elected lane issues; lane 0 polls the barriers and broadcasts the outcome ----
+    const uint32_t idesc = idesc_n(sh.n2);
+    const uint32_t bhi = smem_u32(smem + sh.bhi_off), blo = smem_u32(smem + sh.blo_off);
+    const uint64_t dbh = sw128_desc(bhi), dbl = sw128_desc(blo);
+    const uint32_t bkb16 = (uint32_t)(sh.bkb >> 4), np16 = (uint32_t)(sh.Np * 8);
+    const int nks_last = min(4, (sh.M - 64 * (sh.KB - 1) + 15) / 16);
+    int g = 0, rq = 0;
+    bool ok = true;
+    auto wait_all = [&](uint32_t bar, int parity) {
+      int okw = 1;
+      if (lane == 0) okw = !*abort_flag && mbar_wait(bar, parity, err, wait_ns);
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw && lane == 0) fail();
+      return okw != 0;
+    };
+    for (int w = blockIdx.x; w < sh.Nw && ok; w += gridDim.x) {
+      if (alive && !alive[w]) continue;
+      for (int q = 0; q < rounds && ok; ++q, ++rq) {
+        const bool taylor = q >= 1 && q <= sh.order;
+        if (!wait_all(bready, rq & 1)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (sh.resident && (taylor || sh.eres)) {
+          // every A plane in tensor memory (one tile row, MT = 1)
+          if (elect_one()) {
+            if (sh.KB == 2) {
+              if (taylor)
+                mma_round_tmem<2, 4>(tmem, tmem + (uint32_t)sh.acol, dbh, dbl, bkb16, np16, idesc, nks_last);
+              else
+                mma_round_tmem<2, 2>(tmem, tmem + (uint32_t)sh.ecol, dbh, dbl, bkb16, np16, idesc, nks_last);
+            } else {
+              if (taylor)
+                mma_round_tmem<1, 4>(tmem, tmem + (uint32_t)sh.acol, dbh, dbl, bkb16, np16, idesc, nks_last);
+              else
+                mma_round_tmem<1, 2>(tmem, tmem + (uint32_t)sh.ecol, dbh, dbl, bkb16, np16, idesc, nks_last);
             }
-            bool first = true;
-            for (int kb = 0; kb < sh.KB; ++kb) {
-              const int nks = min(4, (sh.M - 64 * kb + 15) / 16);
-              for (int u = 0; u < 4; ++u) {
-                const uint64_t a = sw128_desc(smem_u32(smem + sh.ares_off + (kb * 4 + u) * kTile));
-                const uint32_t roff = (uint32_t)(kb * sh.bkb + (u >= 2 ? 0 : sh.Np * 128));
-                const uint64_t bh = sw128_desc(bhi + roff), bl = sw128_desc(blo + roff);
-                const bool hi = (u & 1) == 0;
-                for (int ks = 0; ks < nks; ++ks) {
-                  const uint64_t dk = (uint64_t)(2 * ks);
-                  mma_bf16(tmem, a + dk, bh + dk, idesc, first ? 0u : 1u);
-                  first = false;
-                  if (hi) mma_bf16(tmem, a + dk, bl + dk, idesc, 1u);
-                }
-              }
-            }
-            if (q == sh.order) mma_commit(aempty);   // the region is free once these complete
             mma_commit(dfull);
-            continue;
           }
-          for (int t = 0; t < sh.MT && ok; ++t) {
-            const uint32_t d = tmem + (uint32_t)(t * sh.dcol);
-            bool first = true;
-            for (int kb = 0; kb < sh.KB && ok; ++kb) {
-              const int nks = min(4, (sh.M - 64 * kb + 15) / 16);   // K steps holding orbitals
-              for (int u = 0; u < (taylor ? 4 : 2); ++u, ++g) {
-                const int st = g % sh.nst, use = g / sh.nst;
-                if (*abort_flag || !mbar_wait(full0 + 8 * st, use & 1, err, wait_ns)) {
-                  fail();
-                  ok = false;
-                  break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          __syncwarp();
+          continue;
+        }
+        for (int t = 0; t < sh.MT && ok; ++t) {
+          const uint32_t d = tmem + (uint32_t)(t * sh.dcol);
+          for (int kb = 0; kb < sh.KB && ok; ++kb) {
+            const int nks = kb == sh.KB - 1 ? nks_last : 4;   // K steps holding orbitals
+            for (int u = 0; u < (taylor ? 4 : 2); ++u, ++g) {
+              const int st = g % sh.nst, use = g / sh.nst;
+              if (!wait_all(full0 + 8 * st, use & 1)) { ok = false; break; }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              if (elect_one()) {
                 const uint64_t a = sw128_desc(smem_u32(smem + sh.ring_off + st * kTile));
                 // A_im (u >= 2) takes rows 0..2Np of the term operand, A_re and E - I rows Np..3Np
-                const uint32_t roff = (uint32_t)(kb * sh.bkb + ((taylor && u >= 2) ? 0 : sh.Np * 128));
-                const uint64_t bh = sw128_desc(bhi + roff), bl = sw128_desc(blo + roff);
+                const uint64_t roff = (uint64_t)(kb * bkb16 + ((taylor && u >= 2) ? 0u : np16));
                 const bool hi = (u & 1) == 0;
                 for (int ks = 0; ks < nks; ++ks) {
-                  const uint64_t dk = (uint64_t)(2 * ks);     // 16 bf16 = 32 bytes along K
-                  mma_bf16(d, a + dk, bh + dk, idesc, first ? 0u : 1u);
-                  first = false;
-                  if (hi) mma_bf16(d, a + dk, bl + dk, idesc, 1u);
+                  const uint64_t dk = roff + (uint64_t)(2 * ks);   // 16 bf16 = 32 bytes along K
+                  mma_bf16(d, a + (uint64_t)(2 * ks), dbh + dk, idesc, (kb | u | ks) != 0 ? 1u : 0u);
+                  if (hi) mma_bf16(d, a + (uint64_t)(2 * ks), dbl + dk, idesc, 1u);
                 }
                 mma_commit(empty0 + 8 * st);
               }
+              __syncwarp();
             }
           }
-          if (ok) mma_commit(dfull);
+        }
+        if (ok) {
+          if (elect_one()) mma_commit(dfull);
+          __syncwarp();
         }
       }
-      mma_commit(done);   // arrives once every issued MMA has completed
     }
+    if (elect_one()) mma_commit(done);   // arrives once every issued MMA has completed
+    __syncwarp();
   } else {
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31; with 8 epilogue warps two
-    // share each lane quadrant and take alternate 16-column chunks ----
-    const int r = 32 * (warp & 3) + lane;
+    // ---- epilogue: warp w owns TMEM lanes 32 (w % 4) .. + 31 as two 16-lane slabs, read and
+    // written in the mma fragment layout; with 8 epilogue warps two share each lane quadrant and
+    // take alternate 16-column groups.  The term operand is written by transposed 8x8 stores:
+    // one 16-byte row chunk holds 8 consecutive orbitals of one operand row ----
+    const int qd = warp & 3, r = 32 * qd + lane;
     const int half = EPI == 8 ? (warp - 2) >> 2 : 0, cstep = EPI == 8 ? 32 : 16;
-    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
-    uint8_t* bh8 = smem + sh.bhi_off;
-    uint8_t* bl8 = smem + sh.blo_off;
+    const uint32_t lanes = (uint32_t)(32 * qd) << 16;
+    const uint32_t bhi_s = smem_u32(smem + sh.bhi_off), blo_s = smem_u32(smem + sh.blo_off);
     const uint32_t sreg = (uint32_t)(sh.MT * sh.dcol);   // S region after the D columns
-    // term operand entry (row R, K = i): split BF16 into both halves
-    auto put = [&](int R, int i, float x) {
-      const uint32_t o = (uint32_t)((i >> 6) * sh.bkb) + sw128_off(R, i & 63);
-      const __nv_bfloat16 h = __float2bfloat16_rn(x);
-      *reinterpret_cast<__nv_bfloat16*>(bh8 + o) = h;
-      *reinterpret_cast<__nv_bfloat16*>(bl8 + o) = __float2bfloat16_rn(x - __bfloat162float(h));
+    const int jj = lane >> 3, kk = lane & 7, fr = lane >> 2, fc = 2 * (lane & 3);
+    // fragment element j: lane offset fr (+ 8), column offset fc (+ 1) (+ 8)
+    auto lane_of = [&](int j) { return fr + ((j & 2) ? 8 : 0); };
+    auto col_of = [&](int j) { return fc + (j & 1) + ((j & 4) ? 8 : 0); };
+    // shared address of the row chunk (operand row R, orbitals i0 .. i0 + 7) of one 8x8 store
+    auto chunk = [&](uint32_t buf, int R, int i0) {
+      return buf + (uint32_t)((i0 >> 6) * sh.bkb + R * 128 + ((((i0 & 63) >> 3) ^ (R & 7)) << 4));
     };
-    // column c of a tile: real part of column b = c (c < Np) or imaginary part of b = c - Np
-    auto put_term = [&](int i, int c, float x, bool neg_copy) {
-      if (c < sh.Np) {
-        put(sh.Np + c, i, x);
+    // the block's values (orbitals i0b .., columns c0 ..) into operand rows Np + c, and with neg,
+    // -value into rows c - Np for the imaginary columns c >= Np
+    auto put_block = [&](const float (&v)[8], int i0b, int c0, bool neg) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) split_pair(v[2 * j], v[2 * j + 1], h[j], l[j]);
+      // matrix jj: orbitals i0b + 8 (jj & 1) .., columns c0 + 8 (jj >> 1) ..; this lane: row kk
+      const int i0 = i0b + 8 * (jj & 1), c = c0 + 8 * (jj >> 1) + kk;
+      stsm_x4_t(chunk(bhi_s, sh.Np + c, i0), h);
+      stsm_x4_t(chunk(blo_s, sh.Np + c, i0), l);
+      if (!neg || c0 + 8 < sh.Np) return;   // no imaginary column in the group
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        h[j] ^= 0x80008000u;
+        l[j] ^= 0x80008000u;
+      }
+      if (c0 >= sh.Np) {
+        stsm_x4_t(chunk(bhi_s, c - sh.Np, i0), h);
+        stsm_x4_t(chunk(blo_s, c - sh.Np, i0), l);
       } else {
-        put(sh.Np + c, i, x);                 // rows 2Np..3Np: T_im
-        if (neg_copy) put(c - sh.Np, i, -x);  // rows 0..Np: -T_im
+        // only the second 8-column block is imaginary: matrices 2, 3 (lanes 0..15 give rows)
+        const int cn = c0 + 8 + kk - sh.Np;
+        stsm_x2_t(chunk(bhi_s, cn, i0), h[2], h[3]);
+        stsm_x2_t(chunk(blo_s, cn, i0), l[2], l[3]);
       }
     };
-    int rq = 0;
+    int rq = 0, jw = 0;
     bool ok = true;
+    // resident A: the staging tiles into tensor memory; lane r takes row r of every tile (16-byte
+    // chunks in the 128-byte swizzle), the two warps of a lane quadrant take planes
+    // {2 half, 2 half + 1} of the first np planes, from TMEM column col0
+    auto copy_planes = [&](int np, int col0) {
+      const bool okw = !*abort_flag && mbar_wait(afull, jw & 1, err, wait_ns);
+      if (!__all_sync(0xffffffffu, okw)) { fail(); return false; }
+      for (int u = 2 * half; u < 2 * half + 2 && u < np; ++u)
+        for (int kb = 0; kb < sh.KB; ++kb) {
+          const uint4* row = reinterpret_cast<const uint4*>(smem + sh.ares_off + (kb * 4 + u) * kTile + r * 128);
+          uint32_t v[32];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const uint4 c = row[j ^ (r & 7)];
+            v[4 * j] = c.x; v[4 * j + 1] = c.y; v[4 * j + 2] = c.z; v[4 * j + 3] = c.w;
+          }
+          const uint32_t ta = tmem + lanes + (uint32_t)(col0 + 32 * (u * sh.KB + kb));
+          tmem_st16(ta, *reinterpret_cast<const uint32_t(*)[16]>(v));
+          tmem_st16(ta + 16, *reinterpret_cast<const uint32_t(*)[16]>(v + 16));
+        }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      mbar_arrive(acopied);   // the staging region may take the next tiles
+      ++jw;
+      return true;
+    };
+    if (sh.eres && !copy_planes(2, sh.ecol)) ok = false;
     for (int w = blockIdx.x; w < sh.Nw && ok; w += gridDim.x) {
       if (alive && !alive[w]) continue;
+      if (sh.resident && !copy_planes(4, sh.acol)) { ok = false; break; }
       // S = X (this walker's columns) and the operand [X_re; X_im] for the first one-body round
-      for (int t = 0; t < sh.MT; ++t) {
-        const int i = 128 * t + r;
-        const bool in_b = i < 64 * sh.KB;
-        for (int c0 = 16 * half; c0 < sh.n2; c0 += cstep) {
-          // the chunk's 16 loads first, all in flight together, then the operand stores
-          double xv[16];
+      for (int t = 0; t < sh.MT; ++t)
+        for (int sl = 0; sl < 2; ++sl) {
+          const int i0b = 128 * t + 32 * qd + 16 * sl;
+          const bool in_b = i0b < 64 * sh.KB;
+          const uint32_t tl = tmem + ((uint32_t)(32 * qd + 16 * sl) << 16);
+          for (int c0 = 16 * half; c0 < sh.n2; c0 += cstep) {
+            double xv[8];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int c = c0 + e, b = c < sh.Np ? c : c - sh.Np;
-            xv[e] = (i < sh.M && b < sh.N)
-                        ? phi_in[(c < sh.Np ? 0 : plane) + ((int64_t)w * sh.N + b) * sh.M + i]
-                        : 0.0;
-          }
-          uint32_t v[16];
+            for (int j = 0; j < 8; ++j) {
+              const int i = i0b + lane_of(j), c = c0 + col_of(j), b = c < sh.Np ? c : c - sh.Np;
+              xv[j] = (i < sh.M && b < sh.N)
+                          ? phi_in[(c < sh.Np ? 0 : plane) + ((int64_t)w * sh.N + b) * sh.M + i]
+                          : 0.0;
+            }
+            float x[8];
+            uint32_t v[8];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const float x = (float)xv[e];
-            v[e] = __float_as_uint(x);
-            if (in_b) put_term(i, c0 + e, x, false);
+            for (int j = 0; j < 8; ++j) {
+              x[j] = (float)xv[j];
+              v[j] = __float_as_uint(x[j]);
+            }
+            tmem_st_frag(tl + sreg + (uint32_t)(t * sh.dcol + c0), v);
+            if (in_b) put_block(x, i0b, c0, false);
           }
-          tmem_st16(tmem + lanes + sreg + (uint32_t)(t * sh.dcol + c0), v);
         }
-      }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -357,47 +486,52 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
         if (!__all_sync(0xffffffffu, okw)) { fail(); ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const float inv = (q >= 1 && q <= sh.order) ? 1.f / (float)q : 1.f;
-        for (int t = 0; t < sh.MT; ++t) {
-          const int i = 128 * t + r;
-          const bool in_b = i < 64 * sh.KB;
-          for (int c0 = 16 * half; c0 < sh.n2; c0 += cstep) {
-            uint32_t dv[16], sv[16];
-            tmem_ld16(tmem + lanes + (uint32_t)(t * sh.dcol + c0), dv);
-            tmem_ld16(tmem + lanes + sreg + (uint32_t)(t * sh.dcol + c0), sv);
-            if (q == 0) {
-              // T_0 = X + (E - I) X: S = T_0, operand = T_0
+        for (int t = 0; t < sh.MT; ++t)
+          for (int sl = 0; sl < 2; ++sl) {
+            const int i0b = 128 * t + 32 * qd + 16 * sl;
+            const bool in_b = i0b < 64 * sh.KB;
+            const uint32_t tl = tmem + ((uint32_t)(32 * qd + 16 * sl) << 16);
+            for (int c0 = 16 * half; c0 < sh.n2; c0 += cstep) {
+              uint32_t dv[8], sv[8];
+              tmem_ld_frag(tl + (uint32_t)(t * sh.dcol + c0), dv);
+              tmem_ld_frag(tl + sreg + (uint32_t)(t * sh.dcol + c0), sv);
+              tmem_wait_ld();
+              float x[8];
+              if (q == 0) {
+                // T_0 = X + (E - I) X: S = T_0, operand = T_0
 #pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                const float x = __uint_as_float(sv[e]) + __uint_as_float(dv[e]);
-                sv[e] = __float_as_uint(x);
-                if (in_b) put_term(i, c0 + e, x, true);
-              }
-              tmem_st16(tmem + lanes + sreg + (uint32_t)(t * sh.dcol + c0), sv);
-            } else if (!last) {
-              // T_q = A T_{q-1} / q; S += T_q; operand = T_q, or S after the last term
+                for (int j = 0; j < 8; ++j) {
+                  x[j] = __uint_as_float(sv[j]) + __uint_as_float(dv[j]);
+                  sv[j] = __float_as_uint(x[j]);
+                }
+                tmem_st_frag(tl + sreg + (uint32_t)(t * sh.dcol + c0), sv);
+                if (in_b) put_block(x, i0b, c0, true);
+              } else if (!last) {
+                // T_q = A T_{q-1} / q; S += T_q; operand = T_q, or S after the last term
+                float y[8];
 #pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                const float x = __uint_as_float(dv[e]) * inv;
-                const float y = __uint_as_float(sv[e]) + x;
-                sv[e] = __float_as_uint(y);
-                if (in_b) put_term(i, c0 + e, q < sh.order ? x : y, q < sh.order);
-              }
-              tmem_st16(tmem + lanes + sreg + (uint32_t)(t * sh.dcol + c0), sv);
-            } else if (i < sh.M) {
-              // Phi' = S + (E - I) S
+                for (int j = 0; j < 8; ++j) {
+                  x[j] = __uint_as_float(dv[j]) * inv;
+                  y[j] = __uint_as_float(sv[j]) + x[j];
+                  sv[j] = __float_as_uint(y[j]);
+                }
+                tmem_st_frag(tl + sreg + (uint32_t)(t * sh.dcol + c0), sv);
+                if (in_b) put_block(q < sh.order ? x : y, i0b, c0, q < sh.order);
+              } else {
+                // Phi' = S + (E - I) S
 #pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                const int c = c0 + e, b = c < sh.Np ? c : c - sh.Np;
-                if (b < sh.N) {
-                  const float y = __uint_as_float(sv[e]) + __uint_as_float(dv[e]);
-                  const int64_t gi = (c < sh.Np ? 0 : plane) + ((int64_t)w * sh.N + b) * sh.M + i;
-                  phi_out[gi] = (double)y;
-                  if (phi_out32) phi_out32[gi] = y;
+                for (int j = 0; j < 8; ++j) {
+                  const int i = i0b + lane_of(j), c = c0 + col_of(j), b = c < sh.Np ? c : c - sh.Np;
+                  if (i < sh.M && b < sh.N) {
+                    const float y = __uint_as_float(sv[j]) + __uint_as_float(dv[j]);
+                    const int64_t gi = (c < sh.Np ? 0 : plane) + ((int64_t)w * sh.N + b) * sh.M + i;
+                    phi_out[gi] = (double)y;
+                    if (phi_out32) phi_out32[gi] = y;
+                  }
                 }
               }
             }
           }
-        }
         if (!last) {
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -475,7 +609,11 @@ TclShape shape_of(const Ctx& c, int nst, int resident) {
   s.nst = nst;
   s.bkb = 3 * s.Np * 128;
   s.dcol = (s.n2 + 63) / 64 * 64;
-  uint32_t need = (uint32_t)(2 * s.MT * s.dcol), cols = 32;
+  s.acol = 2 * s.MT * s.dcol;
+  uint32_t need = (uint32_t)(s.acol + (resident ? 4 * 32 * s.KB : 0)), cols = 32;
+  s.ecol = (int)need;
+  s.eres = resident && need + 2 * 32 * s.KB <= 512u;
+  if (s.eres) need += 2 * 32 * s.KB;
   while (cols < need) cols <<= 1;
   s.tcols = cols;
   s.order = c.opt.taylor_order;
@@ -517,7 +655,7 @@ bool two_per_sm(const TclShape& s) { return !s.resident && s.smem_bytes <= 113 *
 bool propagate_tcl_ok(const Ctx& c) {
   if (c.M < 1 || c.M > 256 || c.N < 1 || c.N > 32 || c.opt.taylor_order < 1) return false;
   const TclShape s = plan(c);
-  return s.smem_bytes <= 227 * 1024 && s.tcols <= 256;
+  return s.smem_bytes <= 227 * 1024 && s.tcols <= (two_per_sm(s) ? 256u : 512u);
 }
 
 int propagate_tcl_mp(int M) { return (M + 7) / 8 * 8; }
