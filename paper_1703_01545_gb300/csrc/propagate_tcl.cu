@@ -120,6 +120,33 @@ __device__ __forceinline__ uint32_t elect_one() {
   return p;
 }
 
+// binary64 -> binary32 with round-to-nearest-even, on the integer pipes (IEEE 754 layouts:
+// sign, 11 / 8 exponent bits biased by 1023 / 127, 52 / 23 fraction bits); the FP64 pipe, which
+// also carries the conversion instructions, is thin on this part.  Results in the binary32
+// normal range are formed here (a carry out of the fraction rounds up into the exponent, up
+// to infinity); zero, subnormal, out-of-range and non-finite inputs take the conversion
+// instruction.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;                 // binary32 biased exponent
+  if (e < 1 || e > 254) return __double2float_rn(x);
+  const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29), rem = lo & 0x1fffffffu;
+  const uint32_t up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) | ((((uint32_t)e << 23) | m) + up));
+}
+
+// binary32 -> binary64 (exact) on the integer pipes; zero keeps its sign, subnormal and
+// non-finite inputs take the conversion instruction
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f), e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 255u) {
+    if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    return (double)f;
+  }
+  const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 // x = hi + lo for a pair of floats (a in the low half): both halves as packed BF16 pairs
 __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -446,36 +473,50 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
       ++jw;
       return true;
     };
+    // this warp's (tile, slab, 16-column group) items: item it -> tile it / (2 ngh), slab
+    // (it % 2 ngh) / ngh, columns 16 half + (it % ngh) cstep
+    const int ngh = (sh.n2 - 16 * half + cstep - 1) / cstep;
+    const int nitems = sh.MT * 2 * ngh;
     if (sh.eres && !copy_planes(2, sh.ecol)) ok = false;
     for (int w = blockIdx.x; w < sh.Nw && ok; w += gridDim.x) {
       if (alive && !alive[w]) continue;
-      if (sh.resident && !copy_planes(4, sh.acol)) { ok = false; break; }
-      // S = X (this walker's columns) and the operand [X_re; X_im] for the first one-body round
-      for (int t = 0; t < sh.MT; ++t)
-        for (int sl = 0; sl < 2; ++sl) {
-          const int i0b = 128 * t + 32 * qd + 16 * sl;
-          const bool in_b = i0b < 64 * sh.KB;
-          const uint32_t tl = tmem + ((uint32_t)(32 * qd + 16 * sl) << 16);
-          for (int c0 = 16 * half; c0 < sh.n2; c0 += cstep) {
-            double xv[8];
+      // S = X (this walker's columns) and the operand [X_re; X_im] for the first one-body round.
+      // The (tile, slab, column group) items of this warp go in batches of 4: every load of a
+      // batch is issued first, so the walker pays one memory latency per batch, and the first
+      // batch's loads are in flight while A moves into tensor memory.
+      for (int b0 = 0; b0 == 0 || b0 < nitems; b0 += 4) {   // one pass at least: the A copy
+        double xv[4][8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int i = i0b + lane_of(j), c = c0 + col_of(j), b = c < sh.Np ? c : c - sh.Np;
-              xv[j] = (i < sh.M && b < sh.N)
-                          ? phi_in[(c < sh.Np ? 0 : plane) + ((int64_t)w * sh.N + b) * sh.M + i]
-                          : 0.0;
-            }
-            float x[8];
-            uint32_t v[8];
+        for (int u = 0; u < 4; ++u) {
+          const int it = b0 + u, t = it / (2 * ngh), sl = (it % (2 * ngh)) / ngh;
+          const int c0 = 16 * half + (it % ngh) * cstep, i0b = 128 * t + 32 * qd + 16 * sl;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              x[j] = (float)xv[j];
-              v[j] = __float_as_uint(x[j]);
-            }
-            tmem_st_frag(tl + sreg + (uint32_t)(t * sh.dcol + c0), v);
-            if (in_b) put_block(x, i0b, c0, false);
+          for (int j = 0; j < 8; ++j) {
+            const int i = i0b + lane_of(j), c = c0 + col_of(j), b = c < sh.Np ? c : c - sh.Np;
+            xv[u][j] = (it < nitems && i < sh.M && b < sh.N)
+                           ? phi_in[(c < sh.Np ? 0 : plane) + ((int64_t)w * sh.N + b) * sh.M + i]
+                           : 0.0;
           }
         }
+        if (b0 == 0 && sh.resident && !copy_planes(4, sh.acol)) { ok = false; break; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int it = b0 + u, t = it / (2 * ngh), sl = (it % (2 * ngh)) / ngh;
+          const int c0 = 16 * half + (it % ngh) * cstep, i0b = 128 * t + 32 * qd + 16 * sl;
+          if (it >= nitems) break;
+          const uint32_t tl = tmem + ((uint32_t)(32 * qd + 16 * sl) << 16);
+          float x[8];
+          uint32_t v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            x[j] = f64_to_f32_rn(xv[u][j]);
+            v[j] = __float_as_uint(x[j]);
+          }
+          tmem_st_frag(tl + sreg + (uint32_t)(t * sh.dcol + c0), v);
+          if (i0b < 64 * sh.KB) put_block(x, i0b, c0, false);
+        }
+      }
+      if (!ok) break;
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -525,7 +566,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
                   if (i < sh.M && b < sh.N) {
                     const float y = __uint_as_float(sv[j]) + __uint_as_float(dv[j]);
                     const int64_t gi = (c < sh.Np ? 0 : plane) + ((int64_t)w * sh.N + b) * sh.M + i;
-                    phi_out[gi] = (double)y;
+                    phi_out[gi] = f32_to_f64(y);
                     if (phi_out32) phi_out32[gi] = y;
                   }
                 }

@@ -43,18 +43,6 @@ struct FastOvArgs {
   double log_shift;
 };
 
-// s + c += (h + l) x for FP32 h, l, x with the product and the addition error-free (Dekker
-// product through FMA, Knuth two-sum); the intrinsics keep the compiler from contracting them.
-__device__ __forceinline__ void df_acc(float& s, float& c, float h, float l, float x) {
-  const float p = __fmul_rn(h, x);
-  const float e = __fmaf_rn(h, x, -p);                  // h x - p, exactly
-  const float t = __fadd_rn(s, p);
-  const float bp = __fsub_rn(t, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));   // s + p - t
-  s = t;
-  c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(l, x, e)));
-}
-
 // (s, c) += (s2, c2) for unevaluated FP32 pairs, the leading sum error-free (two-sum)
 __device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
   const float t = __fadd_rn(s, s2);
@@ -231,18 +219,17 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
       else { sp = 1; const int e2 = ent - nu * nu; r = e2 / nd; c = e2 % nd; }
       const int n0 = sp ? nu : 0;
       if (f32) {
-        // phi is exactly representable in FP32 here: each term psi*phi is formed exactly as
-        // (psih*phi rounded) + (its FMA residual) + psil*phi and summed as an unevaluated pair
-        // (s, c) with error-free additions, ~2^-46 relative to sum |terms|; the FP64 pipe
-        // sees only the final conversions
+        // phi is FP32 here (the propagator's FP32 output): FP32 products of psi (rounded to
+        // FP32) and phi, summed in FP32 (~2^-24 relative to sum |terms| per part; the log
+        // determinant then carries ~1e-6 of rounding, far below the step's other FP32 and
+        // split-BF16 errors); the FP64 pipe sees only the final conversions
         const float* hs = a.psih + (int64_t)(n0 + r) * M;
-        const float* ls = a.psil + (int64_t)(n0 + r) * M;
         const float* xr = pfr + (n0 + c) * MP;
         const float* xi = pfi + (n0 + c) * MP;
         for (int i = part; i < M; i += 4) {
-          const float h = __ldg(hs + i), l = __ldg(ls + i);
-          df_acc(sr, cr, h, l, xr[i]);
-          df_acc(si, ci, h, l, xi[i]);
+          const float h = __ldg(hs + i);
+          sr = fmaf(h, xr[i], sr);
+          si = fmaf(h, xi[i], si);
         }
       } else {
         const double* ps = a.psi + (int64_t)(n0 + r) * M;

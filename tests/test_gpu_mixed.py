@@ -168,10 +168,18 @@ def test_cholesky_qr_orthonormalises_and_lowers_log_overlap(cfg, which):
     g.close()
 
 
+# The split path's overlap update sums Psi^T Phi' in FP32, so its log O carries ~1e-6 of
+# rounding against an FP64 recomputation.  That error does not accumulate in the weights: each
+# step's ratio log O(Phi') - log O(Phi) cancels the previous step's error (the sum telescopes),
+# so a weight carries at most the last update's rounding.
+LOGO_F32 = 1e-5
+
+
 def test_gram_schmidt_log_overlap_update_matches_recomputation():
     """Split path: Gram-Schmidt lowers log O by sum_j log R_jj (Sec. II.D; Phi -> Phi R^{-1}) instead
     of recomputing the overlaps.  A refresh (the timing call's refresh form recomputes log O and
-    Theta from the walkers in FP64) must land on the same values."""
+    Theta from the walkers in FP64) must land on the same values, up to the FP32 rounding of the
+    overlap update."""
     afq = need_gpu()
     d = system_data("C2", "B", "moderate")
     nw = 64
@@ -186,10 +194,10 @@ def test_gram_schmidt_log_overlap_update_matches_recomputation():
     g.close()
     live = before["alive"]
     assert live.sum() >= nw - 2
-    assert np.abs(after["logO"].real - before["logO"].real)[live].max() < 1e-10
+    assert np.abs(after["logO"].real - before["logO"].real)[live].max() < LOGO_F32
     dphase = np.angle(np.exp(1j * (after["logO"].imag - before["logO"].imag)))
-    assert np.abs(dphase[live]).max() < 1e-10
-    assert abs(em1[0] - em0[0]) < 1e-6 * abs(em0[0])
+    assert np.abs(dphase[live]).max() < LOGO_F32
+    assert abs(em1[0] - em0[0]) < 1e-5 * abs(em0[0])
 
 
 def test_kernel_timing_leaves_the_walkers_unchanged():
@@ -210,8 +218,8 @@ def test_kernel_timing_leaves_the_walkers_unchanged():
     assert np.array_equal(after["w"], before["w"])
     assert np.array_equal(after["alive"], before["alive"])
     live = before["alive"]
-    assert np.abs(after["logO"].real - before["logO"].real)[live].max() < 1e-10
-    assert abs(em1[0] - em0[0]) < 1e-6 * abs(em0[0])
+    assert np.abs(after["logO"].real - before["logO"].real)[live].max() < LOGO_F32
+    assert abs(em1[0] - em0[0]) < 1e-5 * abs(em0[0])
     # Gram-Schmidt of walkers that are already orthonormal changes them only by rounding
     assert afq.afqmc_time_kernel(g.h, afq.K_MGS, 2) > 0
     again = g.state()
