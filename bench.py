@@ -331,8 +331,8 @@ def measure_kernels(afq, A, dA, nw, precision, workload, stream):
       force bias 4 X N M;  V_HS 4 P X, P = M (M + 1) / 2 (packed symmetric L; the full count
       4 M^2 X beside it);  propagator (8 order + 8) M^2 N (Taylor terms and the two one-body
       half steps);  overlap (split path: its FP64 part, the LU, 8/3 sum N_s^3; the overlap sums
-      run as FP32 pairs and are reported beside it);  Gram-Schmidt 8 M sum N_s^2;  local energy
-      4 X M sum N_s^2 + 8 X sum N_s^2.
+      run in FP32 and are reported beside it);  orthonormalisation 8 M sum N_s^2 (Gram-Schmidt
+      and Cholesky QR alike);  local energy 4 X M sum N_s^2 + 8 X sum N_s^2.
     Tensor-core kernels also give the split-BF16 MMA work they issue (3 products per product,
     padded tiles) as mma_flops.  Launches per block: 5 propagation steps, one Gram-Schmidt and
     one energy, for one system (system A)."""
@@ -410,22 +410,34 @@ def measure_kernels(afq, A, dA, nw, precision, workload, stream):
                                       variant=pv)
         lu = 8.0 / 3.0 * N3 * nw
         out["overlap"] = entry(afq.K_OVERLAP_UPDATE, STEPS_PER_BLOCK, lu, "alu", f64,
-                               "k_overlap_fast (update form: overlap sums as FP32 pairs, FP64 LU and "
+                               "k_overlap_fast (update form: overlap sums in FP32, FP64 LU and "
                                "log det, FP32 Theta)",
                                traffic=tr("walker_fast.cu", "overlap_fast"),
-                               fp32_pair_flops_per_launch=4.0 * M * N2 * nw,
+                               fp32_overlap_flops_per_launch=4.0 * M * N2 * nw,
                                fp32_theta_flops_per_launch=8.0 * M * N2 * nw,
                                flops_note="only the FP64 LU counts against the FP64 peak")
-        out["mgs"] = entry(afq.K_MGS, 1, mgs, "alu", f64, "k_mgs_reg / k_mgs_warp (FP64 Gram-Schmidt)",
-                           traffic=tr("walker_fast.cu", "mgs_reg"))
+        if A.info().tuned_orthonormalise == 1:
+            out["mgs"] = entry(afq.K_MGS, 1, mgs, "alu", f64,
+                               "k_mgs_chol (Cholesky QR: Gram matrix in FP32 pairs, FP64 factor "
+                               "and log det, Q in FP32 pairs)",
+                               traffic=tr("walker_fast.cu", "mgs_chol"))
+        else:
+            out["mgs"] = entry(afq.K_MGS, 1, mgs, "alu", f64,
+                               "k_mgs_reg / k_mgs_warp (FP64 Gram-Schmidt)",
+                               traffic=tr("walker_fast.cu", "mgs_reg"))
         p2 = 4
         while p2 < max(nu, nd):
             p2 *= 2
         NPp = 2 * p2
+        if pad(M, 64) > 64:
+            # one product per spin block: rows (g, a < P2) and columns (w, re/im, b < P2) of
+            # each spin, padded to whole 128 x 256 tiles
+            emma = 3.0 * 2.0 * 2 * pad(X * p2, 128) * pad(2 * p2 * nw, 256) * pad(M, 64)
+        else:
+            emma = 3.0 * 2.0 * pad(X * NPp, 128) * pad(2 * NPp * nw, 256) * pad(M, 64)
         out["energy"] = entry(afq.K_EXCHANGE, 1, en, "tensor", bf16,
                               "k_energy_B + k_energy_tc (split-BF16 tcgen05 local energy)",
-                              mma=3.0 * 2.0 * (X * NPp) * (2 * NPp * nw) * pad(M, 64),
-                              traffic=tr("energy_tc.cu", "energy_tc"))
+                              mma=emma, traffic=tr("energy_tc.cu", "energy_tc"))
     else:
         out["force_bias"] = entry(afq.K_FORCE_BIAS, STEPS_PER_BLOCK, fb, "alu", f64,
                                   "k_gemm_f64_force_bias (FP64)")

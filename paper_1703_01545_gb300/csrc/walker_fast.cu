@@ -19,6 +19,16 @@ constexpr int kPad = 4;      // column padding (elements) of the shared copies o
 constexpr int kLd = 24;      // row stride (doubles) of the in-place LU factors of blocks above 8:
                              // the trailing updates' accesses (2 rows per pass) fall in distinct banks
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+
 struct FastOvArgs {
   const double* src;  // [2][Nw][N][M]  (propagated walkers in update mode)
   const float* src32; // the same in FP32 (update mode, may be null): no conversions needed,
@@ -52,8 +62,33 @@ __device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
   c = __fadd_rn(c, __fadd_rn(err, c2));
 }
 
-// LU factorisation with partial (row) pivoting of one spin block, P O = L U, in FP64 by W
-// lanes of a warp (W = 16: both halves of the warp factorise one block each, in step; W = 32:
+// Scalar-type details of the LU: the integer magnitude key of a component (the high word of
+// |x|, monotone in |x|) and its bounds (below: zero or subnormal, above: non-finite), the
+// biased exponent, the exact power of two 2^(bias - e), and a reciprocal.
+template <typename T> struct LuT;
+template <> struct LuT<double> {
+  static constexpr unsigned kMin = 0x00100000u, kInf = 0x7ff00000u;
+  static constexpr int kMaxE = 2046;
+  static __device__ __forceinline__ unsigned key(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
+  static __device__ __forceinline__ int expo(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+  static __device__ __forceinline__ double pow2(int eh) { return __hiloint2double((2046 - eh) << 20, 0); }
+  static __device__ __forceinline__ int bias() { return 1023; }
+  static __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+  static __device__ __forceinline__ double fm(double a, double b, double c) { return fma(a, b, c); }
+};
+template <> struct LuT<float> {
+  static constexpr unsigned kMin = 0x00800000u, kInf = 0x7f800000u;
+  static constexpr int kMaxE = 254;
+  static __device__ __forceinline__ unsigned key(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+  static __device__ __forceinline__ int expo(float x) { return (int)((__float_as_uint(x) >> 23) & 0xffu); }
+  static __device__ __forceinline__ float pow2(int eh) { return __uint_as_float((unsigned)(254 - eh) << 23); }
+  static __device__ __forceinline__ int bias() { return 127; }
+  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+  static __device__ __forceinline__ float fm(float a, float b, float c) { return fmaf(a, b, c); }
+};
+
+// LU factorisation with partial (row) pivoting of one spin block, P O = L U, in FP64 (or FP32,
+// T = float) by W lanes of a warp (W = 16: both halves of the warp factorise one block each, in step; W = 32:
 // one block per warp).  Pivot k interchanges whole rows, scales row k right of the diagonal by
 // 1 / pivot (U is unit upper triangular), stores 1 / pivot on the diagonal and updates the
 // trailing block; L, with the pivots as its diagonal, is left below the diagonal.  The pivots
@@ -65,23 +100,24 @@ __device__ __forceinline__ void df_add(float& s, float& c, float s2, float c2) {
 // scale uses one reciprocal, and row blocks of the trailing update that no lane needs are
 // skipped.  Each complex update is 4 FP64 fused multiply-adds.  Lane l owns column l % ns and
 // rows l / ns + q (W / ns), q < Q.  kmax: the larger block of the warp (uniform loop bound).
-template <int W, int Q, int LD>
-__device__ __forceinline__ void lu_block(double* __restrict__ ar, double* __restrict__ ai, int l,
-                                         int ns, int kmax, int* __restrict__ piv, double& dr,
-                                         double& di, int& dexp, bool& bad) {
+template <int W, int Q, int LD, typename T = double>
+__device__ __forceinline__ void lu_block(T* __restrict__ ar, T* __restrict__ ai, int l,
+                                         int ns, int kmax, int* __restrict__ piv, T& dr,
+                                         T& di, int& dexp, bool& bad) {
+  using S = LuT<T>;
   const int nsd = ns > 0 ? ns : 1, RS = W / nsd;
   const int c = l % nsd, r0 = l / nsd;
   const bool active = ns > 0 && r0 < RS;
-  dr = 1.0;
-  di = 0.0;
+  dr = T(1);
+  di = T(0);
   dexp = 0;
   bad = false;
   for (int k = 0; k < kmax; ++k) {
     const bool live = k < ns && !bad;
     unsigned key = 0u;
     if (live && l >= k && l < ns) {
-      const unsigned hr = (unsigned)__double2hiint(ar[l * LD + k]) & 0x7fffffffu;
-      const unsigned hi = (unsigned)__double2hiint(ai[l * LD + k]) & 0x7fffffffu;
+      const unsigned hr = S::key(ar[l * LD + k]);
+      const unsigned hi = S::key(ai[l * LD + k]);
       key = hr > hi ? hr : hi;
     }
     int p = l;
@@ -92,37 +128,37 @@ __device__ __forceinline__ void lu_block(double* __restrict__ ar, double* __rest
       if (ok > key || (ok == key && op < p)) { key = ok; p = op; }
     }
     // zero, subnormal-only or non-finite column: singular for this kernel
-    if (live && (key < 0x00100000u || key >= 0x7ff00000u)) bad = true;
+    if (live && (key < S::kMin || key >= S::kInf)) bad = true;
     const bool go = live && !bad;
     if (go && l == 0) piv[k] = p;
     if (go && p != k && l < ns) {
-      double t = ar[k * LD + l]; ar[k * LD + l] = ar[p * LD + l]; ar[p * LD + l] = t;
+      T t = ar[k * LD + l]; ar[k * LD + l] = ar[p * LD + l]; ar[p * LD + l] = t;
       t = ai[k * LD + l]; ai[k * LD + l] = ai[p * LD + l]; ai[p * LD + l] = t;
     }
     __syncwarp();
-    const double vr = go ? ar[k * LD + k] : 1.0, vi = go ? ai[k * LD + k] : 0.0;
+    const T vr = go ? ar[k * LD + k] : T(1), vi = go ? ai[k * LD + k] : T(0);
     {
-      const double tr = fma(dr, vr, -di * vi);
-      double ti = fma(dr, vi, di * vr);
-      double trr = tr;
+      const T tr = S::fm(dr, vr, -di * vi);
+      T ti = S::fm(dr, vi, di * vr);
+      T trr = tr;
       if (go && p != k) { trr = -tr; ti = -ti; }
       if (go) { dr = trr; di = ti; }
-      const int e1 = (__double2hiint(dr) >> 20) & 0x7ff, e2 = (__double2hiint(di) >> 20) & 0x7ff;
+      const int e1 = S::expo(dr), e2 = S::expo(di);
       const int eh = e1 > e2 ? e1 : e2;
-      if (eh > 0 && eh < 2046) {
-        const double sc = __hiloint2double((2046 - eh) << 20, 0);   // 2^(1023 - eh), exact
+      if (eh > 0 && eh < S::kMaxE) {
+        const T sc = S::pow2(eh);   // 2^(bias - eh), exact
         dr *= sc;
         di *= sc;
-        dexp += eh - 1023;
+        dexp += eh - S::bias();
       }
     }
-    const double rinv = __drcp_rn(fma(vr, vr, vi * vi));
-    const double ir = vr * rinv, ii = -vi * rinv;          // 1 / pivot
+    const T rinv = S::rcp(S::fm(vr, vr, vi * vi));
+    const T ir = vr * rinv, ii = -vi * rinv;          // 1 / pivot
     __syncwarp();
     if (go && l >= k && l < ns) {
-      const double xr = ar[k * LD + l], xi = ai[k * LD + l];
-      ar[k * LD + l] = (l == k) ? ir : fma(xr, ir, -xi * ii);
-      ai[k * LD + l] = (l == k) ? ii : fma(xr, ii, xi * ir);
+      const T xr = ar[k * LD + l], xi = ai[k * LD + l];
+      ar[k * LD + l] = (l == k) ? ir : S::fm(xr, ir, -xi * ii);
+      ai[k * LD + l] = (l == k) ? ii : S::fm(xr, ii, xi * ir);
     }
     __syncwarp();
     // A[r][c] -= A[r][k] U[k][c] for r, c > k: column k and row k are not written, so no
@@ -130,15 +166,15 @@ __device__ __forceinline__ void lu_block(double* __restrict__ ar, double* __rest
     const bool colk = go && active && c > k;
     const int qf = colk ? max(0, (k + 1 - r0 + RS - 1) / RS) : Q;
     const int q0 = __reduce_min_sync(0xffffffffu, qf);
-    const double kr = colk ? ar[k * LD + c] : 0.0, ki = colk ? ai[k * LD + c] : 0.0;
+    const T kr = colk ? ar[k * LD + c] : T(0), ki = colk ? ai[k * LD + c] : T(0);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       if (q >= q0) {
         const int r = r0 + q * RS;
         if (colk && r < ns && r > k) {
-          const double fr = ar[r * LD + k], fi = ai[r * LD + k];
-          ar[r * LD + c] = fma(-fr, kr, fma(fi, ki, ar[r * LD + c]));
-          ai[r * LD + c] = fma(-fr, ki, fma(-fi, kr, ai[r * LD + c]));
+          const T fr = ar[r * LD + k], fi = ai[r * LD + k];
+          ar[r * LD + c] = S::fm(-fr, kr, S::fm(fi, ki, ar[r * LD + c]));
+          ai[r * LD + c] = S::fm(-fr, ki, S::fm(-fi, kr, ai[r * LD + c]));
         }
       }
     }
@@ -167,7 +203,8 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   double* aug = a.fp64_copy ? pi + NMP : smo;   // LU factors: spin s at aug + s * SPB, re, im [NSM][LDA]
   // FP32 copies for Theta: converting once here keeps double->float conversions (which run
   // on the FP64 pipe) off the Theta loop
-  float* pfr = reinterpret_cast<float*>(aug + 2 * SPB);  // [N][MP]
+  float* pfr = a.fp64_copy ? reinterpret_cast<float*>(aug + 2 * SPB)   // [N][MP]
+                           : reinterpret_cast<float*>(smo);
   float* pfi = pfr + NMP;
   float* invf = pfi + NMP;     // spin s at invf + s * 2 * 16 * 16: re [16][16], im [16][16]
   __shared__ double s_det[2][2];   // per spin: determinant mantissa (re, im) ...
@@ -184,6 +221,27 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
   const int64_t plane = (int64_t)a.Nw * NM, wbase = (int64_t)wk * NM;
   const bool f32 = upd && a.src32 != nullptr;
   const bool inplace = upd && a.src == a.phi;   // the propagator already wrote Phi
+  if (f32 && inplace) {
+    // the FP32 walker into the padded shared layout by asynchronous copies, all in flight at
+    // once (16-byte chunks when the columns allow, else 4-byte words)
+    const uint32_t sr0 = smem_addr(pfr), si0 = smem_addr(pfi);
+    const float* g0 = a.src32 + wbase;
+    if ((M & 3) == 0) {
+      const int q = M >> 2;
+      for (int c = tid; c < N * q; c += blockDim.x) {
+        const int n = c / q, i = (c - n * q) << 2;
+        cp_async16(sr0 + 4u * (uint32_t)(n * MP + i), g0 + n * M + i);
+        cp_async16(si0 + 4u * (uint32_t)(n * MP + i), g0 + plane + n * M + i);
+      }
+    } else {
+      for (int e = tid; e < NM; e += blockDim.x) {
+        const uint32_t es = (uint32_t)(e + (e / M) * kPad);
+        cp_async4(sr0 + 4u * es, g0 + e);
+        cp_async4(si0 + 4u * es, g0 + plane + e);
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else
   for (int e = tid; e < NM; e += blockDim.x) {
     const int es = e + (e / M) * kPad;   // (n, i) in the padded layout
     if (f32) {
@@ -254,9 +312,11 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
       }
       // every lane of the entry holds the combined pair; part 0 converts the real sum and
       // part 1 the imaginary one, so each lane issues 2 conversions and 1 add
+      // (FP32 update: the factorisation below runs in FP32 on these)
       const bool odd = part & 1;
-      const double v = (double)(odd ? si : sr) + (double)(odd ? ci : cr);
-      if (ent < nn && part < 2) aug[sp * SPB + (odd ? PLN : 0) + r * LDA + c] = v;
+      if (ent < nn && part < 2)
+        invf[sp * 2 * kNsMax * kNsMax + (odd ? kNsMax * kNsMax : 0) + r * kNsMax + c] =
+            (odd ? si : sr) + (odd ? ci : cr);
     } else {
       re += __shfl_xor_sync(0xffffffffu, re, 1);
       im += __shfl_xor_sync(0xffffffffu, im, 1);
@@ -271,7 +331,42 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
     }
   }
   __syncthreads();
-  if (NSM == 8) {
+  if (f32) {
+    // FP32 update: the factors in FP32 in place (they are what the Theta solves read), the
+    // determinant as an FP32 mantissa and a power-of-two exponent; log O then carries FP32
+    // rounding, which the next step's ratio cancels
+    if (NSM == 8) {
+      if (warp == 0) {
+        const int h = lane >> 4, l16 = lane & 15, ns = h ? nd : nu;
+        float* ar = invf + h * 2 * kNsMax * kNsMax;
+        float dr, di;
+        int dexp;
+        bool bad;
+        lu_block<16, 4, kNsMax, float>(ar, ar + kNsMax * kNsMax, l16, ns, nu > nd ? nu : nd, s_piv[h],
+                                       dr, di, dexp, bad);
+        if (l16 == 0) {
+          s_det[h][0] = dr;
+          s_det[h][1] = di;
+          s_dexp[h] = dexp;
+          s_bad[h] = bad ? 1 : 0;
+        }
+      }
+    } else if (warp < 2) {
+      const int sp = warp, ns = sp ? nd : nu;
+      float* ar = invf + sp * 2 * kNsMax * kNsMax;
+      float dr, di;
+      int dexp;
+      bool bad;
+      lu_block<32, ROWS, kNsMax, float>(ar, ar + kNsMax * kNsMax, lane, ns, ns, s_piv[sp], dr, di,
+                                        dexp, bad);
+      if (lane == 0) {
+        s_det[sp][0] = dr;
+        s_det[sp][1] = di;
+        s_dexp[sp] = dexp;
+        s_bad[sp] = bad ? 1 : 0;
+      }
+    }
+  } else if (NSM == 8) {
     if (warp == 0) {   // both spin blocks, 16 lanes each
       const int h = lane >> 4, l16 = lane & 15, ns = h ? nd : nu;
       double* ar = aug + h * SPB;
@@ -313,6 +408,7 @@ __global__ void __launch_bounds__(256) k_overlap_fast(FastOvArgs a) {
       }
     s_perm[tid] = pw;
   }
+  if (!f32)
   for (int e = tid; e < nn; e += blockDim.x) {   // the factors (and 1/pivot) to FP32, once
     int sp = 0, r, c;
     if (e < nu * nu) { r = e / nu; c = e % nu; }
@@ -790,7 +886,8 @@ size_t smem_fast_overlap(const Ctx& c, bool fp64_copy = true) {
   const size_t nmp = (size_t)c.N * (c.M + kPad);
   const bool small = std::max(c.n_up, c.N - c.n_up) <= 8;   // the NSM = 8 factor layout
   const size_t aug = small ? 2 * 2 * 8 * 8 : 2 * 2 * kNsMax * kLd;
-  return sizeof(double) * ((fp64_copy ? 2 * nmp : 0) + aug) +
+  // the FP32 update factorises in the FP32 factor arrays: no FP64 copy of Phi, no FP64 factors
+  return sizeof(double) * (fp64_copy ? 2 * nmp + aug : 0) +
          sizeof(float) * (2 * nmp + 2 * 2 * kNsMax * kNsMax);
 }
 size_t smem_mgs_warp(const Ctx& c) { return sizeof(double) * 4 * (size_t)c.N * c.M; }   // two walkers
