@@ -595,6 +595,260 @@ __global__ void __launch_bounds__(EBLayout<NP>::THREADS, 1)
                  : "memory");
 }
 
+// Spin-blocked form with two k slices (64 < M <= 128): a CTA keeps the whole Theta column tile
+// of one spin block resident (both k slices, hi and lo: 128 KB) and streams a group of RG row
+// tiles of L-tilde through a 2-stage ring of one k slice each, so the operand traffic is one
+// Theta tile per item plus the row tiles (the per-tile form reloads both for every tile).
+// Work item = (spin, column tile, row group); each walker's exchange sums over the item's row
+// tiles add up in the epilogue, part[(spin * NG + group) * 2 + re/im) * NwP + w]; the traces
+// tr T^s_g of each tile go to trs.  Warp roles and epilogue as in k_energy_tc (8 epilogue
+// warps, rows staged with one word of padding); 227 KB of shared memory.
+template <int NP>
+struct ES2Layout {
+  static constexpr int NKB = 2;
+  static constexpr int A_BYTES = EBM * EBK * 2;                 // one k slice, one of hi / lo
+  static constexpr int B_BYTES = EBN * EBK * 2;
+  static constexpr int B_REGION = NKB * 2 * B_BYTES;            // (k slice, hi / lo)
+  static constexpr int A_OFFSET = B_REGION;
+  static constexpr int A_STAGE = 2 * A_BYTES;
+  static constexpr int CW = 2 * NP;                             // one walker's re | im columns
+  static_assert(CW == 32, "the swizzled staging assumes 32 columns per group");
+  static constexpr int STG_OFFSET = A_OFFSET + 2 * A_STAGE;
+  static constexpr int STG_BYTES = EWARPS * 32 * 33 * 4;
+  static constexpr int WPT = EBN / (2 * NP);
+  static constexpr int RED_OFFSET = STG_OFFSET + STG_BYTES;
+  static constexpr int RED_BYTES = 2 * 4 * WPT * 2 * 4;
+  static constexpr int BAR_OFFSET = (RED_OFFSET + RED_BYTES + 7) & ~7;
+  static constexpr int SMEM_BYTES = BAR_OFFSET + 128 + 1024;
+  static_assert(SMEM_BYTES <= 232448, "one CTA must fit an SM's shared memory");
+};
+
+template <int NP>
+__global__ void __launch_bounds__(EPTHREADS, 1)
+    k_energy_tc_spin2(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                      int RT, int CT, int RG, int NG, float* __restrict__ part, int NwP, int* err,
+                      uint64_t wait_ns, float2* __restrict__ trs, int X, int Nw) {
+  using Lay = ES2Layout<NP>;
+  constexpr int WPT = Lay::WPT, NKB = Lay::NKB;
+  extern __shared__ uint8_t esm_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(esm_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  float* stg = reinterpret_cast<float*>(smem + Lay::STG_OFFSET);
+  float* red = reinterpret_cast<float*>(smem + Lay::RED_OFFSET);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lay::BAR_OFFSET);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(bars + 11);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12);
+  const uint32_t bfull = smem_u32(bars), bempty = smem_u32(bars + 1);
+  const uint32_t full0 = smem_u32(bars + 2), empty0 = smem_u32(bars + 4);
+  const uint32_t tfull0 = smem_u32(bars + 6), tempty0 = smem_u32(bars + 8), done = smem_u32(bars + 10);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nitems = 2 * CT * NG;
+  const uint32_t sbase = smem_u32(smem);
+  // item -> spin, column tile, row tiles [r0, r1)
+  auto item_of = [&](int it, int& sp, int& ct, int& rg, int& r0, int& r1) {
+    sp = it / (CT * NG);
+    const int rem = it - sp * CT * NG;
+    ct = rem / NG;
+    rg = rem - ct * NG;
+    r0 = rg * RG;
+    r1 = min(RT, r0 + RG);
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(bfull, 1);
+    mbar_init(bempty, 1);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(full0 + 8 * q, 1);
+      mbar_init(empty0 + 8 * q, 1);
+      mbar_init(tfull0 + 8 * q, 1);
+      mbar_init(tempty0 + 8 * q, 32 * EWARPS);
+    }
+    mbar_init(done, 1);
+    *s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == EWARPS) {
+    if (lane == 0) {
+      // ---- TMA producer: the Theta tile once per item (after the previous item's MMAs), one
+      // k slice of the L-tilde row tile per ring stage ----
+      int ga = 0, j = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++j) {
+        int sp, ct, rg, r0, r1;
+        item_of(it, sp, ct, rg, r0, r1);
+        const int n0 = (sp * CT + ct) * EBN;
+        if (j > 0 && !mbar_wait(bempty, (j - 1) & 1, err, wait_ns)) break;
+        mbar_expect_tx(bfull, Lay::B_REGION);
+        for (int kb = 0; kb < NKB; ++kb)
+          for (int lo = 0; lo < 2; ++lo) {
+            const uint32_t dst = sbase + (uint32_t)((kb * 2 + lo) * Lay::B_BYTES);
+            tma_load_2d(dst, lo ? &tmBl : &tmBh, bfull, kb * EBK, n0);
+            tma_load_2d(dst + Lay::B_BYTES / 2, lo ? &tmBl : &tmBh, bfull, kb * EBK, n0 + EBN / 2);
+          }
+        for (int rt = r0; rt < r1 && ok; ++rt)
+          for (int kb = 0; kb < NKB; ++kb, ++ga) {
+            const int s = ga & 1, use = ga >> 1;
+            if (ga >= 2 && !mbar_wait(empty0 + 8 * s, (use - 1) & 1, err, wait_ns)) { ok = false; break; }
+            const uint32_t st = sbase + Lay::A_OFFSET + s * Lay::A_STAGE, fb = full0 + 8 * s;
+            const int m0 = (sp * RT + rt) * EBM;
+            mbar_expect_tx(fb, Lay::A_STAGE);
+            tma_load_2d(st, &tmAh, fb, kb * EBK, m0);
+            tma_load_2d(st + Lay::A_BYTES, &tmAl, fb, kb * EBK, m0);
+          }
+      }
+      // every issued copy must have landed before the CTA may exit
+      if (j > 0) mbar_wait(bfull, (j - 1) & 1, err, wait_ns);
+      for (int q = (ga > 2 ? ga - 2 : 0); q < ga; ++q)
+        mbar_wait(full0 + 8 * (q & 1), (q >> 1) & 1, err, wait_ns);
+    }
+  } else if (warp == EWARPS + 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      const uint32_t idesc = idesc_bf16<EBN>();
+      int ga = 0, i = 0, j = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++j) {
+        int sp, ct, rg, r0, r1;
+        item_of(it, sp, ct, rg, r0, r1);
+        if (!mbar_wait(bfull, j & 1, err, wait_ns)) break;
+        for (int rt = r0; rt < r1 && ok; ++rt, ++i) {
+          const int b = i & 1;
+          if (i >= 2 && !mbar_wait(tempty0 + 8 * b, ((i >> 1) - 1) & 1, err, wait_ns)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d = tmem + (uint32_t)(b * EBN);
+          for (int kb = 0; kb < NKB; ++kb, ++ga) {
+            const int s = ga & 1;
+            if (!mbar_wait(full0 + 8 * s, (ga >> 1) & 1, err, wait_ns)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = sbase + Lay::A_OFFSET + s * Lay::A_STAGE;
+            const uint64_t ah = sw128_desc(st), al = sw128_desc(st + Lay::A_BYTES);
+            const uint64_t bh = sw128_desc(sbase + (uint32_t)(kb * 2 * Lay::B_BYTES));
+            const uint64_t bl = sw128_desc(sbase + (uint32_t)((kb * 2 + 1) * Lay::B_BYTES));
+#pragma unroll
+            for (int kk = 0; kk < EBK / 16; ++kk) {
+              const uint64_t dk = (uint64_t)((kk * 32) >> 4);
+              mma_bf16(d, ah + dk, bh + dk, idesc, (kb | kk) != 0);
+              mma_bf16(d, ah + dk, bl + dk, idesc, 1u);
+              mma_bf16(d, al + dk, bh + dk, idesc, 1u);
+            }
+            mma_commit(empty0 + 8 * s);
+          }
+          if (ok) mma_commit(tfull0 + 8 * b);
+        }
+        mma_commit(bempty);   // the item's MMAs are done with the Theta tile once this arrives
+      }
+      mma_commit(done);
+    }
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows (g, a)), column groups of half
+    // w / 4; per group one walker's re | im columns ----
+    constexpr int NGR = EBN / 32, NGH = NGR / 2;
+    float* S = stg + warp * 32 * 33;
+    const int quad = warp & 3, half = warp >> 2;
+    const int a = lane % NP, gl = lane / NP;
+    int i = 0;
+    bool stop = false;
+    for (int it = blockIdx.x; it < nitems && !stop; it += gridDim.x) {
+      int sp, ct, rg, r0, r1;
+      item_of(it, sp, ct, rg, r0, r1);
+      float accr = 0.f, acci = 0.f;   // threads < WPT: walker ct * WPT + threadIdx.x
+      for (int rt = r0; rt < r1; ++rt, ++i) {
+        const int b = i & 1;
+        float* rb = red + b * (4 * WPT * 2);
+        const bool ok = mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, err, wait_ns);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (__all_sync(0xffffffffu, ok)) {
+          const int g = (rt * EBM + quad * 32 + lane) / NP;
+          for (int gg = 0; gg < NGH; ++gg) {
+            const int grp = half * NGH + gg;
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * EBN + grp * 32), v);
+            // staged rows of 33 words: the row writes and the column reads below fall in
+            // distinct banks
+#pragma unroll
+            for (int q = 0; q < 32; ++q) S[lane * 33 + q] = __uint_as_float(v[q]);
+            __syncwarp();
+            // exchange of (g, w): sum_b T[a][b] T[b][a], T[b][a] from row (gl NP + b), column a
+            const float* colp = S + gl * NP * 33 + a;
+            float exr0 = 0.f, exi0 = 0.f, exr1 = 0.f, exi1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              const float ur = colp[q * 33], ui = colp[q * 33 + NP];
+              const float tr = __uint_as_float(v[q]), ti = __uint_as_float(v[NP + q]);
+              if (q & 1) {
+                exr1 = fmaf(tr, ur, fmaf(-ti, ui, exr1));
+                exi1 = fmaf(tr, ui, fmaf(ti, ur, exi1));
+              } else {
+                exr0 = fmaf(tr, ur, fmaf(-ti, ui, exr0));
+                exi0 = fmaf(tr, ui, fmaf(ti, ur, exi0));
+              }
+            }
+            float dr = S[lane * 33 + a], di = S[lane * 33 + NP + a];   // T[a][a]
+            float exr = exr0 + exr1, exi = exi0 + exi1;
+#pragma unroll
+            for (int o = NP / 2; o > 0; o >>= 1) {      // sums over the g block
+              exr += __shfl_xor_sync(0xffffffffu, exr, o);
+              exi += __shfl_xor_sync(0xffffffffu, exi, o);
+              dr += __shfl_xor_sync(0xffffffffu, dr, o);
+              di += __shfl_xor_sync(0xffffffffu, di, o);
+            }
+            const int w = ct * WPT + grp;
+            if (a == 0 && g < X && w < Nw) trs[((int64_t)sp * Nw + w) * X + g] = make_float2(dr, di);
+            float er = a == 0 ? -0.5f * exr : 0.f, ei = a == 0 ? -0.5f * exi : 0.f;
+#pragma unroll
+            for (int o = NP; o < 32; o <<= 1) {         // over the warp's g blocks
+              er += __shfl_xor_sync(0xffffffffu, er, o);
+              ei += __shfl_xor_sync(0xffffffffu, ei, o);
+            }
+            if (lane == 0) {
+              rb[(quad * WPT + grp) * 2] = er;
+              rb[(quad * WPT + grp) * 2 + 1] = ei;
+            }
+            __syncwarp();
+          }
+        } else if (lane == 0) {
+          *s_fail = 1;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(tempty0 + 8 * b);
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * EWARPS) : "memory");   // the epilogue warps
+        if (*s_fail) { stop = true; break; }
+        if (threadIdx.x < WPT)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            accr += rb[(q * WPT + threadIdx.x) * 2];
+            acci += rb[(q * WPT + threadIdx.x) * 2 + 1];
+          }
+      }
+      if (!stop && threadIdx.x < WPT) {
+        const int w = ct * WPT + threadIdx.x, row = sp * NG + rg;
+        part[(int64_t)(2 * row) * NwP + w] = accr;
+        part[(int64_t)(2 * row + 1) * NwP + w] = acci;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(done, 0, err, wait_ns);   // no MMA may still write TMEM
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                 : "memory");
+}
+
 // eloc[w] = sum_e htil[e] Theta_w[e] (FP64) + sum over row tiles of part for the first nw of
 // the Nw walkers (one warp per walker;
 // every sum in a fixed order, so repeated evaluations agree bit for bit).
@@ -649,12 +903,25 @@ cudaError_t launch_spin(const Ctx& c, const EnergyTc& et, int n_walkers, cudaStr
       c.theta32, c.Nw, c.N, c.M, c.n_up, NPS, et.Kp, CTs, nw, et.B->hi, et.B->lo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int grid = std::min(2 * RTs * CTs, 152);
-  k_energy_tc<NPS, true><<<grid, EPTHREADS, Lay::SMEM_BYTES, s>>>(
-      et.A->map_hi, et.A->map_lo, et.B->map_hi, et.B->map_lo, et.Kp / EBK, RTs, CTs, et.part,
-      et.NwP, c.d_tc_err, kEWaitNs, reinterpret_cast<float2*>(et.trs), c.X, c.Nw);
+  int nparts = et.RT;
+  if (NPS == 16 && et.Kp == 2 * EBK) {
+    // Theta tile resident per (spin, column tile, row group) item, about 8 items per SM
+    const int ng = std::max(1, std::min(RTs, (152 * 8 + 2 * CTs - 1) / (2 * CTs)));
+    const int rg = (RTs + ng - 1) / ng;
+    const int NG = (RTs + rg - 1) / rg;
+    nparts = 2 * NG;
+    const int grid = std::min(2 * CTs * NG, 152);
+    k_energy_tc_spin2<16><<<grid, EPTHREADS, ES2Layout<16>::SMEM_BYTES, s>>>(
+        et.A->map_hi, et.A->map_lo, et.B->map_hi, et.B->map_lo, RTs, CTs, rg, NG, et.part, et.NwP,
+        c.d_tc_err, kEWaitNs, reinterpret_cast<float2*>(et.trs), c.X, c.Nw);
+  } else {
+    const int grid = std::min(2 * RTs * CTs, 152);
+    k_energy_tc<NPS, true><<<grid, EPTHREADS, Lay::SMEM_BYTES, s>>>(
+        et.A->map_hi, et.A->map_lo, et.B->map_hi, et.B->map_lo, et.Kp / EBK, RTs, CTs, et.part,
+        et.NwP, c.d_tc_err, kEWaitNs, reinterpret_cast<float2*>(et.trs), c.X, c.Nw);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_energy_tc_reduce<<<(nw + 7) / 8, 256, 0, s>>>(et.part, et.RT, et.NwP, c.theta32, c.htil, c.eloc,
+  k_energy_tc_reduce<<<(nw + 7) / 8, 256, 0, s>>>(et.part, nparts, et.NwP, c.theta32, c.htil, c.eloc,
                                                   c.Nw, nw, NM, reinterpret_cast<const float2*>(et.trs),
                                                   c.X);
   return cudaGetLastError();
@@ -718,6 +985,9 @@ cudaError_t prepare_energy_tc_kernels() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_energy_tc<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              ELayout<16>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_energy_tc_spin2<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             ES2Layout<16>::SMEM_BYTES);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_energy_tc_bres<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              EBLayout<8>::SMEM_BYTES);
