@@ -95,6 +95,8 @@ void free_ctx(Ctx* h) {
       }
     if (h->etc->part) cudaFree(h->etc->part);
     if (h->etc->trs) cudaFree(h->etc->trs);
+    if (h->etc->hh) cudaFree(h->etc->hh);
+    if (h->etc->hl) cudaFree(h->etc->hl);
     delete h->etc;
     h->etc = nullptr;
   }
@@ -204,6 +206,7 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
       if (dalloc(h, &h->etc->A->hi, ka) != AFQMC_OK || dalloc(h, &h->etc->A->lo, ka) != AFQMC_OK ||
           dalloc(h, &h->etc->B->hi, kb) != AFQMC_OK || dalloc(h, &h->etc->B->lo, kb) != AFQMC_OK ||
           dalloc(h, &h->etc->part, 2 * (size_t)h->etc->RT * h->etc->NwP) != AFQMC_OK ||
+          dalloc(h, &h->etc->hh, (size_t)NM) != AFQMC_OK || dalloc(h, &h->etc->hl, (size_t)NM) != AFQMC_OK ||
           (afq::energy_tc_spin(*h) &&
            dalloc(h, &h->etc->trs, 2 * 2 * (size_t)Nw * X) != AFQMC_OK)) {
         if (own) {

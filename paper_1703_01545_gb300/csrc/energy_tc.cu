@@ -595,6 +595,20 @@ __global__ void __launch_bounds__(EBLayout<NP>::THREADS, 1)
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld32_nw(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+        "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+        "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld_e() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // Spin-blocked form with two k slices (64 < M <= 128): a CTA keeps the whole Theta column tile
 // of one spin block resident (both k slices, hi and lo: 128 KB) and streams a group of RG row
 // tiles of L-tilde through a 2-stage ring of one k slice each, so the operand traffic is one
@@ -772,10 +786,16 @@ __global__ void __launch_bounds__(EPTHREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (__all_sync(0xffffffffu, ok)) {
           const int g = (rt * EBM + quad * 32 + lane) / NP;
+          const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * EBN + half * NGH * 32);
+          // group gg + 1's TMEM load is in flight while group gg is reduced
+          uint32_t va[32], vb[32];
+          tmem_ld32_nw(tq, va);
+          tmem_wait_ld_e();
+#pragma unroll
           for (int gg = 0; gg < NGH; ++gg) {
+            uint32_t(&v)[32] = (gg & 1) ? vb : va;
+            if (gg + 1 < NGH) tmem_ld32_nw(tq + (uint32_t)(32 * (gg + 1)), (gg & 1) ? va : vb);
             const int grp = half * NGH + gg;
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * EBN + grp * 32), v);
             // staged rows of 33 words: the row writes and the column reads below fall in
             // distinct banks
 #pragma unroll
@@ -818,6 +838,7 @@ __global__ void __launch_bounds__(EPTHREADS, 1)
               rb[(quad * WPT + grp) * 2 + 1] = ei;
             }
             __syncwarp();
+            tmem_wait_ld_e();
           }
         } else if (lane == 0) {
           *s_fail = 1;
@@ -849,7 +870,20 @@ __global__ void __launch_bounds__(EPTHREADS, 1)
                  : "memory");
 }
 
-// eloc[w] = sum_e htil[e] Theta_w[e] (FP64) + sum over row tiles of part for the first nw of
+// (s, c) += (h + l) x, the product h x formed exactly (its rounding error recovered by an FMA,
+// Dekker's two-product) and added to s by Knuth's two-sum; the intrinsics keep the compiler
+// from contracting the error terms away
+__device__ __forceinline__ void pair_acc(float& s, float& c, float h, float l, float x) {
+  const float p = __fmul_rn(h, x);
+  const float e = __fmaf_rn(h, x, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(l, x, e)));
+}
+
+// eloc[w] = sum_e htil[e] Theta_w[e] (FP32 pairs) + sum over row tiles of part for the first nw of
 // the Nw walkers (one warp per walker;
 // every sum in a fixed order, so repeated evaluations agree bit for bit).
 // E_L per walker: the one-body term sum htil . Theta (FP64), the row tiles' partial two-body
@@ -857,19 +891,24 @@ __global__ void __launch_bounds__(EPTHREADS, 1)
 // from the traces trs ([2][Nw][X] complex); trs null: already in the partials.
 __global__ void __launch_bounds__(256) k_energy_tc_reduce(const float* __restrict__ part, int RT, int NwP,
                                                           const float* __restrict__ th,
-                                                          const double* __restrict__ htil,
+                                                          const float* __restrict__ hh,
+                                                          const float* __restrict__ hl,
                                                           double* __restrict__ eloc, int Nw, int nw,
                                                           int NM, const float2* __restrict__ trs,
                                                           int X) {
   const int lane = threadIdx.x & 31, w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= nw) return;
   const int64_t plane = (int64_t)Nw * NM;
-  double r = 0.0, i = 0.0;
+  // one-body term in FP32 pairs (GB300's FP64 pipe is thin): each product (hh + hl) theta
+  // formed exactly up to the hl term (two-product by FMA) and added with a two-sum
+  float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
   for (int e = lane; e < NM; e += 32) {
-    const double h = __ldg(htil + e);
-    r = fma(h, (double)th[(int64_t)w * NM + e], r);
-    i = fma(h, (double)th[plane + (int64_t)w * NM + e], i);
+    const float h = __ldg(hh + e), l = __ldg(hl + e);
+    const float tr = th[(int64_t)w * NM + e], ti = th[plane + (int64_t)w * NM + e];
+    pair_acc(sr, cr, h, l, tr);
+    pair_acc(si, ci, h, l, ti);
   }
+  double r = (double)sr + (double)cr, i = (double)si + (double)ci;
   if (trs)
     for (int g = lane; g < X; g += 32) {
       const float2 u = trs[(int64_t)w * X + g], d = trs[((int64_t)Nw + w) * X + g];
@@ -892,6 +931,16 @@ __global__ void __launch_bounds__(256) k_energy_tc_reduce(const float* __restric
 }
 
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+// x (FP64) as the FP32 pair hi + lo
+__global__ void k_split_pair(const double* __restrict__ x, int n, float* __restrict__ hi,
+                             float* __restrict__ lo) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const float h = (float)x[e];
+    hi[e] = h;
+    lo[e] = (float)(x[e] - (double)h);
+  }
+}
 
 // spin-blocked form (M > 64): NPS = P2 rows per Cholesky vector and spin
 template <int NPS>
@@ -921,7 +970,7 @@ cudaError_t launch_spin(const Ctx& c, const EnergyTc& et, int n_walkers, cudaStr
         et.NwP, c.d_tc_err, kEWaitNs, reinterpret_cast<float2*>(et.trs), c.X, c.Nw);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_energy_tc_reduce<<<(nw + 7) / 8, 256, 0, s>>>(et.part, nparts, et.NwP, c.theta32, c.htil, c.eloc,
+  k_energy_tc_reduce<<<(nw + 7) / 8, 256, 0, s>>>(et.part, nparts, et.NwP, c.theta32, et.hh, et.hl, c.eloc,
                                                   c.Nw, nw, NM, reinterpret_cast<const float2*>(et.trs),
                                                   c.X);
   return cudaGetLastError();
@@ -953,7 +1002,7 @@ cudaError_t launch_np(const Ctx& c, const EnergyTc& et, int n_walkers, cudaStrea
         et.NwP, c.d_tc_err, kEWaitNs, nullptr, c.X, c.Nw);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_energy_tc_reduce<<<(nw + 7) / 8, 256, 0, s>>>(et.part, nparts, et.NwP, c.theta32, c.htil, c.eloc,
+  k_energy_tc_reduce<<<(nw + 7) / 8, 256, 0, s>>>(et.part, nparts, et.NwP, c.theta32, et.hh, et.hl, c.eloc,
                                                  c.Nw, nw, NM, nullptr, 0);
   return cudaGetLastError();
 }
@@ -1035,6 +1084,8 @@ cudaError_t energy_tc_init(const Ctx& c, EnergyTc& et, cudaStream_t s) {
   else
     k_energy_A<<<grid_for((int64_t)c.X * et.NP * et.Kp), 256, 0, s>>>(c.Ltil, c.X, c.N, c.M, c.n_up,
                                                                      et.NP, et.Kp, et.A->hi, et.A->lo);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_split_pair<<<grid_for((int64_t)c.N * c.M), 256, 0, s>>>(c.htil, c.N * c.M, et.hh, et.hl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = tc_make_operand(*et.A, et.A->hi, et.A->lo, et.A->rows, et.Kp, EBM)) != cudaSuccess) return e;
   return tc_make_operand(*et.B, et.B->hi, et.B->lo, et.B->rows, et.Kp, EBN / 2);

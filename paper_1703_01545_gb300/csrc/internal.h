@@ -44,6 +44,8 @@ struct EnergyTc {
   TcOperand* B = nullptr;     // rows (w, re/im, n') of Theta
   float* part = nullptr;      // [RT][2][NwP] partial two-body energies per row tile
   float* trs = nullptr;       // spin-blocked form: [2 spins][Nw][X] (re, im) traces tr T^s_g
+  float* hh = nullptr;        // [N][M] Psi^T h1 as FP32 pairs hh + hl (the one-body term)
+  float* hl = nullptr;
   int NP = 0, Kp = 0, RT = 0, NwP = 0;
 };
 
