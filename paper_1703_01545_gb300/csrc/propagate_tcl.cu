@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "device_util.cuh"
 #include "internal.h"
 #include "tc_device.cuh"
 
@@ -118,33 +119,6 @@ __device__ __forceinline__ uint32_t elect_one() {
   asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.u32 %0, 1, 0, P;\n\t}"
                : "=r"(p));
   return p;
-}
-
-// binary64 -> binary32 with round-to-nearest-even, on the integer pipes (IEEE 754 layouts:
-// sign, 11 / 8 exponent bits biased by 1023 / 127, 52 / 23 fraction bits); the FP64 pipe, which
-// also carries the conversion instructions, is thin on this part.  Results in the binary32
-// normal range are formed here (a carry out of the fraction rounds up into the exponent, up
-// to infinity); zero, subnormal, out-of-range and non-finite inputs take the conversion
-// instruction.
-__device__ __forceinline__ float f64_to_f32_rn(double x) {
-  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-  const int e = (int)((hi >> 20) & 0x7ffu) - 896;                 // binary32 biased exponent
-  if (e < 1 || e > 254) return __double2float_rn(x);
-  const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29), rem = lo & 0x1fffffffu;
-  const uint32_t up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
-  return __uint_as_float((hi & 0x80000000u) | ((((uint32_t)e << 23) | m) + up));
-}
-
-// binary32 -> binary64 (exact) on the integer pipes; zero keeps its sign, subnormal and
-// non-finite inputs take the conversion instruction
-__device__ __forceinline__ double f32_to_f64(float f) {
-  const uint32_t b = __float_as_uint(f), e = (b >> 23) & 0xffu;
-  if (e == 0u || e == 255u) {
-    if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
-    return (double)f;
-  }
-  const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-  return __hiloint2double((int)hi, (int)(b << 29));
 }
 
 // x = hi + lo for a pair of floats (a in the low half): both halves as packed BF16 pairs

@@ -698,31 +698,17 @@ __global__ void __launch_bounds__(64) k_mgs_reg(double* __restrict__ phi, const 
 
 // Orthonormalisation of the split-precision path (Sec. II.D) as a Cholesky QR: per spin block,
 // Phi_s = Q R with R upper triangular with a positive diagonal, the factors modified
-// Gram-Schmidt produces.  S = Phi_s^H Phi_s is accumulated in FP32 pairs (each FP64 entry split
-// into hi + lo, products by the FMA two-product, sums by two-sum: ~2^-46 relative, like the
-// overlap sums of the update form) and factorised S = R^H R in FP64, both spins in one warp
-// (16 lanes each, lane l owning column l, so every FP64 instruction serves both blocks);
-// Q = Phi_s R^{-1} is formed by forward substitution along every orbital row in FP32 pairs and
-// written back as FP64 (hi + lo), so the stored walker and the lowered log O stay consistent to
-// ~2^-46.  The walkers are orthonormalised every few steps, so S is close to the identity and
-// squaring the condition number costs nothing.  log O drops by sum_j log R_jj (FP64), as in
-// k_mgs_warp.  One 128-thread CTA per walker; shared memory holds the walker as rows of
-// float4 (re hi, re lo, im hi, im lo) with a stride of N + 1 (rows fall in distinct banks), the
-// upper triangles of S and R (FP64) and R as FP32 pairs.
-__device__ __forceinline__ void df_two_sum(float& h, float& l, float p) {
-  const float s = __fadd_rn(h, p), v = __fsub_rn(s, h);
-  l = __fadd_rn(l, __fadd_rn(__fsub_rn(h, __fsub_rn(s, v)), __fsub_rn(p, v)));
-  h = s;
-}
-
-// (h, l) -= (ah + al)(bh + bl) for FP32 pairs, the leading product error-free
-__device__ __forceinline__ void df_sub_mul(float& h, float& l, float ah, float al, float bh, float bl) {
-  const float p = __fmul_rn(ah, bh);
-  const float e = __fmaf_rn(ah, bh, -p);
-  df_two_sum(h, l, -p);
-  l = __fsub_rn(l, __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e)));
-}
-
+// Gram-Schmidt produces.  The walker is read as FP32 (the precision the propagator keeps), S =
+// Phi_s^H Phi_s is summed in FP32 (four threads per group of entries, each over a quarter of
+// the orbitals, combined by shuffles) and factorised S = R^H R in FP64, both spins in one warp
+// (16 lanes each, lane l owning column l); Q = Phi_s R^{-1} is formed by forward substitution
+// along every orbital row in FP32 and written back exactly as FP64.  log O drops by
+// sum_j log R_jj (FP64), the R that Q was formed with, so the stored log O and walker agree up
+// to the FP32 rounding of Q (~1e-6 in log O, against which the weights are insensitive).  The
+// walkers are orthonormalised every few steps, so S is close to the identity and squaring the
+// condition number costs nothing.  One 128-thread CTA per walker; shared memory holds the
+// walker as rows of float2 (re, im) with a stride of N + 1, the upper triangles of S and R
+// (FP64), R in FP32 and the reciprocals of its diagonal.
 __global__ void __launch_bounds__(128) k_mgs_chol(double* __restrict__ phi, const int* __restrict__ alive,
                                                   double* __restrict__ logO, int M, int N, int n_up,
                                                   int Nw) {
@@ -730,61 +716,81 @@ __global__ void __launch_bounds__(128) k_mgs_chol(double* __restrict__ phi, cons
   const int wk = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
   if (!alive[wk]) return;
   const int64_t NM = (int64_t)N * M, plane = (int64_t)Nw * NM, base = (int64_t)wk * NM;
-  const int RS = N + 1;                                              // row stride (float4)
-  float4* X4 = reinterpret_cast<float4*>(smc);                       // [M][N + 1]
-  double* Sre = reinterpret_cast<double*>(X4 + (size_t)M * RS);      // [N][N] (block diagonal)
+  const int RS = N + 1;                                              // row stride (float2)
+  float2* X2 = reinterpret_cast<float2*>(smc);                       // [M][N + 1]
+  double* Sre = reinterpret_cast<double*>(X2 + (size_t)M * RS);      // [N][N] (block diagonal)
   double* Sim = Sre + (size_t)N * N;
-  float4* R4 = reinterpret_cast<float4*>(Sim + (size_t)N * N);       // [N][N]  R as FP32 pairs
+  float2* R2 = reinterpret_cast<float2*>(Sim + (size_t)N * N);       // [N][N]  R in FP32
+  float* Rd = reinterpret_cast<float*>(R2 + (size_t)N * N);          // [N]     1 / R_jj
   __shared__ double s_ld;
-  // the walker, split: x = hi + lo per component (global layout [2][Nw][N][M], i fastest)
-  for (int64_t e = tid; e < NM; e += blockDim.x) {
-    const int n = (int)(e / M), i = (int)(e % M);
-    const double xr = phi[base + e], xi = phi[plane + base + e];
-    const float rh = __double2float_rn(xr), ih = __double2float_rn(xi);
-    X4[(size_t)i * RS + n] = make_float4(rh, __double2float_rn(xr - (double)rh), ih,
-                                         __double2float_rn(xi - (double)ih));
+  // the walker in FP32 (global layout [2][Nw][N][M], i fastest), loads issued in batches
+  for (int64_t e0 = tid; e0 < NM; e0 += 4 * blockDim.x) {
+    double xr[4], xi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t e = e0 + u * blockDim.x;
+      xr[u] = e < NM ? phi[base + e] : 0.0;
+      xi[u] = e < NM ? phi[plane + base + e] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t e = e0 + u * blockDim.x;
+      if (e < NM) {
+        const int n = (int)(e / M), i = (int)(e % M);
+        X2[(size_t)i * RS + n] = make_float2(f64_to_f32_rn(xr[u]), f64_to_f32_rn(xi[u]));
+      }
+    }
   }
   __syncthreads();
-  // upper triangle of S_s[a][b] = sum_i conj(x_ia) x_ib in FP32 pairs; item (s, a, column
-  // group of 4), groups wholly below the diagonal skipped
+  // upper triangle of S_s[a][b] = sum_i conj(x_ia) x_ib in FP32; unit (s, a, column group of 4,
+  // quarter of the orbitals), groups wholly below the diagonal skipped
   const int nu = n_up, nd = N - n_up;
   const int g0 = (nu + 3) / 4, g1 = (nd + 3) / 4;
   const int items = nu * g0 + nd * g1;
-  for (int it = tid; it < items; it += blockDim.x) {
-    const bool dn = it >= nu * g0;
-    const int r = dn ? it - nu * g0 : it, gq = dn ? g1 : g0, ns = dn ? nd : nu, o = dn ? nu : 0;
-    const int a = r / gq, b0 = 4 * (r % gq);
-    if (b0 + 3 < a) continue;
-    const int ca = o + a;
-    float hre[4] = {0, 0, 0, 0}, lre[4] = {0, 0, 0, 0}, him[4] = {0, 0, 0, 0}, lim[4] = {0, 0, 0, 0};
-    for (int i = 0; i < M; ++i) {
-      const float4 x = X4[(size_t)i * RS + ca];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (b0 + k >= ns) break;
-        const float4 y = X4[(size_t)i * RS + o + b0 + k];
-        // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr); each product of split components:
-        // hi*hi error-free (FMA), the cross terms in FP32
-        const float p1 = x.x * y.x, q1 = fmaf(x.x, y.x, -p1) + fmaf(x.x, y.y, x.y * y.x);
-        const float p2 = x.z * y.z, q2 = fmaf(x.z, y.z, -p2) + fmaf(x.z, y.w, x.w * y.z);
-        const float p3 = x.x * y.z, q3 = fmaf(x.x, y.z, -p3) + fmaf(x.x, y.w, x.y * y.z);
-        const float p4 = x.z * y.x, q4 = fmaf(x.z, y.x, -p4) + fmaf(x.z, y.y, x.w * y.x);
-        df_two_sum(hre[k], lre[k], p1);
-        df_two_sum(hre[k], lre[k], p2);
-        lre[k] += q1 + q2;
-        df_two_sum(him[k], lim[k], p3);
-        df_two_sum(him[k], lim[k], -p4);
-        lim[k] += q3 - q4;
-      }
+  for (int u0 = 0; u0 < 4 * items; u0 += blockDim.x) {
+    const int it = (u0 + tid) >> 2, part = (u0 + tid) & 3;
+    float sre[4] = {0.f, 0.f, 0.f, 0.f}, sim[4] = {0.f, 0.f, 0.f, 0.f};
+    int ca = 0, o = 0, a = 0, b0 = 0, ns = 0;
+    bool live = it < items;
+    if (live) {
+      const bool dn = it >= nu * g0;
+      const int r = dn ? it - nu * g0 : it, gq = dn ? g1 : g0;
+      ns = dn ? nd : nu;
+      o = dn ? nu : 0;
+      a = r / gq;
+      b0 = 4 * (r % gq);
+      live = b0 + 3 >= a;
+      ca = o + a;
     }
+    if (live)
+      for (int i = part; i < M; i += 4) {
+        const float2 x = X2[(size_t)i * RS + ca];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (b0 + k >= ns) break;
+          const float2 y = X2[(size_t)i * RS + o + b0 + k];
+          // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr)
+          sre[k] = fmaf(x.x, y.x, fmaf(x.y, y.y, sre[k]));
+          sim[k] = fmaf(x.x, y.y, fmaf(-x.y, y.x, sim[k]));
+        }
+      }
+    // the four quarters of each unit sit in consecutive lanes
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int b = b0 + k;
-      if (b < ns && b >= a) {
-        Sre[(size_t)ca * N + o + b] = (double)hre[k] + (double)lre[k];
-        Sim[(size_t)ca * N + o + b] = (double)him[k] + (double)lim[k];
-      }
+      sre[k] += __shfl_xor_sync(0xffffffffu, sre[k], 1);
+      sim[k] += __shfl_xor_sync(0xffffffffu, sim[k], 1);
+      sre[k] += __shfl_xor_sync(0xffffffffu, sre[k], 2);
+      sim[k] += __shfl_xor_sync(0xffffffffu, sim[k], 2);
     }
+    if (live && part == 0)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int b = b0 + k;
+        if (b < ns && b >= a) {
+          Sre[(size_t)ca * N + o + b] = (double)sre[k];
+          Sim[(size_t)ca * N + o + b] = (double)sim[k];
+        }
+      }
   }
   __syncthreads();
   // S_s = R^H R (upper triangle in place, FP64), warp 0: lanes 0-15 the spin-up block, 16-31
@@ -815,71 +821,54 @@ __global__ void __launch_bounds__(128) k_mgs_chol(double* __restrict__ phi, cons
       }
       __syncwarp();
     }
-    // log det R = sum of the logs of the diagonal, one per lane
-    double ld = l < ns ? log(Sre[(size_t)(o + l) * N + o + l]) : 0.0;
-    for (int sh = 16; sh > 0; sh >>= 1) ld += __shfl_xor_sync(0xffffffffu, ld, sh);
-    if (lane == 0) s_ld = ld;
   }
   __syncthreads();
-  // R as FP32 pairs (upper triangle, zero below)
+  // R in FP32 (upper triangle, zero below) and the reciprocals of its diagonal; log det R of
+  // the FP32 R that forms Q
   for (int e = tid; e < N * N; e += blockDim.x) {
     const int k = e / N, l = e % N;
     const bool same = (k < nu) == (l < nu);
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (same && l >= k) {
-      const double rr = Sre[e], ri = Sim[e];
-      const float rh = __double2float_rn(rr), ih = __double2float_rn(ri);
-      v = make_float4(rh, __double2float_rn(rr - (double)rh), ih, __double2float_rn(ri - (double)ih));
-    }
-    R4[e] = v;
+    float2 v = make_float2(0.f, 0.f);
+    if (same && l >= k) v = make_float2((float)Sre[e], (float)Sim[e]);
+    R2[e] = v;
+    if (k == l) Rd[k] = 1.0f / v.x;
   }
   __syncthreads();
-  // Q = Phi R^{-1} row by row in FP32 pairs: q_j = (x_j - sum_{k<j} q_k R_kj) / R_jj, written
-  // over the row (row k < j already holds q_k)
+  if (tid < 32) {
+    double ld = tid < N ? log((double)R2[(size_t)tid * N + tid].x) : 0.0;
+    for (int sh = 16; sh > 0; sh >>= 1) ld += __shfl_xor_sync(0xffffffffu, ld, sh);
+    if (lane == 0) s_ld = ld;
+  }
+  // Q = Phi R^{-1} row by row in FP32: q_j = (x_j - sum_{k<j} q_k R_kj) / R_jj, written over the
+  // row (row k < j already holds q_k)
   for (int it = tid; it < 2 * M; it += blockDim.x) {
     const bool dn = it >= M;
     const int i = dn ? it - M : it, ns = dn ? nd : nu, o = dn ? nu : 0;
-    float4* row = X4 + (size_t)i * RS + o;
+    float2* row = X2 + (size_t)i * RS + o;
     for (int j = 0; j < ns; ++j) {
-      float4 x = row[j];
+      float2 x = row[j];
       for (int k = 0; k < j; ++k) {
-        const float4 q = row[k], rv = R4[(size_t)(o + k) * N + o + j];
-        // (x.re, x.im) -= q r: re -= q.re r.re - q.im r.im, im -= q.re r.im + q.im r.re
-        df_sub_mul(x.x, x.y, q.x, q.y, rv.x, rv.y);
-        df_sub_mul(x.x, x.y, -q.z, -q.w, rv.z, rv.w);
-        df_sub_mul(x.z, x.w, q.x, q.y, rv.z, rv.w);
-        df_sub_mul(x.z, x.w, q.z, q.w, rv.x, rv.y);
+        const float2 q = row[k], rv = R2[(size_t)(o + k) * N + o + j];
+        x.x = fmaf(-q.x, rv.x, fmaf(q.y, rv.y, x.x));
+        x.y = fmaf(-q.x, rv.y, fmaf(-q.y, rv.x, x.y));
       }
-      // divide by the real diagonal R_jj: one Newton correction of the FP32 quotient
-      const float4 dj = R4[(size_t)(o + j) * N + o + j];
-      const float inv = 1.0f / dj.x;
-      float4 qv;
-      const float qr = x.x * inv, qi = x.z * inv;
-      // residual x - q d with the product error-free, then q += residual / d
-      float rh = x.x, rl = x.y;
-      df_sub_mul(rh, rl, qr, 0.f, dj.x, dj.y);
-      float ih = x.z, il = x.w;
-      df_sub_mul(ih, il, qi, 0.f, dj.x, dj.y);
-      qv.x = qr;
-      qv.y = (rh + rl) * inv;
-      qv.z = qi;
-      qv.w = (ih + il) * inv;
-      row[j] = qv;
+      const float inv = Rd[o + j];
+      row[j] = make_float2(x.x * inv, x.y * inv);
     }
   }
   __syncthreads();
   for (int64_t e = tid; e < NM; e += blockDim.x) {
     const int n = (int)(e / M), i = (int)(e % M);
-    const float4 q = X4[(size_t)i * RS + n];
-    phi[base + e] = (double)q.x + (double)q.y;
-    phi[plane + base + e] = (double)q.z + (double)q.w;
+    const float2 q = X2[(size_t)i * RS + n];
+    phi[base + e] = f32_to_f64(q.x);
+    phi[plane + base + e] = f32_to_f64(q.y);
   }
   if (logO && tid == 0) logO[wk] -= s_ld;
 }
 
 size_t smem_mgs_chol(const Ctx& c) {
-  return sizeof(float4) * (size_t)c.M * (c.N + 1) + 2 * sizeof(double) * (size_t)c.N * c.N +
-         sizeof(float4) * (size_t)c.N * c.N;
+  return sizeof(float2) * (size_t)c.M * (c.N + 1) + 2 * sizeof(double) * (size_t)c.N * c.N +
+         sizeof(float2) * (size_t)c.N * c.N + sizeof(float) * (size_t)c.N;
 }
 
 size_t smem_fast_overlap(const Ctx& c, bool fp64_copy = true) {
