@@ -330,9 +330,9 @@ def measure_kernels(afq, A, dA, nw, precision, workload, stream):
     counts per walker (real flops; complex x real MAC = 4, complex x complex = 8):
       force bias 4 X N M;  V_HS 4 P X, P = M (M + 1) / 2 (packed symmetric L; the full count
       4 M^2 X beside it);  propagator (8 order + 8) M^2 N (Taylor terms and the two one-body
-      half steps);  overlap (split path: its FP64 part, the LU, 8/3 sum N_s^3; the overlap sums
-      run in FP32 and are reported beside it);  orthonormalisation 8 M sum N_s^2 (Gram-Schmidt
-      and Cholesky QR alike);  local energy 4 X M sum N_s^2 + 8 X sum N_s^2.
+      half steps);  overlap (split path, all FP32: the overlap sums 4 M sum N_s^2, the LU
+      8/3 sum N_s^3 and the Theta solves 8 M sum N_s^2);  orthonormalisation 8 M sum N_s^2
+      (Gram-Schmidt and Cholesky QR alike);  local energy 4 X M sum N_s^2 + 8 X sum N_s^2.
     Tensor-core kernels also give the split-BF16 MMA work they issue (3 products per product,
     padded tiles) as mma_flops.  Launches per block: 5 propagation steps, one Gram-Schmidt and
     one energy, for one system (system A)."""
@@ -408,18 +408,17 @@ def measure_kernels(afq, A, dA, nw, precision, workload, stream):
             out["propagator"] = entry(afq.K_TAYLOR, STEPS_PER_BLOCK, prop, "alu", f32, name,
                                       traffic=tr("propagate_f32.cu", "propagate_f32") if pv == 2 else None,
                                       variant=pv)
-        lu = 8.0 / 3.0 * N3 * nw
-        out["overlap"] = entry(afq.K_OVERLAP_UPDATE, STEPS_PER_BLOCK, lu, "alu", f64,
-                               "k_overlap_fast (update form: overlap sums in FP32, FP64 LU and "
-                               "log det, FP32 Theta)",
+        ov = 4.0 * M * N2 * nw + 8.0 / 3.0 * N3 * nw + 8.0 * M * N2 * nw
+        out["overlap"] = entry(afq.K_OVERLAP_UPDATE, STEPS_PER_BLOCK, ov, "alu", f32,
+                               "k_overlap_fast (update form: overlap sums, LU and Theta in FP32, "
+                               "log det accumulated with a power-of-two exponent)",
                                traffic=tr("walker_fast.cu", "overlap_fast"),
-                               fp32_overlap_flops_per_launch=4.0 * M * N2 * nw,
-                               fp32_theta_flops_per_launch=8.0 * M * N2 * nw,
-                               flops_note="only the FP64 LU counts against the FP64 peak")
+                               flops_note="overlap sums 4 M sum N_s^2, LU 8/3 sum N_s^3, Theta "
+                                          "solves 8 M sum N_s^2")
         if A.info().tuned_orthonormalise == 1:
-            out["mgs"] = entry(afq.K_MGS, 1, mgs, "alu", f64,
-                               "k_mgs_chol (Cholesky QR: Gram matrix in FP32 pairs, FP64 factor "
-                               "and log det, Q in FP32 pairs)",
+            out["mgs"] = entry(afq.K_MGS, 1, mgs, "alu", f32,
+                               "k_mgs_chol (Cholesky QR: Gram matrix and Q in FP32, FP64 factor "
+                               "and log det)",
                                traffic=tr("walker_fast.cu", "mgs_chol"))
         else:
             out["mgs"] = entry(afq.K_MGS, 1, mgs, "alu", f64,

@@ -47,6 +47,7 @@ using namespace tc;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kTile = 128 * 64 * 2;       // one 128-row x 64-K bf16 tile, 128-byte swizzle
 constexpr int kMaxStages = 12;
+constexpr int kXu = 4;                    // staged-X elements per epilogue thread and round
 
 __device__ __forceinline__ uint32_t idesc_n(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
@@ -171,6 +172,9 @@ struct TclShape {
   int dcol;              // TMEM column stride between tiles (D and S regions)
   uint32_t tcols;        // TMEM columns allocated
   int order, Nw;
+  int xs, xs_ld;         // 1: the next walker's X (FP32, rows c of xs_ld floats) staged in the ring
+                         // region during the current walker's rounds (resident form with E in
+                         // tensor memory, which leaves the ring unused)
   int ring_off, bhi_off, blo_off, bar_off, smem_bytes;
 };
 
@@ -193,7 +197,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
   const uint32_t dfull = smem_u32(bars + 2 * kMaxStages), bready = smem_u32(bars + 2 * kMaxStages + 1);
   const uint32_t done = smem_u32(bars + 2 * kMaxStages + 2);
   const uint32_t afull = smem_u32(bars + 2 * kMaxStages + 3), acopied = smem_u32(bars + 2 * kMaxStages + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kMaxStages + 5);
+  const uint32_t xfull = smem_u32(bars + 2 * kMaxStages + 5), xread = smem_u32(bars + 2 * kMaxStages + 6);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kMaxStages + 7);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rounds = sh.order + 2;
@@ -209,6 +214,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
     mbar_init(done, 1);
     mbar_init(afull, 1);
     mbar_init(acopied, 32 * EPI);
+    mbar_init(xfull, 32 * EPI);
+    mbar_init(xread, 32 * EPI);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -452,8 +459,70 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
     const int ngh = (sh.n2 - 16 * half + cstep - 1) / cstep;
     const int nitems = sh.MT * 2 * ngh;
     if (sh.eres && !copy_planes(2, sh.ecol)) ok = false;
+    // staged X: element e of a walker is column c = e / M, orbital i = e % M (FP32); thread t of
+    // the epilogue takes e = t + 32 EPI (q + rounds u) in round q, so a walker's X is loaded
+    // during the previous walker's rounds, each load issued before the round's wait
+    float* xst = reinterpret_cast<float*>(smem + sh.ring_off);
+    const int et = threadIdx.x - 64, nte = 32 * EPI, nx = sh.n2 * sh.M;
+    const int xu = (nx + nte * rounds - 1) / (nte * rounds);     // elements per thread and round
+    const int xdc = nte / sh.M, xdi = nte - (nte / sh.M) * sh.M;
+    auto x_elem = [&](int wn, int e) -> double {
+      const int c = e / sh.M, i = e - c * sh.M, b = c < sh.Np ? c : c - sh.Np;
+      return b < sh.N ? phi_in[(c < sh.Np ? 0 : plane) + ((int64_t)wn * sh.N + b) * sh.M + i] : 0.0;
+    };
+    auto x_put = [&](int e, double v) {
+      const int c = e / sh.M, i = e - c * sh.M;
+      xst[c * sh.xs_ld + i] = f64_to_f32_rn(v);
+    };
+    auto next_live = [&](int w) {
+      int wn = w + (int)gridDim.x;
+      while (wn < sh.Nw && alive && !alive[wn]) wn += (int)gridDim.x;
+      return wn;
+    };
+    if (sh.xs && ok) {
+      int w0 = blockIdx.x;
+      while (w0 < sh.Nw && alive && !alive[w0]) w0 += (int)gridDim.x;
+      if (w0 < sh.Nw)
+        for (int e0 = et; e0 < nx; e0 += 4 * nte) {
+          double v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = e0 + u * nte < nx ? x_elem(w0, e0 + u * nte) : 0.0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (e0 + u * nte < nx) x_put(e0 + u * nte, v[u]);
+        }
+      mbar_arrive(xfull);
+    }
+    int kx = 0;   // live walkers of this CTA so far
     for (int w = blockIdx.x; w < sh.Nw && ok; w += gridDim.x) {
       if (alive && !alive[w]) continue;
+      const int wn = sh.xs ? next_live(w) : sh.Nw;
+      const int kw = kx++;
+      // element cursor of this thread's share of the next walker's X: e = et + nte j,
+      // (column, orbital) = divmod(e, M), advanced by (xdc, xdi) = divmod(nte, M)
+      int xe = et, xc = et / sh.M, xi = et - (et / sh.M) * sh.M;
+      if (sh.xs) {
+        // this walker's X, staged by every epilogue thread, is complete
+        const bool okx = !*abort_flag && mbar_wait(xfull, kw & 1, err, wait_ns);
+        if (!__all_sync(0xffffffffu, okx)) { fail(); ok = false; break; }
+        if (!copy_planes(4, sh.acol)) { ok = false; break; }
+        for (int it = 0; it < nitems; ++it) {
+          const int t = it / (2 * ngh), sl = (it % (2 * ngh)) / ngh;
+          const int c0 = 16 * half + (it % ngh) * cstep, i0b = 128 * t + 32 * qd + 16 * sl;
+          const uint32_t tl = tmem + ((uint32_t)(32 * qd + 16 * sl) << 16);
+          float x[8];
+          uint32_t v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int i = i0b + lane_of(j), c = c0 + col_of(j);
+            x[j] = i < sh.M ? xst[c * sh.xs_ld + i] : 0.f;
+            v[j] = __float_as_uint(x[j]);
+          }
+          tmem_st_frag(tl + sreg + (uint32_t)(t * sh.dcol + c0), v);
+          if (i0b < 64 * sh.KB) put_block(x, i0b, c0, false);
+        }
+        mbar_arrive(xread);   // the staged X may take the next walker's once all have read it
+      } else
       // S = X (this walker's columns) and the operand [X_re; X_im] for the first one-body round.
       // The (tile, slab, column group) items of this warp go in batches of 4: every load of a
       // batch is issued first, so the walker pays one memory latency per batch, and the first
@@ -497,7 +566,30 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
       mbar_arrive(bready);
       for (int q = 0; q < rounds && ok; ++q, ++rq) {
         const bool last = q == rounds - 1;
-        const bool okw = !*abort_flag && mbar_wait(dfull, rq & 1, err, wait_ns);
+        // this round's share of the next walker's X: loaded now, staged after the round's
+        // results are handed to the MMA warp, so the loads have the MMAs and the round's
+        // epilogue to land
+        double xp[kXu];
+        int xo[kXu];
+        const bool pre = sh.xs && wn < sh.Nw;
+        if (pre)
+#pragma unroll
+          for (int u = 0; u < kXu; ++u) {
+            const bool v = u < xu && xe < nx;
+            const int b = xc < sh.Np ? xc : xc - sh.Np;
+            xp[u] = v && b < sh.N
+                        ? phi_in[(xc < sh.Np ? 0 : plane) + ((int64_t)wn * sh.N + b) * sh.M + xi]
+                        : 0.0;
+            xo[u] = v ? xc * sh.xs_ld + xi : -1;
+            if (v) {   // the thread's next element: e + nte
+              xe += nte;
+              xc += xdc;
+              xi += xdi;
+              if (xi >= sh.M) { xi -= sh.M; ++xc; }
+            }
+          }
+        bool okw = !*abort_flag && mbar_wait(dfull, rq & 1, err, wait_ns);
+        if (pre && q == 0) okw = okw && !*abort_flag && mbar_wait(xread, kw & 1, err, wait_ns);
         if (!__all_sync(0xffffffffu, okw)) { fail(); ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const float inv = (q >= 1 && q <= sh.order) ? 1.f / (float)q : 1.f;
@@ -552,6 +644,12 @@ __global__ void __launch_bounds__(64 + 32 * EPI, EPI == 4 ? 2 : 1)
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           mbar_arrive(bready);
+        }
+        if (pre) {
+#pragma unroll
+          for (int u = 0; u < kXu; ++u)
+            if (xo[u] >= 0) xst[xo[u]] = f64_to_f32_rn(xp[u]);
+          if (last) mbar_arrive(xfull);   // the next walker's X is staged
         }
       }
     }
@@ -635,11 +733,14 @@ TclShape shape_of(const Ctx& c, int nst, int resident) {
   s.Nw = c.Nw;
   s.resident = resident;
   s.ring_off = 0;
-  s.ares_off = nst * kTile;
+  // (the staging covers kXu elements per epilogue thread and round)
+  s.xs = resident && s.eres && s.n2 * s.M <= kXu * 32 * 8 * (s.order + 2);
+  s.xs_ld = s.M + 4;   // rows 4 floats apart: the fragment reads below fall in distinct banks
+  s.ares_off = s.xs ? (s.n2 * s.xs_ld * 4 + 1023) / 1024 * 1024 : nst * kTile;
   s.bhi_off = s.ares_off + (resident ? 4 * s.KB * kTile : 0);
   s.blo_off = s.bhi_off + s.KB * s.bkb;
   s.bar_off = s.blo_off + s.KB * s.bkb;
-  s.smem_bytes = s.bar_off + 8 * (2 * kMaxStages + 5) + 16 + 1024;
+  s.smem_bytes = s.bar_off + 8 * (2 * kMaxStages + 7) + 16 + 1024;
   return s;
 }
 
