@@ -105,10 +105,11 @@ def parse():
                                          "overlap_update", "mgs"],
                     help="profiling aid: set up the workload, take one step, then launch only "
                          "this kernel --reps times (no JSON line)")
-    ap.add_argument("--study", choices=["correlation"],
+    ap.add_argument("--study", choices=["correlation", "pes"],
                     help="correlation: sigma_dE of correlated against independent fields for "
-                         "6..192 walkers per repeat (one JSON line per population, no "
-                         "benchmark line)")
+                         "6..192 walkers per repeat (one JSON line per population); pes: the "
+                         "correlated run from the trial against the same run after the "
+                         "preliminary equilibration scheme (one JSON line); no benchmark line")
     ap.add_argument("--walkers", type=int, default=None, help="override walkers per system")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--compare-steps", type=int, default=None,
@@ -590,6 +591,69 @@ def run_study(args, wl):
         print(json.dumps(row), flush=True)
 
 
+def run_pes_study(args, wl):
+    """Preliminary equilibration scheme (Sec. II.C) against starting both systems at their
+    trials. Plain: the pair from the trials for --steps blocks, tau_eq = tau / 4. PES: the
+    primary system alone for --steps blocks of [5 steps, orthonormalisation, comb of every
+    repeat], the secondary seeded from its walkers (weights by the overlap ratio), then the
+    pair for --steps blocks from there with tau_eq = 0. sigma_dE and Delta E of both, and
+    the GPU time of each part."""
+    import numpy as np
+    import torch
+    import paper_1703_01545_gb300 as afq
+
+    afq.build()
+    dt, R, nw = wl["dt"], wl["repeats"], args.walkers or wl["n_walkers"]
+    n_steps = args.steps * STEPS_PER_BLOCK
+    prec = {"fp64": afq.FP64, "bf16x3": afq.BF16X3}[args.precision]
+    dA, dB = systems(wl, args.coupling)
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(1703)
+
+    def make():
+        return [afq.System(d["h1"], d["L"], d["trial"], d["n_up"], d["n_dn"], dt=dt,
+                           n_walkers=nw, seed=1, n_repeats=R, precision=prec,
+                           autotune_cache=args.autotune_cache) for d in (dA, dB)]
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    row = {"study": "pes", "workload": wl["cfg"], "coupling": args.coupling,
+           "precision": args.precision, "repeats": R, "walkers_per_system": nw,
+           "propagation_steps": n_steps}
+    A, B = make()
+    res, ms = timed(lambda: afq.pair_delta_E(A, B, n_steps, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
+                                             tau_eq=0.25 * n_steps * dt, raise_on_dead=False))
+    row["from_trial"] = {"dE_mean_Ha": res["dE_mean"], "dE_sigma_Ha": res["dE_sigma"],
+                         "tau_eq": 0.25 * n_steps * dt, "ms": ms}
+    A.close()
+    B.close()
+    A, B = make()
+
+    def equilibrate():
+        for _ in range(args.steps):
+            A.propagate(STEPS_PER_BLOCK)
+            A.orthonormalise()
+            A.population_control(rng.random(R))
+        B.seed_from(A)
+
+    _, ms_eq = timed(equilibrate)
+    res, ms = timed(lambda: afq.pair_delta_E(A, B, n_steps, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
+                                             tau_eq=0.0, raise_on_dead=False))
+    row["pes"] = {"dE_mean_Ha": res["dE_mean"], "dE_sigma_Ha": res["dE_sigma"], "tau_eq": 0.0,
+                  "ms_equilibration": ms_eq, "ms": ms,
+                  "alive": [h.info().n_alive for h in (A, B)]}
+    A.close()
+    B.close()
+    print(json.dumps(row), flush=True)
+
+
 def run_ours(args, wl, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -781,6 +845,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.kernel:
         run_kernel(args, wl)
+    elif args.study == "pes":
+        run_pes_study(args, wl)
     elif args.study:
         run_study(args, wl)
     elif args.impl == "reference":

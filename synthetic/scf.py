@@ -112,4 +112,12 @@ def scf_trial(h1, L, n_up: int, n_dn: int, max_iter: int = 60, tol: float = 1e-1
     if n_up == n_dn:
         C = [C[0], C[0].copy()]
     trial = np.concatenate(C, axis=1)
+    # sign convention: each orbital's largest-magnitude coefficient positive (ties: the first).
+    # Nothing of one system depends on its orbitals' signs; the overlap ratio between two
+    # systems' trials that seeds a secondary system does (its sign is that of the product of
+    # the flips), and a common convention makes it that of the physical overlap.
+    for j in range(trial.shape[1]):
+        k = int(np.argmax(np.abs(trial[:, j])))
+        if trial[k, j] < 0:
+            trial[:, j] = -trial[:, j]
     return np.ascontiguousarray(trial), converged, it

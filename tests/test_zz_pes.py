@@ -60,7 +60,11 @@ def test_population_control_matches_oracle():
 def test_seeding_and_correlated_run_match_oracle():
     afq = need_gpu()
     cfg = CONFIGS["C1"]
-    dA, dB = system_data("C1", "A"), system_data("C1", "B")      # neutral 2/2, ion 2/1
+    # neutral 2/2, ion 2/1 at the moderate coupling: there the two SCF trials share their
+    # orbitals (overlaps 0.97-0.98), so a walker of the neutral seeds the ion with R > 0; at the
+    # literal coupling the ion's trial is rotated far from the neutral's and R < 0 for every
+    # walker, which the phaseless projection of the seeding kills
+    dA, dB = system_data("C1", "A", "moderate"), system_data("C1", "B", "moderate")
     nw, R, seed, n_eq, n_steps = 32, 2, 43, 10, 20
     u = np.array([[0.25, 0.75], [0.6, 0.1]])
     gA, oA = pair(afq, dA, nw, cfg["dt"], seed=seed, R=R)
