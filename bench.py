@@ -96,6 +96,10 @@ def parse():
     ap.add_argument("--mode", default="phaseless", choices=["phaseless", "free"],
                     help="free: correlated free projection (x_bar = 0, complex weights)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pair-form", type=int, choices=[0, 1], default=1,
+                    help="1: each pair call is one graph launch looping over the measurement "
+                         "blocks on the device (default); 0: the block graph is launched once per "
+                         "block (same kernels and results; a profiler sees every kernel node)")
     ap.add_argument("--no-multidet", action="store_true",
                     help="skip the multi-determinant-trial pair measurement")
     ap.add_argument("--autotune-cache", default=None,
@@ -678,13 +682,15 @@ def run_ours(args, wl, rank, world, local_rank):
                           autotune_cache=args.autotune_cache, independent_fields=independent,
                           mode=afq.FREE if args.mode == "free" else afq.PHASELESS)
 
-    def timed(prec, coupling, clocks=None, independent=False, blocks=None):
+    def timed(prec, coupling, clocks=None, independent=False, blocks=None, form=1):
         """Pair run of `blocks` (default K) timed measurement blocks after W warm-up blocks;
-        independent=True gives B its own field key (uncorrelated sampling)."""
+        independent=True gives B its own field key (uncorrelated sampling); form 1 runs the
+        call as one graph launch, form 0 launches the block graph once per block."""
         n_steps_run = (K if blocks is None else blocks) * STEPS_PER_BLOCK
         dA, dB = systems(wl, coupling)
         A = make(dA, prec, 1, independent)
         B = make(dB, prec, 2 if independent else 1, independent)
+        A.select_kernel(afq.K_PAIR_LOOP, form)
         afq.pair_delta_E(A, B, W * STEPS_PER_BLOCK, STEPS_PER_BLOCK, STEPS_PER_BLOCK,
                          raise_on_dead=False)
         torch.cuda.synchronize()
@@ -712,9 +718,11 @@ def run_ours(args, wl, rank, world, local_rank):
             ms = float(t.item())
         alive = [A.info().n_alive, B.info().n_alive]
         return dict(ms=ms, res=res, alive=alive, clocks=ck, A=A, B=B, dA=dA,
-                    graph_kernels=afq.pair_graph_kernels(A), steps=n_steps_run)
+                    graph_kernels=afq.pair_graph_kernels(A), steps=n_steps_run,
+                    form=afq.pair_run_form(A))
 
-    main = timed(args.precision, args.coupling, ClockSampler(torch.cuda.current_device()))
+    main = timed(args.precision, args.coupling, ClockSampler(torch.cuda.current_device()),
+                 form=args.pair_form)
     ms = main["ms"]
     # Delta E over the repeats of every replica (gathered after the timed region)
     replicas = None
@@ -769,18 +777,40 @@ def run_ours(args, wl, rank, world, local_rank):
     dA, dB = systems(wl, args.coupling)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    A2, B2 = make(dA, args.precision), make(dB, args.precision)
+    A2 = make(dA, args.precision)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    B2 = make(dB, args.precision)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     res2 = afq.pair_delta_E(A2, B2, n_steps, STEPS_PER_BLOCK, STEPS_PER_BLOCK, raise_on_dead=False)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    e2e_s = t3 - t0
     A2.close()
     B2.close()
     h2d = sum(8 * (d["h1"].size + d["L"].size + d["trial"].size) for d in (dA, dB))
     d2h = 8 * res2["E"].size
     e2e = {"value": world * nw * n_steps / e2e_s, "unit": "walker-steps/s",
            "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+           "seconds": {"setup_A": t1 - t0, "setup_B": t2 - t1, "pair_run": t3 - t2},
            "note": "setup of both systems from host arrays (H2D copies, setup kernels and the "
                    "kernel-variant autotuning inside) + the same pair run + energy series to host"}
+
+    # the same run with the block graph launched once per measurement block instead of one
+    # launch looping on the device (identical kernels and results)
+    launch = None
+    if world == 1:
+        r0 = timed(args.precision, args.coupling, form=1 - args.pair_form)
+        r0["A"].close()
+        r0["B"].close()
+        one, per = (main, r0) if main["form"] == 1 else (r0, main)
+        launch = {"form": main["form"], "ms_per_block_one_launch": one["ms"] / K,
+                  "ms_per_block_launch_per_block": per["ms"] / K,
+                  "kernels_per_block": main["graph_kernels"],
+                  "identical_dE": bool(r0["res"]["dE_mean"] == main["res"]["dE_mean"]),
+                  "note": "one graph launch per pair call (device-side while loop over the "
+                          "measurement blocks) against one block-graph launch per block"}
 
     # correlated against independent fields at the same workload and precision (Sec. III):
     # GPU time to reach a given sigma_dE scales as sigma^2 * t
@@ -827,7 +857,9 @@ def run_ours(args, wl, rank, world, local_rank):
                        "fp64_comparison_blocks": cmp_blocks,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clocks"],
-            "gpu_launches": per_block * K, "alive_walkers": main["alive"],
+            "gpu_launches": per_block * K + (1 if main["form"] == 1 else 0),
+            "alive_walkers": main["alive"],
+            "pair_launch": launch,
             "sigma_sqrt_t": comp, "correlated_vs_independent": corr, "kernels": kernels,
             "multidet": md,
             "replicas_dE": replicas,

@@ -272,8 +272,12 @@ afqmc_status afqmc_energy(afqmc_handle h, double* e_local, double* e_mixed, doub
  * with different X share the first min(X_A, X_B) fields).  No population control;
  * each system keeps its own force bias and mean field.  Runs n_steps steps of both
  * systems; every mgs_every steps orthonormalises, every energy_every steps measures
- * (order: propagate, orthonormalise, measure).  One measurement block is captured
- * once as a CUDA graph and replayed.  Requirements: same seed, Nw, R, dt, mode and
+ * (order: propagate, orthonormalise, measure).  One measurement block of both systems
+ * (A and B on two concurrent branches) is captured once as a CUDA graph and cached on A.
+ * By default that block is the body of a device-side while loop, so the whole run is one
+ * graph launch: the block's last kernel counts the blocks and ends the loop after
+ * n_steps / energy_every of them (afqmc_select_kernel AFQMC_K_PAIR_LOOP 0 launches the
+ * block graph once per block instead; both give identical results).  Requirements: same seed, Nw, R, dt, mode and
  * step counter on both handles; the step counter a multiple of energy_every;
  * energy_every a multiple of mgs_every; n_steps a multiple of energy_every.  With
  * independent_fields = 1 on both handles the seeds must differ instead: each system then
@@ -300,6 +304,14 @@ afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n_steps,
  * not synchronise.  Errors: ARG (null pointer), CUDA.
  */
 afqmc_status afqmc_pair_graph_kernels(afqmc_handle A, int* n_kernels);
+
+/*
+ * afqmc_pair_run_form -- instrumentation, no counterpart in the paper.  *form = 1 when the
+ * pair graph cached on A runs the whole call as one graph launch (device-side loop over the
+ * measurement blocks), 0 when it is launched once per block, -1 when no graph is cached.
+ * Host only.  Errors: ARG (null pointer).
+ */
+afqmc_status afqmc_pair_run_form(afqmc_handle A, int* form);
 
 /*
  * afqmc_set_tangent -- tangent-mode (forward) derivative along a one-body perturbation
@@ -382,7 +394,8 @@ afqmc_status afqmc_delta_E_stats(const double* dE, const double* taus, int n_mea
  * Synchronises the stream.  Errors: ARG, CUDA.
  */
 enum { AFQMC_K_VHS = 0, AFQMC_K_FORCE_BIAS = 1, AFQMC_K_TAYLOR = 2, AFQMC_K_EXCHANGE = 3,
-       AFQMC_K_OVERLAP = 4, AFQMC_K_OVERLAP_UPDATE = 5, AFQMC_K_MGS = 6 };
+       AFQMC_K_OVERLAP = 4, AFQMC_K_OVERLAP_UPDATE = 5, AFQMC_K_MGS = 6,
+       AFQMC_K_PAIR_LOOP = 7 /* afqmc_select_kernel only */ };
 afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms,
                                cudaStream_t stream);
 
@@ -399,9 +412,13 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms,
  *                           shared memory (1);
  *   which AFQMC_K_MGS:      the orthonormalisation: 1 = Cholesky QR (Gram matrix in FP32
  *                           pairs, R and log det R in FP64, Q in FP32), 0 = modified
- *                           Gram-Schmidt in FP64.
- * The choice shows in afqmc_get_info.  Errors: ARG (FP64 handle, unknown kernel, or a
- * variant this shape does not support).
+ *                           Gram-Schmidt in FP64;
+ *   which AFQMC_K_PAIR_LOOP (either precision; applies to runs with h as the first handle
+ *                           of afqmc_pair_delta_E): 1 = the whole run as one graph launch
+ *                           with a device-side loop over the measurement blocks (default),
+ *                           0 = one launch of the block graph per measurement block.
+ * The kernel choices show in afqmc_get_info.  Errors: ARG (FP64 handle for a kernel
+ * variant, unknown kernel, or a variant this shape does not support).
  */
 afqmc_status afqmc_select_kernel(afqmc_handle h, int which, int variant);
 

@@ -55,6 +55,7 @@ SIGNATURES = {
     "afqmc_pair_delta_E": (ctypes.c_int, [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, VP, VP, VP, VP, VP]),
     "afqmc_pair_graph_kernels": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
+    "afqmc_pair_run_form": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
     "afqmc_delta_E_stats": (ctypes.c_int, [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            VP, VP, VP]),
     "afqmc_reblock_error": (ctypes.c_double, [VP, ctypes.c_int]),

@@ -157,6 +157,14 @@ def afqmc_pair_graph_kernels(A):
     return n.value
 
 
+def afqmc_pair_run_form(A):
+    """1: the pair graph cached on handle A runs a whole call as one graph launch (device-side
+    loop over the measurement blocks); 0: one launch per block; -1: no graph cached."""
+    f = ctypes.c_int(0)
+    _check(_lib.load().afqmc_pair_run_form(A, ctypes.byref(f)), A, "afqmc_pair_run_form")
+    return f.value
+
+
 def afqmc_delta_E_stats(dE, taus, tau_eq):
     """Host statistics; returns (mean_tau, se_tau, (mean, se, tau_at_min))."""
     dE = np.ascontiguousarray(dE, dtype=np.float64)
@@ -170,6 +178,7 @@ def afqmc_delta_E_stats(dE, taus, tau_eq):
 
 
 K_VHS, K_FORCE_BIAS, K_TAYLOR, K_EXCHANGE, K_OVERLAP, K_OVERLAP_UPDATE, K_MGS = 0, 1, 2, 3, 4, 5, 6
+K_PAIR_LOOP = 7   # select_kernel only: pair run as one graph launch (1) or one per block (0)
 
 
 def afqmc_time_kernel(h, which, reps, stream=None):
@@ -284,7 +293,8 @@ class System:
 
     def select_kernel(self, which, variant):
         """Fix a tunable kernel's variant (K_EXCHANGE: 0 tensor cores, 2/4/8 FP32 walkers per
-        CTA; K_TAYLOR: 0 L1, 1 shared memory), overriding the autotuner."""
+        CTA; K_TAYLOR: 0 L1, 1 shared memory), overriding the autotuner; K_PAIR_LOOP (either
+        precision): 1 one graph launch per pair run, 0 one launch per measurement block."""
         _check(_lib.load().afqmc_select_kernel(self.h, int(which), int(variant)), self.h,
                "afqmc_select_kernel")
 
@@ -345,6 +355,12 @@ class System:
 def pair_graph_kernels(A: System):
     """Kernel launches per measurement block of the last pair run with A as its first system."""
     return afqmc_pair_graph_kernels(A.h)
+
+
+def pair_run_form(A: System):
+    """1 when the last pair run with A as its first system was one graph launch, 0 when it
+    launched the block graph once per measurement block."""
+    return afqmc_pair_run_form(A.h)
 
 
 def pair_delta_E(A: System, B: System, n_steps, energy_every=5, mgs_every=5, tau_eq=0.0,

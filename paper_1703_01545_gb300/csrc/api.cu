@@ -1100,6 +1100,11 @@ afqmc_status afqmc_get_tangent_state(afqmc_handle h, double* dlogw, cudaStream_t
 
 afqmc_status afqmc_select_kernel(afqmc_handle h, int which, int variant) {
   if (!h) return AFQMC_ERR_ARG;
+  if (which == AFQMC_K_PAIR_LOOP) {
+    if (variant != 0 && variant != 1) return set_err(h, AFQMC_ERR_ARG, "pair-run form is 0 or 1");
+    h->pair_loop = variant;
+    return AFQMC_OK;
+  }
   if (h->opt.precision != AFQMC_BF16X3) return set_err(h, AFQMC_ERR_ARG, "FP64 handles have no variants");
   if (which == AFQMC_K_EXCHANGE) {
     const bool ok = variant == 0 ? h->etc != nullptr

@@ -60,8 +60,10 @@ void save(const char* path, const std::map<std::string, int>& m) {
   f << "\n}\n";
 }
 
+// Median of three timed launches after a warm one; a variant whose first timed launch takes
+// more than twice the best median so far cannot win and is not timed further.
 template <class F>
-float time_variant(F launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+float time_variant(F launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float best) {
   if (launch() != cudaSuccess) return 1e30f;
   std::vector<float> t;
   for (int r = 0; r < 3; ++r) {
@@ -71,6 +73,7 @@ float time_variant(F launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
     if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
+    if (r == 0 && ms > 2.f * best) return ms;
     t.push_back(ms);
   }
   std::sort(t.begin(), t.end());
@@ -103,7 +106,7 @@ cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s) {
           [&]() {
             return wb == 0 ? launch_energy_tc(c, s) : launch_energy_tiled(c, c.theta32, c.LtT, s, -1, wb);
           },
-          s, e0, e1);
+          s, e0, e1, best);
       if (t < best) { best = t; c.tune_energy_wb = wb; }
     }
     cache[ke] = c.tune_energy_wb;
@@ -119,7 +122,7 @@ cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s) {
     for (int v : {3, 4, 2, 1, 0}) {
       if (!taylor_variant_ok(c, v)) continue;
       const float t = time_variant([&]() { return launch_propagation(c, v, c.theta, c.phi32, s); },
-                                   s, e0, e1);
+                                   s, e0, e1, best);
       if (t < best) { best = t; c.tune_taylor_smem = v; }
     }
     cache[kt] = c.tune_taylor_smem;
@@ -135,7 +138,7 @@ cudaError_t autotune_mixed(Ctx& c, const char* cache_path, cudaStream_t s) {
     for (int v : {1, 0}) {
       if (v == 1 && !mgs_chol_ok(c)) continue;
       c.tune_mgs = v;
-      const float t = time_variant([&]() { return launch_mgs_warp(c, s, false); }, s, e0, e1);
+      const float t = time_variant([&]() { return launch_mgs_warp(c, s, false); }, s, e0, e1, best);
       if (t < best) { best = t; cache[km] = v; }
     }
     c.tune_mgs = cache[km];

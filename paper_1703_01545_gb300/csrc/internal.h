@@ -131,6 +131,8 @@ struct Ctx {
   double* md_eloc = nullptr;   // [Nd][2][Nw] local energy of each determinant
   // pair-run graph cache (owned; see pair.cu)
   void* pair_cache = nullptr;
+  int pair_loop = 1;          // pair run: 1 one graph launch looping over the blocks on the device,
+                              // 0 one launch of the block graph per measurement block
   uint64_t uid = 0;           // unique per handle, so a cached graph never outlives its partner
   std::string err;
 };

@@ -1,8 +1,11 @@
 // Correlated-sampling pair run (Sec. II.B): both systems advance in lockstep on the
 // shared field stream.  One measurement block (energy_every steps of A and B on two
-// forked capture streams, the Gram-Schmidt passes, both energies and their per-repeat
-// sums) is captured once as a CUDA graph and replayed n_meas times; the only host
-// crossing is one copy of the energy series at the end.
+// forked capture streams, the orthonormalisation passes, both energies and their
+// per-repeat sums) is captured once as a CUDA graph.  Default form: the block is the body
+// of a device-side while loop, so the whole run of both systems is one graph launch; the
+// block's last kernel counts the blocks and ends the loop.  Form 0 (afqmc_select_kernel
+// AFQMC_K_PAIR_LOOP): the block graph is launched once per measurement block.  Either way
+// the only host crossing is one copy of the energy series at the end.
 #include <cmath>
 #include <string>
 #include <vector>
@@ -21,17 +24,18 @@ cudaError_t launch_meas_advance(int* meas, cudaStream_t s);
 
 namespace {
 
-// Captured measurement block of one (A, B, energy_every, mgs_every) pair, kept in A.
+// Captured pair run of one (A, B, energy_every, mgs_every, form) combination, kept in A.
 struct Res {
   uint64_t partner_uid = 0;
   int ee = 0, me = 0, capacity = 0;
+  int form = 0;   // 1: graph = while loop around the block; 0: graph = the block
   cudaStream_t cs = nullptr, cs2 = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr, ready = nullptr, done = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   double* series = nullptr;
-  int* meas = nullptr;
-  int n_kernels = 0;   // kernel nodes of the captured graph
+  int* meas = nullptr;   // [0] blocks done in this call, [1] blocks this call asks for
+  int n_kernels = 0;     // kernel nodes of one captured block
   ~Res() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -48,6 +52,124 @@ afqmc_status fail(afqmc_ctx* A, afqmc_ctx* B, afqmc_status code, const std::stri
   if (A) A->err = msg;
   if (B) B->err = msg;
   return code;
+}
+
+// Loop form: the last kernel of every block counts it and clears the loop's condition once
+// the call's blocks are done (meas[1]) or the series buffer is full (capacity), whichever
+// comes first, so the loop ends after at most `capacity` blocks whatever meas[1] holds.
+__global__ void k_meas_next(int* meas, int capacity, cudaGraphConditionalHandle loop) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int m = meas[0] + 1;
+    meas[0] = m;
+    if (m >= meas[1] || m >= capacity) cudaGraphSetConditional(loop, 0);
+  }
+}
+
+__global__ void k_meas_start(int* meas, int n_meas) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    meas[0] = 0;
+    meas[1] = n_meas;
+  }
+}
+
+// Records one measurement block of A (on r->cs) and B (on r->cs2) into the capture running
+// on r->cs; `last` adds the block's final kernel on r->cs after the two branches join.
+template <class F>
+afqmc_status record_block(afqmc_ctx* A, afqmc_ctx* B, Res* r, F last) {
+  const int R = A->R, stride = 8 * R;
+  afqmc_status st = AFQMC_OK;
+  cudaError_t ce = cudaEventRecord(r->fork, r->cs);
+  if (ce == cudaSuccess) ce = cudaStreamWaitEvent(r->cs2, r->fork, 0);
+  for (int j = 0; j < r->ee && st == AFQMC_OK && ce == cudaSuccess; ++j) {
+    st = afq::pair_step(A, r->cs);
+    if (st == AFQMC_OK) st = afq::pair_step(B, r->cs2);
+    if (st == AFQMC_OK && (j + 1) % r->me == 0) {
+      st = afq::pair_ortho(A, r->cs);
+      if (st == AFQMC_OK) st = afq::pair_ortho(B, r->cs2);
+    }
+  }
+  if (st == AFQMC_OK && ce == cudaSuccess) st = afq::pair_energy(A, r->cs);
+  if (st == AFQMC_OK && ce == cudaSuccess) st = afq::pair_energy(B, r->cs2);
+  if (st == AFQMC_OK && ce == cudaSuccess) {
+    ce = afq::launch_mixed_sum(*A, r->series, r->meas, stride, r->cs);
+    if (ce == cudaSuccess) ce = afq::launch_mixed_sum(*B, r->series + 4 * R, r->meas, stride, r->cs2);
+    if (ce == cudaSuccess) ce = cudaEventRecord(r->join, r->cs2);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(r->cs, r->join, 0);
+    if (ce == cudaSuccess) ce = last();
+  }
+  if (st != AFQMC_OK) return st;
+  if (ce != cudaSuccess)
+    return fail(A, B, AFQMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  return AFQMC_OK;
+}
+
+afqmc_status count_kernels(afqmc_ctx* A, afqmc_ctx* B, cudaGraph_t g, int* n) {
+  size_t n_nodes = 0;
+  *n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n_nodes) != cudaSuccess)
+    return fail(A, B, AFQMC_ERR_CUDA, "cudaGraphGetNodes failed");
+  std::vector<cudaGraphNode_t> nodes(n_nodes);
+  if (n_nodes && cudaGraphGetNodes(g, nodes.data(), &n_nodes) != cudaSuccess)
+    return fail(A, B, AFQMC_ERR_CUDA, "cudaGraphGetNodes failed");
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess)
+      return fail(A, B, AFQMC_ERR_CUDA, "cudaGraphNodeGetType failed");
+    if (ty == cudaGraphNodeTypeKernel) ++*n;
+  }
+  return AFQMC_OK;
+}
+
+// Form 0: the block alone, launched once per measurement block.
+afqmc_status build_block_graph(afqmc_ctx* A, afqmc_ctx* B, Res* r) {
+  cudaError_t ce = cudaStreamBeginCapture(r->cs, cudaStreamCaptureModeRelaxed);
+  if (ce != cudaSuccess)
+    return fail(A, B, AFQMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  afqmc_status st = record_block(A, B, r, [&]() { return afq::launch_meas_advance(r->meas, r->cs); });
+  ce = cudaStreamEndCapture(r->cs, &r->graph);
+  if (st != AFQMC_OK) return st;
+  if (ce != cudaSuccess)
+    return fail(A, B, AFQMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  if ((ce = cudaGraphInstantiate(&r->exec, r->graph, 0)) != cudaSuccess)
+    return fail(A, B, AFQMC_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(ce));
+  return count_kernels(A, B, r->graph, &r->n_kernels);
+}
+
+// Form 1: a graph whose only node is a while loop with the block as its body; one launch
+// runs every block of the call.
+afqmc_status build_loop_graph(afqmc_ctx* A, afqmc_ctx* B, Res* r) {
+  cudaGraphConditionalHandle cond;
+  cudaError_t ce = cudaGraphCreate(&r->graph, 0);
+  if (ce == cudaSuccess)
+    ce = cudaGraphConditionalHandleCreate(&cond, r->graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = cond;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (ce == cudaSuccess) ce = cudaGraphAddNode(&node, r->graph, nullptr, nullptr, 0, &p);
+  if (ce != cudaSuccess)
+    return fail(A, B, AFQMC_ERR_CUDA, std::string("loop node: ") + cudaGetErrorString(ce));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  ce = cudaStreamBeginCaptureToGraph(r->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (ce != cudaSuccess)
+    return fail(A, B, AFQMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  const int cap = r->capacity;
+  int* meas = r->meas;
+  cudaStream_t cs = r->cs;
+  afqmc_status st = record_block(A, B, r, [&]() {
+    k_meas_next<<<1, 32, 0, cs>>>(meas, cap, cond);
+    return cudaGetLastError();
+  });
+  cudaGraph_t got = nullptr;
+  ce = cudaStreamEndCapture(r->cs, &got);
+  if (st != AFQMC_OK) return st;
+  if (ce != cudaSuccess)
+    return fail(A, B, AFQMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  if ((ce = cudaGraphInstantiate(&r->exec, r->graph, 0)) != cudaSuccess)
+    return fail(A, B, AFQMC_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(ce));
+  return count_kernels(A, B, body, &r->n_kernels);
 }
 
 }  // namespace
@@ -95,8 +217,9 @@ extern "C" afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n
       return fail(A, B, AFQMC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
   Res* r = static_cast<Res*>(A->pair_cache);
+  const int form = A->pair_loop ? 1 : 0;
   if (n_meas > 0 && (!r || r->partner_uid != B->uid || r->ee != energy_every ||
-                     r->me != mgs_every || r->capacity < n_meas)) {
+                     r->me != mgs_every || r->capacity < n_meas || r->form != form)) {
     afq::destroy_pair_cache(A);
     r = new Res();
     A->pair_cache = r;
@@ -104,52 +227,19 @@ extern "C" afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n
     r->ee = energy_every;
     r->me = mgs_every;
     r->capacity = n_meas;
+    r->form = form;
     AFQ_PCK(cudaMalloc(&r->series, sizeof(double) * (size_t)n_meas * stride));
-    AFQ_PCK(cudaMalloc(&r->meas, sizeof(int)));
+    AFQ_PCK(cudaMalloc(&r->meas, 2 * sizeof(int)));
     AFQ_PCK(cudaStreamCreateWithFlags(&r->cs, cudaStreamNonBlocking));
     AFQ_PCK(cudaStreamCreateWithFlags(&r->cs2, cudaStreamNonBlocking));
     AFQ_PCK(cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming));
     AFQ_PCK(cudaEventCreateWithFlags(&r->join, cudaEventDisableTiming));
     AFQ_PCK(cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming));
     AFQ_PCK(cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming));
-
-    AFQ_PCK(cudaStreamBeginCapture(r->cs, cudaStreamCaptureModeRelaxed));
-    afqmc_status st = AFQMC_OK;
-    cudaError_t ce = cudaEventRecord(r->fork, r->cs);
-    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(r->cs2, r->fork, 0);
-    for (int j = 0; j < energy_every && st == AFQMC_OK && ce == cudaSuccess; ++j) {
-      st = afq::pair_step(A, r->cs);
-      if (st == AFQMC_OK) st = afq::pair_step(B, r->cs2);
-      if (st == AFQMC_OK && (j + 1) % mgs_every == 0) {
-        st = afq::pair_ortho(A, r->cs);
-        if (st == AFQMC_OK) st = afq::pair_ortho(B, r->cs2);
-      }
-    }
-    if (st == AFQMC_OK && ce == cudaSuccess) st = afq::pair_energy(A, r->cs);
-    if (st == AFQMC_OK && ce == cudaSuccess) st = afq::pair_energy(B, r->cs2);
-    if (st == AFQMC_OK && ce == cudaSuccess) {
-      ce = afq::launch_mixed_sum(*A, r->series, r->meas, stride, r->cs);
-      if (ce == cudaSuccess) ce = afq::launch_mixed_sum(*B, r->series + 4 * R, r->meas, stride, r->cs2);
-      if (ce == cudaSuccess) ce = cudaEventRecord(r->join, r->cs2);
-      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(r->cs, r->join, 0);
-      if (ce == cudaSuccess) ce = afq::launch_meas_advance(r->meas, r->cs);
-    }
-    cudaError_t ce2 = cudaStreamEndCapture(r->cs, &r->graph);
-    if (st != AFQMC_OK || ce != cudaSuccess || ce2 != cudaSuccess) {
+    const afqmc_status st = form ? build_loop_graph(A, B, r) : build_block_graph(A, B, r);
+    if (st != AFQMC_OK) {
       afq::destroy_pair_cache(A);
-      if (st != AFQMC_OK) return st;
-      return fail(A, B, AFQMC_ERR_CUDA, std::string("graph capture: ") +
-                                            cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
-    }
-    AFQ_PCK(cudaGraphInstantiate(&r->exec, r->graph, 0));
-    size_t n_nodes = 0;
-    AFQ_PCK(cudaGraphGetNodes(r->graph, nullptr, &n_nodes));
-    std::vector<cudaGraphNode_t> nodes(n_nodes);
-    if (n_nodes) AFQ_PCK(cudaGraphGetNodes(r->graph, nodes.data(), &n_nodes));
-    for (cudaGraphNode_t nd : nodes) {
-      cudaGraphNodeType ty;
-      AFQ_PCK(cudaGraphNodeGetType(nd, &ty));
-      if (ty == cudaGraphNodeTypeKernel) ++r->n_kernels;
+      return st;
     }
   }
   cudaStream_t cs = s;
@@ -157,8 +247,14 @@ extern "C" afqmc_status afqmc_pair_delta_E(afqmc_handle A, afqmc_handle B, int n
     cs = r->cs;
     AFQ_PCK(cudaEventRecord(r->ready, s));
     AFQ_PCK(cudaStreamWaitEvent(r->cs, r->ready, 0));
-    AFQ_PCK(cudaMemsetAsync(r->meas, 0, sizeof(int), r->cs));
-    for (int m = 0; m < n_meas; ++m) AFQ_PCK(cudaGraphLaunch(r->exec, r->cs));
+    if (r->form) {
+      k_meas_start<<<1, 32, 0, r->cs>>>(r->meas, n_meas);
+      AFQ_PCK(cudaGetLastError());
+      AFQ_PCK(cudaGraphLaunch(r->exec, r->cs));
+    } else {
+      AFQ_PCK(cudaMemsetAsync(r->meas, 0, sizeof(int), r->cs));
+      for (int m = 0; m < n_meas; ++m) AFQ_PCK(cudaGraphLaunch(r->exec, r->cs));
+    }
     A->step += (uint64_t)n_steps;
     B->step += (uint64_t)n_steps;
   }
@@ -208,5 +304,12 @@ extern "C" afqmc_status afqmc_pair_graph_kernels(afqmc_handle A, int* n_kernels)
   if (!A || !n_kernels) return AFQMC_ERR_ARG;
   const Res* r = static_cast<const Res*>(A->pair_cache);
   *n_kernels = r ? r->n_kernels : 0;
+  return AFQMC_OK;
+}
+
+extern "C" afqmc_status afqmc_pair_run_form(afqmc_handle A, int* form) {
+  if (!A || !form) return AFQMC_ERR_ARG;
+  const Res* r = static_cast<const Res*>(A->pair_cache);
+  *form = r ? r->form : -1;
   return AFQMC_OK;
 }

@@ -700,15 +700,18 @@ __global__ void __launch_bounds__(64) k_mgs_reg(double* __restrict__ phi, const 
 // Phi_s = Q R with R upper triangular with a positive diagonal, the factors modified
 // Gram-Schmidt produces.  The walker is read as FP32 (the precision the propagator keeps), S =
 // Phi_s^H Phi_s is summed in FP32 (four threads per group of entries, each over a quarter of
-// the orbitals, combined by shuffles) and factorised S = R^H R in FP64, both spins in one warp
-// (16 lanes each, lane l owning column l); Q = Phi_s R^{-1} is formed by forward substitution
-// along every orbital row in FP32 and written back exactly as FP64.  log O drops by
-// sum_j log R_jj (FP64), the R that Q was formed with, so the stored log O and walker agree up
-// to the FP32 rounding of Q (~1e-6 in log O, against which the weights are insensitive).  The
-// walkers are orthonormalised every few steps, so S is close to the identity and squaring the
-// condition number costs nothing.  One 128-thread CTA per walker; shared memory holds the
-// walker as rows of float2 (re, im) with a stride of N + 1, the upper triangles of S and R
-// (FP64), R in FP32 and the reciprocals of its diagonal.
+// the orbitals, combined by shuffles) and factorised S = R^H R in FP32, both spins in one warp
+// (16 lanes each, lane l owning column l): S carries the FP32 rounding of its sums already, so
+// an FP64 factor would add no accuracy, and on this part each warp-wide FP64 instruction
+// (square roots and divisions above all) occupies the FP64 pipe for tens of cycles.  Q =
+// Phi_s R^{-1} is formed by forward substitution along every orbital row in FP32 and written
+// back exactly as FP64.  log O drops by sum_j log R_jj (FP64 logarithms of the FP32 diagonal),
+// the R that Q was formed with, so the stored log O and walker agree up to the FP32 rounding
+// of Q (~1e-6 in log O, against which the weights are insensitive).  The walkers are
+// orthonormalised every few steps, so S is close to the identity and squaring the condition
+// number costs nothing.  One 128-thread CTA per walker; shared memory holds the walker as rows
+// of float2 (re, im) with a stride of N + 1, the upper triangle of S factorised in place, R as
+// float2 and the reciprocals of its diagonal.
 __global__ void __launch_bounds__(128) k_mgs_chol(double* __restrict__ phi, const int* __restrict__ alive,
                                                   double* __restrict__ logO, int M, int N, int n_up,
                                                   int Nw) {
@@ -718,8 +721,8 @@ __global__ void __launch_bounds__(128) k_mgs_chol(double* __restrict__ phi, cons
   const int64_t NM = (int64_t)N * M, plane = (int64_t)Nw * NM, base = (int64_t)wk * NM;
   const int RS = N + 1;                                              // row stride (float2)
   float2* X2 = reinterpret_cast<float2*>(smc);                       // [M][N + 1]
-  double* Sre = reinterpret_cast<double*>(X2 + (size_t)M * RS);      // [N][N] (block diagonal)
-  double* Sim = Sre + (size_t)N * N;
+  float* Sre = reinterpret_cast<float*>(X2 + (size_t)M * RS);        // [N][N] (block diagonal)
+  float* Sim = Sre + (size_t)N * N;
   float2* R2 = reinterpret_cast<float2*>(Sim + (size_t)N * N);       // [N][N]  R in FP32
   float* Rd = reinterpret_cast<float*>(R2 + (size_t)N * N);          // [N]     1 / R_jj
   __shared__ double s_ld;
@@ -787,36 +790,36 @@ __global__ void __launch_bounds__(128) k_mgs_chol(double* __restrict__ phi, cons
       for (int k = 0; k < 4; ++k) {
         const int b = b0 + k;
         if (b < ns && b >= a) {
-          Sre[(size_t)ca * N + o + b] = (double)sre[k];
-          Sim[(size_t)ca * N + o + b] = (double)sim[k];
+          Sre[(size_t)ca * N + o + b] = sre[k];
+          Sim[(size_t)ca * N + o + b] = sim[k];
         }
       }
   }
   __syncthreads();
-  // S_s = R^H R (upper triangle in place, FP64), warp 0: lanes 0-15 the spin-up block, 16-31
+  // S_s = R^H R (upper triangle in place, FP32), warp 0: lanes 0-15 the spin-up block, 16-31
   // the spin-down block, lane l of a half owning column l
   if (tid < 32) {
     const int h = lane >> 4, l = lane & 15, ns = h ? nd : nu, o = h ? nu : 0;
     const int kmax = nu > nd ? nu : nd;
     for (int k = 0; k < kmax; ++k) {
       const bool act = k < ns;
-      const double skk = act ? Sre[(size_t)(o + k) * N + o + k] : 1.0;
-      const double d = sqrt(skk), inv = 1.0 / d;
+      const float skk = act ? Sre[(size_t)(o + k) * N + o + k] : 1.0f;
+      const float d = sqrtf(skk), inv = 1.0f / d;
       if (act && l > k && l < ns) {
         Sre[(size_t)(o + k) * N + o + l] *= inv;
         Sim[(size_t)(o + k) * N + o + l] *= inv;
       }
       if (act && l == k) {
         Sre[(size_t)(o + k) * N + o + k] = d;
-        Sim[(size_t)(o + k) * N + o + k] = 0.0;
+        Sim[(size_t)(o + k) * N + o + k] = 0.0f;
       }
       __syncwarp();
       if (act && l > k && l < ns) {
-        const double rr = Sre[(size_t)(o + k) * N + o + l], ri = Sim[(size_t)(o + k) * N + o + l];
+        const float rr = Sre[(size_t)(o + k) * N + o + l], ri = Sim[(size_t)(o + k) * N + o + l];
         for (int m = k + 1; m <= l; ++m) {   // S_ml -= conj(R_km) R_kl
-          const double ar = Sre[(size_t)(o + k) * N + o + m], ai = Sim[(size_t)(o + k) * N + o + m];
-          Sre[(size_t)(o + m) * N + o + l] -= ar * rr + ai * ri;
-          Sim[(size_t)(o + m) * N + o + l] -= ar * ri - ai * rr;
+          const float ar = Sre[(size_t)(o + k) * N + o + m], ai = Sim[(size_t)(o + k) * N + o + m];
+          Sre[(size_t)(o + m) * N + o + l] -= fmaf(ar, rr, ai * ri);
+          Sim[(size_t)(o + m) * N + o + l] -= fmaf(ar, ri, -ai * rr);
         }
       }
       __syncwarp();
@@ -829,7 +832,7 @@ __global__ void __launch_bounds__(128) k_mgs_chol(double* __restrict__ phi, cons
     const int k = e / N, l = e % N;
     const bool same = (k < nu) == (l < nu);
     float2 v = make_float2(0.f, 0.f);
-    if (same && l >= k) v = make_float2((float)Sre[e], (float)Sim[e]);
+    if (same && l >= k) v = make_float2(Sre[e], Sim[e]);
     R2[e] = v;
     if (k == l) Rd[k] = 1.0f / v.x;
   }
@@ -867,7 +870,7 @@ __global__ void __launch_bounds__(128) k_mgs_chol(double* __restrict__ phi, cons
 }
 
 size_t smem_mgs_chol(const Ctx& c) {
-  return sizeof(float2) * (size_t)c.M * (c.N + 1) + 2 * sizeof(double) * (size_t)c.N * c.N +
+  return sizeof(float2) * (size_t)c.M * (c.N + 1) + 2 * sizeof(float) * (size_t)c.N * c.N +
          sizeof(float2) * (size_t)c.N * c.N + sizeof(float) * (size_t)c.N;
 }
 
