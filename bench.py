@@ -385,9 +385,18 @@ def measure_kernels(afq, A, dA, nw, precision, workload, stream):
                                   "k_gemm_bf16x3_tc (force bias, split-BF16 tcgen05)",
                                   mma=3 * 2.0 * pad(X, 128) * pad(N * M, 64) * 2 * nw,
                                   traffic=tr("gemm_tc.cu", "force_bias_tc"))
+        # with the large-M tensor-core propagator the contraction covers only the
+        # lower-triangle 16 x 16 blocks of index pairs (two 128-row tiles each), when the
+        # persistent kernel runs it (at least 2 x 152 tiles of 128 x 256)
+        nb = (M + 15) // 16
+        tri_rows = nb * (nb + 1) // 2 * 256
+        tri = pv == 4 and (tri_rows // 128) * -(-2 * nw // 256) >= 2 * 152 and pad(2 * nw, 128) % 256 == 0
+        vhs_rows = tri_rows if tri else pad(M * M, 128)
         out["vhs"] = entry(afq.K_VHS, STEPS_PER_BLOCK, vhs, "tensor", bf16,
-                           "k_gemm_bf16x3_tc_persist (V_HS, split-BF16 tcgen05, full M^2 rows)",
-                           mma=3 * 2.0 * pad(M * M, 128) * pad(X, 64) * 2 * nw,
+                           "k_gemm_bf16x3_tc_persist (V_HS, split-BF16 tcgen05, "
+                           + ("lower-triangle 16 x 16 blocks of the M^2 rows, mirror written "
+                              "transposed)" if tri else "full M^2 rows)"),
+                           mma=3 * 2.0 * vhs_rows * pad(X, 64) * 2 * nw,
                            traffic=tr("gemm_tc.cu", "vhs_tc"),
                            full_count_flops_per_launch=vhs_full)
         out["vhs"]["frac_full_count"] = out["vhs"]["frac"] * vhs_full / vhs

@@ -64,7 +64,7 @@ void free_ctx(Ctx* h) {
   if (h->alive) cudaFree(h->alive);
   if (h->d_step) cudaFree(h->d_step);
   if (h->d_flags) cudaFree(h->d_flags);
-  for (afq::TcOperand* op : {h->tc_L, h->tc_Ltil, h->tc_U, h->tc_Theta})
+  for (afq::TcOperand* op : {h->tc_L, h->tc_Ltri, h->tc_Ltil, h->tc_U, h->tc_Theta})
     if (op) {
       if (op->hi) cudaFree(op->hi);
       if (op->lo) cudaFree(op->lo);
@@ -160,6 +160,19 @@ afqmc_status setup_mixed(Ctx* h, cudaStream_t s) {
   }
   cudaError_t e = afq::launch_transpose(h->L, tmp, X, (int)MM, s);
   if (e == cudaSuccess) e = afq::split_bf16(tmp, X, (int)MM, X, h->tc_L->Kp, h->tc_L->hi, h->tc_L->lo, s);
+  if (e == cudaSuccess && afq::propagate_tcl_ok(*h) &&
+      afq::tc_persistent_ok(afq::vhs_tri_rows(M), 2 * Nw, h->tc_U->rows)) {
+    // the lower-triangle blocks of the V_HS rows, for the split output the large-M
+    // tensor-core propagator reads (V_HS is symmetric: the kernel writes the mirror half)
+    if ((st = make_operand(h, &h->tc_Ltri, afq::vhs_tri_rows(M), X, s)) != AFQMC_OK) {
+      if (own) {
+        cudaStreamSynchronize(s);
+        cudaFree(tmp);
+      }
+      return st;
+    }
+    e = afq::split_bf16_tri(tmp, X, M, X, h->tc_Ltri->Kp, h->tc_Ltri->hi, h->tc_Ltri->lo, s);
+  }
   if (e == cudaSuccess) e = afq::split_bf16(h->Ltil, NM, X, (int)NM, h->tc_Ltil->Kp, h->tc_Ltil->hi, h->tc_Ltil->lo, s);
   if (e == cudaSuccess) e = afq::to_float(h->expK, h->expK32, MM, s);
   if (e == cudaSuccess) e = afq::to_float(h->Ltil, h->Ltil32, (int64_t)X * NM, s);

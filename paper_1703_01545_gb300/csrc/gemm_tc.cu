@@ -63,6 +63,81 @@ __device__ __forceinline__ void store_split(const SplitOut& so, int m, int n0, i
   }
 }
 
+// Lower-triangle block layout of the V_HS rows: tile tm is half h of block q = tm / 2 in the
+// order (0,0), (1,0), (1,1), (2,0), ...; block (a, b), a >= b, holds the index pairs
+// i in 16 a + [0, 16), j in 16 b + [0, 16), and half h the rows i in 16 a + 8 h + [0, 8).
+// Row r of a tile is (i, j) = (16 a + 8 h + r / 16, 16 b + r % 16).
+__device__ __forceinline__ void tri_tile(int tm, int& a, int& b, int& h) {
+  const int q = tm >> 1;
+  h = tm & 1;
+  a = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+  while ((a + 1) * (a + 2) / 2 <= q) ++a;
+  while (a * (a + 1) / 2 > q) --a;
+  b = q - a * (a + 1) / 2;
+}
+
+// Split output of 32 accumulator columns of the index pair (i, j) (skipped outside the
+// M x M matrix); with `stg`, the pair's hi and lo values also go to column q of the staging
+// arrays [32][128] at row r, for the transposed write of the mirror block.
+__device__ __forceinline__ void store_split_ij(const SplitOut& so, int i, int j, int n0, int Nd,
+                                               float alpha, const uint32_t (&v)[32],
+                                               __nv_bfloat16* stg, int r) {
+  const bool in = i < so.M && j < so.M;
+  const int64_t off = (int64_t)i * so.Mp + j;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    const int n = n0 + q;
+    const float x = alpha * __uint_as_float(v[q]);
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    if (in && n < Nd) {
+      so.hi[(int64_t)n * so.ld + off] = h;
+      so.lo[(int64_t)n * so.ld + off] = l;
+    }
+    if (stg) {
+      stg[q * BM + r] = h;
+      stg[32 * BM + q * BM + r] = l;
+    }
+  }
+}
+
+// The staged 8 x 16 (i, j) half block of 32 columns written transposed: V[j][i0 .. i0 + 7]
+// for the 16 j of the block, 16 bytes per (column, j, hi / lo); task t of the 128 epilogue
+// threads' 1024.
+__device__ __forceinline__ void store_mirror(const SplitOut& so, const __nv_bfloat16* stg, int i0,
+                                             int j0, int n0, int Nd, int tid) {
+  for (int task = tid; task < 32 * 16 * 2; task += 128) {
+    const int q = task >> 5, jj = (task >> 1) & 15, hl = task & 1;
+    const int n = n0 + q, j = j0 + jj;
+    if (n >= Nd || j >= so.M) continue;
+    const __nv_bfloat16* src = stg + hl * 32 * BM + q * BM + jj;   // row r = 16 ii + jj
+    __nv_bfloat16* dst = (hl ? so.lo : so.hi) + (int64_t)n * so.ld + (int64_t)j * so.Mp + i0;
+    if (i0 + 8 <= so.M) {
+      __align__(16) __nv_bfloat16 pk[8];
+#pragma unroll
+      for (int ii = 0; ii < 8; ++ii) pk[ii] = src[16 * ii];
+      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(pk);
+    } else {
+      for (int ii = 0; ii < 8 && i0 + ii < so.M; ++ii) dst[ii] = src[16 * ii];
+    }
+  }
+}
+
+// AND of `ok` over the 128 epilogue threads (named barrier 1): they leave the tile loop
+// together, so none is left waiting at a staging barrier.
+__device__ __forceinline__ bool epilogue_all(bool ok) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)ok)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 template <int BN, int STAGES, class TC>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_bf16x3_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
@@ -185,7 +260,8 @@ struct PLayoutG {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = PBN * BK * 2;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int BAR_OFFSET = PSTAGES * STAGE_BYTES;
+  static constexpr int STG_OFFSET = PSTAGES * STAGE_BYTES;   // mirror staging: hi, lo [32][128]
+  static constexpr int BAR_OFFSET = STG_OFFSET + 2 * 32 * BM * 2;
   static constexpr int SMEM_BYTES = BAR_OFFSET + 256 + 1024;
 };
 
@@ -291,10 +367,34 @@ __global__ void __launch_bounds__(PTHREADS, 1)
   } else {
     // ---- epilogue: warp w drains TMEM lanes 32 w .. 32 w + 31 (output rows m) ----
     int i = 0;
+    __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem + Lay::STG_OFFSET);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int b = i & 1, m0 = (t % mt) * BM, n0 = (t / mt) * PBN;
       const bool ok = mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, err, wait_ns);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (so.tri) {
+        if (!epilogue_all(ok)) break;
+        // lower-triangle block rows: V[i][j] directly and, off the diagonal, V[j][i] through
+        // the staging arrays
+        int ta, tb, th;
+        tri_tile(t % mt, ta, tb, th);
+        const int r = warp * 32 + lane;
+        const int ri = 16 * ta + 8 * th + (r >> 4), rj = 16 * tb + (r & 15);
+        const bool mirror = ta != tb;
+        for (int c0 = 0; c0 < PBN; c0 += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * PBN + c0), v);
+          store_split_ij(so, ri, rj, n0 + c0, Nd, alpha, v, mirror ? stg : nullptr, r);
+          if (mirror) {
+            epilogue_sync();   // the half block's 32 columns are staged
+            store_mirror(so, stg, 16 * ta + 8 * th, 16 * tb, n0 + c0, Nd, r);
+            epilogue_sync();   // and written: the staging arrays are free again
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(tempty0 + 8 * b);
+        continue;
+      }
       if (!__all_sync(0xffffffffu, ok)) break;
       const int m = m0 + warp * 32 + lane;
       for (int c0 = 0; c0 < PBN; c0 += 32) {
@@ -340,6 +440,25 @@ __global__ void k_split_bf16(const double* __restrict__ in, int64_t ld_in, int r
     const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
     hi[e] = h;
     lo[e] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+  }
+}
+
+// The lower-triangle block rows (tri_tile) of the V_HS operand: row r of tile r / 128 is the
+// index pair (i, j) of row i M + j of `in` ([M^2][ld_in]), zero outside the M x M matrix.
+__global__ void k_split_bf16_tri(const double* __restrict__ in, int64_t ld_in, int M, int rows,
+                                 int K, int Kp, __nv_bfloat16* __restrict__ hi,
+                                 __nv_bfloat16* __restrict__ lo) {
+  const int64_t total = (int64_t)rows * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / Kp), k = (int)(e % Kp);
+    int a, b, h;
+    tri_tile(r >> 7, a, b, h);
+    const int i = 16 * a + 8 * h + ((r & 127) >> 4), j = 16 * b + (r & 15);
+    const double x = (k < K && i < M && j < M) ? in[((int64_t)i * M + j) * ld_in + k] : 0.0;
+    const __nv_bfloat16 hh = __float2bfloat16_rn((float)x);
+    hi[e] = hh;
+    lo[e] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hh)));
   }
 }
 
@@ -405,6 +524,28 @@ cudaError_t split_bf16(const double* in, int64_t ld_in, int rows, int K, int Kp,
   return cudaGetLastError();
 }
 
+int vhs_tri_rows(int M) {
+  const int nb = (M + 15) / 16;
+  return nb * (nb + 1) / 2 * 2 * BM;
+}
+
+cudaError_t split_bf16_tri(const double* in, int64_t ld_in, int M, int K, int Kp, __nv_bfloat16* hi,
+                           __nv_bfloat16* lo, cudaStream_t s) {
+  const int rows = vhs_tri_rows(M);
+  const int64_t total = (int64_t)rows * Kp;
+  int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 64);
+  if (grid < 1) grid = 1;
+  k_split_bf16_tri<<<grid, 256, 0, s>>>(in, ld_in, M, rows, K, Kp, hi, lo);
+  return cudaGetLastError();
+}
+
+// The persistent kernel (the only one with the lower-triangle output) takes a product of at
+// least two 128 x 256 tiles per SM whose B rows are whole 256-row tiles.
+bool tc_persistent_ok(int Md, int Nd, int b_rows) {
+  const int64_t tiles = (int64_t)((Md + BM - 1) / BM) * ((Nd + PBN - 1) / PBN);
+  return tiles >= 2 * 152 && b_rows % PBN == 0;
+}
+
 // A operand boxes are BM = 128 rows; B operand boxes are tc_bn() rows.  Operand buffers
 // hold pad_rows(rows) rows (zero-filled beyond `rows`).
 int tc_bn() { return 128; }
@@ -419,7 +560,8 @@ cudaError_t gemm_f32_or_split(const TcOperand& A, const TcOperand& B, int Md, in
   // next tile's MMAs; B tiles of 256 rows stay inside the operand's padded rows (a multiple of
   // 256 here), or read the TMA fill value beyond them
   const int64_t tiles = (int64_t)((Md + BM - 1) / BM) * ((Nd + PBN - 1) / PBN);
-  if (tiles >= 2 * 152 && B.rows % PBN == 0) {
+  if (so.tri && !tc_persistent_ok(Md, Nd, B.rows)) return cudaErrorInvalidValue;
+  if (tc_persistent_ok(Md, Nd, B.rows)) {
     const int grid = (int)std::min<int64_t>(tiles, 152);
     k_gemm_bf16x3_tc_persist<<<grid, PTHREADS, PLayoutG::SMEM_BYTES, s>>>(
         A.map_hi, A.map_lo, B.map_hi, B.map_lo, Md, Nd, A.Kp / BK, alpha, C, ldc, so, err,
@@ -437,8 +579,9 @@ cudaError_t gemm_bf16x3(const TcOperand& A, const TcOperand& B, int Md, int Nd, 
 
 cudaError_t gemm_bf16x3_split_out(const TcOperand& A, const TcOperand& B, int Md, int Nd,
                                   float alpha, const SplitOut& so, int* err, cudaStream_t s) {
-  if (!so.hi || !so.lo || so.M < 1 || so.Mp < so.M || (int64_t)so.M * so.M != Md ||
-      so.ld < (int64_t)so.M * so.Mp)
+  if (!so.hi || !so.lo || so.M < 1 || so.Mp < so.M || so.ld < (int64_t)so.M * so.Mp ||
+      (so.tri ? vhs_tri_rows(so.M) != Md || so.Mp % 8 != 0 || so.ld % 8 != 0
+              : (int64_t)so.M * so.M != Md))
     return cudaErrorInvalidValue;
   return gemm_f32_or_split(A, B, Md, Nd, alpha, nullptr, 0, so, err, s);
 }

@@ -83,6 +83,7 @@ struct Ctx {
   int* d_flags = nullptr;     // [4] error counters: [0] singular overlaps
   // split-precision (AFQMC_BF16X3) operands and FP32 work arrays; null in FP64 mode
   struct TcOperand* tc_L = nullptr;      // A of V_HS: rows ij (M^2), K = g
+  struct TcOperand* tc_Ltri = nullptr;   // the same rows for the lower-triangle blocks only
   struct TcOperand* tc_Ltil = nullptr;   // A of the force bias: rows g, K = (n, i)
   struct TcOperand* tc_U = nullptr;      // B of V_HS: rows (p, w), K = g
   struct TcOperand* tc_Theta = nullptr;  // B of the force bias: rows (p, w), K = (n, i)
@@ -175,7 +176,16 @@ struct SplitOut {
   __nv_bfloat16* lo = nullptr;
   int M = 0, Mp = 0;
   int64_t ld = 0;
+  int tri = 0;   // 1: A's rows are the lower-triangle 16 x 16 (i, j) blocks (vhs_tri_rows)
 };
+// Rows of the V_HS operand that covers only the lower-triangle blocks of the symmetric
+// matrices: block (a, b), a >= b, of 16 x 16 index pairs (i, j) is two 128-row tiles
+// (i in 16 a + 8 h + [0, 8), j in 16 b + [0, 16), h = 0, 1); V_HS[j][i] = V_HS[i][j] gives
+// the rest.
+int vhs_tri_rows(int M);
+bool tc_persistent_ok(int Md, int Nd, int b_rows);
+cudaError_t split_bf16_tri(const double* in, int64_t ld_in, int M, int K, int Kp, __nv_bfloat16* hi,
+                           __nv_bfloat16* lo, cudaStream_t s);
 cudaError_t gemm_bf16x3_split_out(const TcOperand& A, const TcOperand& B, int Md, int Nd,
                                   float alpha, const SplitOut& so, int* err, cudaStream_t s);
 cudaError_t prepare_tc_kernels();

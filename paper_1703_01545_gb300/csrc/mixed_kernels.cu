@@ -723,6 +723,11 @@ cudaError_t vhs_launch(const Ctx& c, int pv, cudaStream_t s) {
     so.M = c.M;
     so.Mp = propagate_tcl_mp(c.M);
     so.ld = (int64_t)c.M * so.Mp;
+    if (c.tc_Ltri) {   // the lower-triangle blocks only, the mirror half written transposed
+      so.tri = 1;
+      return gemm_bf16x3_split_out(*c.tc_Ltri, *c.tc_U, vhs_tri_rows(c.M), 2 * c.Nw, 1.0f, so,
+                                   c.d_tc_err, s);
+    }
     return gemm_bf16x3_split_out(*c.tc_L, *c.tc_U, (int)MM, 2 * c.Nw, 1.0f, so, c.d_tc_err, s);
   }
   return gemm_bf16x3(*c.tc_L, *c.tc_U, (int)MM, 2 * c.Nw, 1.0f, c.Avhs32, MM, c.d_tc_err, s);
