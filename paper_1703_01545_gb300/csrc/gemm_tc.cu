@@ -123,12 +123,12 @@ __device__ __forceinline__ void store_mirror(const SplitOut& so, const __nv_bflo
   }
 }
 
-// AND of `ok` over the 128 epilogue threads (named barrier 1): they leave the tile loop
+// AND of `ok` over the 256 epilogue threads (named barrier 3): they leave the tile loop
 // together, so none is left waiting at a staging barrier.
 __device__ __forceinline__ bool epilogue_all(bool ok) {
   uint32_t r;
   asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 128, p;\n\t"
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 3, 256, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
       : "r"((uint32_t)ok)
@@ -136,7 +136,13 @@ __device__ __forceinline__ bool epilogue_all(bool ok) {
   return r != 0;
 }
 
-__device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// The four warps of epilogue group g (named barrier 1 + g, 128 threads).
+__device__ __forceinline__ void group_sync(int g) {
+  if (g == 0)
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+  else
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+}
 
 template <int BN, int STAGES, class TC>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -247,21 +253,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // Persistent variant for large outputs (the V_HS contraction): 128 x 256 tiles, grid = one CTA
-// per SM looping over tiles, 6 warps.
-//   warp 4 / lane 0  TMA producer over all of the CTA's tiles (2-stage ring of 96 KB stages)
-//   warp 5 / lane 0  MMA issuer: tile i accumulates into TMEM buffer i & 1 (2 x 256 columns),
+// per SM looping over tiles, 10 warps.
+//   warp 8 / lane 0  TMA producer over all of the CTA's tiles (2-stage ring of 96 KB stages)
+//   warp 9 / lane 0  MMA issuer: tile i accumulates into TMEM buffer i & 1 (2 x 256 columns),
 //                    commits "tile full" for the epilogue and waits for "tile empty" before it
 //                    reuses a buffer
-//   warps 0..3       epilogue: drain buffer i & 1 (warp w reads TMEM lanes 32 w ..) while the
-//                    MMAs of tile i + 1 run, then arrive on "tile empty"
+//   warps 0..7       epilogue, two groups of four: group g drains columns 128 g .. 128 g + 127
+//                    of buffer i & 1 (warp w reads TMEM lanes 32 (w % 4) ..) while the MMAs of
+//                    tile i + 1 run, then arrives on "tile empty"
 // Tiles run m-fastest, so consecutive CTAs share B tiles.  Every wait is bounded as above.
-constexpr int PBN = 256, PSTAGES = 2, PTHREADS = 192;
+constexpr int PBN = 256, PSTAGES = 2, PTHREADS = 320, PEPI = 256;   // PEPI: epilogue threads
 struct PLayoutG {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = PBN * BK * 2;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int STG_OFFSET = PSTAGES * STAGE_BYTES;   // mirror staging: hi, lo [32][128]
-  static constexpr int BAR_OFFSET = STG_OFFSET + 2 * 32 * BM * 2;
+  static constexpr int STG_OFFSET = PSTAGES * STAGE_BYTES;   // mirror staging per epilogue
+  static constexpr int STG_GROUP = 2 * 32 * BM;               // group: hi, lo [32][128] bf16
+  static constexpr int BAR_OFFSET = STG_OFFSET + 2 * STG_GROUP * 2;
   static constexpr int SMEM_BYTES = BAR_OFFSET + 256 + 1024;
 };
 
@@ -289,7 +297,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, 128);
+      mbar_init(tempty0 + 8 * b, PEPI);
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -306,7 +314,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
+  if (warp == 8) {
     if (lane == 0) {
       // ---- TMA producer ----
       int g = 0;
@@ -332,7 +340,7 @@ __global__ void __launch_bounds__(PTHREADS, 1)
       for (int q = (g > PSTAGES ? g - PSTAGES : 0); q < g; ++q)
         mbar_wait(full0 + 8 * (q % PSTAGES), (q / PSTAGES) & 1, err, wait_ns);
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     if (lane == 0) {
       // ---- MMA issuer ----
       const uint32_t idesc = idesc_bf16<PBN>();
@@ -365,9 +373,12 @@ __global__ void __launch_bounds__(PTHREADS, 1)
       mma_commit(done);   // arrives once every issued MMA has completed
     }
   } else {
-    // ---- epilogue: warp w drains TMEM lanes 32 w .. 32 w + 31 (output rows m) ----
+    // ---- epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 (output rows m) of its
+    // group's columns 128 g .. 128 g + 127 ----
     int i = 0;
-    __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem + Lay::STG_OFFSET);
+    const int grp = warp >> 2, wq = warp & 3, cbeg = grp * (PBN / 2), cend = cbeg + PBN / 2;
+    __nv_bfloat16* stg =
+        reinterpret_cast<__nv_bfloat16*>(smem + Lay::STG_OFFSET) + grp * Lay::STG_GROUP;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int b = i & 1, m0 = (t % mt) * BM, n0 = (t / mt) * PBN;
       const bool ok = mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, err, wait_ns);
@@ -378,17 +389,17 @@ __global__ void __launch_bounds__(PTHREADS, 1)
         // the staging arrays
         int ta, tb, th;
         tri_tile(t % mt, ta, tb, th);
-        const int r = warp * 32 + lane;
+        const int r = wq * 32 + lane;
         const int ri = 16 * ta + 8 * th + (r >> 4), rj = 16 * tb + (r & 15);
         const bool mirror = ta != tb;
-        for (int c0 = 0; c0 < PBN; c0 += 32) {
+        for (int c0 = cbeg; c0 < cend; c0 += 32) {
           uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * PBN + c0), v);
+          tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(b * PBN + c0), v);
           store_split_ij(so, ri, rj, n0 + c0, Nd, alpha, v, mirror ? stg : nullptr, r);
           if (mirror) {
-            epilogue_sync();   // the half block's 32 columns are staged
+            group_sync(grp);   // the half block's 32 columns are staged
             store_mirror(so, stg, 16 * ta + 8 * th, 16 * tb, n0 + c0, Nd, r);
-            epilogue_sync();   // and written: the staging arrays are free again
+            group_sync(grp);   // and written: the group's staging arrays are free again
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -396,10 +407,10 @@ __global__ void __launch_bounds__(PTHREADS, 1)
         continue;
       }
       if (!__all_sync(0xffffffffu, ok)) break;
-      const int m = m0 + warp * 32 + lane;
-      for (int c0 = 0; c0 < PBN; c0 += 32) {
+      const int m = m0 + wq * 32 + lane;
+      for (int c0 = cbeg; c0 < cend; c0 += 32) {
         uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * PBN + c0), v);
+        tmem_ld32(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(b * PBN + c0), v);
         if (m < Md) {
           if (so.hi) {
             store_split(so, m, n0 + c0, Nd, alpha, v);
