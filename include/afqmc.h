@@ -55,9 +55,10 @@ enum { AFQMC_PHASELESS = 0, AFQMC_FREE = 1 };
  *                 the propagator for M <= 256, N <= 32 (FP32 CUDA-core kernels otherwise)
  *                 and the two-body local energy (the FP32 kernel where the tensor-core one
  *                 does not apply).  Walkers are kept in float64 and float32; the
- *                 overlap-and-Theta kernel and the orthonormalisation work in FP32 pairs
- *                 with float64 log-determinants (Cholesky QR with the Gram matrix in FP32
- *                 pairs, or Gram-Schmidt in float64; select_kernel K_MGS). */
+ *                 overlap-and-Theta kernel (overlap sums, LU, Theta solves) and the
+ *                 orthonormalisation (Cholesky QR: Gram matrix and factor) work in FP32,
+ *                 with the log-determinants formed and kept in float64 (or Gram-Schmidt in
+ *                 float64; select_kernel K_MGS). */
 enum { AFQMC_FP64 = 0, AFQMC_BF16X3 = 1 };
 
 typedef struct afqmc_ctx* afqmc_handle;
@@ -410,9 +411,8 @@ afqmc_status afqmc_time_kernel(afqmc_handle h, int which, int reps, double* ms,
  *                           N <= 16), 2 = one fused FP32 kernel per walker, 0 / 1 = two FP32
  *                           GEMMs around a Taylor kernel reading A through L1 (0) or from
  *                           shared memory (1);
- *   which AFQMC_K_MGS:      the orthonormalisation: 1 = Cholesky QR (Gram matrix in FP32
- *                           pairs, R and log det R in FP64, Q in FP32), 0 = modified
- *                           Gram-Schmidt in FP64;
+ *   which AFQMC_K_MGS:      the orthonormalisation: 1 = Cholesky QR (Gram matrix, R and Q
+ *                           in FP32, log det R in FP64), 0 = modified Gram-Schmidt in FP64;
  *   which AFQMC_K_PAIR_LOOP (either precision; applies to runs with h as the first handle
  *                           of afqmc_pair_delta_E): 1 = the whole run as one graph launch
  *                           with a device-side loop over the measurement blocks (default),
