@@ -119,7 +119,9 @@ def test_full_size_pair_split_precision(data, reference, taylor, energy, mgs):
         dump()
         # a walker may sit on the cos cut within rounding; none of the sample should
         assert err["alive_both"] == err["alive_oracle"], err
-        assert err["E_L"] < 1e-4 and err["w"] < 1e-3 and err["phi"] < 1e-3, err
+        # about ten times the errors measured on the GB300 with every variant (after 50 steps:
+        # E_L <= 3.7e-7 relative, w <= 1.04e-4, phi <= 1.0e-5)
+        assert err["E_L"] < 5e-6 and err["w"] < 1e-3 and err["phi"] < 1e-4, err
 
 
 def test_split_precision_rejects_unsupported_variants(data):
